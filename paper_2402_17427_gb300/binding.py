@@ -1,0 +1,219 @@
+"""ctypes binding of libvgrast.so: the C ABI of ``include/vgrast.h`` with the same names.
+
+Argument marshalling only.  Every entry point takes raw device pointers (Python ints) and a
+CUDA stream handle; all computation happens in the library's CUDA kernels.  There is no CPU
+fallback: if the library cannot be loaded, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvgrast.so")
+
+VG_OK, VG_ERR_INVALID, VG_ERR_CAPACITY, VG_ERR_CUDA, VG_ERR_TIMEOUT, VG_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+VG_STATUS_PAIR_OVERFLOW = 1
+VG_STATUS_WAIT_TIMEOUT = 2
+VG_CNT_PAIRS, VG_CNT_VISIBLE, VG_CNT_STATUS, VG_CNT_DEPTH_BITS, VG_CNT_EVALS, VG_CNT_BLENDS = range(6)
+VG_CNT_LEN = 8
+VG_FLAG_ACCUMULATE_GRADS = 1
+VG_FLAG_COUNT_BLENDS = 2
+
+EXPORTED = ("vg_default_opts", "vg_status_string", "vg_kernel_launches", "vg_workspace_bytes", "vg_rasterize_forward",
+            "vg_rasterize_backward", "vg_read_render_state", "vg_loss_workspace_bytes", "vg_loss_l1_dssim",
+            "vg_batch_workspace_bytes", "vg_render_batch", "vg_render_batch_backward")
+
+
+class vg_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("world_to_cam", ctypes.c_float * 12), ("cam_pos", ctypes.c_float * 3),
+                ("near_plane", ctypes.c_float)]
+
+
+class vg_gaussians(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+VG_STAGE_PROJECT, VG_STAGE_SORT, VG_STAGE_BLEND, VG_STAGE_BLEND_BACKWARD, VG_STAGE_PROJECT_BACKWARD = range(5)
+VG_STAGE_COUNT = 5
+
+
+class vg_stage_events(ctypes.Structure):
+    _fields_ = [("begin", ctypes.c_void_p * VG_STAGE_COUNT), ("end", ctypes.c_void_p * VG_STAGE_COUNT)]
+
+
+class vg_raster_opts(ctypes.Structure):
+    _fields_ = [("tile_size", ctypes.c_int32), ("chunk", ctypes.c_int32), ("bg", ctypes.c_float * 3),
+                ("dilation", ctypes.c_float), ("alpha_max", ctypes.c_float), ("alpha_min", ctypes.c_float),
+                ("t_min", ctypes.c_float), ("guard", ctypes.c_float), ("stop_rule", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("events", ctypes.POINTER(vg_stage_events))]
+
+
+class VGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+_lib = None
+_P = ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+
+def lib():
+    """Loads libvgrast.so (built by ``paper_2402_17427_gb300._build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2402_17427_gb300._build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    L.vg_default_opts.argtypes = [ctypes.POINTER(vg_raster_opts)]
+    L.vg_default_opts.restype = None
+    L.vg_status_string.argtypes = [ctypes.c_int]
+    L.vg_status_string.restype = ctypes.c_char_p
+    L.vg_kernel_launches.argtypes = []
+    L.vg_kernel_launches.restype = ctypes.c_uint64
+    L.vg_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                     ctypes.POINTER(vg_raster_opts)]
+    L.vg_workspace_bytes.restype = ctypes.c_size_t
+    L.vg_rasterize_forward.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.POINTER(vg_camera),
+                                       ctypes.POINTER(vg_raster_opts), _P, ctypes.c_size_t, ctypes.c_int64,
+                                       _P, _P, _P, _P, _P]
+    L.vg_rasterize_forward.restype = ctypes.c_int
+    L.vg_rasterize_backward.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.POINTER(vg_camera),
+                                        ctypes.POINTER(vg_raster_opts), _P, ctypes.c_size_t, ctypes.c_int64,
+                                        _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+    L.vg_rasterize_backward.restype = ctypes.c_int
+    L.vg_read_render_state.argtypes = [_P, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int64, ctypes.POINTER(vg_raster_opts), _P, _P, _P, _P, _P]
+    L.vg_read_render_state.restype = ctypes.c_int
+    L.vg_loss_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    L.vg_loss_workspace_bytes.restype = ctypes.c_size_t
+    L.vg_loss_l1_dssim.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P, ctypes.c_size_t,
+                                   _P, _P, _P]
+    L.vg_loss_l1_dssim.restype = ctypes.c_int
+    if hasattr(L, "vg_render_batch"):
+        L.vg_batch_workspace_bytes.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32,
+                                               ctypes.POINTER(vg_camera), ctypes.POINTER(vg_raster_opts),
+                                               ctypes.c_int64]
+        L.vg_batch_workspace_bytes.restype = ctypes.c_size_t
+        L.vg_render_batch.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32, ctypes.POINTER(vg_camera),
+                                      ctypes.POINTER(vg_raster_opts), _P, ctypes.c_size_t, ctypes.c_int64,
+                                      _PP, _PP, _PP, _P, _P]
+        L.vg_render_batch.restype = ctypes.c_int
+        L.vg_render_batch_backward.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32,
+                                               ctypes.POINTER(vg_camera), ctypes.POINTER(vg_raster_opts), _P,
+                                               ctypes.c_size_t, ctypes.c_int64, _PP, _PP, _PP, _PP, _PP, _PP,
+                                               _PP, _PP, _P]
+        L.vg_render_batch_backward.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().vg_status_string(int(status)).decode()
+    except Exception:  # the library itself may be what is missing
+        return "status"
+
+
+def _check(status: int, where: str):
+    if status != VG_OK:
+        raise VGError(status, where)
+
+
+def vg_kernel_launches() -> int:
+    return int(lib().vg_kernel_launches())
+
+
+def vg_default_opts() -> vg_raster_opts:
+    o = vg_raster_opts()
+    lib().vg_default_opts(ctypes.byref(o))
+    return o
+
+
+def vg_workspace_bytes(n: int, width: int, height: int, pair_capacity: int, opts: vg_raster_opts) -> int:
+    return int(lib().vg_workspace_bytes(n, width, height, pair_capacity, ctypes.byref(opts)))
+
+
+def vg_rasterize_forward(g: vg_gaussians, cam: vg_camera, opts: vg_raster_opts, workspace: int, workspace_bytes: int,
+                         pair_capacity: int, out_rgb: int, out_final_T: int, out_last: int, counters: int,
+                         stream: int) -> None:
+    _check(lib().vg_rasterize_forward(ctypes.byref(g), ctypes.byref(cam), ctypes.byref(opts), workspace,
+                                      workspace_bytes, pair_capacity, out_rgb, out_final_T, out_last, counters,
+                                      stream), "vg_rasterize_forward")
+
+
+def vg_rasterize_backward(g: vg_gaussians, cam: vg_camera, opts: vg_raster_opts, workspace: int,
+                          workspace_bytes: int, pair_capacity: int, out_final_T: int, out_last: int, dL_drgb: int,
+                          g_means: int, g_log_scales: int, g_quats: int, g_opacity_logits: int, g_sh: int,
+                          g_means2d_abs: int | None, stream: int) -> None:
+    _check(lib().vg_rasterize_backward(ctypes.byref(g), ctypes.byref(cam), ctypes.byref(opts), workspace,
+                                       workspace_bytes, pair_capacity, out_final_T, out_last, dL_drgb, g_means,
+                                       g_log_scales, g_quats, g_opacity_logits, g_sh, g_means2d_abs, stream),
+           "vg_rasterize_backward")
+
+
+def vg_read_render_state(workspace: int, workspace_bytes: int, n: int, width: int, height: int, pair_capacity: int,
+                         opts: vg_raster_opts, ranges: int | None, ids: int | None, projected: int | None,
+                         touched: int | None, stream: int) -> None:
+    _check(lib().vg_read_render_state(workspace, workspace_bytes, n, width, height, pair_capacity, ctypes.byref(opts),
+                                      ranges, ids, projected, touched, stream), "vg_read_render_state")
+
+
+def vg_loss_workspace_bytes(width: int, height: int) -> int:
+    return int(lib().vg_loss_workspace_bytes(width, height))
+
+
+def vg_loss_l1_dssim(img: int, target: int, width: int, height: int, lam: float, workspace: int,
+                     workspace_bytes: int, out_loss: int, out_grad: int | None, stream: int) -> None:
+    _check(lib().vg_loss_l1_dssim(img, target, width, height, lam, workspace, workspace_bytes, out_loss, out_grad,
+                                  stream), "vg_loss_l1_dssim")
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))(*[p or None for p in ptrs])
+    return ctypes.cast(arr, _PP), arr
+
+
+def vg_batch_workspace_bytes(cells, cams, opts, pair_capacity: int) -> int:
+    n = len(cells)
+    G = (vg_gaussians * n)(*cells)
+    C = (vg_camera * n)(*cams)
+    O = (vg_raster_opts * n)(*opts)
+    return int(lib().vg_batch_workspace_bytes(G, n, C, O, pair_capacity))
+
+
+def vg_render_batch(cells, cams, opts, workspace: int, workspace_bytes: int, pair_capacity: int, out_rgb, out_final_T,
+                    out_last, counters: int, stream: int) -> None:
+    n = len(cells)
+    G = (vg_gaussians * n)(*cells)
+    C = (vg_camera * n)(*cams)
+    O = (vg_raster_opts * n)(*opts)
+    a, _ka = _ptr_array(out_rgb)
+    b, _kb = _ptr_array(out_final_T)
+    c, _kc = _ptr_array(out_last)
+    _check(lib().vg_render_batch(G, n, C, O, workspace, workspace_bytes, pair_capacity, a, b, c, counters, stream),
+           "vg_render_batch")
+
+
+def vg_render_batch_backward(cells, cams, opts, workspace: int, workspace_bytes: int, pair_capacity: int,
+                             out_final_T, out_last, dL_drgb, g_means, g_log_scales, g_quats, g_opacity_logits, g_sh,
+                             stream: int) -> None:
+    n = len(cells)
+    G = (vg_gaussians * n)(*cells)
+    C = (vg_camera * n)(*cams)
+    O = (vg_raster_opts * n)(*opts)
+    keep = []
+    arrs = []
+    for lst in (out_final_T, out_last, dL_drgb, g_means, g_log_scales, g_quats, g_opacity_logits, g_sh):
+        p, k = _ptr_array(lst)
+        arrs.append(p)
+        keep.append(k)
+    _check(lib().vg_render_batch_backward(G, n, C, O, workspace, workspace_bytes, pair_capacity, *arrs, stream),
+           "vg_render_batch_backward")

@@ -1,0 +1,425 @@
+// C ABI of the rasteriser (declared in include/vgrast.h): argument checks, workspace layout
+// and the launch sequences of the forward and backward passes.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "vg_common.cuh"
+
+namespace vg {
+namespace {
+
+__global__ void init_header(WsHeader* hdr) {
+  hdr->pairs = 0;
+  hdr->evals = 0;
+  hdr->blends = 0;
+  hdr->visible = 0;
+  hdr->status = 0;
+  hdr->dmin = 0xFFFFFFFFu;
+  hdr->dmax = 0;
+  hdr->depth_bits = 0;
+  hdr->pair_n = 0;
+  hdr->tile_bits = 0;
+  for (int k = 0; k < kTileClasses; ++k) hdr->work_fwd[k] = hdr->work_bwd[k] = 0;
+}
+
+__global__ void publish_counters(const WsHeader* hdr, int64_t* c) {
+  c[VG_CNT_PAIRS] = (int64_t)hdr->pairs;
+  c[VG_CNT_VISIBLE] = (int64_t)hdr->visible;
+  c[VG_CNT_STATUS] = (int64_t)hdr->status;
+  c[VG_CNT_DEPTH_BITS] = (int64_t)hdr->depth_bits;
+  c[VG_CNT_EVALS] = (int64_t)hdr->evals;
+  c[VG_CNT_BLENDS] = (int64_t)hdr->blends;
+  c[6] = 0;
+  c[7] = 0;
+}
+
+__global__ void read_state(const Splat* __restrict__ sorted, const Splat* __restrict__ splats,
+                           const uint32_t* __restrict__ touched_in, const WsHeader* __restrict__ hdr, int n,
+                           uint32_t* __restrict__ ids, float* __restrict__ proj, uint32_t* __restrict__ touched) {
+  const unsigned np = hdr->pair_n;
+  const float k = -1.3862943611198906f;   // scaled conic -> inverse covariance
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < np || i < (unsigned)n; i += gridDim.x * blockDim.x) {
+    if (ids && i < np) ids[i] = sorted[i].id;
+    if (i < (unsigned)n) {
+      if (touched) touched[i] = touched_in[i];
+      if (proj) {
+        const Splat s = splats[i];
+        const bool vis = touched_in[i] > 0;
+        float v[12] = {s.u, s.v, s.ca * k, s.cb * 0.5f * k, s.cc * k, s.opacity, s.r, s.g, s.b, (float)s.rank, 0.f, 0.f};
+        for (int f = 0; f < 12; ++f) proj[(size_t)i * 12 + f] = vis ? v[f] : 0.f;
+      }
+    }
+  }
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool valid_opts(const vg_raster_opts* o) {
+  if (!o) return false;
+  if (o->tile_size != 8 && o->tile_size != 16 && o->tile_size != 32) return false;
+  if (o->chunk != 64 && o->chunk != 128 && o->chunk != 256) return false;
+  if (!(o->alpha_max > 0.f && o->alpha_max < 1.f) || !(o->alpha_min >= 0.f && o->alpha_min < o->alpha_max)) return false;
+  if (!(o->t_min > 0.f && o->t_min < 1.f) || !(o->dilation >= 0.f) || !(o->guard > 0.f)) return false;
+  if (o->stop_rule != 0 && o->stop_rule != 1) return false;
+  return true;
+}
+
+bool valid_camera(const vg_camera* c) {
+  if (!c) return false;
+  if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384) return false;
+  if (!(c->fx > 0.f) || !(c->fy > 0.f) || !std::isfinite(c->cx) || !std::isfinite(c->cy)) return false;
+  for (float v : c->world_to_cam)
+    if (!std::isfinite(v)) return false;
+  if (!(c->near_plane > 0.f)) return false;
+  return true;
+}
+
+bool valid_gaussians(const vg_gaussians* g) {
+  if (!g) return false;
+  if (g->n < 0 || g->n > 0x7FFFFFFFll) return false;
+  if (g->sh_degree < 0 || g->sh_degree > 3) return false;
+  if (g->n == 0) return true;
+  if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh) return false;
+  if (!aligned(g->quats, 16)) return false;
+  const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
+  if ((3 * K) % 4 == 0 && !aligned(g->sh, 16)) return false;
+  return aligned(g->means, 4) && aligned(g->log_scales, 4) && aligned(g->opacity_logits, 4) && aligned(g->sh, 4);
+}
+
+KCam make_cam(const vg_camera* c, const vg_raster_opts* o) {
+  KCam k;
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) k.R[3 * r + q] = c->world_to_cam[4 * r + q];
+    k.t[r] = c->world_to_cam[4 * r + 3];
+    k.cam_pos[r] = c->cam_pos[r];
+  }
+  k.fx = c->fx; k.fy = c->fy; k.cx = c->cx; k.cy = c->cy;
+  k.near_plane = c->near_plane;
+  k.limx = o->guard * 0.5f * (float)c->width / c->fx;
+  k.limy = o->guard * 0.5f * (float)c->height / c->fy;
+  k.W = c->width; k.H = c->height;
+  return k;
+}
+
+KOpts make_opts(const vg_raster_opts* o) {
+  KOpts k;
+  for (int c = 0; c < 3; ++c) k.bg[c] = o->bg[c];
+  k.dilation = o->dilation; k.alpha_max = o->alpha_max; k.alpha_min = o->alpha_min; k.t_min = o->t_min;
+  k.stop_rule = o->stop_rule;
+  k.tile = o->tile_size;
+  return k;
+}
+
+KGauss make_gauss(const vg_gaussians* g) {
+  KGauss k;
+  k.means = g->means; k.log_scales = g->log_scales; k.quats = g->quats; k.logits = g->opacity_logits; k.sh = g->sh;
+  k.n = (int)g->n;
+  k.degree = g->sh_degree;
+  return k;
+}
+
+vg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VG_OK : VG_ERR_CUDA; }
+
+int tile_class(int ts) { return ts == 8 ? 0 : (ts == 16 ? 1 : 2); }
+
+// Everything one call needs on the host: the table image and the derived sizes.
+struct Call {
+  std::vector<unsigned char> table;
+  HostPlan plan{};
+  int n_views = 0, n_segs = 0, total_n = 0, total_tiles = 0, degree = 0;
+  int64_t total_n64 = 0, total_tiles64 = 0;
+  KView* views() { return reinterpret_cast<KView*>(table.data() + sizeof(TableHeader)); }
+  KSeg* segs() { return reinterpret_cast<KSeg*>(table.data() + sizeof(TableHeader) + n_views * sizeof(KView)); }
+};
+
+// Validates views and segments and fills the table image.  seg_view[i] is the view segment i
+// is rendered into.
+vg_status make_call(Call& c, const vg_gaussians* segs, int n_segs, const int* seg_view, const vg_camera* cams,
+                    const vg_raster_opts* opts, int n_views) {
+  if (n_views < 1 || n_views > kMaxViews || n_segs < 1 || n_segs > kMaxSegs) return VG_ERR_INVALID;
+  c.n_views = n_views;
+  c.n_segs = n_segs;
+  c.table.assign(table_bytes(n_views, n_segs), 0);
+  int64_t tiles = 0;
+  for (int k = 0; k < kTileClasses; ++k) c.plan.class_tiles[k] = 0;
+  // views are laid out class by class so that each class's tiles are contiguous
+  for (int v = 0; v < n_views; ++v) {
+    if (!valid_camera(&cams[v]) || !valid_opts(&opts[v])) return VG_ERR_INVALID;
+  }
+  for (int v = 0; v < n_views; ++v) {
+    KView& kv = c.views()[v];
+    kv.cam = make_cam(&cams[v], &opts[v]);
+    kv.op = make_opts(&opts[v]);
+    const int ts = opts[v].tile_size;
+    kv.tiles_x = (cams[v].width + ts - 1) / ts;
+    kv.tiles_y = (cams[v].height + ts - 1) / ts;
+    kv.tile_base = (int)tiles;
+    kv.tile_class = tile_class(ts);
+    tiles += (int64_t)kv.tiles_x * kv.tiles_y;
+    c.plan.class_tiles[kv.tile_class] += kv.tiles_x * kv.tiles_y;
+  }
+  if (tiles > 0x7FFFFFFFll) return VG_ERR_INVALID;
+  int b = 0;
+  for (int k = 0; k < kTileClasses; ++k) { c.plan.class_begin[k] = b; b += c.plan.class_tiles[k]; }
+  int64_t n = 0;
+  int degree = -1;
+  for (int i = 0; i < n_segs; ++i) {
+    if (!valid_gaussians(&segs[i])) return VG_ERR_INVALID;
+    if (seg_view[i] < 0 || seg_view[i] >= n_views) return VG_ERR_INVALID;
+    if (segs[i].n > 0) {
+      if (degree >= 0 && segs[i].sh_degree != degree) return VG_ERR_UNSUPPORTED;   // one degree per call
+      degree = segs[i].sh_degree;
+    }
+    KSeg& ks = c.segs()[i];
+    ks.g = make_gauss(&segs[i]);
+    ks.view = seg_view[i];
+    ks.offset = (int)n;
+    n += segs[i].n;
+  }
+  if (n > 0x7FFFFFFFll) return VG_ERR_INVALID;
+  c.total_n = (int)n;
+  c.total_tiles = (int)tiles;
+  c.total_n64 = n;
+  c.total_tiles64 = tiles;
+  c.degree = degree < 0 ? 0 : degree;
+  TableHeader& h = *reinterpret_cast<TableHeader*>(c.table.data());
+  h.n_views = n_views;
+  h.n_segs = n_segs;
+  h.total_n = c.total_n;
+  h.total_tiles = c.total_tiles;
+  h.degree = c.degree;
+  return VG_OK;
+}
+
+// Forward pass of a prepared call: projection, binning, compositing.
+vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, size_t workspace_bytes,
+                      int64_t pair_capacity, int64_t* counters, cudaStream_t s) {
+  if (!workspace || !aligned(workspace, 256) || !counters) return VG_ERR_INVALID;
+  if (pair_capacity < 1 || pair_capacity > 0xFFFFFFFFll) return VG_ERR_INVALID;
+  const Layout L = make_layout(c.total_n64, c.total_tiles64, pair_capacity);
+  if (workspace_bytes < L.total) return VG_ERR_CAPACITY;
+  char* ws = static_cast<char*>(workspace);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
+  const DevTables* tab = reinterpret_cast<const DevTables*>(ws + L.tables);
+  const vg_stage_events* ev = opts0->events;
+  if (cudaMemcpyAsync(ws + L.tables, c.table.data(), c.table.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return VG_ERR_CUDA;
+  init_header<<<1, 1, 0, s>>>(hdr);
+  note_launches(2);   // init_header + publish_counters
+  stage_event(ev, VG_STAGE_PROJECT, true, s);
+  cudaError_t e = launch_preprocess(tab, c.total_n, c.degree, reinterpret_cast<Splat*>(ws + L.splats),
+                                    reinterpret_cast<uint2*>(ws + L.rects), reinterpret_cast<uint32_t*>(ws + L.touched),
+                                    reinterpret_cast<uint32_t*>(ws + L.dkey), hdr, s);
+  if (e != cudaSuccess) return VG_ERR_CUDA;
+  stage_event(ev, VG_STAGE_PROJECT, false, s);
+  stage_event(ev, VG_STAGE_SORT, true, s);
+  e = launch_binning(tab, c.total_n, c.total_tiles, pair_capacity, L, ws, s);
+  if (e != cudaSuccess) return VG_ERR_CUDA;
+  stage_event(ev, VG_STAGE_SORT, false, s);
+  stage_event(ev, VG_STAGE_BLEND, true, s);
+  e = launch_blend_forward(tab, c.plan, L, ws, (opts0->flags & VG_FLAG_COUNT_BLENDS) != 0, s);
+  if (e != cudaSuccess) return VG_ERR_CUDA;
+  stage_event(ev, VG_STAGE_BLEND, false, s);
+  publish_counters<<<1, 1, 0, s>>>(hdr, counters);
+  return cuda_status(cudaGetLastError());
+}
+
+// Backward pass of a prepared call (the table carries dL, final T, last and the gradient outputs).
+vg_status run_backward(Call& c, const vg_raster_opts* opts0, void* workspace, size_t workspace_bytes,
+                       int64_t pair_capacity, bool abs, cudaStream_t s) {
+  if (!workspace || !aligned(workspace, 256)) return VG_ERR_INVALID;
+  if (pair_capacity < 1 || pair_capacity > 0xFFFFFFFFll) return VG_ERR_INVALID;
+  const Layout L = make_layout(c.total_n64, c.total_tiles64, pair_capacity);
+  if (workspace_bytes < L.total) return VG_ERR_CAPACITY;
+  char* ws = static_cast<char*>(workspace);
+  const DevTables* tab = reinterpret_cast<const DevTables*>(ws + L.tables);
+  const vg_stage_events* ev = opts0->events;
+  if (cudaMemcpyAsync(ws + L.tables, c.table.data(), c.table.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return VG_ERR_CUDA;
+  stage_event(ev, VG_STAGE_BLEND_BACKWARD, true, s);
+  cudaError_t e = launch_blend_backward(tab, c.plan, L, ws, abs, s);
+  if (e != cudaSuccess) return VG_ERR_CUDA;
+  stage_event(ev, VG_STAGE_BLEND_BACKWARD, false, s);
+  stage_event(ev, VG_STAGE_PROJECT_BACKWARD, true, s);
+  e = launch_preprocess_backward(tab, c.total_n, c.degree, reinterpret_cast<const Splat*>(ws + L.splats),
+                                 reinterpret_cast<const uint32_t*>(ws + L.touched),
+                                 reinterpret_cast<const float*>(ws + L.g2d),
+                                 (opts0->flags & VG_FLAG_ACCUMULATE_GRADS) != 0, s);
+  stage_event(ev, VG_STAGE_PROJECT_BACKWARD, false, s);
+  return cuda_status(e);
+}
+
+std::atomic<uint64_t> g_launches{0};
+
+}  // namespace
+
+void note_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+}  // namespace vg
+
+using namespace vg;
+
+extern "C" void vg_default_opts(vg_raster_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tile_size = 16;
+  o->chunk = 256;
+  o->dilation = 0.3f;
+  o->alpha_max = 0.99f;
+  o->alpha_min = 1.0f / 255.0f;
+  o->t_min = 1e-4f;
+  o->guard = 1.3f;
+  o->stop_rule = 0;
+  o->flags = 0;
+}
+
+extern "C" const char* vg_status_string(vg_status s) {
+  switch (s) {
+    case VG_OK: return "ok";
+    case VG_ERR_INVALID: return "invalid argument";
+    case VG_ERR_CAPACITY: return "workspace too small";
+    case VG_ERR_CUDA: return "CUDA error";
+    case VG_ERR_TIMEOUT: return "bounded device wait gave up";
+    case VG_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+extern "C" uint64_t vg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" size_t vg_workspace_bytes(int64_t n, int32_t width, int32_t height, int64_t pair_capacity,
+                                     const vg_raster_opts* opts) {
+  if (n < 0 || n > 0x7FFFFFFFll || width < 1 || height < 1 || width > 16384 || height > 16384) return 0;
+  if (pair_capacity < 1 || pair_capacity > 0xFFFFFFFFll || !valid_opts(opts)) return 0;
+  const int ts = opts->tile_size;
+  const int64_t tiles = (int64_t)((width + ts - 1) / ts) * ((height + ts - 1) / ts);
+  return make_layout(n, tiles, pair_capacity).total;
+}
+
+extern "C" vg_status vg_rasterize_forward(const vg_gaussians* g, const vg_camera* cam, const vg_raster_opts* opts,
+                                          void* workspace, size_t workspace_bytes, int64_t pair_capacity,
+                                          float* out_rgb, float* out_final_T, uint32_t* out_last,
+                                          int64_t* counters, vg_stream stream) {
+  if (!g || !cam || !opts || !out_rgb || !out_final_T || !out_last || !counters || !workspace) return VG_ERR_INVALID;
+  Call c;
+  const int view0 = 0;
+  vg_status st = make_call(c, g, 1, &view0, cam, opts, 1);
+  if (st != VG_OK) return st;
+  KView& v = c.views()[0];
+  v.rgb = out_rgb;
+  v.T = out_final_T;
+  v.last = out_last;
+  return run_forward(c, opts, workspace, workspace_bytes, pair_capacity, counters, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" vg_status vg_rasterize_backward(const vg_gaussians* g, const vg_camera* cam, const vg_raster_opts* opts,
+                                           void* workspace, size_t workspace_bytes, int64_t pair_capacity,
+                                           const float* out_final_T, const uint32_t* out_last, const float* dL_drgb,
+                                           float* g_means, float* g_log_scales, float* g_quats,
+                                           float* g_opacity_logits, float* g_sh, float* g_means2d_abs,
+                                           vg_stream stream) {
+  if (!g || !cam || !opts || !out_final_T || !out_last || !dL_drgb || !workspace) return VG_ERR_INVALID;
+  if (g->n > 0 && (!g_means || !g_log_scales || !g_quats || !g_opacity_logits || !g_sh)) return VG_ERR_INVALID;
+  Call c;
+  const int view0 = 0;
+  vg_status st = make_call(c, g, 1, &view0, cam, opts, 1);
+  if (st != VG_OK) return st;
+  KView& v = c.views()[0];
+  v.fT = out_final_T;
+  v.flast = out_last;
+  v.dL = dL_drgb;
+  KSeg& sg = c.segs()[0];
+  sg.gm = g_means; sg.gs = g_log_scales; sg.gq = g_quats; sg.gl = g_opacity_logits; sg.gsh = g_sh;
+  sg.gabs = g_means2d_abs;
+  return run_backward(c, opts, workspace, workspace_bytes, pair_capacity, g_means2d_abs != nullptr,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t vg_batch_workspace_bytes(const vg_gaussians* cells, int32_t n_cells, const vg_camera* cams,
+                                           const vg_raster_opts* opts, int64_t pair_capacity) {
+  if (!cells || !cams || !opts || n_cells < 1 || n_cells > kMaxViews) return 0;
+  if (pair_capacity < 1 || pair_capacity > 0xFFFFFFFFll) return 0;
+  std::vector<int> sv(n_cells);
+  for (int i = 0; i < n_cells; ++i) sv[i] = i;
+  Call c;
+  if (make_call(c, cells, n_cells, sv.data(), cams, opts, n_cells) != VG_OK) return 0;
+  return make_layout(c.total_n64, c.total_tiles64, pair_capacity).total;
+}
+
+extern "C" vg_status vg_render_batch(const vg_gaussians* cells, int32_t n_cells, const vg_camera* cams,
+                                     const vg_raster_opts* opts, void* workspace, size_t workspace_bytes,
+                                     int64_t pair_capacity, float* const* out_rgb, float* const* out_final_T,
+                                     uint32_t* const* out_last, int64_t* counters, vg_stream stream) {
+  if (!cells || !cams || !opts || !out_rgb || !out_final_T || !out_last || n_cells < 1 || n_cells > kMaxViews)
+    return VG_ERR_INVALID;
+  std::vector<int> sv(n_cells);
+  for (int i = 0; i < n_cells; ++i) sv[i] = i;
+  Call c;
+  vg_status st = make_call(c, cells, n_cells, sv.data(), cams, opts, n_cells);
+  if (st != VG_OK) return st;
+  for (int i = 0; i < n_cells; ++i) {
+    if (!out_rgb[i] || !out_final_T[i] || !out_last[i]) return VG_ERR_INVALID;
+    KView& v = c.views()[i];
+    v.rgb = out_rgb[i];
+    v.T = out_final_T[i];
+    v.last = out_last[i];
+  }
+  return run_forward(c, &opts[0], workspace, workspace_bytes, pair_capacity, counters,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" vg_status vg_render_batch_backward(const vg_gaussians* cells, int32_t n_cells, const vg_camera* cams,
+                                              const vg_raster_opts* opts, void* workspace, size_t workspace_bytes,
+                                              int64_t pair_capacity, const float* const* out_final_T,
+                                              const uint32_t* const* out_last, const float* const* dL_drgb,
+                                              float* const* g_means, float* const* g_log_scales,
+                                              float* const* g_quats, float* const* g_opacity_logits,
+                                              float* const* g_sh, vg_stream stream) {
+  if (!cells || !cams || !opts || !out_final_T || !out_last || !dL_drgb || !g_means || !g_log_scales || !g_quats ||
+      !g_opacity_logits || !g_sh || n_cells < 1 || n_cells > kMaxViews)
+    return VG_ERR_INVALID;
+  std::vector<int> sv(n_cells);
+  for (int i = 0; i < n_cells; ++i) sv[i] = i;
+  Call c;
+  vg_status st = make_call(c, cells, n_cells, sv.data(), cams, opts, n_cells);
+  if (st != VG_OK) return st;
+  for (int i = 0; i < n_cells; ++i) {
+    if (!out_final_T[i] || !out_last[i] || !dL_drgb[i]) return VG_ERR_INVALID;
+    if (cells[i].n > 0 && (!g_means[i] || !g_log_scales[i] || !g_quats[i] || !g_opacity_logits[i] || !g_sh[i]))
+      return VG_ERR_INVALID;
+    KView& v = c.views()[i];
+    v.fT = out_final_T[i];
+    v.flast = out_last[i];
+    v.dL = dL_drgb[i];
+    KSeg& sg = c.segs()[i];
+    sg.gm = g_means[i]; sg.gs = g_log_scales[i]; sg.gq = g_quats[i]; sg.gl = g_opacity_logits[i]; sg.gsh = g_sh[i];
+  }
+  return run_backward(c, &opts[0], workspace, workspace_bytes, pair_capacity, false,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" vg_status vg_read_render_state(const void* workspace, size_t workspace_bytes, int64_t n, int32_t width,
+                                          int32_t height, int64_t pair_capacity, const vg_raster_opts* opts,
+                                          uint32_t* ranges, uint32_t* ids, float* projected, uint32_t* touched,
+                                          vg_stream stream) {
+  if (!workspace || !valid_opts(opts) || n < 0 || n > 0x7FFFFFFFll || width < 1 || height < 1 || width > 16384 ||
+      height > 16384 || pair_capacity < 1 || pair_capacity > 0xFFFFFFFFll)
+    return VG_ERR_INVALID;
+  const int ts = opts->tile_size;
+  const int64_t tiles = (int64_t)((width + ts - 1) / ts) * ((height + ts - 1) / ts);
+  const Layout L = make_layout(n, tiles, pair_capacity);
+  if (workspace_bytes < L.total) return VG_ERR_CAPACITY;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const char* ws = static_cast<const char*>(workspace);
+  if (ranges && cudaMemcpyAsync(ranges, ws + L.ranges, (size_t)tiles * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return VG_ERR_CUDA;
+  note_launches(1);
+  read_state<<<1024, 256, 0, s>>>(reinterpret_cast<const Splat*>(ws + L.sorted), reinterpret_cast<const Splat*>(ws + L.splats),
+                                  reinterpret_cast<const uint32_t*>(ws + L.touched),
+                                  reinterpret_cast<const WsHeader*>(ws + L.header), (int)n, ids, projected, touched);
+  return cuda_status(cudaGetLastError());
+}

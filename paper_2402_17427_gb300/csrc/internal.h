@@ -1,0 +1,187 @@
+// Host-side interfaces between the CUDA translation units of the rasteriser library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vgrast.h"
+
+namespace vg {
+
+struct Splat;
+
+// Camera as the kernels take it (by value).
+struct KCam {
+  float R[9], t[3];
+  float fx, fy, cx, cy;
+  float cam_pos[3];
+  float near_plane;
+  float limx, limy;  // guard-band clamp of x/z and y/z for the Jacobian
+  int W, H;
+};
+
+// Rasteriser options as the kernels take them.
+struct KOpts {
+  float bg[3];
+  float dilation, alpha_max, alpha_min, t_min;
+  int stop_rule;
+  int tile;
+};
+
+// Raw Gaussian parameters.
+struct KGauss {
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* logits;
+  const float* sh;
+  int n;
+  int degree;
+};
+
+// One camera view of a render call: its camera, options, tile grid (a slice of the call's
+// global tile space) and its image buffers.
+struct KView {
+  KCam cam;
+  KOpts op;
+  int tiles_x, tiles_y;
+  int tile_base;              // first global tile id of this view
+  int tile_class;             // 0, 1, 2 for tile size 8, 16, 32
+  float* rgb;                 // forward outputs
+  float* T;
+  uint32_t* last;
+  const float* dL;            // backward inputs
+  const float* fT;
+  const uint32_t* flast;
+};
+
+// One run of Gaussians rendered into one view (a cell seen by a camera).  Global Gaussian
+// index = offset + local index; every per-Gaussian workspace array is indexed globally.
+struct KSeg {
+  KGauss g;
+  int view;
+  int offset;
+  float* gm;                  // backward outputs (raw-parameter gradients), may be null
+  float* gs;
+  float* gq;
+  float* gl;
+  float* gsh;
+  float* gabs;                // optional |dL/du| + |dL/dv| sums
+};
+
+constexpr int kMaxViews = 256;
+constexpr int kMaxSegs = 1024;
+constexpr int kTileClasses = 3;
+
+struct TableHeader {
+  int n_views, n_segs, total_n, total_tiles;
+  int degree;
+  int pad[3];
+};
+
+// Lives in the workspace, filled from the host at the start of every call: the header is
+// followed by KView[n_views] and then KSeg[n_segs].
+struct DevTables {
+  TableHeader h;
+};
+static_assert(sizeof(TableHeader) % 16 == 0, "views must stay aligned");
+static_assert(sizeof(KView) % 8 == 0 && sizeof(KSeg) % 8 == 0, "table entries must stay aligned");
+
+__host__ __device__ inline size_t table_bytes(int n_views, int n_segs) {
+  return sizeof(TableHeader) + (size_t)n_views * sizeof(KView) + (size_t)n_segs * sizeof(KSeg);
+}
+__host__ __device__ inline const KView& tview(const DevTables* t, int i) {
+  return reinterpret_cast<const KView*>(reinterpret_cast<const char*>(t) + sizeof(TableHeader))[i];
+}
+__host__ __device__ inline const KSeg& tseg(const DevTables* t, int i) {
+  return reinterpret_cast<const KSeg*>(reinterpret_cast<const char*>(t) + sizeof(TableHeader) +
+                                       (size_t)t->h.n_views * sizeof(KView))[i];
+}
+
+// Device-side bookkeeping at the start of every render workspace.
+struct WsHeader {
+  unsigned long long pairs;     // pairs required
+  unsigned long long evals;     // (pixel, Gaussian) evaluations (optional count)
+  unsigned long long blends;    // composited evaluations (optional count)
+  unsigned int visible;         // V
+  unsigned int status;          // VG_STATUS_* bits
+  unsigned int dmin, dmax;      // min / max depth key over visible Gaussians
+  unsigned int depth_bits;      // significant bits of (key - dmin)
+  unsigned int pair_n;          // min(pairs, capacity): pairs actually sorted
+  unsigned int tile_bits;       // bits of the tile key
+  unsigned int work_fwd[kTileClasses];   // persistent-blend work queues (next item)
+  unsigned int work_bwd[kTileClasses];
+  unsigned int pad[3];
+};
+static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
+
+__device__ __forceinline__ int find_seg(const DevTables* __restrict__ t, int i) {
+  int lo = 0, hi = t->h.n_segs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tseg(t, mid).offset <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_view(const DevTables* __restrict__ t, int tile) {
+  int lo = 0, hi = t->h.n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tview(t, mid).tile_base <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kMaxSortBlocks = 1024;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Offsets (bytes) of the regions of one render workspace (any number of views / segments).
+struct Layout {
+  size_t header, tables, splats, rects, touched, dkey, vkeys[2], vvals[2], pkeys[2], pvals[2], sorted,
+      ranges, order, buckets, hist, blocksums, g2d, total;
+};
+Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t pair_capacity);
+
+int sort_blocks();  // blocks of the segmented sort / scan kernels on the current device
+
+// Process-wide count of kernels enqueued by the library (vg_kernel_launches).
+void note_launches(int k);
+
+// Records the begin / end event of a stage when the caller asked for stage timing.
+inline void stage_event(const vg_stage_events* ev, int stage, bool begin, cudaStream_t s) {
+  if (!ev) return;
+  void* e = begin ? ev->begin[stage] : ev->end[stage];
+  if (e) cudaEventRecord(reinterpret_cast<cudaEvent_t>(e), s);
+}
+
+// Host copy of the tables plus what the launchers need to know on the host.
+struct HostPlan {
+  int class_tiles[kTileClasses];  // tiles of each tile-size class
+  int class_begin[kTileClasses];  // first work item of each class in the ordered tile list
+};
+
+// ---- launchers (each returns the first CUDA error it hits) ----
+cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Splat* splats, uint2* rects,
+                              uint32_t* touched, uint32_t* dkey, WsHeader* hdr, cudaStream_t s);
+cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int degree, const Splat* splats,
+                                       const uint32_t* touched, const float* g2d, bool accumulate, cudaStream_t s);
+
+// Depth order of the visible Gaussians, pair generation, tile sort, ranges, the tile-ordered copy
+// of the splats and the largest-first order of the tiles.
+cudaError_t launch_binning(const DevTables* tab, int total_n, int total_tiles, int64_t capacity, const Layout& L,
+                           char* ws, cudaStream_t s);
+
+cudaError_t launch_blend_forward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool count,
+                                 cudaStream_t s);
+cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool abs,
+                                  cudaStream_t s);
+
+}  // namespace vg

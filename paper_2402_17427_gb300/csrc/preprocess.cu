@@ -1,0 +1,447 @@
+// Per-Gaussian projection (EWA splatting + spherical-harmonic colour) and its adjoint.
+//
+// Paper Sec. 3: each 3D Gaussian (position, anisotropic covariance, opacity, SH colour) is
+// projected to the image as a 2D Gaussian; R is differentiable.  One thread per Gaussian.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "vg_common.cuh"
+
+namespace vg {
+namespace {
+
+// Real spherical harmonics with the Condon-Shortley phase, index l^2 + l + m, written as
+// polynomials in the unit direction (x, y, z).  Constants: sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!)
+// times the Legendre-derivative factors, e.g. C1 = sqrt(3/(4 pi)), C2a = sqrt(15/pi)/2,
+// C2b = sqrt(5/pi)/4, C2c = sqrt(15/pi)/4, C3a = sqrt(35/(32 pi)), C3b = sqrt(105/pi)/2,
+// C3c = sqrt(21/(32 pi)), C3d = sqrt(7/pi)/4, C3e = sqrt(105/pi)/4.
+constexpr float kC0 = 0.28209479177387814f;
+constexpr float kC1 = 0.48860251190291992f;
+constexpr float kC2a = 1.0925484305920792f;
+constexpr float kC2b = 0.31539156525252005f;
+constexpr float kC2c = 0.54627421529603959f;
+constexpr float kC3a = 0.59004358992664352f;
+constexpr float kC3b = 2.8906114426405538f;
+constexpr float kC3c = 0.45704579946446577f;
+constexpr float kC3d = 0.37317633259011540f;
+constexpr float kC3e = 1.4453057213202769f;
+
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+  Y[0] = kC0;
+  if (DEG >= 1) {
+    Y[1] = -kC1 * y;
+    Y[2] = kC1 * z;
+    Y[3] = -kC1 * x;
+  }
+  if (DEG >= 2) {
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kC2a * x * y;
+    Y[5] = -kC2a * y * z;
+    Y[6] = kC2b * (2.f * zz - xx - yy);
+    Y[7] = -kC2a * x * z;
+    Y[8] = kC2c * (xx - yy);
+    if (DEG >= 3) {
+      Y[9] = -kC3a * y * (3.f * xx - yy);
+      Y[10] = kC3b * x * y * z;
+      Y[11] = -kC3c * y * (4.f * zz - xx - yy);
+      Y[12] = kC3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+      Y[13] = -kC3c * x * (4.f * zz - xx - yy);
+      Y[14] = kC3e * z * (xx - yy);
+      Y[15] = -kC3a * x * (xx - 3.f * yy);
+    }
+  }
+}
+
+// Gradient of each basis polynomial with respect to (x, y, z).
+template <int DEG>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float (*G)[3]) {
+  G[0][0] = G[0][1] = G[0][2] = 0.f;
+  if (DEG >= 1) {
+    G[1][0] = 0.f; G[1][1] = -kC1; G[1][2] = 0.f;
+    G[2][0] = 0.f; G[2][1] = 0.f;  G[2][2] = kC1;
+    G[3][0] = -kC1; G[3][1] = 0.f; G[3][2] = 0.f;
+  }
+  if (DEG >= 2) {
+    float xx = x * x, yy = y * y, zz = z * z;
+    G[4][0] = kC2a * y;        G[4][1] = kC2a * x;        G[4][2] = 0.f;
+    G[5][0] = 0.f;             G[5][1] = -kC2a * z;       G[5][2] = -kC2a * y;
+    G[6][0] = -2.f * kC2b * x; G[6][1] = -2.f * kC2b * y; G[6][2] = 4.f * kC2b * z;
+    G[7][0] = -kC2a * z;       G[7][1] = 0.f;             G[7][2] = -kC2a * x;
+    G[8][0] = 2.f * kC2c * x;  G[8][1] = -2.f * kC2c * y; G[8][2] = 0.f;
+    if (DEG >= 3) {
+      G[9][0] = -6.f * kC3a * x * y;  G[9][1] = -3.f * kC3a * (xx - yy); G[9][2] = 0.f;
+      G[10][0] = kC3b * y * z;        G[10][1] = kC3b * x * z;           G[10][2] = kC3b * x * y;
+      G[11][0] = 2.f * kC3c * x * y;  G[11][1] = -kC3c * (4.f * zz - xx - 3.f * yy); G[11][2] = -8.f * kC3c * y * z;
+      G[12][0] = -6.f * kC3d * x * z; G[12][1] = -6.f * kC3d * y * z;    G[12][2] = kC3d * (6.f * zz - 3.f * xx - 3.f * yy);
+      G[13][0] = -kC3c * (4.f * zz - 3.f * xx - yy); G[13][1] = 2.f * kC3c * x * y; G[13][2] = -8.f * kC3c * x * z;
+      G[14][0] = 2.f * kC3e * x * z;  G[14][1] = -2.f * kC3e * y * z;    G[14][2] = kC3e * (xx - yy);
+      G[15][0] = -3.f * kC3a * (xx - yy); G[15][1] = 6.f * kC3a * x * y; G[15][2] = 0.f;
+    }
+  }
+}
+
+// Loads the K x 3 SH block of Gaussian i into registers (vector loads when 16-byte aligned).
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float* __restrict__ sh, int i, float* c) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int F = 3 * K;
+  const float* p = sh + (size_t)i * F;
+  if constexpr (F % 4 == 0) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < F / 4; ++k) {
+      float4 v = __ldg(p4 + k);
+      c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < F; ++k) c[k] = __ldg(p + k);
+  }
+}
+
+// Everything the projection computes that the adjoint needs again.
+struct Proj {
+  float m[3], p[3];
+  float qn[4], qinv;      // normalised quaternion, 1/|q|
+  float Rq[9], s[3];
+  float Sig[6];           // 3D covariance, upper triangle: 00 01 02 11 12 22
+  float T[6];             // J W, 2 x 3
+  float A, B, C;          // 2D covariance (with dilation)
+  float ca, cb, cc;       // conic (inverse 2D covariance)
+  bool clx, cly;          // guard-band clamp active
+  float xzc, yzc;         // clamped x/z, y/z
+  float u, v, depth, r;
+  bool valid;
+};
+
+// Projection of Gaussian i.  The key-defining values (depth, u, v) follow the exact FP32
+// operation order stated for the sort keys; the rest is ordinary FP32.
+__device__ __forceinline__ void project(const KGauss& g, const KCam& cm, const KOpts& op, int i, Proj& P) {
+  P.valid = false;
+  P.m[0] = __ldg(g.means + 3 * i);
+  P.m[1] = __ldg(g.means + 3 * i + 1);
+  P.m[2] = __ldg(g.means + 3 * i + 2);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    P.p[r] = __fmaf_rn(cm.R[3 * r], P.m[0], __fmaf_rn(cm.R[3 * r + 1], P.m[1], __fmaf_rn(cm.R[3 * r + 2], P.m[2], cm.t[r])));
+  const float z = P.p[2];
+  if (!(z > cm.near_plane)) return;
+  const float xz = __fdiv_rn(P.p[0], z), yz = __fdiv_rn(P.p[1], z);
+  P.depth = z;
+  P.u = __fmaf_rn(cm.fx, xz, cm.cx);
+  P.v = __fmaf_rn(cm.fy, yz, cm.cy);
+  // rotation, scale, 3D covariance
+  float4 q = __ldg(reinterpret_cast<const float4*>(g.quats) + i);
+  float qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  if (!(qq > 0.f)) return;
+  P.qinv = rsqrtf(qq);
+  P.qn[0] = q.x * P.qinv; P.qn[1] = q.y * P.qinv; P.qn[2] = q.z * P.qinv; P.qn[3] = q.w * P.qinv;
+  const float w = P.qn[0], x = P.qn[1], y = P.qn[2], zq = P.qn[3];
+  P.Rq[0] = 1.f - 2.f * (y * y + zq * zq); P.Rq[1] = 2.f * (x * y - w * zq);        P.Rq[2] = 2.f * (x * zq + w * y);
+  P.Rq[3] = 2.f * (x * y + w * zq);        P.Rq[4] = 1.f - 2.f * (x * x + zq * zq); P.Rq[5] = 2.f * (y * zq - w * x);
+  P.Rq[6] = 2.f * (x * zq - w * y);        P.Rq[7] = 2.f * (y * zq + w * x);        P.Rq[8] = 1.f - 2.f * (x * x + y * y);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) P.s[k] = expf(__ldg(g.log_scales + 3 * i + k));
+  float M[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[3 * r + c] = P.Rq[3 * r + c] * P.s[c];
+  P.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  P.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  P.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  P.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  P.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  P.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+  // Jacobian of the pinhole map at the guard-band clamped point, T = J W
+  P.xzc = fminf(cm.limx, fmaxf(-cm.limx, xz));
+  P.yzc = fminf(cm.limy, fmaxf(-cm.limy, yz));
+  P.clx = P.xzc != xz;
+  P.cly = P.yzc != yz;
+  const float iz = 1.f / z;
+  const float j00 = cm.fx * iz, j02 = -cm.fx * P.xzc * iz, j11 = cm.fy * iz, j12 = -cm.fy * P.yzc * iz;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    P.T[c] = j00 * cm.R[c] + j02 * cm.R[6 + c];
+    P.T[3 + c] = j11 * cm.R[3 + c] + j12 * cm.R[6 + c];
+  }
+  // 2D covariance T Sigma T^T + dilation I
+  const float* S = P.Sig;
+  float TS[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const float* t = P.T + 3 * a;
+    TS[a][0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
+    TS[a][1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
+    TS[a][2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+  }
+  P.A = TS[0][0] * P.T[0] + TS[0][1] * P.T[1] + TS[0][2] * P.T[2] + op.dilation;
+  P.B = TS[0][0] * P.T[3] + TS[0][1] * P.T[4] + TS[0][2] * P.T[5];
+  P.C = TS[1][0] * P.T[3] + TS[1][1] * P.T[4] + TS[1][2] * P.T[5] + op.dilation;
+  const float det = P.A * P.C - P.B * P.B;
+  if (!(det > 0.f)) return;
+  const float idet = 1.f / det;
+  P.ca = P.C * idet;
+  P.cb = -P.B * idet;
+  P.cc = P.A * idet;
+  const float mid = 0.5f * (P.A + P.C);
+  const float lmax = mid + sqrtf(fmaxf(0.f, mid * mid - det));
+  P.r = 3.f * sqrtf(lmax);
+  P.valid = true;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __restrict__ tab, int total_n,
+                                                         Splat* __restrict__ splats, uint2* __restrict__ rects,
+                                                         uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey,
+                                                         WsHeader* __restrict__ hdr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t key = 0xFFFFFFFFu, lo_key = 0xFFFFFFFFu, hi_key = 0u;
+  if (i < total_n) {
+    const KSeg& sg = tseg(tab, find_seg(tab, i));
+    const KView& vw = tview(tab, sg.view);
+    const KCam cm = vw.cam;
+    const KOpts op = vw.op;
+    const int li = i - sg.offset;
+    Proj P;
+    project(sg.g, cm, op, li, P);
+    uint32_t cnt = 0;
+    if (P.valid) {
+      const int T = op.tile;
+      int xlo = rect_lo(P.u, P.r, cm.W), xhi = rect_hi(P.u, P.r, cm.W);
+      int ylo = rect_lo(P.v, P.r, cm.H), yhi = rect_hi(P.v, P.r, cm.H);
+      if (xlo <= xhi && ylo <= yhi) {
+        const int tx0 = xlo / T, tx1 = xhi / T, ty0 = ylo / T, ty1 = yhi / T;
+        cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        rects[i] = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
+        // colour from spherical harmonics along the viewing direction
+        constexpr int K = (DEG + 1) * (DEG + 1);
+        float d0 = P.m[0] - cm.cam_pos[0], d1 = P.m[1] - cm.cam_pos[1], d2 = P.m[2] - cm.cam_pos[2];
+        const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        d0 *= il; d1 *= il; d2 *= il;
+        float Y[16], c[3 * K];
+        sh_basis<DEG>(d0, d1, d2, Y);
+        load_sh<DEG>(sg.g.sh, li, c);
+        float rgb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          float acc = 0.5f;
+#pragma unroll
+          for (int k = 0; k < K; ++k) acc = fmaf(c[3 * k + ch], Y[k], acc);
+          rgb[ch] = fmaxf(0.f, acc);
+        }
+        const float o = 1.f / (1.f + expf(-__ldg(sg.g.logits + li)));
+        Splat s;
+        s.u = P.u; s.v = P.v;
+        s.ca = -0.5f * kLog2e * P.ca;
+        s.cb = -kLog2e * P.cb;
+        s.cc = -0.5f * kLog2e * P.cc;
+        s.opacity = o;
+        s.r = rgb[0]; s.g = rgb[1]; s.b = rgb[2];
+        s.rank = 0;
+        s.id = (uint32_t)i;
+        s.pad = 0;
+        float4* dst = reinterpret_cast<float4*>(splats + i);
+        const float4* src = reinterpret_cast<const float4*>(&s);
+        dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
+        key = __float_as_uint(P.depth);
+        lo_key = hi_key = key;
+      }
+    }
+    touched[i] = cnt;
+    dkey[i] = key;
+  }
+  // min / max depth key over visible Gaussians (for trimming the depth sort)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo_key = min(lo_key, __shfl_xor_sync(0xffffffffu, lo_key, o));
+    hi_key = max(hi_key, __shfl_xor_sync(0xffffffffu, hi_key, o));
+  }
+  if ((threadIdx.x & 31) == 0 && lo_key <= hi_key) {
+    atomicMin(&hdr->dmin, lo_key);
+    atomicMax(&hdr->dmax, hi_key);
+  }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(128) preprocess_backward_kernel(
+    const DevTables* __restrict__ tab, int total_n, const Splat* __restrict__ splats,
+    const uint32_t* __restrict__ touched, const float* __restrict__ g2d, int accumulate) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total_n) return;
+  const KSeg& sg = tseg(tab, find_seg(tab, i));
+  if (!sg.gm) return;       // this segment asked for no gradients
+  const KGauss g = sg.g;
+  const KCam cm = tview(tab, sg.view).cam;
+  const KOpts op = tview(tab, sg.view).op;
+  const int li = i - sg.offset;
+  float o_m[3] = {0, 0, 0}, o_s[3] = {0, 0, 0}, o_q[4] = {0, 0, 0, 0}, o_l = 0.f, o_sh[3 * K];
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) o_sh[k] = 0.f;
+  if (touched[i] > 0) {
+    const uint32_t rank = splats[i].rank;
+    float d2[9];
+#pragma unroll
+    for (int f = 0; f < 9; ++f) d2[f] = g2d[(size_t)rank * 9 + f];
+    Proj P;
+    project(g, cm, op, li, P);
+    // opacity
+    const float o = 1.f / (1.f + expf(-__ldg(g.logits + li)));
+    o_l = d2[5] * o * (1.f - o);
+    // colour: rgb = max(0, sum_k c_k Y_k(d) + 0.5), d = (m - cam_pos) / |m - cam_pos|
+    float d0 = P.m[0] - cm.cam_pos[0], d1 = P.m[1] - cm.cam_pos[1], dz = P.m[2] - cm.cam_pos[2];
+    const float il = rsqrtf(d0 * d0 + d1 * d1 + dz * dz);
+    d0 *= il; d1 *= il; dz *= il;
+    float Y[16], GY[16][3], c[3 * K];
+    sh_basis<DEG>(d0, d1, dz, Y);
+    sh_basis_grad<DEG>(d0, d1, dz, GY);
+    load_sh<DEG>(g.sh, li, c);
+    float dd[3] = {0, 0, 0};
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float pre = 0.5f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) pre = fmaf(c[3 * k + ch], Y[k], pre);
+      const float dpre = pre > 0.f ? d2[6 + ch] : 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        o_sh[3 * k + ch] = dpre * Y[k];
+        const float w = dpre * c[3 * k + ch];
+        dd[0] += w * GY[k][0]; dd[1] += w * GY[k][1]; dd[2] += w * GY[k][2];
+      }
+    }
+    const float dot = dd[0] * d0 + dd[1] * d1 + dd[2] * dz;
+    o_m[0] = (dd[0] - d0 * dot) * il;
+    o_m[1] = (dd[1] - d1 * dot) * il;
+    o_m[2] = (dd[2] - dz * dot) * il;
+    // conic -> 2D covariance: dS2 = -Q G Q, Q = [[a,b],[b,c]], G = [[da, db/2],[db/2, dc]]
+    const float qa = P.ca, qb = P.cb, qc = P.cc;
+    const float g0 = d2[2], g1 = 0.5f * d2[3], g2 = d2[4];
+    const float m00 = qa * g0 + qb * g1, m01 = qa * g1 + qb * g2;
+    const float m10 = qb * g0 + qc * g1, m11 = qb * g1 + qc * g2;
+    const float s00 = -(m00 * qa + m01 * qb);
+    const float s01 = -(m00 * qb + m01 * qc);
+    const float s11 = -(m10 * qb + m11 * qc);
+    // Sigma2 = T Sigma T^T: dSigma = T^T dS2 T, dT = 2 dS2 T Sigma
+    const float* T = P.T;
+    float U[2][3];   // dS2 T
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) {
+      U[0][c3] = s00 * T[c3] + s01 * T[3 + c3];
+      U[1][c3] = s01 * T[c3] + s11 * T[3 + c3];
+    }
+    float dSig[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) dSig[a][b] = T[a] * U[0][b] + T[3 + a] * U[1][b];
+    const float* S = P.Sig;
+    const float Sf[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
+    float dT[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dT[a][j] = 2.f * (U[a][0] * Sf[0][j] + U[a][1] * Sf[1][j] + U[a][2] * Sf[2][j]);
+    // dJ = dT W^T; only J00, J02, J11, J12 depend on p
+    const float* W = cm.R;
+    const float dJ00 = dT[0][0] * W[0] + dT[0][1] * W[1] + dT[0][2] * W[2];
+    const float dJ02 = dT[0][0] * W[6] + dT[0][1] * W[7] + dT[0][2] * W[8];
+    const float dJ11 = dT[1][0] * W[3] + dT[1][1] * W[4] + dT[1][2] * W[5];
+    const float dJ12 = dT[1][0] * W[6] + dT[1][1] * W[7] + dT[1][2] * W[8];
+    const float z = P.p[2], iz = 1.f / z, iz2 = iz * iz;
+    float dp[3] = {0.f, 0.f, 0.f};
+    dp[2] += -(dJ00 * cm.fx + dJ11 * cm.fy) * iz2;
+    // J02 = -fx xzc / z with xzc = x / z unless clamped
+    if (P.clx) {
+      dp[2] += dJ02 * cm.fx * P.xzc * iz2;
+    } else {
+      dp[0] += -dJ02 * cm.fx * iz2;
+      dp[2] += dJ02 * 2.f * cm.fx * P.p[0] * iz2 * iz;
+    }
+    if (P.cly) {
+      dp[2] += dJ12 * cm.fy * P.yzc * iz2;
+    } else {
+      dp[1] += -dJ12 * cm.fy * iz2;
+      dp[2] += dJ12 * 2.f * cm.fy * P.p[1] * iz2 * iz;
+    }
+    // u = fx x/z + cx, v = fy y/z + cy
+    dp[0] += d2[0] * cm.fx * iz;
+    dp[1] += d2[1] * cm.fy * iz;
+    dp[2] += -(d2[0] * cm.fx * P.p[0] + d2[1] * cm.fy * P.p[1]) * iz2;
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) o_m[c3] += W[c3] * dp[0] + W[3 + c3] * dp[1] + W[6 + c3] * dp[2];
+    // Sigma = M M^T, M = Rq diag(s): dM = 2 dSigma M
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c3 = 0; c3 < 3; ++c3) M[3 * r + c3] = P.Rq[3 * r + c3] * P.s[c3];
+    float dR[9];
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) {
+      float ds = 0.f;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float dMrc = 2.f * (dSig[r][0] * M[c3] + dSig[r][1] * M[3 + c3] + dSig[r][2] * M[6 + c3]);
+        ds += dMrc * P.Rq[3 * r + c3];
+        dR[3 * r + c3] = dMrc * P.s[c3];
+      }
+      o_s[c3] = ds * P.s[c3];
+    }
+    // rotation matrix of the unit quaternion (w, x, y, z)
+    const float w = P.qn[0], x = P.qn[1], y = P.qn[2], zq = P.qn[3];
+    float dqn[4];
+    dqn[0] = 2.f * (-zq * dR[1] + y * dR[2] + zq * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    dqn[1] = 2.f * (y * dR[1] + zq * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + zq * dR[6] + w * dR[7] - 2.f * x * dR[8]);
+    dqn[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + zq * dR[5] - w * dR[6] + zq * dR[7] - 2.f * y * dR[8]);
+    dqn[3] = 2.f * (-2.f * zq * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * zq * dR[4] + y * dR[5] + x * dR[6] + y * dR[7]);
+    const float qd = P.qn[0] * dqn[0] + P.qn[1] * dqn[1] + P.qn[2] * dqn[2] + P.qn[3] * dqn[3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o_q[k] = (dqn[k] - P.qn[k] * qd) * P.qinv;
+  }
+  // write (or accumulate) every output of Gaussian i
+  auto put = [&](float* dst, float v) { if (accumulate) *dst += v; else *dst = v; };
+  const size_t l = (size_t)li;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { put(sg.gm + 3 * l + k, o_m[k]); put(sg.gs + 3 * l + k, o_s[k]); }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) put(sg.gq + 4 * l + k, o_q[k]);
+  put(sg.gl + l, o_l);
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) put(sg.gsh + l * 3 * K + k, o_sh[k]);
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Splat* splats, uint2* rects,
+                              uint32_t* touched, uint32_t* dkey, WsHeader* hdr, cudaStream_t s) {
+  if (total_n == 0) return cudaSuccess;
+  note_launches(1);
+  const int blocks = (total_n + 255) / 256;
+  switch (degree) {
+    case 0: preprocess_kernel<0><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, dkey, hdr); break;
+    case 1: preprocess_kernel<1><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, dkey, hdr); break;
+    case 2: preprocess_kernel<2><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, dkey, hdr); break;
+    default: preprocess_kernel<3><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, dkey, hdr); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int degree, const Splat* splats,
+                                       const uint32_t* touched, const float* g2d, bool accumulate, cudaStream_t s) {
+  if (total_n == 0) return cudaSuccess;
+  note_launches(1);
+  const int blocks = (total_n + 127) / 128;
+  const int acc = accumulate ? 1 : 0;
+  switch (degree) {
+    case 0: preprocess_backward_kernel<0><<<blocks, 128, 0, s>>>(tab, total_n, splats, touched, g2d, acc); break;
+    case 1: preprocess_backward_kernel<1><<<blocks, 128, 0, s>>>(tab, total_n, splats, touched, g2d, acc); break;
+    case 2: preprocess_backward_kernel<2><<<blocks, 128, 0, s>>>(tab, total_n, splats, touched, g2d, acc); break;
+    default: preprocess_backward_kernel<3><<<blocks, 128, 0, s>>>(tab, total_n, splats, touched, g2d, acc); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace vg
