@@ -158,7 +158,8 @@ vg_status vg_rasterize_forward(const vg_gaussians* g, const vg_camera* cam, cons
  * out_final_T and out_last (no per-sample state is stored).  Outputs have the shapes of the
  * inputs and are fully written (zero for culled Gaussians) unless VG_FLAG_ACCUMULATE_GRADS is
  * set, in which case they are added to.  The derivative through an active clamp (alpha at
- * alpha_max, colour at 0, guard-band Jacobian) is zero.
+ * alpha_max, colour at 0, guard-band Jacobian) is zero.  g_quats (and g_sh when 3K is a multiple
+ * of 4) must be 16-byte aligned, like the corresponding inputs.
  *   g_means2d_abs    optional [N] (may be NULL): |dL/du| + |dL/dv| of the projected mean,
  *                    summed over pixels, added to (densification statistics). */
 vg_status vg_rasterize_backward(const vg_gaussians* g, const vg_camera* cam, const vg_raster_opts* opts,

@@ -40,11 +40,13 @@ __global__ void publish_counters(const WsHeader* hdr, int64_t* c) {
 
 __global__ void read_state(const Splat* __restrict__ sorted, const Splat* __restrict__ splats,
                            const uint32_t* __restrict__ touched_in, const WsHeader* __restrict__ hdr, int n,
-                           uint32_t* __restrict__ ids, float* __restrict__ proj, uint32_t* __restrict__ touched) {
+                           const uint32_t* d0, const uint32_t* d1, uint32_t* __restrict__ ids,
+                           float* __restrict__ proj, uint32_t* __restrict__ touched) {
   const unsigned np = hdr->pair_n;
+  const uint32_t* dorder = depth_order(hdr, d0, d1);
   const float k = -1.3862943611198906f;   // scaled conic -> inverse covariance
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < np || i < (unsigned)n; i += gridDim.x * blockDim.x) {
-    if (ids && i < np) ids[i] = sorted[i].id;
+    if (ids && i < np) ids[i] = dorder[sorted[i].rank];
     if (i < (unsigned)n) {
       if (touched) touched[i] = touched_in[i];
       if (proj) {
@@ -89,6 +91,12 @@ bool valid_gaussians(const vg_gaussians* g) {
   const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
   if ((3 * K) % 4 == 0 && !aligned(g->sh, 16)) return false;
   return aligned(g->means, 4) && aligned(g->log_scales, 4) && aligned(g->opacity_logits, 4) && aligned(g->sh, 4);
+}
+
+// Gradient rows written as float4 must start on 16-byte boundaries.
+bool grads_aligned(int degree, const float* gq, const float* gsh) {
+  const int K = (degree + 1) * (degree + 1);
+  return aligned(gq, 16) && ((3 * K) % 4 != 0 || aligned(gsh, 16)) && aligned(gsh, 4);
 }
 
 KCam make_cam(const vg_camera* c, const vg_raster_opts* o) {
@@ -332,6 +340,7 @@ extern "C" vg_status vg_rasterize_backward(const vg_gaussians* g, const vg_camer
   v.fT = out_final_T;
   v.flast = out_last;
   v.dL = dL_drgb;
+  if (g->n > 0 && !grads_aligned(g->sh_degree, g_quats, g_sh)) return VG_ERR_INVALID;
   KSeg& sg = c.segs()[0];
   sg.gm = g_means; sg.gs = g_log_scales; sg.gq = g_quats; sg.gl = g_opacity_logits; sg.gsh = g_sh;
   sg.gabs = g_means2d_abs;
@@ -391,6 +400,7 @@ extern "C" vg_status vg_render_batch_backward(const vg_gaussians* cells, int32_t
     if (!out_final_T[i] || !out_last[i] || !dL_drgb[i]) return VG_ERR_INVALID;
     if (cells[i].n > 0 && (!g_means[i] || !g_log_scales[i] || !g_quats[i] || !g_opacity_logits[i] || !g_sh[i]))
       return VG_ERR_INVALID;
+    if (cells[i].n > 0 && !grads_aligned(cells[i].sh_degree, g_quats[i], g_sh[i])) return VG_ERR_INVALID;
     KView& v = c.views()[i];
     v.fT = out_final_T[i];
     v.flast = out_last[i];
@@ -420,6 +430,8 @@ extern "C" vg_status vg_read_render_state(const void* workspace, size_t workspac
   note_launches(1);
   read_state<<<1024, 256, 0, s>>>(reinterpret_cast<const Splat*>(ws + L.sorted), reinterpret_cast<const Splat*>(ws + L.splats),
                                   reinterpret_cast<const uint32_t*>(ws + L.touched),
-                                  reinterpret_cast<const WsHeader*>(ws + L.header), (int)n, ids, projected, touched);
+                                  reinterpret_cast<const WsHeader*>(ws + L.header), (int)n,
+                                  reinterpret_cast<const uint32_t*>(ws + L.vvals[0]),
+                                  reinterpret_cast<const uint32_t*>(ws + L.vvals[1]), ids, projected, touched);
   return cuda_status(cudaGetLastError());
 }

@@ -18,10 +18,11 @@
 namespace vg {
 namespace {
 
-__device__ __forceinline__ void segment(unsigned n, unsigned& begin, unsigned& end) {
+// Contiguous segment of [0, n) owned by this block; segment lengths are multiples of `gran`.
+__device__ __forceinline__ void segment(unsigned n, unsigned& begin, unsigned& end, unsigned gran = kSortTile) {
   const unsigned B = gridDim.x;
   unsigned seg = (n + B - 1) / B;
-  seg = (seg + kSortTile - 1) / kSortTile * kSortTile;
+  seg = (seg + gran - 1) / gran * gran;
   begin = min(n, blockIdx.x * seg);
   end = min(n, begin + seg);
 }
@@ -135,41 +136,29 @@ __global__ void __launch_bounds__(256) radix_upsweep(const uint32_t* __restrict_
   hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];   // digit-major: [digit][block]
 }
 
-// Single block: with the counts stored digit-major, the scatter offset of (digit d, block b) is
-// the exclusive prefix sum of the flattened [digit][block] array.  Coalesced 1024-wide tiles.
-__global__ void __launch_bounds__(1024) radix_scan(uint32_t* __restrict__ hist, int B, const unsigned* bits_ptr,
-                                                   int shift) {
+// With the counts stored digit-major, the scatter offset of (digit d, block b) is the exclusive
+// prefix sum of the flattened [digit][block] array.  kScanSlices blocks each scan one slice in
+// place and publish the slice total; the downsweep adds the prefix of the slice totals.
+constexpr int kScanSlices = 64;
+
+__device__ __forceinline__ int slice_len(int B) { return (kRadix * B + kScanSlices - 1) / kScanSlices; }
+
+__global__ void __launch_bounds__(256) radix_scan_slices(uint32_t* __restrict__ hist, int B, const unsigned* bits_ptr,
+                                                         int shift, unsigned* __restrict__ slice_tot) {
   if ((unsigned)shift >= *bits_ptr) return;
-  __shared__ unsigned sm[32];
-  const int n = kRadix * B;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ unsigned sm[8];
+  const int n = kRadix * B, L = slice_len(B);
+  const int lo = blockIdx.x * L, hi = min(n, lo + L);
   unsigned run = 0;
-  for (int base = 0; base < n; base += 1024) {
+  for (int base = lo; base < hi; base += 256) {
     const int i = base + threadIdx.x;
-    const unsigned v = i < n ? hist[i] : 0u;
-    unsigned x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) sm[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      unsigned t = sm[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-      }
-      sm[lane] = t;
-    }
-    __syncthreads();
-    const unsigned before = (w > 0 ? sm[w - 1] : 0u) + x - v;
-    if (i < n) hist[i] = run + before;
-    run += sm[31];
-    __syncthreads();
+    const unsigned v = i < hi ? hist[i] : 0u;
+    unsigned tot;
+    const unsigned ex = block_exclusive_scan(v, &tot, sm);
+    if (i < hi) hist[i] = run + ex;
+    run += tot;
   }
+  if (threadIdx.x == 0) slice_tot[blockIdx.x] = run;
 }
 
 // Stable scatter.  A block walks its segment in tiles of 2048 keys; inside a tile, warp w owns
@@ -178,15 +167,31 @@ __global__ void __launch_bounds__(1024) radix_scan(uint32_t* __restrict__ hist, 
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const unsigned* n_ptr, unsigned cap, const unsigned* bits_ptr, int shift,
-    const uint32_t* __restrict__ hist) {
+    const uint32_t* __restrict__ hist, const unsigned* __restrict__ slice_tot) {
   if ((unsigned)shift >= *bits_ptr) return;
   const unsigned n = min(*n_ptr, cap);
   constexpr int WARPS = kSortThreads / 32;
   __shared__ unsigned s_base[kRadix];
   __shared__ unsigned s_cnt[WARPS][kRadix];
   __shared__ unsigned s_tot[kRadix];
+  __shared__ unsigned s_slice[kScanSlices];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  s_base[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
+  if (threadIdx.x < 32) {   // exclusive prefix of the 64 slice totals
+    const unsigned a = slice_tot[2 * lane], b = slice_tot[2 * lane + 1];
+    unsigned x = a + b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    s_slice[2 * lane] = x - a - b;
+    s_slice[2 * lane + 1] = x - b;
+  }
+  __syncthreads();
+  {
+    const int idx = threadIdx.x * gridDim.x + blockIdx.x;
+    s_base[threadIdx.x] = hist[idx] + s_slice[idx / slice_len(gridDim.x)];
+  }
 #pragma unroll
   for (int k = 0; k < WARPS; ++k) s_cnt[k][threadIdx.x] = 0;
   __syncthreads();
@@ -243,19 +248,12 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
 
 // ---- 2. pair offsets in depth order and pair generation -----------------------------------------
 
-// The depth sort runs ceil(depth_bits / 8) active passes (known only on the device); its result
-// sits in buffer (active passes % 2).
-__device__ __forceinline__ const uint32_t* depth_order(const WsHeader* hdr, const uint32_t* b0, const uint32_t* b1) {
-  const unsigned passes = (hdr->depth_bits + kRadixBits - 1) / kRadixBits;
-  return (passes & 1) ? b1 : b0;
-}
-
 __global__ void __launch_bounds__(256) pairs_count(const uint32_t* order0, const uint32_t* order1,
                                                    const uint32_t* __restrict__ touched, const WsHeader* __restrict__ hdr,
                                                    unsigned long long* __restrict__ blocksums) {
   const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
   unsigned begin, end;
-  segment(hdr->visible, begin, end);
+  segment(hdr->visible, begin, end, 256);
   unsigned long long c = 0;
   for (unsigned s = begin + threadIdx.x; s < end; s += blockDim.x) c += touched[order[s]];
 #pragma unroll
@@ -288,8 +286,11 @@ __global__ void __launch_bounds__(256) pairs_scan(unsigned long long* __restrict
   }
 }
 
-// Every visible Gaussian (in depth order s) writes one (global tile, id) pair per tile of its
-// rectangle, tiles row-major, starting at its exclusive offset; it also records its rank s.
+// Every visible Gaussian (in depth order s) owns the pairs [offset, offset + tiles touched): one
+// (global tile, id) pair per tile of its rectangle, tiles row-major; it also records its rank s.
+// A block takes 256 Gaussians at a time and its threads emit their pairs cooperatively (thread k
+// writes pair k of the batch, finding its owner by binary search), so writes are coalesced and
+// large Gaussians do not serialise one thread.
 __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ tab, const uint32_t* order0,
                                                   const uint32_t* order1, const uint32_t* __restrict__ touched,
                                                   const uint2* __restrict__ rects, const WsHeader* __restrict__ hdr,
@@ -298,8 +299,11 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
                                                   uint32_t* __restrict__ pvals, Splat* __restrict__ splats) {
   const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
   __shared__ unsigned long long sm[8];
+  __shared__ unsigned s_off[257];
+  __shared__ uint32_t s_id[256];
+  __shared__ int s_base[256], s_tilesx[256], s_tx0[256], s_ty0[256], s_w[256];
   unsigned begin, end;
-  segment(hdr->visible, begin, end);
+  segment(hdr->visible, begin, end, 256);
   unsigned long long run = blocksums[blockIdx.x];
   for (unsigned t0 = begin; t0 < end; t0 += 256) {
     const unsigned s = t0 + threadIdx.x;
@@ -307,23 +311,37 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
     if (s < end) {
       id = order[s];
       cnt = touched[id];
-    }
-    unsigned long long tot;
-    const unsigned long long off = run + block_exclusive_scan((unsigned long long)cnt, &tot, sm);
-    if (s < end) {
       splats[id].rank = s;
       const KView& vw = tview(tab, tseg(tab, find_seg(tab, (int)id)).view);
-      const int base = vw.tile_base, tiles_x = vw.tiles_x;
       const uint2 rc = rects[id];
-      const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
-      unsigned long long j = off;
-      for (int ty = ty0; ty <= ty1 && j < cap; ++ty)
-        for (int tx = tx0; tx <= tx1 && j < cap; ++tx, ++j) {
-          pkeys[j] = (uint32_t)(base + ty * tiles_x + tx);
-          pvals[j] = id;
-        }
+      s_base[threadIdx.x] = vw.tile_base;
+      s_tilesx[threadIdx.x] = vw.tiles_x;
+      s_tx0[threadIdx.x] = (int)(rc.x & 0xFFFF);
+      s_ty0[threadIdx.x] = (int)(rc.y & 0xFFFF);
+      s_w[threadIdx.x] = (int)(rc.x >> 16) - (int)(rc.x & 0xFFFF) + 1;
+    }
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan((unsigned long long)cnt, &tot, sm);
+    s_off[threadIdx.x] = (unsigned)ex;
+    s_id[threadIdx.x] = id;
+    if (threadIdx.x == 0) s_off[256] = (unsigned)tot;
+    __syncthreads();
+    for (unsigned k = threadIdx.x; k < (unsigned)tot; k += 256) {
+      const unsigned long long j = run + k;
+      if (j >= cap) break;
+      int lo = 0, hi = 255;              // last g with s_off[g] <= k (owners have cnt > 0)
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
+      }
+      const int within = (int)(k - s_off[lo]);
+      const int w = s_w[lo];
+      const int ty = s_ty0[lo] + within / w, tx = s_tx0[lo] + within % w;
+      pkeys[j] = (uint32_t)(s_base[lo] + ty * s_tilesx[lo] + tx);
+      pvals[j] = s_id[lo];
     }
     run += tot;
+    __syncthreads();
   }
 }
 
@@ -431,6 +449,7 @@ Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
   L.buckets = take(2 * kBuckets * 4);
   L.hist = take((size_t)kMaxSortBlocks * kRadix * 4);
   L.blocksums = take((size_t)kMaxSortBlocks * 8);
+  L.slices = take(kScanSlices * 4);
   L.g2d = take(N * 9 * 4);
   L.total = o;
   return L;
@@ -447,6 +466,7 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   unsigned long long* bsum64 = reinterpret_cast<unsigned long long*>(ws + L.blocksums);
   const unsigned cap = (unsigned)(capacity > 0xFFFFFFFFll ? 0xFFFFFFFFll : capacity);
   const unsigned tile_bits = (unsigned)ceil_log2((unsigned)tiles);
+  unsigned* slices = U(L.slices);
 
   // 1. compaction + depth sort
   compact_count<<<B, 256, 0, s>>>(U(L.dkey), (unsigned)n, bsum);
@@ -456,14 +476,15 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
     const int shift = pass * kRadixBits;
     const int src = pass & 1, dst = src ^ 1;
     radix_upsweep<<<B, 256, 0, s>>>(U(L.vkeys[src]), &hdr->visible, 0xFFFFFFFFu, &hdr->depth_bits, shift, hist);
-    radix_scan<<<1, 1024, 0, s>>>(hist, B, &hdr->depth_bits, shift);
+    radix_scan_slices<<<kScanSlices, 256, 0, s>>>(hist, B, &hdr->depth_bits, shift, slices);
     radix_downsweep<<<B, kSortThreads, 0, s>>>(U(L.vkeys[src]), U(L.vvals[src]), U(L.vkeys[dst]), U(L.vvals[dst]),
-                                               &hdr->visible, 0xFFFFFFFFu, &hdr->depth_bits, shift, hist);
+                                               &hdr->visible, 0xFFFFFFFFu, &hdr->depth_bits, shift, hist, slices);
   }
   // 2. pairs in depth order
-  pairs_count<<<B, 256, 0, s>>>(U(L.vvals[0]), U(L.vvals[1]), U(L.touched), hdr, bsum64);
-  pairs_scan<<<1, 256, 0, s>>>(bsum64, B, hdr, (unsigned long long)cap);
-  pairs_emit<<<B, 256, 0, s>>>(tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), reinterpret_cast<const uint2*>(ws + L.rects),
+  const int BP = kMaxSortBlocks < 6 * B / 2 ? kMaxSortBlocks : 6 * B / 2;   // 6 blocks per SM
+  pairs_count<<<BP, 256, 0, s>>>(U(L.vvals[0]), U(L.vvals[1]), U(L.touched), hdr, bsum64);
+  pairs_scan<<<1, 256, 0, s>>>(bsum64, BP, hdr, (unsigned long long)cap);
+  pairs_emit<<<BP, 256, 0, s>>>(tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), reinterpret_cast<const uint2*>(ws + L.rects),
                                hdr, bsum64, (unsigned long long)cap, U(L.pkeys[0]), U(L.pvals[0]), splats);
   // 3. stable sort of the pairs by tile id (tile_bits is known here, so is the pass count)
   const int tpasses = ((int)tile_bits + kRadixBits - 1) / kRadixBits;
@@ -471,9 +492,9 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
     const int shift = pass * kRadixBits;
     const int src = pass & 1, dst = src ^ 1;
     radix_upsweep<<<B, 256, 0, s>>>(U(L.pkeys[src]), &hdr->pair_n, cap, &hdr->tile_bits, shift, hist);
-    radix_scan<<<1, 1024, 0, s>>>(hist, B, &hdr->tile_bits, shift);
+    radix_scan_slices<<<kScanSlices, 256, 0, s>>>(hist, B, &hdr->tile_bits, shift, slices);
     radix_downsweep<<<B, kSortThreads, 0, s>>>(U(L.pkeys[src]), U(L.pvals[src]), U(L.pkeys[dst]), U(L.pvals[dst]),
-                                               &hdr->pair_n, cap, &hdr->tile_bits, shift, hist);
+                                               &hdr->pair_n, cap, &hdr->tile_bits, shift, hist, slices);
   }
   note_launches(3 + 4 * 3 + 3 + 3 * tpasses + 5);
   const int fin = tpasses & 1;

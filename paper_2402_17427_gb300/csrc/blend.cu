@@ -11,6 +11,7 @@
 // the compositing of chunk k.  Thread 0 issues the copies; all threads wait with a bounded wait.
 // Each thread owns several pixels of the tile, which amortises the shared-memory reads of a
 // splat in the forward pass and the warp reduction of its gradient in the backward pass.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -22,19 +23,48 @@ namespace {
 constexpr int kCh = 128;
 constexpr float kNegTwoLn2 = -1.3862943611198906f;   // true conic = scaled conic * (-2 ln 2)
 
-template <int TS>
+// Thread layout of a tile.  The forward pass is latency-bound (short per-pixel chains), so it
+// keeps more warps per tile (4 pixels per thread for TS >= 16); the backward pass is issue-bound
+// and amortises the per-splat work (staging reads, cull test, gradient reduction) over more
+// pixels (8 per thread, one warp per 16x16 tile).
+template <int TS, bool BWD>
 struct TileShape {
   static constexpr int kPix = TS * TS;
-  static constexpr int kPPT = TS >= 16 ? 4 : 1;        // pixels per thread
+  static constexpr int kPPT = TS == 8 ? (BWD ? 2 : 1) : (BWD ? 8 : 4);
   static constexpr int kThreads = kPix / kPPT;
   static constexpr int kClass = TS == 8 ? 0 : (TS == 16 ? 1 : 2);
+  static constexpr int kWarpRows = 32 * kPPT / TS;      // a warp covers TS columns x kWarpRows rows
 };
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float half_lo(float bits) {
+  return __half2float(__ushort_as_half((unsigned short)(__float_as_uint(bits) & 0xFFFFu)));
+}
+__device__ __forceinline__ float half_hi(float bits) {
+  return __half2float(__ushort_as_half((unsigned short)(__float_as_uint(bits) >> 16)));
+}
+
+// Pixel block of the calling warp inside tile (tx, ty): centre and half extents.
+template <int TS, bool BWD>
+__device__ __forceinline__ void warp_block(int tx, int ty, float& cx, float& cy, float& hw, float& hh) {
+  using S = TileShape<TS, BWD>;
+  const int w = threadIdx.x >> 5;
+  hw = 0.5f * (TS - 1);
+  hh = 0.5f * (S::kWarpRows - 1);
+  cx = (float)(tx * TS) + hw;
+  cy = (float)(ty * TS + w * S::kWarpRows) + hh;
+}
 
 // Pixel p of thread t: the kPPT pixels of a thread sit in one column, kPPT consecutive rows,
 // so a warp covers a compact block of the tile.
-template <int TS>
+template <int TS, bool BWD>
 __device__ __forceinline__ void pixel_of(int t, int p, int& lx, int& ly) {
-  using S = TileShape<TS>;
+  using S = TileShape<TS, BWD>;
   lx = t % TS;
   ly = (t / TS) * S::kPPT + p;
 }
@@ -43,6 +73,48 @@ __device__ __forceinline__ void issue_chunk(Splat* dst, const Splat* src, int co
   const uint32_t bytes = (uint32_t)count * (uint32_t)sizeof(Splat);
   mbar_arrive_expect_tx(bar, bytes);
   bulk_copy_g2s(dst, src, bytes, bar);
+}
+
+// Sum of v[0..9] over the 32 lanes of a warp by recursive halving: at each step a lane keeps
+// the part of its vector that its half of the warp owns and receives that part from its
+// partner, so 12 shuffles reduce all 10 values (instead of 50 for 10 butterflies).  On return
+// the lane pair (L, L^1) holds the total of field reduce10_field(L) (-1: none).
+__device__ __forceinline__ float reduce10(const float (&v)[10], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float w[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {   // lanes 0-15 own fields 0..4, lanes 16-31 own fields 5..9
+    const float send = b4 ? v[i] : v[5 + i];
+    const float keep = b4 ? v[5 + i] : v[i];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float x[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {   // w[0..2] | w[3..4]
+    const float hi = i < 2 ? w[3 + i] : 0.f;
+    const float send = b3 ? w[i] : hi;
+    const float keep = b3 ? hi : w[i];
+    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float y[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {   // x[0..1] | x[2]
+    const float hi = i < 1 ? x[2] : 0.f;
+    const float send = b2 ? x[i] : hi;
+    const float keep = b2 ? hi : x[i];
+    y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const float z = (b1 ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, b1 ? y[0] : y[1], 2);
+  return z + __shfl_xor_sync(0xffffffffu, z, 1);
+}
+
+__host__ __device__ constexpr int reduce10_field(int lane) {
+  // bits 4..1 of the lane select the field; see reduce10
+  return ((lane >> 4) & 1) == 0
+             ? (((lane >> 3) & 1) == 0 ? (((lane >> 2) & 1) == 0 ? ((lane >> 1) & 1) : (((lane >> 1) & 1) ? -1 : 2))
+                                      : (((lane >> 2) & 1) == 0 ? 3 + ((lane >> 1) & 1) : -1))
+             : (((lane >> 3) & 1) == 0 ? (((lane >> 2) & 1) == 0 ? 5 + ((lane >> 1) & 1) : (((lane >> 1) & 1) ? -1 : 7))
+                                      : (((lane >> 2) & 1) == 0 ? 8 + ((lane >> 1) & 1) : -1));
 }
 
 // Pulls the next work item of this class; returns -1 when the queue is empty.
@@ -55,11 +127,11 @@ __device__ __forceinline__ int next_item(unsigned* counter, int count, int* s_it
 }
 
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(TileShape<TS>::kThreads)
+__global__ void __launch_bounds__(TileShape<TS, false>::kThreads)
 blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ sorted,
                      const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, int item_begin,
                      int item_count, WsHeader* __restrict__ hdr) {
-  using S = TileShape<TS>;
+  using S = TileShape<TS, false>;
   __shared__ __align__(128) Splat buf[2][kCh];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int s_item;
@@ -79,23 +151,27 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
     const int lt = tile - vw.tile_base;
     const int tx = lt % vw.tiles_x, ty = lt / vw.tiles_x;
     const int W = vw.cam.W, H = vw.cam.H;
-    const float amax = vw.op.alpha_max, amin = vw.op.alpha_min, tmin = vw.op.t_min;
+    const float amax = vw.op.alpha_max, tmin = vw.op.t_min;
     const bool rule0 = vw.op.stop_rule == 0;
+    float wcx, wcy, whw, whh;
+    warp_block<TS, false>(tx, ty, wcx, wcy, whw, whh);
     const uint2 rg = ranges[tile];
     const int n = (int)(rg.y - rg.x);
 
     float px[S::kPPT], py[S::kPPT], T[S::kPPT], C[S::kPPT][3];
+    float pxc = 0.f;    // the thread's pixels share one column
     uint32_t last[S::kPPT];
     bool done[S::kPPT];
 #pragma unroll
     for (int p = 0; p < S::kPPT; ++p) {
       int lx, ly;
-      pixel_of<TS>(threadIdx.x, p, lx, ly);
+      pixel_of<TS, false>(threadIdx.x, p, lx, ly);
       const int x = tx * TS + lx, y = ty * TS + ly;
       px[p] = (float)x;
       py[p] = (float)y;
       done[p] = x >= W || y >= H;
       T[p] = 1.f;
+      pxc = (float)x;
       C[p][0] = C[p][1] = C[p][2] = 0.f;
       last[p] = 0;
     }
@@ -115,20 +191,32 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
         return;
       }
       const Splat* cb = buf[b];
-      const int cnt = min(kCh, n - k * kCh);
+      bool wdone = true;
+#pragma unroll
+      for (int p = 0; p < S::kPPT; ++p) wdone = wdone && done[p];
+      // a warp whose pixels have all terminated skips the chunk (uniform branch)
+      const int cnt = __all_sync(0xffffffffu, wdone) ? 0 : min(kCh, n - k * kCh);
       for (int j = 0; j < cnt; ++j) {
         const float4 f0 = *reinterpret_cast<const float4*>(&cb[j].u);
+        const float4 f2 = *reinterpret_cast<const float4*>(&cb[j].b);
+        // warp-uniform cull: no pixel of this warp can reach alpha_min
+        if (fabsf(f0.x - wcx) > half_lo(f2.w) + whw || fabsf(f0.y - wcy) > half_hi(f2.w) + whh) {
+          if (COUNT) {
+#pragma unroll
+            for (int p = 0; p < S::kPPT; ++p) ev += done[p] ? 0 : 1;
+          }
+          continue;
+        }
         const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
-        const float fb = cb[j].b;
+        float e0, e1;
+        splat_col(f0.z, f0.w, __fsub_rn(pxc, f0.x), e0, e1);
 #pragma unroll
         for (int p = 0; p < S::kPPT; ++p) {
           if (done[p]) continue;
           if (COUNT) ++ev;
-          const float dx = __fsub_rn(px[p], f0.x), dy = __fsub_rn(py[p], f0.y);
-          const float p2 = splat_power2(f0.z, f0.w, f1.x, dx, dy);
-          if (p2 > 0.f) continue;
+          const float p2 = splat_power2(f1.x, e0, e1, __fsub_rn(py[p], f0.y));
+          if (p2 > 0.f || p2 < f2.z) continue;
           const float a = fminf(amax, __fmul_rn(f1.y, ex2_approx(p2)));
-          if (a < amin) continue;
           const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
           const bool stop = Tn < tmin;
           if (stop && rule0) {
@@ -138,7 +226,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
           const float w = __fmul_rn(a, T[p]);
           C[p][0] = __fmaf_rn(f1.z, w, C[p][0]);
           C[p][1] = __fmaf_rn(f1.w, w, C[p][1]);
-          C[p][2] = __fmaf_rn(fb, w, C[p][2]);
+          C[p][2] = __fmaf_rn(f2.x, w, C[p][2]);
           T[p] = Tn;
           last[p] = (uint32_t)(k * kCh + j + 1);
           if (COUNT) ++bl;
@@ -186,11 +274,13 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
 }
 
 template <int TS, bool ABS>
-__global__ void __launch_bounds__(TileShape<TS>::kThreads)
+__global__ void __launch_bounds__(TileShape<TS, true>::kThreads)
 blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ sorted,
                       const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, int item_begin,
-                      int item_count, float* __restrict__ g2d, WsHeader* __restrict__ hdr) {
-  using S = TileShape<TS>;
+                      int item_count, float* __restrict__ g2d, const uint32_t* dorder0, const uint32_t* dorder1,
+                      WsHeader* __restrict__ hdr) {
+  using S = TileShape<TS, true>;
+  const uint32_t* __restrict__ dorder = depth_order(hdr, dorder0, dorder1);
   __shared__ __align__(128) Splat buf[2][kCh];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int s_item;
@@ -211,20 +301,24 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
     const int lt = tile - vw.tile_base;
     const int tx = lt % vw.tiles_x, ty = lt / vw.tiles_x;
     const int W = vw.cam.W, H = vw.cam.H;
-    const float amax = vw.op.alpha_max, amin = vw.op.alpha_min;
+    const float amax = vw.op.alpha_max;
+    float wcx, wcy, whw, whh;
+    warp_block<TS, true>(tx, ty, wcx, wcy, whw, whh);
     const uint2 rg = ranges[tile];
     const uint32_t list_len = rg.y - rg.x;
     float px[S::kPPT], py[S::kPPT], T[S::kPPT], A[S::kPPT][3], G[S::kPPT][3];
+    float pxc = 0.f;
     uint32_t lastp[S::kPPT];
     unsigned mymax = 0;
     const size_t plane = (size_t)W * H;
 #pragma unroll
     for (int p = 0; p < S::kPPT; ++p) {
       int lx, ly;
-      pixel_of<TS>(threadIdx.x, p, lx, ly);
+      pixel_of<TS, true>(threadIdx.x, p, lx, ly);
       const int x = tx * TS + lx, y = ty * TS + ly;
       px[p] = (float)x;
       py[p] = (float)y;
+      pxc = (float)x;
       if (x < W && y < H) {
         const size_t pix = (size_t)y * W + x;
         T[p] = vw.fT[pix];
@@ -271,63 +365,72 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
       for (int j = hi - lo - 1; j >= 0; --j) {
         const uint32_t pos = (uint32_t)(lo + j);
         const float4 f0 = *reinterpret_cast<const float4*>(&cb[j].u);
+        const float4 f2 = *reinterpret_cast<const float4*>(&cb[j].b);
+        if (fabsf(f0.x - wcx) > half_lo(f2.w) + whw || fabsf(f0.y - wcy) > half_hi(f2.w) + whh) continue;
         const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
-        const float fb = cb[j].b;
+        float e0, e1;
+        const float dx = __fsub_rn(pxc, f0.x);
+        splat_col(f0.z, f0.w, dx, e0, e1);
+        // per pixel only the moments of dL/dpower over the column are accumulated:
+        // S0 = sum dpow, S1 = sum dpow dy, S2 = sum dpow dy^2 (the thread's pixels share dx)
         float v[10];
 #pragma unroll
         for (int f = 0; f < 10; ++f) v[f] = 0.f;
+        float S0 = 0.f, S1 = 0.f, S2 = 0.f;
         bool any = false;
 #pragma unroll
         for (int p = 0; p < S::kPPT; ++p) {
           if (pos >= lastp[p]) continue;
-          const float dx = __fsub_rn(px[p], f0.x), dy = __fsub_rn(py[p], f0.y);
-          const float p2 = splat_power2(f0.z, f0.w, f1.x, dx, dy);
-          if (p2 > 0.f) continue;
+          const float dy = __fsub_rn(py[p], f0.y);
+          const float p2 = splat_power2(f1.x, e0, e1, dy);
+          if (p2 > 0.f || p2 < f2.z) continue;
           const float Gv = ex2_approx(p2);
           const float araw = __fmul_rn(f1.y, Gv);
           const float a = fminf(amax, araw);
-          if (a < amin) continue;
           any = true;
-          const float rom = 1.f / (1.f - a);
+          const float rom = rcp_approx(1.f - a);
           const float Tb = T[p] * rom;              // transmittance in front of this Gaussian
           const float aT = a * Tb;
           v[6] += aT * G[p][0];
           v[7] += aT * G[p][1];
           v[8] += aT * G[p][2];
-          const float cg = f1.z * G[p][0] + f1.w * G[p][1] + fb * G[p][2];
+          const float cg = f1.z * G[p][0] + f1.w * G[p][1] + f2.x * G[p][2];
           const float Ag = A[p][0] * G[p][0] + A[p][1] * G[p][1] + A[p][2] * G[p][2];
           const float dal = Tb * cg - Ag * rom;
           A[p][0] += f1.z * aT;
           A[p][1] += f1.w * aT;
-          A[p][2] += fb * aT;
+          A[p][2] += f2.x * aT;
           T[p] = Tb;
           if (araw < amax) {
-            v[5] += dal * Gv;
             const float dpow = dal * a;
-            const float du = dpow * kNegTwoLn2 * (f0.z * dx + 0.5f * f0.w * dy);
-            const float dv = dpow * kNegTwoLn2 * (0.5f * f0.w * dx + f1.x * dy);
-            v[0] += du;
-            v[1] += dv;
-            v[2] += -0.5f * dpow * dx * dx;
-            v[3] += -dpow * dx * dy;
-            v[4] += -0.5f * dpow * dy * dy;
-            if (ABS) v[9] += fabsf(du) + fabsf(dv);
+            const float dpy = dpow * dy;
+            S0 += dpow;
+            S1 += dpy;
+            S2 += dpy * dy;
+            if (ABS) {
+              const float du = kNegTwoLn2 * (f0.z * dx * dpow + 0.5f * f0.w * dpy);
+              const float dv = kNegTwoLn2 * (0.5f * f0.w * dx * dpow + f1.x * dpy);
+              v[9] += fabsf(du) + fabsf(dv);
+            }
           }
         }
         if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int f = 0; f < (ABS ? 10 : 9); ++f) v[f] += __shfl_xor_sync(0xffffffffu, v[f], o);
-          float mine = 0.f;
-#pragma unroll
-          for (int f = 0; f < 9; ++f) mine = lane == f ? v[f] : mine;
-          const uint32_t rank = cb[j].rank;
-          if (lane < 9) red_add_f32(g2d + (size_t)rank * 9 + lane, mine);
-          if (ABS && lane == 9) {
-            const uint32_t id = cb[j].id;
-            const KSeg& sg = tseg(tab, find_seg(tab, (int)id));
-            if (sg.gabs) red_add_f32(sg.gabs + (id - sg.offset), v[9]);
+          // fields: du, dv, d conic (a, b, c), d opacity, d rgb; with alpha = o G unclamped,
+          // dL/do = sum dL/dalpha G = S0 / o
+          v[0] = kNegTwoLn2 * (f0.z * dx * S0 + 0.5f * f0.w * S1);
+          v[1] = kNegTwoLn2 * (0.5f * f0.w * dx * S0 + f1.x * S1);
+          v[2] = -0.5f * dx * dx * S0;
+          v[3] = -dx * S1;
+          v[4] = -0.5f * S2;
+          v[5] = S0 * rcp_approx(f1.y);
+          const float tot = reduce10(v, lane);
+          const int field = reduce10_field(lane);
+          const uint32_t rank = __float_as_uint(f2.y);
+          if ((lane & 1) == 0 && field >= 0 && field < 9) red_add_f32(g2d + (size_t)rank * 9 + field, tot);
+          if (ABS && (lane & 1) == 0 && field == 9) {
+            const int id = (int)dorder[rank];
+            const KSeg& sg = tseg(tab, find_seg(tab, id));
+            if (sg.gabs) red_add_f32(sg.gabs + (id - sg.offset), tot);
           }
         }
       }
@@ -359,7 +462,7 @@ int resident_grid(K kernel, int threads, int items) {
 template <int TS>
 cudaError_t fwd_class(const DevTables* tab, const HostPlan& plan, const Splat* sorted, const uint2* ranges,
                       const uint32_t* order, WsHeader* hdr, bool count, cudaStream_t s) {
-  using S = TileShape<TS>;
+  using S = TileShape<TS, false>;
   const int items = plan.class_tiles[S::kClass];
   if (items == 0) return cudaSuccess;
   note_launches(1);
@@ -376,18 +479,19 @@ cudaError_t fwd_class(const DevTables* tab, const HostPlan& plan, const Splat* s
 
 template <int TS>
 cudaError_t bwd_class(const DevTables* tab, const HostPlan& plan, const Splat* sorted, const uint2* ranges,
-                      const uint32_t* order, float* g2d, WsHeader* hdr, bool abs, cudaStream_t s) {
-  using S = TileShape<TS>;
+                      const uint32_t* order, float* g2d, const uint32_t* d0, const uint32_t* d1, WsHeader* hdr,
+                      bool abs, cudaStream_t s) {
+  using S = TileShape<TS, true>;
   const int items = plan.class_tiles[S::kClass];
   if (items == 0) return cudaSuccess;
   note_launches(1);
   const int begin = plan.class_begin[S::kClass];
   if (abs) {
     auto k = blend_backward_kernel<TS, true>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, sorted, ranges, order, begin, items, g2d, hdr);
+    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, sorted, ranges, order, begin, items, g2d, d0, d1, hdr);
   } else {
     auto k = blend_backward_kernel<TS, false>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, sorted, ranges, order, begin, items, g2d, hdr);
+    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, sorted, ranges, order, begin, items, g2d, d0, d1, hdr);
   }
   return cudaGetLastError();
 }
@@ -416,9 +520,11 @@ cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, co
   reset_bwd_queues<<<1, 32, 0, s>>>(hdr);
   zero_g2d<<<sort_blocks() * 2, 256, 0, s>>>(g2d, hdr);
   note_launches(2);
-  cudaError_t e = bwd_class<8>(tab, plan, sorted, ranges, order, g2d, hdr, abs, s);
-  if (e == cudaSuccess) e = bwd_class<16>(tab, plan, sorted, ranges, order, g2d, hdr, abs, s);
-  if (e == cudaSuccess) e = bwd_class<32>(tab, plan, sorted, ranges, order, g2d, hdr, abs, s);
+  const uint32_t* d0 = reinterpret_cast<const uint32_t*>(ws + L.vvals[0]);
+  const uint32_t* d1 = reinterpret_cast<const uint32_t*>(ws + L.vvals[1]);
+  cudaError_t e = bwd_class<8>(tab, plan, sorted, ranges, order, g2d, d0, d1, hdr, abs, s);
+  if (e == cudaSuccess) e = bwd_class<16>(tab, plan, sorted, ranges, order, g2d, d0, d1, hdr, abs, s);
+  if (e == cudaSuccess) e = bwd_class<32>(tab, plan, sorted, ranges, order, g2d, d0, d1, hdr, abs, s);
   return e;
 }
 

@@ -116,6 +116,13 @@ struct WsHeader {
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
+// The depth sort runs ceil(depth_bits / 8) active passes (known only on the device); its result
+// (Gaussian ids in depth order) sits in buffer (active passes % 2).
+__device__ __forceinline__ const uint32_t* depth_order(const WsHeader* hdr, const uint32_t* b0, const uint32_t* b1) {
+  const unsigned passes = (hdr->depth_bits + 7) / 8;
+  return (passes & 1) ? b1 : b0;
+}
+
 __device__ __forceinline__ int find_seg(const DevTables* __restrict__ t, int i) {
   int lo = 0, hi = t->h.n_segs - 1;
   while (lo < hi) {
@@ -146,7 +153,7 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 // Offsets (bytes) of the regions of one render workspace (any number of views / segments).
 struct Layout {
   size_t header, tables, splats, rects, touched, dkey, vkeys[2], vvals[2], pkeys[2], pvals[2], sorted,
-      ranges, order, buckets, hist, blocksums, g2d, total;
+      ranges, order, buckets, hist, blocksums, slices, g2d, total;
 };
 Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t pair_capacity);
 

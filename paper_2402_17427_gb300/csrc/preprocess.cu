@@ -2,6 +2,7 @@
 //
 // Paper Sec. 3: each 3D Gaussian (position, anisotropic covariance, opacity, SH colour) is
 // projected to the image as a 2D Gaussian; R is differentiable.  One thread per Gaussian.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -240,8 +241,17 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __rest
         s.opacity = o;
         s.r = rgb[0]; s.g = rgb[1]; s.b = rgb[2];
         s.rank = 0;
-        s.id = (uint32_t)i;
-        s.pad = 0;
+        // alpha >= alpha_min  <=>  power2 >= tg;  that region is the ellipse d^T Sigma2^-1 d <= k2
+        // with k2 = 2 ln(opacity / alpha_min), whose bounding box has half-extents k sqrt(A), k sqrt(C)
+        s.tg = log2f(op.alpha_min / o);
+        float hx = -65504.f, hy = -65504.f;
+        if (s.tg <= 0.f) {
+          const float k2 = -2.0f * 0.69314718f * s.tg;
+          hx = sqrtf(k2 * P.A) * 1.001f + 0.01f;
+          hy = sqrtf(k2 * P.C) * 1.001f + 0.01f;
+        }
+        s.hxy = (uint32_t)__half_as_ushort(__float2half_ru(hx)) |
+                ((uint32_t)__half_as_ushort(__float2half_ru(hy)) << 16);
         float4* dst = reinterpret_cast<float4*>(splats + i);
         const float4* src = reinterpret_cast<const float4*>(&s);
         dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
@@ -401,16 +411,29 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(
 #pragma unroll
     for (int k = 0; k < 4; ++k) o_q[k] = (dqn[k] - P.qn[k] * qd) * P.qinv;
   }
-  // write (or accumulate) every output of Gaussian i
+  // write (or accumulate) every output of Gaussian i; 16-byte rows go out as float4
   auto put = [&](float* dst, float v) { if (accumulate) *dst += v; else *dst = v; };
+  auto put4 = [&](float* dst, float a, float b, float c, float d) {
+    float4* p = reinterpret_cast<float4*>(dst);
+    float4 v = make_float4(a, b, c, d);
+    if (accumulate) {
+      const float4 o = *p;
+      v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+    }
+    *p = v;
+  };
   const size_t l = (size_t)li;
 #pragma unroll
   for (int k = 0; k < 3; ++k) { put(sg.gm + 3 * l + k, o_m[k]); put(sg.gs + 3 * l + k, o_s[k]); }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) put(sg.gq + 4 * l + k, o_q[k]);
+  put4(sg.gq + 4 * l, o_q[0], o_q[1], o_q[2], o_q[3]);
   put(sg.gl + l, o_l);
+  if constexpr ((3 * K) % 4 == 0) {
 #pragma unroll
-  for (int k = 0; k < 3 * K; ++k) put(sg.gsh + l * 3 * K + k, o_sh[k]);
+    for (int k = 0; k < 3 * K; k += 4) put4(sg.gsh + l * 3 * K + k, o_sh[k], o_sh[k + 1], o_sh[k + 2], o_sh[k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) put(sg.gsh + l * 3 * K + k, o_sh[k]);
+  }
 }
 
 }  // namespace

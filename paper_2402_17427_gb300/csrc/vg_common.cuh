@@ -14,15 +14,17 @@ constexpr int kMaxChunk = 256;
 // One projected 2D Gaussian as the blend kernels consume it (48 bytes, 16-byte aligned so a
 // run of records can be moved by one bulk copy).  The conic is pre-scaled to log2 units:
 //   power2(dx, dy) = ca dx^2 + cb dx dy + cc dy^2 = log2(e) * (-(a dx^2 + c dy^2)/2 - b dx dy)
-// with (a, b, c) the inverse 2D covariance and dx = px - u, dy = py - v, so that
-// G = exp(power) = 2^power2.
+// with (a, b, c) the inverse 2D covariance and dx = px - u, dy = py - v, so G = 2^power2.
+// tg = log2(alpha_min / opacity): a pixel is skipped when power2 < tg (alpha below alpha_min)
+// or power2 > 0.  hx, hy (binary16, rounded up and inflated) bound the region power2 >= tg,
+// so a warp whose pixels all lie outside [u -+ hx] x [v -+ hy] can skip the splat unevaluated.
 struct __align__(16) Splat {
   float u, v, ca, cb;
   float cc, opacity, r, g;
   float b;
   uint32_t rank;    // position of the Gaussian in the depth order (index of its 2D gradient slot)
-  uint32_t id;      // index of the Gaussian in the input arrays
-  uint32_t pad;
+  float tg;
+  uint32_t hxy;     // half2 (hx, hy)
 };
 static_assert(sizeof(Splat) == 48, "Splat must stay 48 bytes");
 
@@ -47,13 +49,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Exponent (log2 units) of one Gaussian at one pixel.  Written with explicit round-to-nearest
-// intrinsics so every kernel that evaluates it (forward and backward) takes bit-identical
-// decisions.
-__device__ __forceinline__ float splat_power2(float ca, float cb, float cc, float dx, float dy) {
-  float t = __fmaf_rn(ca, dx, __fmul_rn(cb, dy));
-  float q = __fmul_rn(__fmul_rn(cc, dy), dy);
-  return __fmaf_rn(t, dx, q);
+// Exponent (log2 units) of one Gaussian at one pixel, split so that the terms that depend only
+// on the pixel column are shared by the pixels of a thread:
+//   e0 = ca dx dx, e1 = cb dx;  power2 = dy (cc dy + e1) + e0.
+// Written with explicit round-to-nearest intrinsics so the forward and the backward kernels take
+// bit-identical decisions.
+__device__ __forceinline__ void splat_col(float ca, float cb, float dx, float& e0, float& e1) {
+  e0 = __fmul_rn(__fmul_rn(ca, dx), dx);
+  e1 = __fmul_rn(cb, dx);
+}
+__device__ __forceinline__ float splat_power2(float cc, float e0, float e1, float dy) {
+  return __fmaf_rn(dy, __fmaf_rn(cc, dy, e1), e0);
 }
 
 // ------------------------------------------------------------------------------------------
