@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for the CPU baseline")
+    ap.add_argument("--no-patterns", action="store_true", help="skip the batched-cells and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
     return ap.parse_args()
 
 
@@ -184,6 +186,79 @@ def run_reference(args, ws, rank):
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------ patterns
+
+def batch_pattern(dev, steps=10, warmup=3):
+    """Eight uneven aerial cells trained together (one batched call per stage) against the same
+    cells trained one after another (three calls per cell), fwd + loss + bwd, same GPU."""
+    import torch
+    from paper_2402_17427_gb300 import batch as BT, rasterize as R, scenes
+    cells = scenes.aerial_cells(step=0)
+    params = [[t.to(dev) for t in R.to_device(c.gaussians, "cpu")] for c in cells]
+    cams = [c.camera for c in cells]
+    targets = [torch.from_numpy(c.target).to(dev) for c in cells]
+    tuner = BT.AutoTuner()
+    settings = [tuner.choose(p, 3, cam) for p, cam in zip(params, cams)]
+    grads = [tuple(torch.empty_like(t) for t in p) for p in params]
+    losses = [R.LossL1DSSIM(0.2) for _ in cells]
+    br = BT.BatchRasterizer(settings, device=dev)
+    ras = [R.Rasterizer(s, device=dev) for s in settings]
+
+    def batched():
+        outs = br.forward(params, 3, cams)
+        dLs = [losses[k](outs[k][0], targets[k], reuse=True)[1] for k in range(len(cells))]
+        br.backward(params, 3, cams, outs, dLs, grads=grads)
+
+    def sequential():
+        for k in range(len(cells)):
+            rgb, T, last = ras[k].forward(*params[k], 3, cams[k])
+            _, dL = losses[k](rgb, targets[k], reuse=True)
+            ras[k].backward(*params[k], 3, cams[k], T, last, dL, grads=grads[k])
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    batched()
+    sequential()
+    br.check = "defer"
+    for r in ras:
+        r.check = "defer"
+    ms_b = timed(batched)
+    ms_s = timed(sequential)
+    br.verify()
+    for r in ras:
+        r.verify()
+    return {"workload": "8 aerial cells (0.3M..3.0M Gaussians, 11.8M total, SH3), 1152x864 nadir view each, "
+                        "fwd + L1/D-SSIM + bwd for all cells",
+            "batched_steps_per_s": 1000.0 / ms_b, "sequential_steps_per_s": 1000.0 / ms_s,
+            "batched_ms": ms_b, "sequential_ms": ms_s, "speedup": ms_s / ms_b,
+            "tiles": [s.tile_size for s in settings], "chunks": [s.chunk for s in settings]}
+
+
+def serving_pattern(dev, seconds=30.0):
+    """The merged 20M-Gaussian city (16 cells) served under a 200 req/s Poisson stream."""
+    from paper_2402_17427_gb300 import scenes, serving
+    cells = scenes.merged_city()
+    srv = serving.SceneServer(cells, device=dev, slots=3, max_batch=8)
+    reqs = scenes.request_stream(duration_s=seconds)
+    srv.render([r.camera for r in reqs[:4]])      # allocate workspaces, learn the pairs ratio
+    st = srv.serve(reqs, warmup_s=2.0)
+    d = st.summary()
+    d["workload"] = ("merged city: 16 cells, 20M Gaussians SH3 resident; Poisson 200 req/s for %.0f s; "
+                     "50%% 1280x720, 35%% 1920x1080, 15%% 3840x2160; first 2 s excluded" % seconds)
+    d["resident_gb"] = srv.resident_bytes / 1e9
+    return d
 
 
 # ------------------------------------------------------------------------------------------ GPU arm
@@ -335,6 +410,12 @@ def main():
         except Exception as e:  # the oracle is test infrastructure; report, never fail the GPU number
             cpu = {"value": None, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {e}"}
+    patterns = None
+    if not args.no_patterns and ws == 1:
+        try:
+            patterns = {"batched_cells": batch_pattern(dev), "serving": serving_pattern(dev, args.serve_seconds)}
+        except Exception as e:  # report, never lose the main number
+            patterns = {"error": repr(e)}
     line = {
         "metric": METRIC, "value": ws * 1000.0 / ms, "unit": "steps/s", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -354,6 +435,7 @@ def main():
         "step_hbm": {"bytes": int(step_bytes), "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm,
                      "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "patterns": patterns,
     }
     print(json.dumps(line), flush=True)
     if pg:

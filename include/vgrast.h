@@ -100,13 +100,13 @@ typedef struct {
   void* end[VG_STAGE_COUNT];
 } vg_stage_events;
 
-/* Rasteriser settings.  vg_default_opts() fills the method's values: tile 16, bg black,
+/* Rasteriser settings.  vg_default_opts() fills the method's values: tile 16, chunk 128, bg black,
  * dilation 0.3 (low-pass added to the 2D covariance), alpha_max 0.99, alpha_min 1/255,
  * t_min 1e-4 (stop when transmittance would fall below it), guard 1.3 (Jacobian clamp,
  * fraction of the half field of view), stop_rule 0.                                          */
 typedef struct {
   int32_t tile_size;           /* 8, 16 or 32                                                 */
-  int32_t chunk;               /* Gaussians staged per shared-memory chunk: 64, 128 or 256    */
+  int32_t chunk;               /* splats staged per shared-memory chunk: 32, 64 or 128       */
   float bg[3];                 /* background colour                                           */
   float dilation, alpha_max, alpha_min, t_min, guard;
   int32_t stop_rule;           /* 0: the Gaussian that would take T below t_min is not
@@ -176,7 +176,8 @@ vg_status vg_rasterize_backward(const vg_gaussians* g, const vg_camera* cam, con
  *   ids          uint32 [pair_capacity]: Gaussian index of every (tile, Gaussian) pair, tile
  *                lists concatenated, each ordered front to back
  *   projected    float32 [n, 12]: u, v, conic a, b, c (inverse 2D covariance), opacity, r, g,
- *                b, depth rank (as float), 0, 0 — valid for Gaussians that touch a tile
+ *                b, depth rank (as float), u remainder, v remainder — the projected mean is
+ *                (u + u remainder, v + v remainder); valid for Gaussians that touch a tile
  *   touched      uint32 [n]: number of tiles each Gaussian touches (0 = culled)            */
 vg_status vg_read_render_state(const void* workspace, size_t workspace_bytes, int64_t n, int32_t width,
                                int32_t height, int64_t pair_capacity, const vg_raster_opts* opts,
@@ -217,6 +218,26 @@ vg_status vg_render_batch_backward(const vg_gaussians* cells, int32_t n_cells, c
                                    const uint32_t* const* out_last, const float* const* dL_drgb,
                                    float* const* g_means, float* const* g_log_scales, float* const* g_quats,
                                    float* const* g_opacity_logits, float* const* g_sh, vg_stream stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Novel views of a merged scene (Sec. 4.3: the merged scene is the union of the cells; Sec. 5:
+ * real-time rendering).  n_views cameras, forward only, over n_cells resident cells.  For each
+ * view, a cell is rendered only if its axis-aligned box cell_aabbs[c] = (xmin, ymin, zmin, xmax,
+ * ymax, zmax) (host array; it must bound the cell's Gaussians including their 3-sigma extent)
+ * intersects the view frustum widened by a safety margin; with cell_aabbs == NULL every cell is
+ * rendered in every view.  Each view's image depends only on its own camera and cells: the same
+ * view renders bit-identically alone or batched with others.
+ *   out_cells_rendered  optional host array [n_views]: cells kept for each view
+ * ------------------------------------------------------------------------------------------ */
+size_t vg_views_workspace_bytes(const vg_gaussians* cells, int32_t n_cells, const float* cell_aabbs,
+                                const vg_camera* cams, const vg_raster_opts* opts, int32_t n_views,
+                                int64_t pair_capacity);
+vg_status vg_render_views(const vg_gaussians* cells /* host [n_cells] */, int32_t n_cells,
+                          const float* cell_aabbs /* host [n_cells * 6] or NULL */,
+                          const vg_camera* cams /* host [n_views] */, const vg_raster_opts* opts /* host [n_views] */,
+                          int32_t n_views, void* workspace, size_t workspace_bytes, int64_t pair_capacity,
+                          float* const* out_rgb, float* const* out_final_T, uint32_t* const* out_last,
+                          int32_t* out_cells_rendered, int64_t* counters, vg_stream stream);
 
 #ifdef __cplusplus
 }

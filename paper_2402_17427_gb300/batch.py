@@ -115,7 +115,7 @@ class AutoTuner:
     """Per-cell tile size / chunk choice by measurement, cached by a coarse workload key."""
 
     TILES = (8, 16, 32)
-    CHUNKS = (64, 128)
+    CHUNKS = (32, 64, 128)
 
     def __init__(self, base: RasterSettings | None = None, trials: int = 3):
         self.base = base or RasterSettings()

@@ -22,7 +22,8 @@ VG_FLAG_COUNT_BLENDS = 2
 
 EXPORTED = ("vg_default_opts", "vg_status_string", "vg_kernel_launches", "vg_workspace_bytes", "vg_rasterize_forward",
             "vg_rasterize_backward", "vg_read_render_state", "vg_loss_workspace_bytes", "vg_loss_l1_dssim",
-            "vg_batch_workspace_bytes", "vg_render_batch", "vg_render_batch_backward")
+            "vg_batch_workspace_bytes", "vg_render_batch", "vg_render_batch_backward",
+            "vg_views_workspace_bytes", "vg_render_views")
 
 
 class vg_camera(ctypes.Structure):
@@ -111,6 +112,14 @@ def lib():
                                                ctypes.c_size_t, ctypes.c_int64, _PP, _PP, _PP, _PP, _PP, _PP,
                                                _PP, _PP, _P]
         L.vg_render_batch_backward.restype = ctypes.c_int
+    L.vg_views_workspace_bytes.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32, _P,
+                                           ctypes.POINTER(vg_camera), ctypes.POINTER(vg_raster_opts), ctypes.c_int32,
+                                           ctypes.c_int64]
+    L.vg_views_workspace_bytes.restype = ctypes.c_size_t
+    L.vg_render_views.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32, _P, ctypes.POINTER(vg_camera),
+                                  ctypes.POINTER(vg_raster_opts), ctypes.c_int32, _P, ctypes.c_size_t,
+                                  ctypes.c_int64, _PP, _PP, _PP, _P, _P, _P]
+    L.vg_render_views.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -217,3 +226,30 @@ def vg_render_batch_backward(cells, cams, opts, workspace: int, workspace_bytes:
         keep.append(k)
     _check(lib().vg_render_batch_backward(G, n, C, O, workspace, workspace_bytes, pair_capacity, *arrs, stream),
            "vg_render_batch_backward")
+
+
+def vg_views_workspace_bytes(cells, aabbs, cams, opts, pair_capacity: int) -> int:
+    """aabbs: None or a C float array / numpy float32 [n_cells, 6] kept alive by the caller."""
+    n, nv = len(cells), len(cams)
+    G = (vg_gaussians * n)(*cells)
+    C = (vg_camera * nv)(*cams)
+    O = (vg_raster_opts * nv)(*opts)
+    ab = None if aabbs is None else aabbs.ctypes.data
+    return int(lib().vg_views_workspace_bytes(G, n, ab, C, O, nv, pair_capacity))
+
+
+def vg_render_views(cells, aabbs, cams, opts, workspace: int, workspace_bytes: int, pair_capacity: int, out_rgb,
+                    out_final_T, out_last, counters: int, stream: int):
+    """Returns the number of cells rendered in each view."""
+    n, nv = len(cells), len(cams)
+    G = (vg_gaussians * n)(*cells)
+    C = (vg_camera * nv)(*cams)
+    O = (vg_raster_opts * nv)(*opts)
+    ab = None if aabbs is None else aabbs.ctypes.data
+    kept = (ctypes.c_int32 * nv)()
+    a, _ka = _ptr_array(out_rgb)
+    b, _kb = _ptr_array(out_final_T)
+    c, _kc = _ptr_array(out_last)
+    _check(lib().vg_render_views(G, n, ab, C, O, nv, workspace, workspace_bytes, pair_capacity, a, b, c, kept,
+                                 counters, stream), "vg_render_views")
+    return list(kept)

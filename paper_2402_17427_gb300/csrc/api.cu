@@ -1,5 +1,6 @@
 // C ABI of the rasteriser (declared in include/vgrast.h): argument checks, workspace layout
 // and the launch sequences of the forward and backward passes.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -52,7 +53,9 @@ __global__ void read_state(const Splat* __restrict__ sorted, const Splat* __rest
       if (proj) {
         const Splat s = splats[i];
         const bool vis = touched_in[i] > 0;
-        float v[12] = {s.u, s.v, s.ca * k, s.cb * 0.5f * k, s.cc * k, s.opacity, s.r, s.g, s.b, (float)s.rank, 0.f, 0.f};
+        const float ulo = __half2float(__ushort_as_half((unsigned short)(s.uvlo & 0xFFFFu)));
+        const float vlo = __half2float(__ushort_as_half((unsigned short)(s.uvlo >> 16)));
+        float v[12] = {s.u, s.v, s.ca * k, s.cb * 0.5f * k, s.cc * k, exp2f(s.lo), s.r, s.g, s.b, (float)s.rank, ulo, vlo};
         for (int f = 0; f < 12; ++f) proj[(size_t)i * 12 + f] = vis ? v[f] : 0.f;
       }
     }
@@ -64,7 +67,7 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 bool valid_opts(const vg_raster_opts* o) {
   if (!o) return false;
   if (o->tile_size != 8 && o->tile_size != 16 && o->tile_size != 32) return false;
-  if (o->chunk != 64 && o->chunk != 128 && o->chunk != 256) return false;
+  if (o->chunk != 32 && o->chunk != 64 && o->chunk != 128) return false;
   if (!(o->alpha_max > 0.f && o->alpha_max < 1.f) || !(o->alpha_min >= 0.f && o->alpha_min < o->alpha_max)) return false;
   if (!(o->t_min > 0.f && o->t_min < 1.f) || !(o->dilation >= 0.f) || !(o->guard > 0.f)) return false;
   if (o->stop_rule != 0 && o->stop_rule != 1) return false;
@@ -120,6 +123,7 @@ KOpts make_opts(const vg_raster_opts* o) {
   k.dilation = o->dilation; k.alpha_max = o->alpha_max; k.alpha_min = o->alpha_min; k.t_min = o->t_min;
   k.stop_rule = o->stop_rule;
   k.tile = o->tile_size;
+  k.chunk = o->chunk;
   return k;
 }
 
@@ -204,6 +208,57 @@ vg_status make_call(Call& c, const vg_gaussians* segs, int n_segs, const int* se
   return VG_OK;
 }
 
+// Conservative test of an axis-aligned box against a camera's view frustum (near plane and the
+// four image-edge planes, widened by `margin_px`): false only if every corner of the box lies
+// outside one plane, so no Gaussian inside the box can reach the image.
+bool box_in_view(const float* bb, const vg_camera* c, float margin_px) {
+  const float xmin = (-margin_px - c->cx) / c->fx, xmax = (c->width - 1 + margin_px - c->cx) / c->fx;
+  const float ymin = (-margin_px - c->cy) / c->fy, ymax = (c->height - 1 + margin_px - c->cy) / c->fy;
+  const float* M = c->world_to_cam;
+  int out[5] = {0, 0, 0, 0, 0};
+  for (int k = 0; k < 8; ++k) {
+    const float X = (k & 1) ? bb[3] : bb[0], Y = (k & 2) ? bb[4] : bb[1], Z = (k & 4) ? bb[5] : bb[2];
+    const float x = M[0] * X + M[1] * Y + M[2] * Z + M[3];
+    const float y = M[4] * X + M[5] * Y + M[6] * Z + M[7];
+    const float z = M[8] * X + M[9] * Y + M[10] * Z + M[11];
+    out[0] += z <= c->near_plane;
+    out[1] += x < xmin * z;
+    out[2] += x > xmax * z;
+    out[3] += y < ymin * z;
+    out[4] += y > ymax * z;
+  }
+  for (int p = 0; p < 5; ++p)
+    if (out[p] == 8) return false;
+  return true;
+}
+
+// Segments of a multi-view call: every (view, visible cell) pair, views in order, cells in order.
+vg_status make_views_call(Call& c, const vg_gaussians* cells, int n_cells, const float* aabbs, const vg_camera* cams,
+                          const vg_raster_opts* opts, int n_views, int32_t* kept) {
+  if (!cells || !cams || !opts || n_cells < 1 || n_views < 1 || n_views > kMaxViews) return VG_ERR_INVALID;
+  std::vector<vg_gaussians> segs;
+  std::vector<int> sv;
+  for (int v = 0; v < n_views; ++v) {
+    if (!valid_camera(&cams[v])) return VG_ERR_INVALID;
+    int k = 0;
+    for (int i = 0; i < n_cells; ++i) {
+      if (aabbs && !box_in_view(aabbs + 6 * i, &cams[v], 8.0f)) continue;
+      segs.push_back(cells[i]);
+      sv.push_back(v);
+      ++k;
+    }
+    if (kept) kept[v] = k;
+  }
+  if (segs.empty()) {   // nothing visible anywhere: render one empty segment into view 0
+    vg_gaussians e = cells[0];
+    e.n = 0;
+    segs.push_back(e);
+    sv.push_back(0);
+  }
+  if ((int)segs.size() > kMaxSegs) return VG_ERR_INVALID;
+  return make_call(c, segs.data(), (int)segs.size(), sv.data(), cams, opts, n_views);
+}
+
 // Forward pass of a prepared call: projection, binning, compositing.
 vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, size_t workspace_bytes,
                       int64_t pair_capacity, int64_t* counters, cudaStream_t s) {
@@ -275,7 +330,7 @@ extern "C" void vg_default_opts(vg_raster_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->tile_size = 16;
-  o->chunk = 256;
+  o->chunk = 128;
   o->dilation = 0.3f;
   o->alpha_max = 0.99f;
   o->alpha_min = 1.0f / 255.0f;
@@ -410,6 +465,35 @@ extern "C" vg_status vg_render_batch_backward(const vg_gaussians* cells, int32_t
   }
   return run_backward(c, &opts[0], workspace, workspace_bytes, pair_capacity, false,
                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t vg_views_workspace_bytes(const vg_gaussians* cells, int32_t n_cells, const float* cell_aabbs,
+                                           const vg_camera* cams, const vg_raster_opts* opts, int32_t n_views,
+                                           int64_t pair_capacity) {
+  if (pair_capacity < 1 || pair_capacity > 0xFFFFFFFFll) return 0;
+  Call c;
+  if (make_views_call(c, cells, n_cells, cell_aabbs, cams, opts, n_views, nullptr) != VG_OK) return 0;
+  return make_layout(c.total_n64, c.total_tiles64, pair_capacity).total;
+}
+
+extern "C" vg_status vg_render_views(const vg_gaussians* cells, int32_t n_cells, const float* cell_aabbs,
+                                     const vg_camera* cams, const vg_raster_opts* opts, int32_t n_views,
+                                     void* workspace, size_t workspace_bytes, int64_t pair_capacity,
+                                     float* const* out_rgb, float* const* out_final_T, uint32_t* const* out_last,
+                                     int32_t* out_cells_rendered, int64_t* counters, vg_stream stream) {
+  if (!out_rgb || !out_final_T || !out_last) return VG_ERR_INVALID;
+  Call c;
+  vg_status st = make_views_call(c, cells, n_cells, cell_aabbs, cams, opts, n_views, out_cells_rendered);
+  if (st != VG_OK) return st;
+  for (int v = 0; v < n_views; ++v) {
+    if (!out_rgb[v] || !out_final_T[v] || !out_last[v]) return VG_ERR_INVALID;
+    KView& kv = c.views()[v];
+    kv.rgb = out_rgb[v];
+    kv.T = out_final_T[v];
+    kv.last = out_last[v];
+  }
+  return run_forward(c, &opts[0], workspace, workspace_bytes, pair_capacity, counters,
+                     reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" vg_status vg_read_render_state(const void* workspace, size_t workspace_bytes, int64_t n, int32_t width,

@@ -20,7 +20,7 @@
 namespace vg {
 namespace {
 
-constexpr int kCh = 128;
+constexpr int kCh = 128;   // shared-memory capacity of one chunk buffer (the chunk option is <= this)
 constexpr float kNegTwoLn2 = -1.3862943611198906f;   // true conic = scaled conic * (-2 ln 2)
 
 // Thread layout of a tile.  The forward pass is latency-bound (short per-pixel chains), so it
@@ -152,11 +152,13 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
     const int tx = lt % vw.tiles_x, ty = lt / vw.tiles_x;
     const int W = vw.cam.W, H = vw.cam.H;
     const float amax = vw.op.alpha_max, tmin = vw.op.t_min;
+    const float lamin = log2f(vw.op.alpha_min);
     const bool rule0 = vw.op.stop_rule == 0;
     float wcx, wcy, whw, whh;
     warp_block<TS, false>(tx, ty, wcx, wcy, whw, whh);
     const uint2 rg = ranges[tile];
     const int n = (int)(rg.y - rg.x);
+    const int ch = vw.op.chunk;
 
     float px[S::kPPT], py[S::kPPT], T[S::kPPT], C[S::kPPT][3];
     float pxc = 0.f;    // the thread's pixels share one column
@@ -175,13 +177,13 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
       C[p][0] = C[p][1] = C[p][2] = 0.f;
       last[p] = 0;
     }
-    const int nch = (n + kCh - 1) / kCh;
-    if (threadIdx.x == 0 && nch > 0) issue_chunk(buf[0], sorted + rg.x, min(kCh, n), &bar[0]);
+    const int nch = (n + ch - 1) / ch;
+    if (threadIdx.x == 0 && nch > 0) issue_chunk(buf[0], sorted + rg.x, min(ch, n), &bar[0]);
     for (int k = 0; k < nch; ++k) {
       const int b = k & 1;
       const bool more = k + 1 < nch;
       if (threadIdx.x == 0 && more)
-        issue_chunk(buf[b ^ 1], sorted + rg.x + (k + 1) * kCh, min(kCh, n - (k + 1) * kCh), &bar[b ^ 1]);
+        issue_chunk(buf[b ^ 1], sorted + rg.x + (k + 1) * ch, min(ch, n - (k + 1) * ch), &bar[b ^ 1]);
       const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
       if (b) ph1 ^= 1; else ph0 ^= 1;
       if (!__syncthreads_and(ok)) {
@@ -195,7 +197,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
 #pragma unroll
       for (int p = 0; p < S::kPPT; ++p) wdone = wdone && done[p];
       // a warp whose pixels have all terminated skips the chunk (uniform branch)
-      const int cnt = __all_sync(0xffffffffu, wdone) ? 0 : min(kCh, n - k * kCh);
+      const int cnt = __all_sync(0xffffffffu, wdone) ? 0 : min(ch, n - k * ch);
       for (int j = 0; j < cnt; ++j) {
         const float4 f0 = *reinterpret_cast<const float4*>(&cb[j].u);
         const float4 f2 = *reinterpret_cast<const float4*>(&cb[j].b);
@@ -209,14 +211,16 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
         }
         const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
         float e0, e1;
-        splat_col(f0.z, f0.w, __fsub_rn(pxc, f0.x), e0, e1);
+        splat_col(f0.z, f0.w, __fsub_rn(__fsub_rn(pxc, f0.x), half_lo(f2.z)), e0, e1);
+        const float vlo = half_hi(f2.z);
 #pragma unroll
         for (int p = 0; p < S::kPPT; ++p) {
           if (done[p]) continue;
           if (COUNT) ++ev;
-          const float p2 = splat_power2(f1.x, e0, e1, __fsub_rn(py[p], f0.y));
-          if (p2 > 0.f || p2 < f2.z) continue;
-          const float a = fminf(amax, __fmul_rn(f1.y, ex2_approx(p2)));
+          const float p2 = splat_power2(f1.x, e0, e1, __fsub_rn(__fsub_rn(py[p], f0.y), vlo));
+          const float q = __fadd_rn(p2, f1.y);
+          if (p2 > 0.f || q < lamin) continue;
+          const float a = fminf(amax, ex2_approx(q));
           const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
           const bool stop = Tn < tmin;
           if (stop && rule0) {
@@ -228,7 +232,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
           C[p][1] = __fmaf_rn(f1.w, w, C[p][1]);
           C[p][2] = __fmaf_rn(f2.x, w, C[p][2]);
           T[p] = Tn;
-          last[p] = (uint32_t)(k * kCh + j + 1);
+          last[p] = (uint32_t)(k * ch + j + 1);
           if (COUNT) ++bl;
           if (stop) done[p] = true;
         }
@@ -302,10 +306,12 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
     const int tx = lt % vw.tiles_x, ty = lt / vw.tiles_x;
     const int W = vw.cam.W, H = vw.cam.H;
     const float amax = vw.op.alpha_max;
+    const float lamin = log2f(vw.op.alpha_min);
     float wcx, wcy, whw, whh;
     warp_block<TS, true>(tx, ty, wcx, wcy, whw, whh);
     const uint2 rg = ranges[tile];
     const uint32_t list_len = rg.y - rg.x;
+    const int ch = vw.op.chunk;
     float px[S::kPPT], py[S::kPPT], T[S::kPPT], A[S::kPPT][3], G[S::kPPT][3];
     float pxc = 0.f;
     uint32_t lastp[S::kPPT];
@@ -342,17 +348,17 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
     if (lane == 0) atomicMax(&s_maxlast, mymax);
     __syncthreads();
     const int maxlast = (int)s_maxlast;
-    const int nch = (maxlast + kCh - 1) / kCh;
-    // chunk k covers list positions [max(0, maxlast - (k+1) kCh), maxlast - k kCh), back to front
+    const int nch = (maxlast + ch - 1) / ch;
+    // chunk k covers list positions [max(0, maxlast - (k+1) ch), maxlast - k ch), back to front
     if (threadIdx.x == 0 && nch > 0) {
-      const int lo = max(0, maxlast - kCh);
+      const int lo = max(0, maxlast - ch);
       issue_chunk(buf[0], sorted + rg.x + lo, maxlast - lo, &bar[0]);
     }
     for (int k = 0; k < nch; ++k) {
       const int b = k & 1;
-      const int hi = maxlast - k * kCh, lo = max(0, hi - kCh);
+      const int hi = maxlast - k * ch, lo = max(0, hi - ch);
       if (threadIdx.x == 0 && k + 1 < nch) {
-        const int lo2 = max(0, lo - kCh);
+        const int lo2 = max(0, lo - ch);
         issue_chunk(buf[b ^ 1], sorted + rg.x + lo2, lo - lo2, &bar[b ^ 1]);
       }
       const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
@@ -369,8 +375,9 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
         if (fabsf(f0.x - wcx) > half_lo(f2.w) + whw || fabsf(f0.y - wcy) > half_hi(f2.w) + whh) continue;
         const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
         float e0, e1;
-        const float dx = __fsub_rn(pxc, f0.x);
+        const float dx = __fsub_rn(__fsub_rn(pxc, f0.x), half_lo(f2.z));
         splat_col(f0.z, f0.w, dx, e0, e1);
+        const float vlo = half_hi(f2.z);
         // per pixel only the moments of dL/dpower over the column are accumulated:
         // S0 = sum dpow, S1 = sum dpow dy, S2 = sum dpow dy^2 (the thread's pixels share dx)
         float v[10];
@@ -381,11 +388,11 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
 #pragma unroll
         for (int p = 0; p < S::kPPT; ++p) {
           if (pos >= lastp[p]) continue;
-          const float dy = __fsub_rn(py[p], f0.y);
+          const float dy = __fsub_rn(__fsub_rn(py[p], f0.y), vlo);
           const float p2 = splat_power2(f1.x, e0, e1, dy);
-          if (p2 > 0.f || p2 < f2.z) continue;
-          const float Gv = ex2_approx(p2);
-          const float araw = __fmul_rn(f1.y, Gv);
+          const float q = __fadd_rn(p2, f1.y);
+          if (p2 > 0.f || q < lamin) continue;
+          const float araw = ex2_approx(q);
           const float a = fminf(amax, araw);
           any = true;
           const float rom = rcp_approx(1.f - a);
@@ -422,7 +429,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
           v[2] = -0.5f * dx * dx * S0;
           v[3] = -dx * S1;
           v[4] = -0.5f * S2;
-          v[5] = S0 * rcp_approx(f1.y);
+          v[5] = S0 * ex2_approx(-f1.y);   // 1 / opacity
           const float tot = reduce10(v, lane);
           const int field = reduce10_field(lane);
           const uint32_t rank = __float_as_uint(f2.y);

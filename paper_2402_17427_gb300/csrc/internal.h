@@ -27,6 +27,7 @@ struct KOpts {
   float dilation, alpha_max, alpha_min, t_min;
   int stop_rule;
   int tile;
+  int chunk;      // splats staged per shared-memory chunk (32, 64 or 128)
 };
 
 // Raw Gaussian parameters.

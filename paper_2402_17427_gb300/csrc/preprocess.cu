@@ -233,20 +233,33 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __rest
           rgb[ch] = fmaxf(0.f, acc);
         }
         const float o = 1.f / (1.f + expf(-__ldg(sg.g.logits + li)));
+        // the mean's projection in FP64 for blending: FP32 loses ~1e-4 px to the cancellation in
+        // R m + t at world scale, which matters for small, nearly opaque splats
+        double pd[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          pd[r] = fma((double)cm.R[3 * r], (double)P.m[0],
+                      fma((double)cm.R[3 * r + 1], (double)P.m[1], fma((double)cm.R[3 * r + 2], (double)P.m[2], (double)cm.t[r])));
+        const double ud = (double)cm.fx * (pd[0] / pd[2]) + (double)cm.cx;
+        const double vd = (double)cm.fy * (pd[1] / pd[2]) + (double)cm.cy;
         Splat s;
-        s.u = P.u; s.v = P.v;
+        s.u = (float)ud;
+        s.v = (float)vd;
+        s.uvlo = (uint32_t)__half_as_ushort(__float2half_rn((float)(ud - (double)s.u))) |
+                 ((uint32_t)__half_as_ushort(__float2half_rn((float)(vd - (double)s.v))) << 16);
         s.ca = -0.5f * kLog2e * P.ca;
         s.cb = -kLog2e * P.cb;
         s.cc = -0.5f * kLog2e * P.cc;
-        s.opacity = o;
+        s.lo = log2f(o);
         s.r = rgb[0]; s.g = rgb[1]; s.b = rgb[2];
         s.rank = 0;
-        // alpha >= alpha_min  <=>  power2 >= tg;  that region is the ellipse d^T Sigma2^-1 d <= k2
-        // with k2 = 2 ln(opacity / alpha_min), whose bounding box has half-extents k sqrt(A), k sqrt(C)
-        s.tg = log2f(op.alpha_min / o);
+        // alpha >= alpha_min  <=>  power2 >= tg = log2(alpha_min) - lo;  that region is the
+        // ellipse d^T Sigma2^-1 d <= k2, k2 = 2 ln(opacity / alpha_min), whose bounding box has
+        // half-extents k sqrt(A), k sqrt(C)
+        const float tg = log2f(op.alpha_min) - s.lo;
         float hx = -65504.f, hy = -65504.f;
-        if (s.tg <= 0.f) {
-          const float k2 = -2.0f * 0.69314718f * s.tg;
+        if (tg <= 0.f) {
+          const float k2 = -2.0f * 0.69314718f * tg;
           hx = sqrtf(k2 * P.A) * 1.001f + 0.01f;
           hy = sqrtf(k2 * P.C) * 1.001f + 0.01f;
         }

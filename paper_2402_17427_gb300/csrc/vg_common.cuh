@@ -12,18 +12,22 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kMaxChunk = 256;
 
 // One projected 2D Gaussian as the blend kernels consume it (48 bytes, 16-byte aligned so a
-// run of records can be moved by one bulk copy).  The conic is pre-scaled to log2 units:
-//   power2(dx, dy) = ca dx^2 + cb dx dy + cc dy^2 = log2(e) * (-(a dx^2 + c dy^2)/2 - b dx dy)
-// with (a, b, c) the inverse 2D covariance and dx = px - u, dy = py - v, so G = 2^power2.
-// tg = log2(alpha_min / opacity): a pixel is skipped when power2 < tg (alpha below alpha_min)
-// or power2 > 0.  hx, hy (binary16, rounded up and inflated) bound the region power2 >= tg,
-// so a warp whose pixels all lie outside [u -+ hx] x [v -+ hy] can skip the splat unevaluated.
+// run of records can be moved by one bulk copy).
+//  - (u + ulo, v + vlo): the projected mean.  (u, v) is the FP32 value nearest to the mean's
+//    projection computed in FP64, and (ulo, vlo) (binary16) the remainder, so pixel offsets
+//    dx = (px - u) - ulo are accurate to ~1e-7 px even 2000 px from the origin.
+//  - The conic is pre-scaled to log2 units:
+//      power2(dx, dy) = ca dx^2 + cb dx dy + cc dy^2 = log2(e) (-(a dx^2 + c dy^2)/2 - b dx dy)
+//    with (a, b, c) the inverse 2D covariance, so alpha = 2^(power2 + lo), lo = log2(opacity).
+//  - A pixel is skipped when power2 > 0 or power2 + lo < log2(alpha_min).  hx, hy (binary16,
+//    rounded up and inflated) bound the region where alpha >= alpha_min, so a warp whose pixels
+//    all lie outside [u -+ hx] x [v -+ hy] can skip the splat unevaluated.
 struct __align__(16) Splat {
   float u, v, ca, cb;
-  float cc, opacity, r, g;
+  float cc, lo, r, g;
   float b;
   uint32_t rank;    // position of the Gaussian in the depth order (index of its 2D gradient slot)
-  float tg;
+  uint32_t uvlo;    // half2 (ulo, vlo)
   uint32_t hxy;     // half2 (hx, hy)
 };
 static_assert(sizeof(Splat) == 48, "Splat must stay 48 bytes");

@@ -23,7 +23,7 @@ from .scenes import Camera
 @dataclasses.dataclass
 class RasterSettings:
     tile_size: int = 16
-    chunk: int = 256
+    chunk: int = 128
     bg: tuple = (0.0, 0.0, 0.0)
     dilation: float = 0.3
     alpha_max: float = 0.99

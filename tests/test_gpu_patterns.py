@@ -1,0 +1,170 @@
+"""GPU tests of batched multi-cell rendering and of the multi-view server, through the C ABI.
+
+Batched cells must render exactly what each cell renders alone (same kernels, same per-tile
+lists) and match the oracle per cell; every view served must be the same alone and in a batch
+with other views, and the frustum cull must not change any image (checked against the oracle
+rendering all cells).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2402_17427_gb300 import batch as BT
+from paper_2402_17427_gb300 import rasterize as R
+from paper_2402_17427_gb300 import scenes, serving
+
+from _gpu import group_errors, oracle_opts, reachable_subset, run_backward, run_forward
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2402_17427_gb300 import _build
+    _build.build()
+    oracle.build()
+    assert torch.cuda.is_available()
+
+
+def _tiny_cells():
+    out = []
+    for k, (n, W, H) in enumerate([(150, 48, 40), (90, 33, 35), (220, 64, 32)]):
+        g, cam, _ = scenes.tiny_scene(n=n, width=W, height=H, degree=2, seed=20 + k)
+        out.append((g, cam))
+    return out
+
+
+def test_batch_equals_single_views_mixed_tile_sizes():
+    cells = _tiny_cells()
+    tiles = [8, 16, 32]
+    settings = [R.RasterSettings(tile_size=t) for t in tiles]
+    br = BT.BatchRasterizer(settings)
+    params = [R.to_device(g) for g, _ in cells]
+    outs = br.forward(params, 2, [c for _, c in cells])
+    rng = np.random.default_rng(0)
+    dLs = [torch.from_numpy(rng.standard_normal((3, c.height, c.width)).astype(np.float32)).cuda() for _, c in cells]
+    grads = br.backward(params, 2, [c for _, c in cells], outs, dLs)
+    torch.cuda.synchronize()
+    for k, ((g, cam), s) in enumerate(zip(cells, settings)):
+        r, p1, single = run_forward(g, cam, s)
+        assert np.array_equal(outs[k][0].cpu().numpy(), single["image"])
+        assert np.array_equal(outs[k][1].cpu().numpy(), single["T"])
+        assert np.array_equal(outs[k][2].cpu().numpy().astype(np.int64), single["last"])
+        gs = run_backward(r, p1, g, cam, single, dLs[k].cpu().numpy())
+        for name, a in zip(["means", "log_scales", "quats", "logits", "sh"], grads[k]):
+            b = gs[name]
+            a = a.cpu().numpy()
+            assert np.abs(a - b).max() <= 1e-5 * (np.abs(b).max() + 1e-12), name
+        orc = oracle.render(g, cam, oracle_opts(s))
+        ok = ~orc.amb.astype(bool)
+        assert np.abs(outs[k][0].cpu().numpy() - orc.image)[:, ok].max() <= 1e-4
+
+
+@pytest.mark.slow
+def test_aerial_cells_batched_sampled_parity():
+    """Eight uneven cells (0.3M..3.0M Gaussians, 1152x864 nadir views) in one batched call."""
+    cells = scenes.aerial_cells(step=3)
+    br = BT.BatchRasterizer()
+    params = [R.to_device(c.gaussians) for c in cells]
+    cams = [c.camera for c in cells]
+    outs = br.forward(params, 3, cams)
+    rng = np.random.default_rng(1)
+    dLs, masks, picks = [], [], []
+    for c in cells:
+        cam = c.camera
+        tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+        tiles = sorted(set(rng.choice(tx * ty, 3, replace=False).tolist()) | {(ty // 2) * tx + tx // 2})
+        m = np.zeros(tx * ty, np.uint8)
+        m[tiles] = 1
+        pm = np.repeat(np.repeat(m.reshape(ty, tx).astype(bool), 16, 0), 16, 1)[:cam.height, :cam.width]
+        w = rng.standard_normal((3, cam.height, cam.width)).astype(np.float32)
+        w[:, ~pm] = 0
+        dLs.append(w)
+        masks.append(m)
+        picks.append((tiles, pm))
+    grads = br.backward(params, 3, cams, outs, [torch.from_numpy(d).cuda() for d in dLs])
+    torch.cuda.synchronize()
+    for k, c in enumerate(cells):
+        g, cam = c.gaussians, c.camera
+        tiles, pm = picks[k]
+        sub = reachable_subset(g, cam, tiles, 16)
+        orc = oracle.render(g.subset(sub), cam, oracle.Options(), tile_mask=masks[k])
+        amb = orc.amb.astype(bool)
+        img = outs[k][0].cpu().numpy()
+        assert np.abs(img - orc.image)[:, pm & ~amb].max() <= 1e-4
+        w = dLs[k].copy()
+        w[:, amb] = 0
+        if amb.any():   # ambiguous pixels were weighted on the GPU: redo that cell's backward alone
+            r, p1, single = run_forward(g, cam)
+            gk = run_backward(r, p1, g, cam, single, w)
+        else:
+            gk = {n: t.cpu().numpy().astype(np.float64) for n, t in
+                  zip(["means", "log_scales", "quats", "logits", "sh"], grads[k])}
+        ref = orc.backward(w.astype(np.float64))
+        keep = ~(orc.rec["grad_amb"] | orc.rec["rect_amb"])
+        errs = group_errors({n: v[sub] for n, v in gk.items()}, ref, keep)
+        for name, (rel, _e, norm) in errs.items():
+            if norm > 0:
+                assert rel <= 2e-3, (k, name, errs)
+
+
+def _small_city():
+    return scenes.merged_city(seed=4100, total_scale=0.02)
+
+
+def _views(n, seed, sizes=((640, 360), (1280, 720), (800, 600))):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        W, H = sizes[i % len(sizes)]
+        yaw = rng.uniform(0, 2 * np.pi)
+        pitch = np.radians(rng.uniform(-80, -35))
+        eye = (rng.uniform(200, 800), rng.uniform(40, 120), rng.uniform(200, 800))
+        out.append(scenes.camera_from_forward(eye, scenes.yaw_pitch_forward(yaw, pitch), W, H))
+    return out
+
+
+def test_views_same_alone_and_in_the_mix():
+    srv = serving.SceneServer(_small_city())
+    cams = _views(5, seed=3)
+    mix, _, kept = srv.render(cams)
+    assert max(kept) <= 16 and min(kept) >= 0
+    for i, cam in enumerate(cams):
+        alone, _, _ = srv.render([cam])
+        for a, b in zip(alone[0], mix[i]):
+            assert torch.equal(a, b), i
+
+
+def test_view_culling_matches_oracle_over_all_cells():
+    cells = _small_city()
+    srv = serving.SceneServer(cells)
+    cam = _views(1, seed=7, sizes=((1280, 720),))[0]
+    outs, counters, kept = srv.render([cam])
+    assert kept[0] < 16      # some cells are culled for this view
+    merged = scenes.Gaussians.concat([c.gaussians for c in cells])
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    rng = np.random.default_rng(2)
+    tiles = sorted(rng.choice(tx * ty, 12, replace=False).tolist())
+    sub = reachable_subset(merged, cam, tiles, 16)
+    m = np.zeros(tx * ty, np.uint8)
+    m[tiles] = 1
+    orc = oracle.render(merged.subset(sub), cam, oracle.Options(), tile_mask=m)
+    pm = np.repeat(np.repeat(m.reshape(ty, tx).astype(bool), 16, 0), 16, 1)[:cam.height, :cam.width]
+    img = outs[0][0].cpu().numpy()
+    ok = pm & ~orc.amb.astype(bool)
+    assert np.abs(img - orc.image)[:, ok].max() <= 1e-4
+
+
+def test_serve_loop_short_stream():
+    srv = serving.SceneServer(_small_city(), slots=3, max_batch=4)
+    reqs = scenes.request_stream(seed=11, rate_hz=60.0, duration_s=1.5, bounds=(100, 900, 100, 900))
+    for r in reqs:   # keep the test light: shrink 4K requests to 1080p
+        if r.camera.width > 1920:
+            c = r.camera
+            r.camera = scenes.camera_from_forward(c.cam_pos, np.asarray(c.R)[2], 1920, 1080)
+    stats, outs = srv.serve(reqs, keep_outputs=True)
+    assert stats.requests == len(reqs) and stats.p99_ms >= stats.p50_ms > 0
+    for r in reqs[:: max(1, len(reqs) // 5)]:
+        alone, _, _ = srv.render([r.camera])
+        assert torch.equal(alone[0][0], outs[r.rid][0])
