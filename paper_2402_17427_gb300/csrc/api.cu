@@ -311,6 +311,8 @@ vg_status run_backward(Call& c, const vg_raster_opts* opts0, void* workspace, si
   stage_event(ev, VG_STAGE_PROJECT_BACKWARD, true, s);
   e = launch_preprocess_backward(tab, c.total_n, c.degree, reinterpret_cast<const Splat*>(ws + L.splats),
                                  reinterpret_cast<const uint32_t*>(ws + L.touched),
+                                 reinterpret_cast<const uint32_t*>(ws + L.vis_ids),
+                                 reinterpret_cast<const WsHeader*>(ws + L.header),
                                  reinterpret_cast<const float*>(ws + L.g2d),
                                  (opts0->flags & VG_FLAG_ACCUMULATE_GRADS) != 0, s);
   stage_event(ev, VG_STAGE_PROJECT_BACKWARD, false, s);

@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(256) compact_scan(unsigned* __restrict__ block
 __global__ void __launch_bounds__(256) compact_scatter(const uint32_t* __restrict__ dkey, unsigned n,
                                                        const unsigned* __restrict__ blocksums,
                                                        const WsHeader* __restrict__ hdr,
-                                                       uint32_t* __restrict__ vkeys, uint32_t* __restrict__ vvals) {
+                                                       uint32_t* __restrict__ vkeys, uint32_t* __restrict__ vvals,
+                                                       uint32_t* __restrict__ vis_ids) {
   __shared__ unsigned sm[8];
   unsigned begin, end;
   segment(n, begin, end);
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(256) compact_scatter(const uint32_t* __restric
     if (f) {
       vkeys[run + ex] = k - lo;
       vvals[run + ex] = i;
+      vis_ids[run + ex] = i;     // kept in index order for the adjoint of the projection
     }
     run += tot;
   }
@@ -439,6 +441,7 @@ Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
   L.rects = take(N * 8);
   L.touched = take(N * 4);
   L.dkey = take(N * 4);
+  L.vis_ids = take(N * 4);
   L.vkeys[0] = take(N * 4); L.vkeys[1] = take(N * 4);
   L.vvals[0] = take(N * 4); L.vvals[1] = take(N * 4);
   L.pkeys[0] = take(P * 4); L.pkeys[1] = take(P * 4);
@@ -471,7 +474,7 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   // 1. compaction + depth sort
   compact_count<<<B, 256, 0, s>>>(U(L.dkey), (unsigned)n, bsum);
   compact_scan<<<1, 256, 0, s>>>(bsum, B, hdr, tile_bits);
-  compact_scatter<<<B, 256, 0, s>>>(U(L.dkey), (unsigned)n, bsum, hdr, U(L.vkeys[0]), U(L.vvals[0]));
+  compact_scatter<<<B, 256, 0, s>>>(U(L.dkey), (unsigned)n, bsum, hdr, U(L.vkeys[0]), U(L.vvals[0]), U(L.vis_ids));
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = pass * kRadixBits;
     const int src = pass & 1, dst = src ^ 1;

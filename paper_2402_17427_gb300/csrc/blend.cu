@@ -212,12 +212,13 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
         const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
         float e0, e1;
         splat_col(f0.z, f0.w, __fsub_rn(__fsub_rn(pxc, f0.x), half_lo(f2.z)), e0, e1);
-        const float vlo = half_hi(f2.z);
+        // the thread's pixels are consecutive rows: dy of row p is dy0 + p
+        const float dy0 = __fsub_rn(__fsub_rn(py[0], f0.y), half_hi(f2.z));
 #pragma unroll
         for (int p = 0; p < S::kPPT; ++p) {
           if (done[p]) continue;
           if (COUNT) ++ev;
-          const float p2 = splat_power2(f1.x, e0, e1, __fsub_rn(__fsub_rn(py[p], f0.y), vlo));
+          const float p2 = splat_power2(f1.x, e0, e1, __fadd_rn(dy0, (float)p));
           const float q = __fadd_rn(p2, f1.y);
           if (p2 > 0.f || q < lamin) continue;
           const float a = fminf(amax, ex2_approx(q));
@@ -377,7 +378,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
         float e0, e1;
         const float dx = __fsub_rn(__fsub_rn(pxc, f0.x), half_lo(f2.z));
         splat_col(f0.z, f0.w, dx, e0, e1);
-        const float vlo = half_hi(f2.z);
+        const float dy0 = __fsub_rn(__fsub_rn(py[0], f0.y), half_hi(f2.z));
         // per pixel only the moments of dL/dpower over the column are accumulated:
         // S0 = sum dpow, S1 = sum dpow dy, S2 = sum dpow dy^2 (the thread's pixels share dx)
         float v[10];
@@ -388,7 +389,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
 #pragma unroll
         for (int p = 0; p < S::kPPT; ++p) {
           if (pos >= lastp[p]) continue;
-          const float dy = __fsub_rn(__fsub_rn(py[p], f0.y), vlo);
+          const float dy = __fadd_rn(dy0, (float)p);
           const float p2 = splat_power2(f1.x, e0, e1, dy);
           const float q = __fadd_rn(p2, f1.y);
           if (p2 > 0.f || q < lamin) continue;

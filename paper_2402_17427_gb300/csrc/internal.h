@@ -153,7 +153,7 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 // Offsets (bytes) of the regions of one render workspace (any number of views / segments).
 struct Layout {
-  size_t header, tables, splats, rects, touched, dkey, vkeys[2], vvals[2], pkeys[2], pvals[2], sorted,
+  size_t header, tables, splats, rects, touched, dkey, vis_ids, vkeys[2], vvals[2], pkeys[2], pvals[2], sorted,
       ranges, order, buckets, hist, blocksums, slices, g2d, total;
 };
 Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t pair_capacity);
@@ -180,7 +180,8 @@ struct HostPlan {
 cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Splat* splats, uint2* rects,
                               uint32_t* touched, uint32_t* dkey, WsHeader* hdr, cudaStream_t s);
 cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int degree, const Splat* splats,
-                                       const uint32_t* touched, const float* g2d, bool accumulate, cudaStream_t s);
+                                       const uint32_t* touched, const uint32_t* vis_ids, const WsHeader* hdr,
+                                       const float* g2d, bool accumulate, cudaStream_t s);
 
 // Depth order of the visible Gaussians, pair generation, tile sort, ranges, the tile-ordered copy
 // of the splats and the largest-first order of the tiles.

@@ -22,10 +22,11 @@ struct Win {
   float w[11];
 };
 
-__device__ __forceinline__ double block_sum_double(double v, double* sm) {
+// Block sum: FP32 inside each warp (FP64 is slow on this part), FP64 across the warps.
+__device__ __forceinline__ double block_sum(float v, double* sm) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = (double)v;
   __syncthreads();
   double t = 0;
   if (threadIdx.x == 0)
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(256) ssim_forward_kernel(const float* __restri
   }
   __syncthreads();
   const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-  double ssum = 0.0, l1sum = 0.0;
+  float ssum = 0.f, l1sum = 0.f;     // at most 4 pixels per thread; the block sum is in FP64
   for (int i = threadIdx.x; i < LT * LT; i += blockDim.x) {
     const int r = i / LT, q = i % LT;
     const int gx = ox + q, gy = oy + r;
@@ -87,10 +88,11 @@ __global__ void __launch_bounds__(256) ssim_forward_kernel(const float* __restri
     const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
     const float N1 = 2.f * mx * my + C1, N2 = 2.f * sxy + C2;
     const float D1 = mx * mx + my * my + C1, D2 = sxx + syy + C2;
-    const float iD = 1.f / (D1 * D2);
+    const float iD1 = __frcp_rn(D1), iD2 = __frcp_rn(D2);
+    const float iD = iD1 * iD2;
     const float S = N1 * N2 * iD;
-    const float dS_dmx = (2.f * my * N2 - 2.f * my * N1) * iD - S * (2.f * mx / D1 - 2.f * mx / D2);
-    const float dS_dexx = -S / D2;
+    const float dS_dmx = 2.f * my * (N2 - N1) * iD - 2.f * mx * S * (iD1 - iD2);
+    const float dS_dexx = -S * iD2;
     const float dS_dexy = 2.f * N1 * iD;
     const size_t pix = (size_t)gy * W + gx;
     maps[(0 * 3 + c) * plane + pix] = dLdS * dS_dmx;
@@ -99,8 +101,8 @@ __global__ void __launch_bounds__(256) ssim_forward_kernel(const float* __restri
     ssum += S;
     l1sum += fabsf(sx[r + HALO][q + HALO] - sy[r + HALO][q + HALO]);
   }
-  const double ts = block_sum_double(ssum, red);
-  const double tl = block_sum_double(l1sum, red);
+  const double ts = block_sum(ssum, red);
+  const double tl = block_sum(l1sum, red);
   if (threadIdx.x == 0) {
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     partials[2 * b] = ts;
@@ -108,17 +110,27 @@ __global__ void __launch_bounds__(256) ssim_forward_kernel(const float* __restri
   }
 }
 
-__global__ void __launch_bounds__(256) loss_finalize(const double* __restrict__ partials, int nb, double inv, float lambda,
-                                                     float* __restrict__ out_loss) {
-  __shared__ double red[8];
+__global__ void __launch_bounds__(1024) loss_finalize(const double* __restrict__ partials, int nb, double inv,
+                                                      float lambda, float* __restrict__ out_loss) {
+  __shared__ double sm[2][32];
   double s = 0, l = 0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    s += partials[2 * b];
-    l += partials[2 * b + 1];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {   // independent loads, fixed order
+    const double2 p = reinterpret_cast<const double2*>(partials)[b];
+    s += p.x;
+    l += p.y;
   }
-  const double ts = block_sum_double(s, red);
-  const double tl = block_sum_double(l, red);
-  if (threadIdx.x == 0) *out_loss = (float)((1.0 - lambda) * tl * inv + lambda * (1.0 - ts * inv));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    l += __shfl_xor_sync(0xffffffffu, l, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sm[0][threadIdx.x >> 5] = s; sm[1][threadIdx.x >> 5] = l; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ts = 0, tl = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { ts += sm[0][k]; tl += sm[1][k]; }
+    *out_loss = (float)((1.0 - lambda) * tl * inv + lambda * (1.0 - ts * inv));
+  }
 }
 
 __global__ void __launch_bounds__(256) ssim_backward_kernel(const float* __restrict__ x, const float* __restrict__ y,
@@ -207,7 +219,7 @@ extern "C" vg_status vg_loss_l1_dssim(const float* img, const float* target, int
   const Win win = make_window();
   note_launches(out_grad ? 3 : 2);
   ssim_forward_kernel<<<grid, 256, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
-  loss_finalize<<<1, 256, 0, s>>>(partials, nb, inv, lambda, out_loss);
+  loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
   if (out_grad)
     ssim_backward_kernel<<<grid, 256, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
   return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;

@@ -82,6 +82,49 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float (
   }
 }
 
+// ---- double-float arithmetic (pairs hi + lo of FP32 numbers, error-free transformations) ----
+// Used for the projected mean: R m + t cancels large terms at city scale, and FP32 alone loses
+// ~1e-4 px there; the pair keeps ~1e-14 relative, at FP32 speed (FP64 is slow on this part).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// row . m + t as a double-float
+__device__ __forceinline__ void df_dot3(const float* row, float t, const float* m, float& hi, float& lo) {
+  float p0, e0, p1, e1, p2, e2, s, f0, f1, f2;
+  two_prod(row[0], m[0], p0, e0);
+  two_prod(row[1], m[1], p1, e1);
+  two_prod(row[2], m[2], p2, e2);
+  two_sum(t, p0, s, f0);
+  two_sum(s, p1, s, f1);
+  two_sum(s, p2, s, f2);
+  const float l = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), e2), __fadd_rn(__fadd_rn(f0, f1), f2));
+  fast_two_sum(s, l, hi, lo);
+}
+// f * (xh + xl) / (zh + zl) + c as a double-float
+__device__ __forceinline__ void df_project(float xh, float xl, float zh, float zl, float f, float c, float& hi,
+                                           float& lo) {
+  const float q = __fdiv_rn(xh, zh);
+  float ph, pl;
+  two_prod(q, zh, ph, pl);
+  // x - q z, where xh - ph is exact (the two are within a factor of two)
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(xh, ph), pl), __fsub_rn(xl, __fmul_rn(q, zl)));
+  const float ql = __fdiv_rn(r, zh);
+  float ah, al, sh, se;
+  two_prod(f, q, ah, al);
+  two_sum(ah, c, sh, se);
+  fast_two_sum(sh, __fadd_rn(__fadd_rn(se, al), __fmul_rn(f, ql)), hi, lo);
+}
+
 // Loads the K x 3 SH block of Gaussian i into registers (vector loads when 16-byte aligned).
 template <int DEG>
 __device__ __forceinline__ void load_sh(const float* __restrict__ sh, int i, float* c) {
@@ -233,20 +276,18 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __rest
           rgb[ch] = fmaxf(0.f, acc);
         }
         const float o = 1.f / (1.f + expf(-__ldg(sg.g.logits + li)));
-        // the mean's projection in FP64 for blending: FP32 loses ~1e-4 px to the cancellation in
-        // R m + t at world scale, which matters for small, nearly opaque splats
-        double pd[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-          pd[r] = fma((double)cm.R[3 * r], (double)P.m[0],
-                      fma((double)cm.R[3 * r + 1], (double)P.m[1], fma((double)cm.R[3 * r + 2], (double)P.m[2], (double)cm.t[r])));
-        const double ud = (double)cm.fx * (pd[0] / pd[2]) + (double)cm.cx;
-        const double vd = (double)cm.fy * (pd[1] / pd[2]) + (double)cm.cy;
+        // the mean's projection for blending, as a double-float (see df_dot3)
+        float xh, xl, yh, yl, zh, zl;
+        df_dot3(cm.R, cm.t[0], P.m, xh, xl);
+        df_dot3(cm.R + 3, cm.t[1], P.m, yh, yl);
+        df_dot3(cm.R + 6, cm.t[2], P.m, zh, zl);
+        float uh, ul, vh, vl;
+        df_project(xh, xl, zh, zl, cm.fx, cm.cx, uh, ul);
+        df_project(yh, yl, zh, zl, cm.fy, cm.cy, vh, vl);
         Splat s;
-        s.u = (float)ud;
-        s.v = (float)vd;
-        s.uvlo = (uint32_t)__half_as_ushort(__float2half_rn((float)(ud - (double)s.u))) |
-                 ((uint32_t)__half_as_ushort(__float2half_rn((float)(vd - (double)s.v))) << 16);
+        s.u = uh;
+        s.v = vh;
+        s.uvlo = (uint32_t)__half_as_ushort(__float2half_rn(ul)) | ((uint32_t)__half_as_ushort(__float2half_rn(vl)) << 16);
         s.ca = -0.5f * kLog2e * P.ca;
         s.cb = -kLog2e * P.cb;
         s.cc = -0.5f * kLog2e * P.cc;
@@ -287,144 +328,63 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __rest
   }
 }
 
+// Zero gradients of the Gaussians that touch no tile (skipped when accumulating).  A warp owns
+// 32 consecutive Gaussians and writes their SH gradient rows cooperatively, so consecutive
+// lanes store consecutive 16-byte words.
 template <int DEG>
-__global__ void __launch_bounds__(128) preprocess_backward_kernel(
-    const DevTables* __restrict__ tab, int total_n, const Splat* __restrict__ splats,
-    const uint32_t* __restrict__ touched, const float* __restrict__ g2d, int accumulate) {
+__global__ void __launch_bounds__(256) zero_culled_grads(const DevTables* __restrict__ tab, int total_n,
+                                                         const uint32_t* __restrict__ touched) {
+  constexpr int F = 3 * (DEG + 1) * (DEG + 1);
+  const int lane = threadIdx.x & 31;
+  const int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31;
+  const int i = base + lane;
+  bool zero = false;
+  float* gsh = nullptr;
+  if (i < total_n && touched[i] == 0) {
+    const KSeg& sg = tseg(tab, find_seg(tab, i));
+    if (sg.gm) {
+      zero = true;
+      const size_t l = (size_t)(i - sg.offset);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { sg.gm[3 * l + k] = 0.f; sg.gs[3 * l + k] = 0.f; }
+      *reinterpret_cast<float4*>(sg.gq + 4 * l) = make_float4(0.f, 0.f, 0.f, 0.f);
+      sg.gl[l] = 0.f;
+      gsh = sg.gsh + l * F;
+    }
+  }
+  const unsigned any = __ballot_sync(0xffffffffu, zero);
+  if (!any) return;
+  const unsigned long long me = reinterpret_cast<unsigned long long>(gsh);
+  if constexpr (F % 4 == 0) {
+    constexpr int Q = F / 4;   // float4 words per Gaussian
+    for (int f = lane; f < 32 * Q; f += 32) {
+      const int src = f / Q;
+      const unsigned long long p = __shfl_sync(0xffffffffu, me, src);
+      if ((any >> src) & 1u) reinterpret_cast<float4*>(p)[f % Q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  } else {
+    for (int f = lane; f < 32 * F; f += 32) {
+      const int src = f / F;
+      const unsigned long long p = __shfl_sync(0xffffffffu, me, src);
+      if ((any >> src) & 1u) reinterpret_cast<float*>(p)[f % F] = 0.f;
+    }
+  }
+}
+
+// Adjoint of the projection for the visible Gaussians, taken from the compact list of visible
+// ids in index order (every lane of a warp has work, neighbouring lanes read nearby rows).
+template <int DEG>
+__global__ void __launch_bounds__(128, 4) preprocess_backward_kernel(
+    const DevTables* __restrict__ tab, const uint32_t* __restrict__ vis_ids, const WsHeader* __restrict__ hdr,
+    const Splat* __restrict__ splats, const float* __restrict__ g2d, int accumulate) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= total_n) return;
+  constexpr int F = 3 * K;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int)hdr->visible) return;
+  const int i = (int)vis_ids[t];
   const KSeg& sg = tseg(tab, find_seg(tab, i));
   if (!sg.gm) return;       // this segment asked for no gradients
-  const KGauss g = sg.g;
-  const KCam cm = tview(tab, sg.view).cam;
-  const KOpts op = tview(tab, sg.view).op;
-  const int li = i - sg.offset;
-  float o_m[3] = {0, 0, 0}, o_s[3] = {0, 0, 0}, o_q[4] = {0, 0, 0, 0}, o_l = 0.f, o_sh[3 * K];
-#pragma unroll
-  for (int k = 0; k < 3 * K; ++k) o_sh[k] = 0.f;
-  if (touched[i] > 0) {
-    const uint32_t rank = splats[i].rank;
-    float d2[9];
-#pragma unroll
-    for (int f = 0; f < 9; ++f) d2[f] = g2d[(size_t)rank * 9 + f];
-    Proj P;
-    project(g, cm, op, li, P);
-    // opacity
-    const float o = 1.f / (1.f + expf(-__ldg(g.logits + li)));
-    o_l = d2[5] * o * (1.f - o);
-    // colour: rgb = max(0, sum_k c_k Y_k(d) + 0.5), d = (m - cam_pos) / |m - cam_pos|
-    float d0 = P.m[0] - cm.cam_pos[0], d1 = P.m[1] - cm.cam_pos[1], dz = P.m[2] - cm.cam_pos[2];
-    const float il = rsqrtf(d0 * d0 + d1 * d1 + dz * dz);
-    d0 *= il; d1 *= il; dz *= il;
-    float Y[16], GY[16][3], c[3 * K];
-    sh_basis<DEG>(d0, d1, dz, Y);
-    sh_basis_grad<DEG>(d0, d1, dz, GY);
-    load_sh<DEG>(g.sh, li, c);
-    float dd[3] = {0, 0, 0};
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float pre = 0.5f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) pre = fmaf(c[3 * k + ch], Y[k], pre);
-      const float dpre = pre > 0.f ? d2[6 + ch] : 0.f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        o_sh[3 * k + ch] = dpre * Y[k];
-        const float w = dpre * c[3 * k + ch];
-        dd[0] += w * GY[k][0]; dd[1] += w * GY[k][1]; dd[2] += w * GY[k][2];
-      }
-    }
-    const float dot = dd[0] * d0 + dd[1] * d1 + dd[2] * dz;
-    o_m[0] = (dd[0] - d0 * dot) * il;
-    o_m[1] = (dd[1] - d1 * dot) * il;
-    o_m[2] = (dd[2] - dz * dot) * il;
-    // conic -> 2D covariance: dS2 = -Q G Q, Q = [[a,b],[b,c]], G = [[da, db/2],[db/2, dc]]
-    const float qa = P.ca, qb = P.cb, qc = P.cc;
-    const float g0 = d2[2], g1 = 0.5f * d2[3], g2 = d2[4];
-    const float m00 = qa * g0 + qb * g1, m01 = qa * g1 + qb * g2;
-    const float m10 = qb * g0 + qc * g1, m11 = qb * g1 + qc * g2;
-    const float s00 = -(m00 * qa + m01 * qb);
-    const float s01 = -(m00 * qb + m01 * qc);
-    const float s11 = -(m10 * qb + m11 * qc);
-    // Sigma2 = T Sigma T^T: dSigma = T^T dS2 T, dT = 2 dS2 T Sigma
-    const float* T = P.T;
-    float U[2][3];   // dS2 T
-#pragma unroll
-    for (int c3 = 0; c3 < 3; ++c3) {
-      U[0][c3] = s00 * T[c3] + s01 * T[3 + c3];
-      U[1][c3] = s01 * T[c3] + s11 * T[3 + c3];
-    }
-    float dSig[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) dSig[a][b] = T[a] * U[0][b] + T[3 + a] * U[1][b];
-    const float* S = P.Sig;
-    const float Sf[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
-    float dT[2][3];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) dT[a][j] = 2.f * (U[a][0] * Sf[0][j] + U[a][1] * Sf[1][j] + U[a][2] * Sf[2][j]);
-    // dJ = dT W^T; only J00, J02, J11, J12 depend on p
-    const float* W = cm.R;
-    const float dJ00 = dT[0][0] * W[0] + dT[0][1] * W[1] + dT[0][2] * W[2];
-    const float dJ02 = dT[0][0] * W[6] + dT[0][1] * W[7] + dT[0][2] * W[8];
-    const float dJ11 = dT[1][0] * W[3] + dT[1][1] * W[4] + dT[1][2] * W[5];
-    const float dJ12 = dT[1][0] * W[6] + dT[1][1] * W[7] + dT[1][2] * W[8];
-    const float z = P.p[2], iz = 1.f / z, iz2 = iz * iz;
-    float dp[3] = {0.f, 0.f, 0.f};
-    dp[2] += -(dJ00 * cm.fx + dJ11 * cm.fy) * iz2;
-    // J02 = -fx xzc / z with xzc = x / z unless clamped
-    if (P.clx) {
-      dp[2] += dJ02 * cm.fx * P.xzc * iz2;
-    } else {
-      dp[0] += -dJ02 * cm.fx * iz2;
-      dp[2] += dJ02 * 2.f * cm.fx * P.p[0] * iz2 * iz;
-    }
-    if (P.cly) {
-      dp[2] += dJ12 * cm.fy * P.yzc * iz2;
-    } else {
-      dp[1] += -dJ12 * cm.fy * iz2;
-      dp[2] += dJ12 * 2.f * cm.fy * P.p[1] * iz2 * iz;
-    }
-    // u = fx x/z + cx, v = fy y/z + cy
-    dp[0] += d2[0] * cm.fx * iz;
-    dp[1] += d2[1] * cm.fy * iz;
-    dp[2] += -(d2[0] * cm.fx * P.p[0] + d2[1] * cm.fy * P.p[1]) * iz2;
-#pragma unroll
-    for (int c3 = 0; c3 < 3; ++c3) o_m[c3] += W[c3] * dp[0] + W[3 + c3] * dp[1] + W[6 + c3] * dp[2];
-    // Sigma = M M^T, M = Rq diag(s): dM = 2 dSigma M
-    float M[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c3 = 0; c3 < 3; ++c3) M[3 * r + c3] = P.Rq[3 * r + c3] * P.s[c3];
-    float dR[9];
-#pragma unroll
-    for (int c3 = 0; c3 < 3; ++c3) {
-      float ds = 0.f;
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float dMrc = 2.f * (dSig[r][0] * M[c3] + dSig[r][1] * M[3 + c3] + dSig[r][2] * M[6 + c3]);
-        ds += dMrc * P.Rq[3 * r + c3];
-        dR[3 * r + c3] = dMrc * P.s[c3];
-      }
-      o_s[c3] = ds * P.s[c3];
-    }
-    // rotation matrix of the unit quaternion (w, x, y, z)
-    const float w = P.qn[0], x = P.qn[1], y = P.qn[2], zq = P.qn[3];
-    float dqn[4];
-    dqn[0] = 2.f * (-zq * dR[1] + y * dR[2] + zq * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    dqn[1] = 2.f * (y * dR[1] + zq * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + zq * dR[6] + w * dR[7] - 2.f * x * dR[8]);
-    dqn[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + zq * dR[5] - w * dR[6] + zq * dR[7] - 2.f * y * dR[8]);
-    dqn[3] = 2.f * (-2.f * zq * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * zq * dR[4] + y * dR[5] + x * dR[6] + y * dR[7]);
-    const float qd = P.qn[0] * dqn[0] + P.qn[1] * dqn[1] + P.qn[2] * dqn[2] + P.qn[3] * dqn[3];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o_q[k] = (dqn[k] - P.qn[k] * qd) * P.qinv;
-  }
-  // write (or accumulate) every output of Gaussian i; 16-byte rows go out as float4
+  const size_t l = (size_t)(i - sg.offset);
   auto put = [&](float* dst, float v) { if (accumulate) *dst += v; else *dst = v; };
   auto put4 = [&](float* dst, float a, float b, float c, float d) {
     float4* p = reinterpret_cast<float4*>(dst);
@@ -435,18 +395,154 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(
     }
     *p = v;
   };
-  const size_t l = (size_t)li;
+  float* gsh = sg.gsh + l * F;
+  const KGauss g = sg.g;
+  const KCam cm = tview(tab, sg.view).cam;
+  const KOpts op = tview(tab, sg.view).op;
+  const int li = (int)l;
+  const uint32_t rank = splats[i].rank;
+  float d2[9];
+#pragma unroll
+  for (int f = 0; f < 9; ++f) d2[f] = g2d[(size_t)rank * 9 + f];
+  Proj P;
+  project(g, cm, op, li, P);
+  float o_m[3], o_s[3], o_q[4];
+  // opacity
+  const float o = 1.f / (1.f + expf(-__ldg(g.logits + li)));
+  put(sg.gl + l, d2[5] * o * (1.f - o));
+  // colour: rgb = max(0, sum_k c_k Y_k(d) + 0.5), d = (m - cam_pos) / |m - cam_pos|
+  float d0 = P.m[0] - cm.cam_pos[0], d1 = P.m[1] - cm.cam_pos[1], dz = P.m[2] - cm.cam_pos[2];
+  const float il = rsqrtf(d0 * d0 + d1 * d1 + dz * dz);
+  d0 *= il; d1 *= il; dz *= il;
+  float Y[16];
+  sh_basis<DEG>(d0, d1, dz, Y);
+  const float* shp = g.sh + l * F;
+  // one pass over the coefficients: pre_ch = 0.5 + sum_k c_k,ch Y_k and, per channel,
+  // D_ch = sum_k c_k,ch grad Y_k (the direction gradient once the clamp mask is known)
+  float pre[3] = {0.5f, 0.5f, 0.5f};
+  float D[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  {
+    float G[16][3];
+    sh_basis_grad<DEG>(d0, d1, dz, G);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float c = __ldg(shp + 3 * k + ch);
+        pre[ch] = fmaf(c, Y[k], pre[ch]);
+        D[ch][0] = fmaf(c, G[k][0], D[ch][0]);
+        D[ch][1] = fmaf(c, G[k][1], D[ch][1]);
+        D[ch][2] = fmaf(c, G[k][2], D[ch][2]);
+      }
+  }
+  float dpre[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) dpre[ch] = pre[ch] > 0.f ? d2[6 + ch] : 0.f;
+  // d loss / d coefficient = dpre * Y, written as it is formed
+  if constexpr (F % 4 == 0) {
+#pragma unroll
+    for (int f = 0; f < F; f += 4)
+      put4(gsh + f, dpre[f % 3] * Y[f / 3], dpre[(f + 1) % 3] * Y[(f + 1) / 3], dpre[(f + 2) % 3] * Y[(f + 2) / 3],
+           dpre[(f + 3) % 3] * Y[(f + 3) / 3]);
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f) put(gsh + f, dpre[f % 3] * Y[f / 3]);
+  }
+  // d loss / d direction = sum_ch dpre_ch D_ch, projected on the tangent plane
+  float dd[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dd[c] = dpre[0] * D[0][c] + dpre[1] * D[1][c] + dpre[2] * D[2][c];
+  const float dot = dd[0] * d0 + dd[1] * d1 + dd[2] * dz;
+  o_m[0] = (dd[0] - d0 * dot) * il;
+  o_m[1] = (dd[1] - d1 * dot) * il;
+  o_m[2] = (dd[2] - dz * dot) * il;
+  // conic -> 2D covariance: dS2 = -Q G Q, Q = [[a,b],[b,c]], G = [[da, db/2],[db/2, dc]]
+  const float qa = P.ca, qb = P.cb, qc = P.cc;
+  const float g0 = d2[2], g1 = 0.5f * d2[3], g2 = d2[4];
+  const float m00 = qa * g0 + qb * g1, m01 = qa * g1 + qb * g2;
+  const float m10 = qb * g0 + qc * g1, m11 = qb * g1 + qc * g2;
+  const float s00 = -(m00 * qa + m01 * qb);
+  const float s01 = -(m00 * qb + m01 * qc);
+  const float s11 = -(m10 * qb + m11 * qc);
+  // Sigma2 = T Sigma T^T: dSigma = T^T dS2 T, dT = 2 dS2 T Sigma
+  const float* T = P.T;
+  float U[2][3];   // dS2 T
+#pragma unroll
+  for (int c3 = 0; c3 < 3; ++c3) {
+    U[0][c3] = s00 * T[c3] + s01 * T[3 + c3];
+    U[1][c3] = s01 * T[c3] + s11 * T[3 + c3];
+  }
+  float dSig[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) dSig[a][b] = T[a] * U[0][b] + T[3 + a] * U[1][b];
+  const float* S = P.Sig;
+  const float Sf[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
+  float dT[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dT[a][j] = 2.f * (U[a][0] * Sf[0][j] + U[a][1] * Sf[1][j] + U[a][2] * Sf[2][j]);
+  // dJ = dT W^T; only J00, J02, J11, J12 depend on p
+  const float* W = cm.R;
+  const float dJ00 = dT[0][0] * W[0] + dT[0][1] * W[1] + dT[0][2] * W[2];
+  const float dJ02 = dT[0][0] * W[6] + dT[0][1] * W[7] + dT[0][2] * W[8];
+  const float dJ11 = dT[1][0] * W[3] + dT[1][1] * W[4] + dT[1][2] * W[5];
+  const float dJ12 = dT[1][0] * W[6] + dT[1][1] * W[7] + dT[1][2] * W[8];
+  const float z = P.p[2], iz = 1.f / z, iz2 = iz * iz;
+  float dp[3] = {0.f, 0.f, 0.f};
+  dp[2] += -(dJ00 * cm.fx + dJ11 * cm.fy) * iz2;
+  // J02 = -fx xzc / z with xzc = x / z unless clamped
+  if (P.clx) {
+    dp[2] += dJ02 * cm.fx * P.xzc * iz2;
+  } else {
+    dp[0] += -dJ02 * cm.fx * iz2;
+    dp[2] += dJ02 * 2.f * cm.fx * P.p[0] * iz2 * iz;
+  }
+  if (P.cly) {
+    dp[2] += dJ12 * cm.fy * P.yzc * iz2;
+  } else {
+    dp[1] += -dJ12 * cm.fy * iz2;
+    dp[2] += dJ12 * 2.f * cm.fy * P.p[1] * iz2 * iz;
+  }
+  // u = fx x/z + cx, v = fy y/z + cy
+  dp[0] += d2[0] * cm.fx * iz;
+  dp[1] += d2[1] * cm.fy * iz;
+  dp[2] += -(d2[0] * cm.fx * P.p[0] + d2[1] * cm.fy * P.p[1]) * iz2;
+#pragma unroll
+  for (int c3 = 0; c3 < 3; ++c3) o_m[c3] += W[c3] * dp[0] + W[3 + c3] * dp[1] + W[6 + c3] * dp[2];
+  // Sigma = M M^T, M = Rq diag(s): dM = 2 dSigma M
+  float M[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) M[3 * r + c3] = P.Rq[3 * r + c3] * P.s[c3];
+  float dR[9];
+#pragma unroll
+  for (int c3 = 0; c3 < 3; ++c3) {
+    float ds = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float dMrc = 2.f * (dSig[r][0] * M[c3] + dSig[r][1] * M[3 + c3] + dSig[r][2] * M[6 + c3]);
+      ds += dMrc * P.Rq[3 * r + c3];
+      dR[3 * r + c3] = dMrc * P.s[c3];
+    }
+    o_s[c3] = ds * P.s[c3];
+  }
+  // rotation matrix of the unit quaternion (w, x, y, z)
+  const float w = P.qn[0], x = P.qn[1], y = P.qn[2], zq = P.qn[3];
+  float dqn[4];
+  dqn[0] = 2.f * (-zq * dR[1] + y * dR[2] + zq * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+  dqn[1] = 2.f * (y * dR[1] + zq * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + zq * dR[6] + w * dR[7] - 2.f * x * dR[8]);
+  dqn[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + zq * dR[5] - w * dR[6] + zq * dR[7] - 2.f * y * dR[8]);
+  dqn[3] = 2.f * (-2.f * zq * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * zq * dR[4] + y * dR[5] + x * dR[6] + y * dR[7]);
+  const float qd = P.qn[0] * dqn[0] + P.qn[1] * dqn[1] + P.qn[2] * dqn[2] + P.qn[3] * dqn[3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o_q[k] = (dqn[k] - P.qn[k] * qd) * P.qinv;
 #pragma unroll
   for (int k = 0; k < 3; ++k) { put(sg.gm + 3 * l + k, o_m[k]); put(sg.gs + 3 * l + k, o_s[k]); }
   put4(sg.gq + 4 * l, o_q[0], o_q[1], o_q[2], o_q[3]);
-  put(sg.gl + l, o_l);
-  if constexpr ((3 * K) % 4 == 0) {
-#pragma unroll
-    for (int k = 0; k < 3 * K; k += 4) put4(sg.gsh + l * 3 * K + k, o_sh[k], o_sh[k + 1], o_sh[k + 2], o_sh[k + 3]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 3 * K; ++k) put(sg.gsh + l * 3 * K + k, o_sh[k]);
-  }
 }
 
 }  // namespace
@@ -466,16 +562,29 @@ cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Spl
 }
 
 cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int degree, const Splat* splats,
-                                       const uint32_t* touched, const float* g2d, bool accumulate, cudaStream_t s) {
+                                       const uint32_t* touched, const uint32_t* vis_ids, const WsHeader* hdr,
+                                       const float* g2d, bool accumulate, cudaStream_t s) {
   if (total_n == 0) return cudaSuccess;
-  note_launches(1);
-  const int blocks = (total_n + 127) / 128;
   const int acc = accumulate ? 1 : 0;
+  const int zb = (total_n + 255) / 256, blocks = (total_n + 127) / 128;
+  note_launches(accumulate ? 1 : 2);
   switch (degree) {
-    case 0: preprocess_backward_kernel<0><<<blocks, 128, 0, s>>>(tab, total_n, splats, touched, g2d, acc); break;
-    case 1: preprocess_backward_kernel<1><<<blocks, 128, 0, s>>>(tab, total_n, splats, touched, g2d, acc); break;
-    case 2: preprocess_backward_kernel<2><<<blocks, 128, 0, s>>>(tab, total_n, splats, touched, g2d, acc); break;
-    default: preprocess_backward_kernel<3><<<blocks, 128, 0, s>>>(tab, total_n, splats, touched, g2d, acc); break;
+    case 0:
+      if (!accumulate) zero_culled_grads<0><<<zb, 256, 0, s>>>(tab, total_n, touched);
+      preprocess_backward_kernel<0><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc);
+      break;
+    case 1:
+      if (!accumulate) zero_culled_grads<1><<<zb, 256, 0, s>>>(tab, total_n, touched);
+      preprocess_backward_kernel<1><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc);
+      break;
+    case 2:
+      if (!accumulate) zero_culled_grads<2><<<zb, 256, 0, s>>>(tab, total_n, touched);
+      preprocess_backward_kernel<2><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc);
+      break;
+    default:
+      if (!accumulate) zero_culled_grads<3><<<zb, 256, 0, s>>>(tab, total_n, touched);
+      preprocess_backward_kernel<3><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc);
+      break;
   }
   return cudaGetLastError();
 }
