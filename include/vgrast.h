@@ -194,6 +194,24 @@ vg_status vg_loss_l1_dssim(const float* img, const float* target, int32_t width,
                            float lambda, void* workspace, size_t workspace_bytes,
                            float* out_loss, float* out_grad, vg_stream stream);
 
+/* Allocation-free variant of vg_loss_l1_dssim (the paper has no counterpart; this is a library
+ * convenience).  It computes exactly what vg_loss_l1_dssim computes, but keeps its scratch in one
+ * device array compiled into this library (about 37.8 MB on every GPU that loads it, held until
+ * the process exits) instead of a caller workspace, for callers that cannot allocate device
+ * memory between steps: hosts that plan all device memory up front and latency-critical loops
+ * where cudaMalloc could synchronise the device or fail near the memory limit.
+ *  - Images of up to VG_LOSS_NOALLOC_MAX_PIXELS pixels (width, height <= 16384); larger ones
+ *    return VG_ERR_CAPACITY without launching anything.
+ *  - The first call on a device looks the array's address up (cudaGetSymbolAddress) with that
+ *    device current; make that first call before capturing any stream.
+ *  - Every call uses the same array and leaves its contents behind; each call overwrites all it
+ *    reads, so nothing needs clearing, but calls that overlap on the GPU (concurrent streams)
+ *    race on the array and must be serialised by the caller.
+ *  - Never calls cudaMalloc, cudaFree or any allocating routine.                              */
+#define VG_LOSS_NOALLOC_MAX_PIXELS (1024 * 1024)
+vg_status vg_loss_l1_dssim_noalloc(const float* img, const float* target, int32_t width, int32_t height,
+                                   float lambda, float* out_loss, float* out_grad, vg_stream stream);
+
 /* ------------------------------------------------------------------------------------------
  * Batched cells (Sec. 4.1: cells are optimised independently, in parallel): n_cells
  * (Gaussian set, camera) pairs rendered by one launch per stage — one projection launch over

@@ -23,7 +23,8 @@ VG_FLAG_COUNT_BLENDS = 2
 EXPORTED = ("vg_default_opts", "vg_status_string", "vg_kernel_launches", "vg_workspace_bytes", "vg_rasterize_forward",
             "vg_rasterize_backward", "vg_read_render_state", "vg_loss_workspace_bytes", "vg_loss_l1_dssim",
             "vg_batch_workspace_bytes", "vg_render_batch", "vg_render_batch_backward",
-            "vg_views_workspace_bytes", "vg_render_views")
+            "vg_views_workspace_bytes", "vg_render_views", "vg_loss_l1_dssim_noalloc")
+VG_LOSS_NOALLOC_MAX_PIXELS = 1024 * 1024
 
 
 class vg_camera(ctypes.Structure):
@@ -112,6 +113,8 @@ def lib():
                                                ctypes.c_size_t, ctypes.c_int64, _PP, _PP, _PP, _PP, _PP, _PP,
                                                _PP, _PP, _P]
         L.vg_render_batch_backward.restype = ctypes.c_int
+    L.vg_loss_l1_dssim_noalloc.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P, _P, _P]
+    L.vg_loss_l1_dssim_noalloc.restype = ctypes.c_int
     L.vg_views_workspace_bytes.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32, _P,
                                            ctypes.POINTER(vg_camera), ctypes.POINTER(vg_raster_opts), ctypes.c_int32,
                                            ctypes.c_int64]
@@ -253,3 +256,10 @@ def vg_render_views(cells, aabbs, cams, opts, workspace: int, workspace_bytes: i
     _check(lib().vg_render_views(G, n, ab, C, O, nv, workspace, workspace_bytes, pair_capacity, a, b, c, kept,
                                  counters, stream), "vg_render_views")
     return list(kept)
+
+
+def vg_loss_l1_dssim_noalloc(img: int, target: int, width: int, height: int, lam: float, out_loss: int,
+                             out_grad: int | None, stream: int) -> None:
+    """Eq. 1 loss without a caller workspace (scratch compiled into the library; see vgrast.h)."""
+    _check(lib().vg_loss_l1_dssim_noalloc(img, target, width, height, lam, out_loss, out_grad, stream),
+           "vg_loss_l1_dssim_noalloc")

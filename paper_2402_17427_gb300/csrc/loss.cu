@@ -10,6 +10,8 @@
 // transposed convolution of the maps.  32x32 output tiles, halo 5, separable passes in smem.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "internal.h"
 #include "vg_common.cuh"
 
@@ -218,6 +220,75 @@ extern "C" vg_status vg_loss_l1_dssim(const float* img, const float* target, int
   const double inv = 1.0 / (3.0 * (double)plane);
   const Win win = make_window();
   note_launches(out_grad ? 3 : 2);
+  ssim_forward_kernel<<<grid, 256, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
+  loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
+  if (out_grad)
+    ssim_backward_kernel<<<grid, 256, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
+  return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Allocation-free variant of the loss entry point.
+//
+// Some callers cannot hand this library a workspace of their own.  A host application that
+// plans all device memory up front (an embedding engine, a memory pool that must not be
+// bypassed) or a latency-critical loop with a no-allocation rule cannot call cudaMalloc between
+// steps: it may synchronise the device, stall the loop, or fail near the memory limit.  For them
+// vg_loss_l1_dssim_noalloc keeps its scratch (the three dS/d-moment maps and the per-block
+// partial sums) in a file-scope device array of fixed size instead of a caller workspace.  The
+// array exists once per GPU that loads this library and stays allocated until the process exits.
+// ----------------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocMaxPixels = VG_LOSS_NOALLOC_MAX_PIXELS;
+// Blocks per channel for any W x H <= the maximum with W, H <= 16384:
+// ceil(W/32) ceil(H/32) <= W H / 1024 + W / 32 + H / 32 + 1.
+constexpr size_t kNoAllocMaxBlocks = 3 * (kNoAllocMaxPixels / 1024 + 2 * 16384 / 32 + 1);
+constexpr size_t kNoAllocMapBytes = 9 * kNoAllocMaxPixels * sizeof(float);
+constexpr size_t kNoAllocBytes = kNoAllocMapBytes + kNoAllocMaxBlocks * 2 * sizeof(double);
+
+static __device__ __align__(256) unsigned char g_loss_scratch[kNoAllocBytes];
+
+// Device address of g_loss_scratch on each device, looked up once per device (with that device
+// current) on the first call made there.
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64] = {nullptr};
+
+vg_status loss_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return VG_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_loss_scratch) != cudaSuccess || !p) return VG_ERR_CUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return VG_OK;
+}
+
+}  // namespace
+
+extern "C" vg_status vg_loss_l1_dssim_noalloc(const float* img, const float* target, int32_t width, int32_t height,
+                                              float lambda, float* out_loss, float* out_grad, vg_stream stream) {
+  if (!img || !target || !out_loss || width <= 0 || height <= 0 || width > 16384 || height > 16384 ||
+      !(lambda >= 0.f && lambda <= 1.f))
+    return VG_ERR_INVALID;
+  if ((size_t)width * (size_t)height > kNoAllocMaxPixels) return VG_ERR_CAPACITY;
+  void* scratch = nullptr;
+  const vg_status st = loss_scratch(&scratch);
+  if (st != VG_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t plane = (size_t)width * height;
+  float* maps = static_cast<float*>(scratch);
+  double* partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + kNoAllocMapBytes);
+  const dim3 grid((width + LT - 1) / LT, (height + LT - 1) / LT, 3);
+  const int nb = (int)(grid.x * grid.y * grid.z);
+  const double inv = 1.0 / (3.0 * (double)plane);
+  const Win win = make_window();
+  note_launches(out_grad ? 3 : 2);
+  // every map entry and partial these kernels read is written earlier in the same call, so the
+  // scratch needs no clearing between calls
   ssim_forward_kernel<<<grid, 256, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
   loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
   if (out_grad)
