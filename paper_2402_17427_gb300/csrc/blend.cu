@@ -143,6 +143,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
   __syncthreads();
   uint32_t ph0 = 0, ph1 = 0;        // phase parity of each buffer's barrier (uniform)
   unsigned long long ev = 0, bl = 0;
+  const int lane = threadIdx.x & 31;
   for (;;) {
     const int item = next_item(&hdr->work_fwd[S::kClass], item_count, &s_item);
     if (item < 0) break;
@@ -198,44 +199,72 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
       for (int p = 0; p < S::kPPT; ++p) wdone = wdone && done[p];
       // a warp whose pixels have all terminated skips the chunk (uniform branch)
       const int cnt = __all_sync(0xffffffffu, wdone) ? 0 : min(ch, n - k * ch);
-      for (int j = 0; j < cnt; ++j) {
-        const float4 f0 = *reinterpret_cast<const float4*>(&cb[j].u);
-        const float4 f2 = *reinterpret_cast<const float4*>(&cb[j].b);
-        // warp-uniform cull: no pixel of this warp can reach alpha_min
-        if (fabsf(f0.x - wcx) > half_lo(f2.w) + whw || fabsf(f0.y - wcy) > half_hi(f2.w) + whh) {
-          if (COUNT) {
+      // warp-ballot culling: lane l tests splat jb + l against this warp's pixel block, and the
+      // warp then walks only the survivors (a culled splat costs the warp nothing)
+      for (int jb = 0; jb < cnt; jb += 32) {
+        bool fin = true;
 #pragma unroll
-            for (int p = 0; p < S::kPPT; ++p) ev += done[p] ? 0 : 1;
+        for (int p = 0; p < S::kPPT; ++p) fin = fin && done[p];
+        if (__all_sync(0xffffffffu, fin)) break;     // every pixel of the warp has terminated
+        unsigned live;
+        {
+          const int jl = jb + lane;
+          bool pass = false;
+          if (jl < cnt) {
+            const float4 g0 = *reinterpret_cast<const float4*>(&cb[jl].u);
+            const float hxy = __uint_as_float(cb[jl].hxy);
+            pass = fabsf(g0.x - wcx) <= half_lo(hxy) + whw && fabsf(g0.y - wcy) <= half_hi(hxy) + whh;
           }
-          continue;
+          live = __ballot_sync(0xffffffffu, pass);
         }
-        const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
-        float e0, e1;
-        splat_col(f0.z, f0.w, __fsub_rn(__fsub_rn(pxc, f0.x), half_lo(f2.z)), e0, e1);
-        // the thread's pixels are consecutive rows: dy of row p is dy0 + p
-        const float dy0 = __fsub_rn(__fsub_rn(py[0], f0.y), half_hi(f2.z));
+        // evaluation count: a culled splat counts for each pixel still running when the list
+        // reaches it (the pixels' state changes only at surviving splats)
+        const int span = min(32, cnt - jb);
+        unsigned culled = COUNT ? (~live & (span == 32 ? 0xffffffffu : ((1u << span) - 1u))) : 0u;
+        while (live) {
+          const int bit = __ffs(live) - 1;
+          const int j = jb + bit;
+          live &= live - 1;
+          if (COUNT) {
+            const unsigned before = culled & ((1u << bit) - 1u);
+            culled &= ~before;
 #pragma unroll
-        for (int p = 0; p < S::kPPT; ++p) {
-          if (done[p]) continue;
-          if (COUNT) ++ev;
-          const float p2 = splat_power2(f1.x, e0, e1, __fadd_rn(dy0, (float)p));
-          const float q = __fadd_rn(p2, f1.y);
-          if (p2 > 0.f || q < lamin) continue;
-          const float a = fminf(amax, ex2_approx(q));
-          const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
-          const bool stop = Tn < tmin;
-          if (stop && rule0) {
-            done[p] = true;
-            continue;
+            for (int p = 0; p < S::kPPT; ++p) ev += done[p] ? 0 : (unsigned)__popc(before);
           }
-          const float w = __fmul_rn(a, T[p]);
-          C[p][0] = __fmaf_rn(f1.z, w, C[p][0]);
-          C[p][1] = __fmaf_rn(f1.w, w, C[p][1]);
-          C[p][2] = __fmaf_rn(f2.x, w, C[p][2]);
-          T[p] = Tn;
-          last[p] = (uint32_t)(k * ch + j + 1);
-          if (COUNT) ++bl;
-          if (stop) done[p] = true;
+          const float4 f0 = *reinterpret_cast<const float4*>(&cb[j].u);
+          const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
+          const float4 f2 = *reinterpret_cast<const float4*>(&cb[j].b);
+          float e0, e1;
+          splat_col(f0.z, f0.w, __fsub_rn(__fsub_rn(pxc, f0.x), half_lo(f2.z)), e0, e1);
+          // the thread's pixels are consecutive rows: dy of row p is dy0 + p
+          const float dy0 = __fsub_rn(__fsub_rn(py[0], f0.y), half_hi(f2.z));
+#pragma unroll
+          for (int p = 0; p < S::kPPT; ++p) {
+            if (done[p]) continue;
+            if (COUNT) ++ev;
+            const float p2 = splat_power2(f1.x, e0, e1, __fadd_rn(dy0, (float)p));
+            const float q = __fadd_rn(p2, f1.y);
+            if (p2 > 0.f || q < lamin) continue;
+            const float a = fminf(amax, ex2_approx(q));
+            const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
+            const bool stop = Tn < tmin;
+            if (stop && rule0) {
+              done[p] = true;
+              continue;
+            }
+            const float w = __fmul_rn(a, T[p]);
+            C[p][0] = __fmaf_rn(f1.z, w, C[p][0]);
+            C[p][1] = __fmaf_rn(f1.w, w, C[p][1]);
+            C[p][2] = __fmaf_rn(f2.x, w, C[p][2]);
+            T[p] = Tn;
+            last[p] = (uint32_t)(k * ch + j + 1);
+            if (COUNT) ++bl;
+            if (stop) done[p] = true;
+          }
+        }
+        if (COUNT) {
+#pragma unroll
+          for (int p = 0; p < S::kPPT; ++p) ev += done[p] ? 0 : (unsigned)__popc(culled);
         }
       }
       bool mine = true;
@@ -313,7 +342,9 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
     const uint2 rg = ranges[tile];
     const uint32_t list_len = rg.y - rg.x;
     const int ch = vw.op.chunk;
-    float px[S::kPPT], py[S::kPPT], T[S::kPPT], A[S::kPPT][3], G[S::kPPT][3];
+    // per pixel: T (transmittance, walked back to front), G (dL/dpixel colour) and
+    // B = G . (colour accumulated behind the current Gaussian, background included)
+    float py[S::kPPT], T[S::kPPT], B[S::kPPT], G[S::kPPT][3];
     float pxc = 0.f;
     uint32_t lastp[S::kPPT];
     unsigned mymax = 0;
@@ -323,7 +354,6 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
       int lx, ly;
       pixel_of<TS, true>(threadIdx.x, p, lx, ly);
       const int x = tx * TS + lx, y = ty * TS + ly;
-      px[p] = (float)x;
       py[p] = (float)y;
       pxc = (float)x;
       if (x < W && y < H) {
@@ -338,8 +368,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
         lastp[p] = 0;
         G[p][0] = G[p][1] = G[p][2] = 0.f;
       }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) A[p][c] = T[p] * vw.op.bg[c];
+      B[p] = T[p] * (vw.op.bg[0] * G[p][0] + vw.op.bg[1] * G[p][1] + vw.op.bg[2] * G[p][2]);
       mymax = max(mymax, lastp[p]);
     }
     if (threadIdx.x == 0) s_maxlast = 0;
@@ -369,48 +398,61 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
         return;
       }
       const Splat* cb = buf[b];
-      for (int j = hi - lo - 1; j >= 0; --j) {
-        const uint32_t pos = (uint32_t)(lo + j);
-        const float4 f0 = *reinterpret_cast<const float4*>(&cb[j].u);
-        const float4 f2 = *reinterpret_cast<const float4*>(&cb[j].b);
-        if (fabsf(f0.x - wcx) > half_lo(f2.w) + whw || fabsf(f0.y - wcy) > half_hi(f2.w) + whh) continue;
-        const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
-        float e0, e1;
-        const float dx = __fsub_rn(__fsub_rn(pxc, f0.x), half_lo(f2.z));
-        splat_col(f0.z, f0.w, dx, e0, e1);
-        const float dy0 = __fsub_rn(__fsub_rn(py[0], f0.y), half_hi(f2.z));
-        // per pixel only the moments of dL/dpower over the column are accumulated:
-        // S0 = sum dpow, S1 = sum dpow dy, S2 = sum dpow dy^2 (the thread's pixels share dx)
-        float v[10];
+      const int cnt = hi - lo;
+      // warp-ballot culling, walking each group of 32 splats back to front
+      for (int jb = ((cnt - 1) >> 5) << 5; jb >= 0; jb -= 32) {
+        unsigned live;
+        {
+          const int jl = jb + lane;
+          bool pass = false;
+          if (jl < cnt) {
+            const float4 g0 = *reinterpret_cast<const float4*>(&cb[jl].u);
+            const float hxy = __uint_as_float(cb[jl].hxy);
+            pass = fabsf(g0.x - wcx) <= half_lo(hxy) + whw && fabsf(g0.y - wcy) <= half_hi(hxy) + whh;
+          }
+          live = __ballot_sync(0xffffffffu, pass);
+        }
+        while (live) {
+          const int bit = 31 - __clz(live);
+          live &= ~(1u << bit);
+          const int j = jb + bit;
+          const uint32_t pos = (uint32_t)(lo + j);
+          const float4 f0 = *reinterpret_cast<const float4*>(&cb[j].u);
+          const float4 f2 = *reinterpret_cast<const float4*>(&cb[j].b);
+          const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
+          float e0, e1;
+          const float dx = __fsub_rn(__fsub_rn(pxc, f0.x), half_lo(f2.z));
+          splat_col(f0.z, f0.w, dx, e0, e1);
+          const float dy0 = __fsub_rn(__fsub_rn(py[0], f0.y), half_hi(f2.z));
+          // per pixel only the moments of dL/dpower over the column are accumulated:
+          // S0 = sum dpow, S1 = sum dpow dy, S2 = sum dpow dy^2 (the thread's pixels share dx)
+          float v[10];
 #pragma unroll
-        for (int f = 0; f < 10; ++f) v[f] = 0.f;
-        float S0 = 0.f, S1 = 0.f, S2 = 0.f;
-        bool any = false;
+          for (int f = 0; f < 10; ++f) v[f] = 0.f;
+          float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+          bool any = false;
 #pragma unroll
-        for (int p = 0; p < S::kPPT; ++p) {
-          if (pos >= lastp[p]) continue;
-          const float dy = __fadd_rn(dy0, (float)p);
-          const float p2 = splat_power2(f1.x, e0, e1, dy);
-          const float q = __fadd_rn(p2, f1.y);
-          if (p2 > 0.f || q < lamin) continue;
-          const float araw = ex2_approx(q);
-          const float a = fminf(amax, araw);
-          any = true;
-          const float rom = rcp_approx(1.f - a);
-          const float Tb = T[p] * rom;              // transmittance in front of this Gaussian
-          const float aT = a * Tb;
-          v[6] += aT * G[p][0];
-          v[7] += aT * G[p][1];
-          v[8] += aT * G[p][2];
-          const float cg = f1.z * G[p][0] + f1.w * G[p][1] + f2.x * G[p][2];
-          const float Ag = A[p][0] * G[p][0] + A[p][1] * G[p][1] + A[p][2] * G[p][2];
-          const float dal = Tb * cg - Ag * rom;
-          A[p][0] += f1.z * aT;
-          A[p][1] += f1.w * aT;
-          A[p][2] += f2.x * aT;
-          T[p] = Tb;
-          if (araw < amax) {
-            const float dpow = dal * a;
+          for (int p = 0; p < S::kPPT; ++p) {
+            if (pos >= lastp[p]) continue;
+            const float dy = __fadd_rn(dy0, (float)p);
+            const float p2 = splat_power2(f1.x, e0, e1, dy);
+            const float q = __fadd_rn(p2, f1.y);
+            if (p2 > 0.f || q < lamin) continue;
+            const float araw = ex2_approx(q);
+            const float a = fminf(amax, araw);
+            any = true;
+            const float rom = rcp_approx(1.f - a);
+            const float Tb = T[p] * rom;              // transmittance in front of this Gaussian
+            const float aT = a * Tb;
+            v[6] += aT * G[p][0];
+            v[7] += aT * G[p][1];
+            v[8] += aT * G[p][2];
+            const float cg = f1.z * G[p][0] + f1.w * G[p][1] + f2.x * G[p][2];
+            const float dal = Tb * cg - B[p] * rom;
+            B[p] = fmaf(cg, aT, B[p]);
+            T[p] = Tb;
+            // where alpha is clamped to alpha_max it does not depend on the power
+            const float dpow = araw < amax ? dal * a : 0.f;
             const float dpy = dpow * dy;
             S0 += dpow;
             S1 += dpy;
@@ -421,24 +463,24 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
               v[9] += fabsf(du) + fabsf(dv);
             }
           }
-        }
-        if (__any_sync(0xffffffffu, any)) {
-          // fields: du, dv, d conic (a, b, c), d opacity, d rgb; with alpha = o G unclamped,
-          // dL/do = sum dL/dalpha G = S0 / o
-          v[0] = kNegTwoLn2 * (f0.z * dx * S0 + 0.5f * f0.w * S1);
-          v[1] = kNegTwoLn2 * (0.5f * f0.w * dx * S0 + f1.x * S1);
-          v[2] = -0.5f * dx * dx * S0;
-          v[3] = -dx * S1;
-          v[4] = -0.5f * S2;
-          v[5] = S0 * ex2_approx(-f1.y);   // 1 / opacity
-          const float tot = reduce10(v, lane);
-          const int field = reduce10_field(lane);
-          const uint32_t rank = __float_as_uint(f2.y);
-          if ((lane & 1) == 0 && field >= 0 && field < 9) red_add_f32(g2d + (size_t)rank * 9 + field, tot);
-          if (ABS && (lane & 1) == 0 && field == 9) {
-            const int id = (int)dorder[rank];
-            const KSeg& sg = tseg(tab, find_seg(tab, id));
-            if (sg.gabs) red_add_f32(sg.gabs + (id - sg.offset), tot);
+          if (__any_sync(0xffffffffu, any)) {
+            // fields: du, dv, d conic (a, b, c), d opacity, d rgb; with alpha = o G unclamped,
+            // dL/do = sum dL/dalpha G = S0 / o
+            v[0] = kNegTwoLn2 * (f0.z * dx * S0 + 0.5f * f0.w * S1);
+            v[1] = kNegTwoLn2 * (0.5f * f0.w * dx * S0 + f1.x * S1);
+            v[2] = -0.5f * dx * dx * S0;
+            v[3] = -dx * S1;
+            v[4] = -0.5f * S2;
+            v[5] = S0 * ex2_approx(-f1.y);   // 1 / opacity
+            const float tot = reduce10(v, lane);
+            const int field = reduce10_field(lane);
+            const uint32_t rank = __float_as_uint(f2.y);
+            if ((lane & 1) == 0 && field >= 0 && field < 9) red_add_f32(g2d + (size_t)rank * 9 + field, tot);
+            if (ABS && (lane & 1) == 0 && field == 9) {
+              const int id = (int)dorder[rank];
+              const KSeg& sg = tseg(tab, find_seg(tab, id));
+              if (sg.gabs) red_add_f32(sg.gabs + (id - sg.offset), tot);
+            }
           }
         }
       }
