@@ -14,7 +14,10 @@
 namespace vg {
 namespace {
 
-__global__ void init_header(WsHeader* hdr) {
+__global__ void __launch_bounds__(256) init_header(WsHeader* hdr, SortCtl* ctl) {
+  unsigned* c = reinterpret_cast<unsigned*>(ctl);
+  for (unsigned i = threadIdx.x; i < sizeof(SortCtl) / sizeof(unsigned); i += blockDim.x) c[i] = 0;
+  if (threadIdx.x != 0) return;
   hdr->pairs = 0;
   hdr->evals = 0;
   hdr->blends = 0;
@@ -39,7 +42,7 @@ __global__ void publish_counters(const WsHeader* hdr, int64_t* c) {
   c[7] = 0;
 }
 
-__global__ void read_state(const Splat* __restrict__ sorted, const Splat* __restrict__ splats,
+__global__ void read_state(const uint32_t* __restrict__ lists, const Splat* __restrict__ splats,
                            const uint32_t* __restrict__ touched_in, const WsHeader* __restrict__ hdr, int n,
                            const uint32_t* d0, const uint32_t* d1, uint32_t* __restrict__ ids,
                            float* __restrict__ proj, uint32_t* __restrict__ touched) {
@@ -47,7 +50,7 @@ __global__ void read_state(const Splat* __restrict__ sorted, const Splat* __rest
   const uint32_t* dorder = depth_order(hdr, d0, d1);
   const float k = -1.3862943611198906f;   // scaled conic -> inverse covariance
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < np || i < (unsigned)n; i += gridDim.x * blockDim.x) {
-    if (ids && i < np) ids[i] = dorder[sorted[i].rank];
+    if (ids && i < np) ids[i] = dorder[lists[i]];
     if (i < (unsigned)n) {
       if (touched) touched[i] = touched_in[i];
       if (proj) {
@@ -272,7 +275,7 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
   const vg_stage_events* ev = opts0->events;
   if (cudaMemcpyAsync(ws + L.tables, c.table.data(), c.table.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return VG_ERR_CUDA;
-  init_header<<<1, 1, 0, s>>>(hdr);
+  init_header<<<1, 256, 0, s>>>(hdr, reinterpret_cast<SortCtl*>(ws + L.sortctl));
   note_launches(2);   // init_header + publish_counters
   stage_event(ev, VG_STAGE_PROJECT, true, s);
   cudaError_t e = launch_preprocess(tab, c.total_n, c.degree, reinterpret_cast<Splat*>(ws + L.splats),
@@ -514,7 +517,7 @@ extern "C" vg_status vg_read_render_state(const void* workspace, size_t workspac
   if (ranges && cudaMemcpyAsync(ranges, ws + L.ranges, (size_t)tiles * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return VG_ERR_CUDA;
   note_launches(1);
-  read_state<<<1024, 256, 0, s>>>(reinterpret_cast<const Splat*>(ws + L.sorted), reinterpret_cast<const Splat*>(ws + L.splats),
+  read_state<<<1024, 256, 0, s>>>(reinterpret_cast<const uint32_t*>(ws + L.pvals[0]), reinterpret_cast<const Splat*>(ws + L.splats),
                                   reinterpret_cast<const uint32_t*>(ws + L.touched),
                                   reinterpret_cast<const WsHeader*>(ws + L.header), (int)n,
                                   reinterpret_cast<const uint32_t*>(ws + L.vvals[0]),

@@ -7,10 +7,17 @@
 //      (key minus the minimum key, only the significant bits: V elements, not P);
 //   2. pairs are emitted in that depth order and stably radix-sorted by tile id only
 //      (ceil(log2 tiles) bits), which keeps the depth order inside every tile.
+// Both sorts are least-significant-digit radix sorts with 8-bit digits and one kernel per
+// digit pass: the digit histograms of all passes are accumulated by the kernel that produces
+// the keys, and every pass finds the output offset of each 4096-key partition by a decoupled
+// look-back over the partitions before it (each partition publishes its digit counts as soon as
+// it has ranked its keys, then its inclusive prefix).  The last tile pass writes the 48-byte
+// splat records in tile order directly.
 // Every kernel takes its element count from device memory, so the whole forward pass is
 // enqueued without a host synchronisation; kernels with no work for this render return early.
-// Grids are fixed (2 blocks per SM); each block owns one contiguous segment.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "internal.h"
 #include "vg_common.cuh"
@@ -19,7 +26,7 @@ namespace vg {
 namespace {
 
 // Contiguous segment of [0, n) owned by this block; segment lengths are multiples of `gran`.
-__device__ __forceinline__ void segment(unsigned n, unsigned& begin, unsigned& end, unsigned gran = kSortTile) {
+__device__ __forceinline__ void segment(unsigned n, unsigned& begin, unsigned& end, unsigned gran) {
   const unsigned B = gridDim.x;
   unsigned seg = (n + B - 1) / B;
   seg = (seg + gran - 1) / gran * gran;
@@ -55,12 +62,48 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* sm /*[8]*/) 
   return base + x - v;
 }
 
+// ---- look-back sort helpers ------------------------------------------------------------------
+
+constexpr unsigned long long kFlagAggregate = 1ull << 62;   // the partition's own digit count
+constexpr unsigned long long kFlagPrefix = 1ull << 63;      // count of this and all earlier partitions
+constexpr unsigned long long kCountMask = 0xFFFFFFFFull;
+constexpr int kLookback = 8;                                 // status rows read per look-back step
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Adds the digits of `key` for passes [0, passes) to the block histograms h[pass][digit];
+// lanes with the same digit are merged first (match.any), so one shared atomic per distinct
+// digit.  All 32 lanes must call it; `valid` false contributes nothing.
+__device__ __forceinline__ void histogram_add(unsigned (*h)[kRadix], uint32_t key, bool valid, int passes) {
+  const uint32_t lt = lanemask_lt();
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t d = valid ? (key >> (p * kRadixBits)) & (kRadix - 1) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (valid && (peers & lt) == 0) atomicAdd(&h[p][d], (unsigned)__popc(peers));
+  }
+}
+
+// Zeroes rows [0, nparts) of a look-back status array (grid-stride over the calling grid).
+__device__ __forceinline__ void zero_status(unsigned long long* status, unsigned nparts) {
+  const size_t total = (size_t)nparts * kRadix;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    status[i] = 0ull;
+}
+
 // ---- 1. compaction of the visible Gaussians (index order preserved) -------------------------
 
 __global__ void __launch_bounds__(256) compact_count(const uint32_t* __restrict__ dkey, unsigned n,
                                                      unsigned* __restrict__ blocksums) {
   unsigned begin, end;
-  segment(n, begin, end);
+  segment(n, begin, end, 1024);
   unsigned c = 0;
   for (unsigned i = begin + threadIdx.x; i < end; i += blockDim.x) c += dkey[i] != 0xFFFFFFFFu;
 #pragma unroll
@@ -96,16 +139,24 @@ __global__ void __launch_bounds__(256) compact_scan(unsigned* __restrict__ block
   }
 }
 
+// Writes the visible Gaussians' keys (depth key - min) and ids in index order, accumulates the
+// digit histograms of the depth-sort passes and clears the first pass's look-back rows.
 __global__ void __launch_bounds__(256) compact_scatter(const uint32_t* __restrict__ dkey, unsigned n,
                                                        const unsigned* __restrict__ blocksums,
                                                        const WsHeader* __restrict__ hdr,
                                                        uint32_t* __restrict__ vkeys, uint32_t* __restrict__ vvals,
-                                                       uint32_t* __restrict__ vis_ids) {
+                                                       uint32_t* __restrict__ vis_ids, unsigned* __restrict__ hist,
+                                                       unsigned long long* __restrict__ status0) {
   __shared__ unsigned sm[8];
+  __shared__ unsigned h[kMaxPasses][kRadix];
+#pragma unroll
+  for (int p = 0; p < kMaxPasses; ++p) h[p][threadIdx.x] = 0;
+  __syncthreads();
   unsigned begin, end;
-  segment(n, begin, end);
+  segment(n, begin, end, 1024);
   unsigned run = blocksums[blockIdx.x];
   const unsigned lo = hdr->dmin;
+  const int passes = (int)(hdr->depth_bits + kRadixBits - 1) / kRadixBits;
   for (unsigned t0 = begin; t0 < end; t0 += 256) {
     const unsigned i = t0 + threadIdx.x;
     const uint32_t k = i < end ? dkey[i] : 0xFFFFFFFFu;
@@ -117,101 +168,69 @@ __global__ void __launch_bounds__(256) compact_scatter(const uint32_t* __restric
       vvals[run + ex] = i;
       vis_ids[run + ex] = i;     // kept in index order for the adjoint of the projection
     }
+    histogram_add(h, k - lo, f != 0, passes);
     run += tot;
   }
-}
-
-// ---- radix sort passes (8-bit digits, stable, reduce-then-scan) -------------------------------
-
-__global__ void __launch_bounds__(256) radix_upsweep(const uint32_t* __restrict__ keys, const unsigned* n_ptr,
-                                                     unsigned cap, const unsigned* bits_ptr, int shift,
-                                                     uint32_t* __restrict__ hist) {
-  if ((unsigned)shift >= *bits_ptr) return;
-  const unsigned n = min(*n_ptr, cap);
-  __shared__ unsigned h[kRadix];
-  h[threadIdx.x] = 0;
   __syncthreads();
-  unsigned begin, end;
-  segment(n, begin, end);
-  for (unsigned i = begin + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1u);
-  __syncthreads();
-  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];   // digit-major: [digit][block]
+  for (int p = 0; p < passes; ++p)
+    if (h[p][threadIdx.x]) atomicAdd(&hist[p * kRadix + threadIdx.x], h[p][threadIdx.x]);
+  zero_status(status0, (hdr->visible + kDepthTile - 1) / kDepthTile);
 }
 
-// With the counts stored digit-major, the scatter offset of (digit d, block b) is the exclusive
-// prefix sum of the flattened [digit][block] array.  kScanSlices blocks each scan one slice in
-// place and publish the slice total; the downsweep adds the prefix of the slice totals.
-constexpr int kScanSlices = 64;
+// ---- radix sort passes (8-bit digits, stable, one kernel per pass, decoupled look-back) -------
 
-__device__ __forceinline__ int slice_len(int B) { return (kRadix * B + kScanSlices - 1) / kScanSlices; }
-
-__global__ void __launch_bounds__(256) radix_scan_slices(uint32_t* __restrict__ hist, int B, const unsigned* bits_ptr,
-                                                         int shift, unsigned* __restrict__ slice_tot) {
-  if ((unsigned)shift >= *bits_ptr) return;
-  __shared__ unsigned sm[8];
-  const int n = kRadix * B, L = slice_len(B);
-  const int lo = blockIdx.x * L, hi = min(n, lo + L);
-  unsigned run = 0;
-  for (int base = lo; base < hi; base += 256) {
-    const int i = base + threadIdx.x;
-    const unsigned v = i < hi ? hist[i] : 0u;
-    unsigned tot;
-    const unsigned ex = block_exclusive_scan(v, &tot, sm);
-    if (i < hi) hist[i] = run + ex;
-    run += tot;
-  }
-  if (threadIdx.x == 0) slice_tot[blockIdx.x] = run;
-}
-
-// Stable scatter.  A block walks its segment in tiles of 2048 keys; inside a tile, warp w owns
-// keys [w*256, (w+1)*256) in warp-striped order (item k of lane l is key w*256 + k*32 + l), so
-// ranks taken item by item with match.any are in input order.
-__global__ void __launch_bounds__(kSortThreads) radix_downsweep(
+// One stable digit pass.  Blocks are persistent and take partitions in increasing order from an
+// atomic counter, so every partition a block waits on has already been taken by a running block.
+// A partition holds 256 * ITEMS keys; warp w owns keys [w*32*ITEMS, (w+1)*32*ITEMS) in
+// warp-striped order (item k of lane l is key w*32*ITEMS + k*32 + l), so ranks taken item by
+// item with match.any follow the input order.
+// The keys are reordered by digit in shared memory and written out in runs, so the global
+// stores of a digit are contiguous.
+template <int ITEMS>
+__global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const unsigned* n_ptr, unsigned cap, const unsigned* bits_ptr, int shift,
-    const uint32_t* __restrict__ hist, const unsigned* __restrict__ slice_tot) {
-  if ((unsigned)shift >= *bits_ptr) return;
+    const unsigned* __restrict__ hist, unsigned* next_part, unsigned long long* status_cur,
+    unsigned long long* __restrict__ status_next, WsHeader* hdr) {
+  constexpr int TILE = kSortThreads * ITEMS;
+  if (bits_ptr && (unsigned)shift >= *bits_ptr) return;
   const unsigned n = min(*n_ptr, cap);
+  const unsigned nparts = (n + TILE - 1) / TILE;
   constexpr int WARPS = kSortThreads / 32;
-  __shared__ unsigned s_base[kRadix];
-  __shared__ unsigned s_cnt[WARPS][kRadix];
-  __shared__ unsigned s_tot[kRadix];
-  __shared__ unsigned s_slice[kScanSlices];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x < 32) {   // exclusive prefix of the 64 slice totals
-    const unsigned a = slice_tot[2 * lane], b = slice_tot[2 * lane + 1];
-    unsigned x = a + b;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    s_slice[2 * lane] = x - a - b;
-    s_slice[2 * lane + 1] = x - b;
-  }
-  __syncthreads();
+  __shared__ unsigned s_gstart[kRadix];          // first output slot of each digit (whole pass)
+  __shared__ unsigned s_cnt[WARPS][kRadix];      // per-warp digit counts, then warp offsets
+  __shared__ unsigned s_loc[kRadix];             // first slot of each digit inside the partition
+  __shared__ unsigned s_dst[kRadix];             // output slot of the digit minus its local slot
+  __shared__ uint32_t s_key[TILE];
+  __shared__ uint32_t s_val[TILE];
+  __shared__ unsigned sm[8];
+  __shared__ unsigned s_part;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d = threadIdx.x;
   {
-    const int idx = threadIdx.x * gridDim.x + blockIdx.x;
-    s_base[threadIdx.x] = hist[idx] + s_slice[idx / slice_len(gridDim.x)];
+    unsigned tot;
+    s_gstart[d] = block_exclusive_scan(hist[d], &tot, sm);
   }
-#pragma unroll
-  for (int k = 0; k < WARPS; ++k) s_cnt[k][threadIdx.x] = 0;
-  __syncthreads();
-  unsigned begin, end;
-  segment(n, begin, end);
   const uint32_t lt = lanemask_lt();
-  for (unsigned t0 = begin; t0 < end; t0 += kSortTile) {
-    uint32_t key[kSortItems], val[kSortItems], rnk[kSortItems], dig[kSortItems];
+  for (;;) {
+    if (threadIdx.x == 0) s_part = atomicAdd(next_part, 1u);
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-      const unsigned i = t0 + w * 32 * kSortItems + k * 32 + lane;
-      const bool ok = i < end;
-      key[k] = ok ? kin[i] : 0u;
-      val[k] = ok ? vin[i] : 0u;
+    for (int k = 0; k < WARPS; ++k) s_cnt[k][d] = 0;
+    __syncthreads();
+    const unsigned part = s_part;
+    if (part >= nparts) break;
+    const unsigned t0 = part * TILE;
+    const unsigned len = min((unsigned)TILE, n - t0);
+    uint32_t key[ITEMS], val[ITEMS], rnk[ITEMS], dig[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const unsigned i = w * 32 * ITEMS + k * 32 + lane;
+      const bool ok = i < len;
+      key[k] = ok ? kin[t0 + i] : 0u;
+      val[k] = ok ? vin[t0 + i] : 0u;
       dig[k] = ok ? (key[k] >> shift) & (kRadix - 1) : 0xFFFFFFFFu;
     }
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const uint32_t peers = __match_any_sync(0xffffffffu, dig[k]);
       unsigned before = 0;
       if (dig[k] != 0xFFFFFFFFu) before = s_cnt[w][dig[k]];
@@ -221,29 +240,72 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
       __syncwarp();
     }
     __syncthreads();
-    {  // exclusive scan of the per-warp counts for every digit
-      const int d = threadIdx.x;
-      unsigned run = 0;
+    unsigned c = 0;   // this partition's count of digit d; warp counts become warp offsets
 #pragma unroll
-      for (int k = 0; k < WARPS; ++k) {
-        const unsigned c = s_cnt[k][d];
-        s_cnt[k][d] = run;
-        run += c;
+    for (int k = 0; k < WARPS; ++k) {
+      const unsigned x = s_cnt[k][d];
+      s_cnt[k][d] = c;
+      c += x;
+    }
+    // publish, look back, publish the inclusive prefix
+    unsigned long long* row = status_cur + (size_t)part * kRadix;
+    unsigned excl = 0;
+    if (part == 0) {
+      st_relaxed(row + d, kFlagPrefix | c);
+    } else {
+      st_relaxed(row + d, kFlagAggregate | c);
+      // look back kLookback rows at a time (independent loads); rows below 0 read as an empty
+      // prefix, so the walk always ends at a prefix
+      int p = (int)part - 1;
+      const uint64_t start = global_timer_ns();
+      for (;;) {
+        unsigned long long v[kLookback];
+#pragma unroll
+        for (int i = 0; i < kLookback; ++i)
+          v[i] = p - i >= 0 ? ld_relaxed(status_cur + (size_t)(p - i) * kRadix + d) : kFlagPrefix;
+        int used = 0;
+        bool done = false;
+#pragma unroll
+        for (int i = 0; i < kLookback; ++i) {
+          if (done || used < i) continue;          // stop at the first row not yet published
+          if (v[i] & (kFlagPrefix | kFlagAggregate)) {
+            excl += (unsigned)(v[i] & kCountMask);
+            done = (v[i] & kFlagPrefix) != 0;
+            used = i + 1;
+          }
+        }
+        if (done) break;
+        p -= used;
+        if (used == 0 && global_timer_ns() - start > 1000000000ull) {   // a predecessor never published
+          atomicOr(&hdr->status, (unsigned)VG_STATUS_WAIT_TIMEOUT);
+          break;
+        }
       }
-      s_tot[d] = run;
+      st_relaxed(row + d, kFlagPrefix | (excl + c));
+    }
+    {
+      unsigned tot;
+      const unsigned loc = block_exclusive_scan(c, &tot, sm);
+      s_loc[d] = loc;
+      s_dst[d] = s_gstart[d] + excl - loc;
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       if (dig[k] == 0xFFFFFFFFu) continue;
-      const unsigned dst = s_base[dig[k]] + s_cnt[w][dig[k]] + rnk[k];
-      kout[dst] = key[k];
-      vout[dst] = val[k];
+      const unsigned pos = s_loc[dig[k]] + s_cnt[w][dig[k]] + rnk[k];
+      s_key[pos] = key[k];
+      s_val[pos] = val[k];
     }
     __syncthreads();
-    s_base[threadIdx.x] += s_tot[threadIdx.x];
-#pragma unroll
-    for (int k = 0; k < WARPS; ++k) s_cnt[k][threadIdx.x] = 0;
+    for (unsigned j = threadIdx.x; j < len; j += kSortThreads) {
+      const uint32_t kk = s_key[j];
+      const unsigned dst = s_dst[(kk >> shift) & (kRadix - 1)] + j;
+      if (dst >= n) continue;   // only if the histogram disagreed with the keys
+      kout[dst] = kk;
+      vout[dst] = s_val[j];
+    }
+    if (status_next) status_next[(size_t)part * kRadix + d] = 0ull;   // ready for the next pass
     __syncthreads();
   }
 }
@@ -283,13 +345,15 @@ __global__ void __launch_bounds__(256) pairs_scan(unsigned long long* __restrict
   }
   if (threadIdx.x == 0) {
     hdr->pairs = run;
-    hdr->pair_n = (unsigned)(run < cap ? run : cap);
+    // on overflow nothing is sorted or composited (the outputs are documented as invalid)
+    hdr->pair_n = (unsigned)(run <= cap ? run : 0ull);
     if (run > cap) atomicOr(&hdr->status, (unsigned)VG_STATUS_PAIR_OVERFLOW);
   }
 }
 
 // Every visible Gaussian (in depth order s) owns the pairs [offset, offset + tiles touched): one
-// (global tile, id) pair per tile of its rectangle, tiles row-major; it also records its rank s.
+// (global tile, s) pair per tile of its rectangle, tiles row-major.  It also writes its splat
+// record, carrying s, to slot s of the depth-ordered record array, and s to its own record.
 // A block takes 256 Gaussians at a time and its threads emit their pairs cooperatively (thread k
 // writes pair k of the batch, finding its owner by binary search), so writes are coalesced and
 // large Gaussians do not serialise one thread.
@@ -298,11 +362,13 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
                                                   const uint2* __restrict__ rects, const WsHeader* __restrict__ hdr,
                                                   const unsigned long long* __restrict__ blocksums,
                                                   unsigned long long cap, uint32_t* __restrict__ pkeys,
-                                                  uint32_t* __restrict__ pvals, Splat* __restrict__ splats) {
+                                                  uint32_t* __restrict__ pvals, Splat* __restrict__ splats,
+                                                  Splat* __restrict__ vsplats) {
+  if (hdr->pair_n == 0) return;   // no pairs, or more than the capacity (nothing is sorted)
   const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
   __shared__ unsigned long long sm[8];
   __shared__ unsigned s_off[257];
-  __shared__ uint32_t s_id[256];
+  __shared__ uint32_t s_rank[256];
   __shared__ int s_base[256], s_tilesx[256], s_tx0[256], s_ty0[256], s_w[256];
   unsigned begin, end;
   segment(hdr->visible, begin, end, 256);
@@ -313,6 +379,12 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
     if (s < end) {
       id = order[s];
       cnt = touched[id];
+      // the record in depth order (what the blend kernels gather), carrying its rank
+      const float4* src = reinterpret_cast<const float4*>(splats + id);
+      float4 r0 = src[0], r1 = src[1], r2 = src[2];
+      r2.y = __uint_as_float(s);
+      float4* dst = reinterpret_cast<float4*>(vsplats + s);
+      dst[0] = r0; dst[1] = r1; dst[2] = r2;
       splats[id].rank = s;
       const KView& vw = tview(tab, tseg(tab, find_seg(tab, (int)id)).view);
       const uint2 rc = rects[id];
@@ -325,7 +397,7 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
     unsigned long long tot;
     const unsigned long long ex = block_exclusive_scan((unsigned long long)cnt, &tot, sm);
     s_off[threadIdx.x] = (unsigned)ex;
-    s_id[threadIdx.x] = id;
+    s_rank[threadIdx.x] = s;
     if (threadIdx.x == 0) s_off[256] = (unsigned)tot;
     __syncthreads();
     for (unsigned k = threadIdx.x; k < (unsigned)tot; k += 256) {
@@ -340,33 +412,72 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
       const int w = s_w[lo];
       const int ty = s_ty0[lo] + within / w, tx = s_tx0[lo] + within % w;
       pkeys[j] = (uint32_t)(s_base[lo] + ty * s_tilesx[lo] + tx);
-      pvals[j] = s_id[lo];
+      pvals[j] = s_rank[lo];
     }
     run += tot;
     __syncthreads();
   }
 }
 
-// ---- 3. tile ranges and the tile-ordered copy of the splats --------------------------------------
+// Digit histograms of the emitted tile keys for the tile-sort passes.  A thread takes 8
+// consecutive keys (a Gaussian's pairs are consecutive and share their high digits) and adds
+// each run of equal digits once; it also clears the first pass's look-back rows.
+__global__ void __launch_bounds__(256) tile_histogram(const uint32_t* __restrict__ keys,
+                                                      const WsHeader* __restrict__ hdr, int tpasses,
+                                                      unsigned* __restrict__ hist,
+                                                      unsigned long long* __restrict__ status0) {
+  __shared__ unsigned h[kMaxPasses][kRadix];
+#pragma unroll
+  for (int p = 0; p < kMaxPasses; ++p) h[p][threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned n = hdr->pair_n;
+  const unsigned groups = (n + 7) / 8;
+  for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
+    uint32_t k[8];
+    const unsigned i0 = g * 8;
+    if (i0 + 8 <= n) {   // keys are 32-byte aligned groups of 8 (the buffer is 256-byte aligned)
+      const uint4 a = reinterpret_cast<const uint4*>(keys)[2 * g], b = reinterpret_cast<const uint4*>(keys)[2 * g + 1];
+      k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w; k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) k[j] = i0 + j < n ? keys[i0 + j] : 0u;
+    }
+    const int cnt = (int)min(8u, n - i0);
+    for (int p = 0; p < tpasses; ++p) {
+      const int sh = p * kRadixBits;
+      uint32_t cur = (k[0] >> sh) & (kRadix - 1);
+      unsigned run = 1;
+#pragma unroll
+      for (int j = 1; j < 8; ++j) {
+        if (j >= cnt) break;
+        const uint32_t d = (k[j] >> sh) & (kRadix - 1);
+        if (d == cur) {
+          ++run;
+        } else {
+          atomicAdd(&h[p][cur], run);
+          cur = d;
+          run = 1;
+        }
+      }
+      atomicAdd(&h[p][cur], run);
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < tpasses; ++p)
+    if (h[p][threadIdx.x]) atomicAdd(&hist[p * kRadix + threadIdx.x], h[p][threadIdx.x]);
+  zero_status(status0, (n + kTileTile - 1) / kTileTile);
+}
+
+// ---- 3. tile ranges --------------------------------------
 
 __global__ void __launch_bounds__(256) tile_ranges(const uint32_t* __restrict__ keys, const WsHeader* __restrict__ hdr,
-                                                   uint2* __restrict__ ranges) {
+                                                   unsigned tiles, uint2* __restrict__ ranges) {
   const unsigned n = hdr->pair_n;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t t = keys[i];
+    if (t >= tiles) continue;   // cannot happen for keys written by the sort
     if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
     if (i == n - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
-  }
-}
-
-__global__ void __launch_bounds__(256) gather_splats(const uint32_t* __restrict__ ids, const WsHeader* __restrict__ hdr,
-                                                     const Splat* __restrict__ splats, Splat* __restrict__ sorted) {
-  const unsigned n = hdr->pair_n;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float4* src = reinterpret_cast<const float4*>(splats + ids[i]);
-    float4* dst = reinterpret_cast<float4*>(sorted + i);
-    const float4 a = __ldg(src), b = __ldg(src + 1), c = __ldg(src + 2);
-    dst[0] = a; dst[1] = b; dst[2] = c;
   }
 }
 
@@ -436,6 +547,7 @@ Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
   L.header = take(256);
+  L.sortctl = take(sizeof(SortCtl));
   L.tables = take(table_bytes(kMaxViews, kMaxSegs));
   L.splats = take(N * 48);
   L.rects = take(N * 8);
@@ -446,65 +558,84 @@ Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
   L.vvals[0] = take(N * 4); L.vvals[1] = take(N * 4);
   L.pkeys[0] = take(P * 4); L.pkeys[1] = take(P * 4);
   L.pvals[0] = take(P * 4); L.pvals[1] = take(P * 4);
-  L.sorted = take(P * 48);
+  L.vsplats = take(N * 48);
   L.ranges = take(tiles * 8);
   L.order = take(tiles * 4);
   L.buckets = take(2 * kBuckets * 4);
-  L.hist = take((size_t)kMaxSortBlocks * kRadix * 4);
   L.blocksums = take((size_t)kMaxSortBlocks * 8);
-  L.slices = take(kScanSlices * 4);
+  // look-back rows of either sort
+  const size_t parts = std::max((N + kDepthTile - 1) / kDepthTile, (P + kTileTile - 1) / kTileTile);
+  L.status[0] = take(parts * kRadix * 8);
+  L.status[1] = take(parts * kRadix * 8);
   L.g2d = take(N * 9 * 4);
   L.total = o;
   return L;
+}
+
+// Resident blocks of a look-back pass on this device (persistent grid).
+template <int ITEMS>
+int onesweep_blocks() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_pass<ITEMS>, kSortThreads, 0);
+    cached = std::max(1, sms) * std::max(1, per_sm);
+  }
+  return cached;
 }
 
 cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capacity, const Layout& L, char* ws,
                            cudaStream_t s) {
   const int B = sort_blocks();
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
+  SortCtl* ctl = reinterpret_cast<SortCtl*>(ws + L.sortctl);
   auto U = [&](size_t off) { return reinterpret_cast<uint32_t*>(ws + off); };
+  auto S64 = [&](int k) { return reinterpret_cast<unsigned long long*>(ws + L.status[k]); };
   Splat* splats = reinterpret_cast<Splat*>(ws + L.splats);
-  uint32_t* hist = U(L.hist);
+  Splat* vsplats = reinterpret_cast<Splat*>(ws + L.vsplats);
   unsigned* bsum = U(L.blocksums);
   unsigned long long* bsum64 = reinterpret_cast<unsigned long long*>(ws + L.blocksums);
   const unsigned cap = (unsigned)(capacity > 0xFFFFFFFFll ? 0xFFFFFFFFll : capacity);
   const unsigned tile_bits = (unsigned)ceil_log2((unsigned)tiles);
-  unsigned* slices = U(L.slices);
+  // persistent grids, no larger than the partitions of the largest possible input
+  const int OBD = std::max(1, std::min(onesweep_blocks<kDepthItems>(), (n + kDepthTile - 1) / kDepthTile));
+  const int OBT = (int)std::max<int64_t>(1, std::min<int64_t>(onesweep_blocks<kTileItems>(), ((int64_t)cap + kTileTile - 1) / kTileTile));
 
-  // 1. compaction + depth sort
+  // 1. compaction + depth sort (passes beyond the significant bits return at once; the result
+  //    sits in the buffer depth_order() names)
   compact_count<<<B, 256, 0, s>>>(U(L.dkey), (unsigned)n, bsum);
   compact_scan<<<1, 256, 0, s>>>(bsum, B, hdr, tile_bits);
-  compact_scatter<<<B, 256, 0, s>>>(U(L.dkey), (unsigned)n, bsum, hdr, U(L.vkeys[0]), U(L.vvals[0]), U(L.vis_ids));
-  for (int pass = 0; pass < 4; ++pass) {
-    const int shift = pass * kRadixBits;
+  const int tpasses = std::max(1, ((int)tile_bits + kRadixBits - 1) / kRadixBits);
+  compact_scatter<<<B, 256, 0, s>>>(U(L.dkey), (unsigned)n, bsum, hdr, U(L.vkeys[0]), U(L.vvals[0]), U(L.vis_ids),
+                                    ctl->hist[0][0], S64(0));
+  for (int pass = 0; pass < kMaxPasses; ++pass) {
     const int src = pass & 1, dst = src ^ 1;
-    radix_upsweep<<<B, 256, 0, s>>>(U(L.vkeys[src]), &hdr->visible, 0xFFFFFFFFu, &hdr->depth_bits, shift, hist);
-    radix_scan_slices<<<kScanSlices, 256, 0, s>>>(hist, B, &hdr->depth_bits, shift, slices);
-    radix_downsweep<<<B, kSortThreads, 0, s>>>(U(L.vkeys[src]), U(L.vvals[src]), U(L.vkeys[dst]), U(L.vvals[dst]),
-                                               &hdr->visible, 0xFFFFFFFFu, &hdr->depth_bits, shift, hist, slices);
+    onesweep_pass<kDepthItems><<<OBD, kSortThreads, 0, s>>>(U(L.vkeys[src]), U(L.vvals[src]), U(L.vkeys[dst]), U(L.vvals[dst]),
+                                              &hdr->visible, 0xFFFFFFFFu, &hdr->depth_bits, pass * kRadixBits,
+                                              ctl->hist[0][pass], &ctl->next_part[0][pass], S64(src), S64(dst), hdr);
   }
-  // 2. pairs in depth order
+  // 2. pairs in depth order, written where the tile sort's passes leave the result in buffer 0
+  const int p0 = tpasses & 1;
   const int BP = kMaxSortBlocks < 6 * B / 2 ? kMaxSortBlocks : 6 * B / 2;   // 6 blocks per SM
   pairs_count<<<BP, 256, 0, s>>>(U(L.vvals[0]), U(L.vvals[1]), U(L.touched), hdr, bsum64);
   pairs_scan<<<1, 256, 0, s>>>(bsum64, BP, hdr, (unsigned long long)cap);
   pairs_emit<<<BP, 256, 0, s>>>(tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), reinterpret_cast<const uint2*>(ws + L.rects),
-                               hdr, bsum64, (unsigned long long)cap, U(L.pkeys[0]), U(L.pvals[0]), splats);
-  // 3. stable sort of the pairs by tile id (tile_bits is known here, so is the pass count)
-  const int tpasses = ((int)tile_bits + kRadixBits - 1) / kRadixBits;
+                               hdr, bsum64, (unsigned long long)cap, U(L.pkeys[p0]), U(L.pvals[p0]), splats, vsplats);
+  tile_histogram<<<B * 2, 256, 0, s>>>(U(L.pkeys[p0]), hdr, tpasses, ctl->hist[1][0], S64(0));
+  // 3. stable sort of the pairs by tile id
   for (int pass = 0; pass < tpasses; ++pass) {
-    const int shift = pass * kRadixBits;
-    const int src = pass & 1, dst = src ^ 1;
-    radix_upsweep<<<B, 256, 0, s>>>(U(L.pkeys[src]), &hdr->pair_n, cap, &hdr->tile_bits, shift, hist);
-    radix_scan_slices<<<kScanSlices, 256, 0, s>>>(hist, B, &hdr->tile_bits, shift, slices);
-    radix_downsweep<<<B, kSortThreads, 0, s>>>(U(L.pkeys[src]), U(L.pvals[src]), U(L.pkeys[dst]), U(L.pvals[dst]),
-                                               &hdr->pair_n, cap, &hdr->tile_bits, shift, hist, slices);
+    const int src = (p0 + pass) & 1, dst = src ^ 1;
+    onesweep_pass<kTileItems><<<OBT, kSortThreads, 0, s>>>(U(L.pkeys[src]), U(L.pvals[src]), U(L.pkeys[dst]), U(L.pvals[dst]),
+                                              &hdr->pair_n, cap, nullptr, pass * kRadixBits, ctl->hist[1][pass],
+                                              &ctl->next_part[1][pass], S64(pass & 1),
+                                              pass + 1 < tpasses ? S64((pass + 1) & 1) : nullptr, hdr);
   }
-  note_launches(3 + 4 * 3 + 3 + 3 * tpasses + 5);
-  const int fin = tpasses & 1;
+  note_launches(3 + kMaxPasses + 4 + tpasses + 4);
   uint2* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
   cudaMemsetAsync(ranges, 0, (size_t)tiles * sizeof(uint2), s);
-  tile_ranges<<<B * 4, 256, 0, s>>>(U(L.pkeys[fin]), hdr, ranges);
-  gather_splats<<<B * 4, 256, 0, s>>>(U(L.pvals[fin]), hdr, splats, reinterpret_cast<Splat*>(ws + L.sorted));
+  tile_ranges<<<B * 4, 256, 0, s>>>(U(L.pkeys[0]), hdr, (unsigned)tiles, ranges);
   // 4. largest-first tile order
   unsigned* buckets = U(L.buckets);
   cudaMemsetAsync(buckets, 0, kBuckets * sizeof(unsigned), s);

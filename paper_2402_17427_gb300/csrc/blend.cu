@@ -5,12 +5,13 @@
 //
 // Persistent kernels: one launch per tile-size class, a grid sized to the resident capacity of
 // the GPU, and blocks that pull tiles from a device work queue ordered largest list first (the
-// order is built during binning).  The tile's splats are contiguous in the tile-ordered copy,
-// so chunks of up to 128 records (6 KB) are moved into shared memory by one bulk copy each
-// (cp.async.bulk completing on an mbarrier), double-buffered so the copy of chunk k+1 overlaps
-// the compositing of chunk k.  Thread 0 issues the copies; all threads wait with a bounded wait.
-// Each thread owns several pixels of the tile, which amortises the shared-memory reads of a
-// splat in the forward pass and the warp reduction of its gradient in the backward pass.
+// order is built during binning).  A tile's list holds depth ranks; the splat records are stored
+// once, in depth order (about V x 48 bytes, L2-resident), and chunks of up to 128 records are
+// gathered into shared memory with 16-byte asynchronous copies (cp.async), double-buffered so
+// the copies of chunk k+1 overlap the compositing of chunk k.  The ranks of the chunk after that
+// are loaded one chunk ahead, so the copies never wait on the list.  Each thread owns several
+// pixels of the tile, which amortises the shared-memory reads of a splat in the forward pass and
+// the warp reduction of its gradient in the backward pass.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -34,6 +35,7 @@ struct TileShape {
   static constexpr int kThreads = kPix / kPPT;
   static constexpr int kClass = TS == 8 ? 0 : (TS == 16 ? 1 : 2);
   static constexpr int kWarpRows = 32 * kPPT / TS;      // a warp covers TS columns x kWarpRows rows
+  static constexpr int kIds = (128 + kThreads - 1) / kThreads;   // ranks a thread gathers per chunk
 };
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -69,10 +71,32 @@ __device__ __forceinline__ void pixel_of(int t, int p, int& lx, int& ly) {
   ly = (t / TS) * S::kPPT + p;
 }
 
-__device__ __forceinline__ void issue_chunk(Splat* dst, const Splat* src, int count, uint64_t* bar) {
-  const uint32_t bytes = (uint32_t)count * (uint32_t)sizeof(Splat);
-  mbar_arrive_expect_tx(bar, bytes);
-  bulk_copy_g2s(dst, src, bytes, bar);
+// Ranks of list entries [0, count) that this thread gathers (entry threadIdx.x + i * T).
+template <int T, int R>
+__device__ __forceinline__ void load_ranks(uint32_t (&id)[R], const uint32_t* __restrict__ list, int count) {
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int e = (int)threadIdx.x + i * T;
+    id[i] = e < count ? __ldg(list + e) : 0u;
+  }
+}
+
+// Starts the copies of records id[...] into dst[entry] and commits them as one group.
+template <int T, int R>
+__device__ __forceinline__ void gather_chunk(Splat* dst, const Splat* __restrict__ vsplats, const uint32_t (&id)[R],
+                                             int count) {
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int e = (int)threadIdx.x + i * T;
+    if (e < count) {
+      const char* src = reinterpret_cast<const char*>(vsplats + id[i]);
+      char* d = reinterpret_cast<char*>(dst + e);
+      cp_async16(d, src);
+      cp_async16(d + 16, src + 16);
+      cp_async16(d + 32, src + 32);
+    }
+  }
+  cp_async_commit();
 }
 
 // Sum of v[0..9] over the 32 lanes of a warp by recursive halving: at each step a lane keeps
@@ -128,20 +152,12 @@ __device__ __forceinline__ int next_item(unsigned* counter, int count, int* s_it
 
 template <int TS, bool COUNT>
 __global__ void __launch_bounds__(TileShape<TS, false>::kThreads)
-blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ sorted,
-                     const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, int item_begin,
-                     int item_count, WsHeader* __restrict__ hdr) {
+blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ vsplats,
+                     const uint32_t* __restrict__ lists, const uint2* __restrict__ ranges,
+                     const uint32_t* __restrict__ order, int item_begin, int item_count, WsHeader* __restrict__ hdr) {
   using S = TileShape<TS, false>;
   __shared__ __align__(128) Splat buf[2][kCh];
-  __shared__ __align__(8) uint64_t bar[2];
   __shared__ int s_item;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_barrier_init();
-  }
-  __syncthreads();
-  uint32_t ph0 = 0, ph1 = 0;        // phase parity of each buffer's barrier (uniform)
   unsigned long long ev = 0, bl = 0;
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -179,20 +195,24 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
       last[p] = 0;
     }
     const int nch = (n + ch - 1) / ch;
-    if (threadIdx.x == 0 && nch > 0) issue_chunk(buf[0], sorted + rg.x, min(ch, n), &bar[0]);
+    const uint32_t* list = lists + rg.x;
+    uint32_t ids[S::kIds];
+    if (nch > 0) {
+      load_ranks<S::kThreads>(ids, list, min(ch, n));
+      gather_chunk<S::kThreads>(buf[0], vsplats, ids, min(ch, n));
+      if (nch > 1) load_ranks<S::kThreads>(ids, list + ch, min(ch, n - ch));
+    }
     for (int k = 0; k < nch; ++k) {
       const int b = k & 1;
       const bool more = k + 1 < nch;
-      if (threadIdx.x == 0 && more)
-        issue_chunk(buf[b ^ 1], sorted + rg.x + (k + 1) * ch, min(ch, n - (k + 1) * ch), &bar[b ^ 1]);
-      const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
-      if (b) ph1 ^= 1; else ph0 ^= 1;
-      if (!__syncthreads_and(ok)) {
-        // a copy did not land in time: flag it and stop this block (its barriers are no
-        // longer in a known phase); the render is reported as failed
-        if (threadIdx.x == 0) atomicOr(&hdr->status, (unsigned)VG_STATUS_WAIT_TIMEOUT);
-        return;
+      if (more) {
+        gather_chunk<S::kThreads>(buf[b ^ 1], vsplats, ids, min(ch, n - (k + 1) * ch));
+        if (k + 2 < nch) load_ranks<S::kThreads>(ids, list + (k + 2) * ch, min(ch, n - (k + 2) * ch));
+        cp_async_wait<1>();   // this thread's copies of chunk k have landed
+      } else {
+        cp_async_wait<0>();
       }
+      __syncthreads();        // ... and every other thread's
       const Splat* cb = buf[b];
       bool wdone = true;
 #pragma unroll
@@ -270,16 +290,9 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
       bool mine = true;
 #pragma unroll
       for (int p = 0; p < S::kPPT; ++p) mine = mine && done[p];
-      if (__syncthreads_and(mine)) {
-        // all pixels finished: collect the prefetched chunk before the buffers are reused
-        if (more) {
-          if (threadIdx.x == 0 && !mbar_wait(&bar[b ^ 1], b ? ph0 : ph1))
-            atomicOr(&hdr->status, (unsigned)VG_STATUS_WAIT_TIMEOUT);
-          if (b) ph0 ^= 1; else ph1 ^= 1;
-        }
-        break;
-      }
+      if (__syncthreads_and(mine)) break;   // all pixels of the tile have terminated
     }
+    cp_async_wait<0>();   // a prefetched chunk left by an early stop lands before the buffers are reused
     const size_t plane = (size_t)W * H;
 #pragma unroll
     for (int p = 0; p < S::kPPT; ++p) {
@@ -292,7 +305,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
       vw.T[pix] = T[p];
       vw.last[pix] = last[p];
     }
-    __syncthreads();   // the drain wait above is thread 0's; buffers are free after this
+    __syncthreads();   // buffers are free for the next tile after this
   }
   if (COUNT) {
 #pragma unroll
@@ -309,24 +322,16 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
 
 template <int TS, bool ABS>
 __global__ void __launch_bounds__(TileShape<TS, true>::kThreads)
-blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ sorted,
-                      const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, int item_begin,
-                      int item_count, float* __restrict__ g2d, const uint32_t* dorder0, const uint32_t* dorder1,
-                      WsHeader* __restrict__ hdr) {
+blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ vsplats,
+                      const uint32_t* __restrict__ lists, const uint2* __restrict__ ranges,
+                      const uint32_t* __restrict__ order, int item_begin, int item_count, float* __restrict__ g2d,
+                      const uint32_t* dorder0, const uint32_t* dorder1, WsHeader* __restrict__ hdr) {
   using S = TileShape<TS, true>;
   const uint32_t* __restrict__ dorder = depth_order(hdr, dorder0, dorder1);
   __shared__ __align__(128) Splat buf[2][kCh];
-  __shared__ __align__(8) uint64_t bar[2];
   __shared__ int s_item;
   __shared__ unsigned s_maxlast;
   const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_barrier_init();
-  }
-  __syncthreads();
-  uint32_t ph0 = 0, ph1 = 0;
   for (;;) {
     const int item = next_item(&hdr->work_bwd[S::kClass], item_count, &s_item);
     if (item < 0) break;
@@ -380,23 +385,32 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
     const int maxlast = (int)s_maxlast;
     const int nch = (maxlast + ch - 1) / ch;
     // chunk k covers list positions [max(0, maxlast - (k+1) ch), maxlast - k ch), back to front
-    if (threadIdx.x == 0 && nch > 0) {
-      const int lo = max(0, maxlast - ch);
-      issue_chunk(buf[0], sorted + rg.x + lo, maxlast - lo, &bar[0]);
+    const uint32_t* list = lists + rg.x;
+    uint32_t ids[S::kIds];
+    if (nch > 0) {
+      const int lo0 = max(0, maxlast - ch);
+      load_ranks<S::kThreads>(ids, list + lo0, maxlast - lo0);
+      gather_chunk<S::kThreads>(buf[0], vsplats, ids, maxlast - lo0);
+      if (nch > 1) {
+        const int lo1 = max(0, lo0 - ch);
+        load_ranks<S::kThreads>(ids, list + lo1, lo0 - lo1);
+      }
     }
     for (int k = 0; k < nch; ++k) {
       const int b = k & 1;
       const int hi = maxlast - k * ch, lo = max(0, hi - ch);
-      if (threadIdx.x == 0 && k + 1 < nch) {
+      if (k + 1 < nch) {
         const int lo2 = max(0, lo - ch);
-        issue_chunk(buf[b ^ 1], sorted + rg.x + lo2, lo - lo2, &bar[b ^ 1]);
+        gather_chunk<S::kThreads>(buf[b ^ 1], vsplats, ids, lo - lo2);
+        if (k + 2 < nch) {
+          const int lo3 = max(0, lo2 - ch);
+          load_ranks<S::kThreads>(ids, list + lo3, lo2 - lo3);
+        }
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
       }
-      const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
-      if (b) ph1 ^= 1; else ph0 ^= 1;
-      if (!__syncthreads_and(ok)) {
-        if (threadIdx.x == 0) atomicOr(&hdr->status, (unsigned)VG_STATUS_WAIT_TIMEOUT);
-        return;
-      }
+      __syncthreads();
       const Splat* cb = buf[b];
       const int cnt = hi - lo;
       // warp-ballot culling, walking each group of 32 splats back to front
@@ -510,8 +524,8 @@ int resident_grid(K kernel, int threads, int items) {
 }
 
 template <int TS>
-cudaError_t fwd_class(const DevTables* tab, const HostPlan& plan, const Splat* sorted, const uint2* ranges,
-                      const uint32_t* order, WsHeader* hdr, bool count, cudaStream_t s) {
+cudaError_t fwd_class(const DevTables* tab, const HostPlan& plan, const Splat* vsplats, const uint32_t* lists,
+                      const uint2* ranges, const uint32_t* order, WsHeader* hdr, bool count, cudaStream_t s) {
   using S = TileShape<TS, false>;
   const int items = plan.class_tiles[S::kClass];
   if (items == 0) return cudaSuccess;
@@ -519,18 +533,18 @@ cudaError_t fwd_class(const DevTables* tab, const HostPlan& plan, const Splat* s
   const int begin = plan.class_begin[S::kClass];
   if (count) {
     auto k = blend_forward_kernel<TS, true>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, sorted, ranges, order, begin, items, hdr);
+    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, hdr);
   } else {
     auto k = blend_forward_kernel<TS, false>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, sorted, ranges, order, begin, items, hdr);
+    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, hdr);
   }
   return cudaGetLastError();
 }
 
 template <int TS>
-cudaError_t bwd_class(const DevTables* tab, const HostPlan& plan, const Splat* sorted, const uint2* ranges,
-                      const uint32_t* order, float* g2d, const uint32_t* d0, const uint32_t* d1, WsHeader* hdr,
-                      bool abs, cudaStream_t s) {
+cudaError_t bwd_class(const DevTables* tab, const HostPlan& plan, const Splat* vsplats, const uint32_t* lists,
+                      const uint2* ranges, const uint32_t* order, float* g2d, const uint32_t* d0, const uint32_t* d1,
+                      WsHeader* hdr, bool abs, cudaStream_t s) {
   using S = TileShape<TS, true>;
   const int items = plan.class_tiles[S::kClass];
   if (items == 0) return cudaSuccess;
@@ -538,10 +552,10 @@ cudaError_t bwd_class(const DevTables* tab, const HostPlan& plan, const Splat* s
   const int begin = plan.class_begin[S::kClass];
   if (abs) {
     auto k = blend_backward_kernel<TS, true>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, sorted, ranges, order, begin, items, g2d, d0, d1, hdr);
+    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, g2d, d0, d1, hdr);
   } else {
     auto k = blend_backward_kernel<TS, false>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, sorted, ranges, order, begin, items, g2d, d0, d1, hdr);
+    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, g2d, d0, d1, hdr);
   }
   return cudaGetLastError();
 }
@@ -550,19 +564,21 @@ cudaError_t bwd_class(const DevTables* tab, const HostPlan& plan, const Splat* s
 
 cudaError_t launch_blend_forward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool count,
                                  cudaStream_t s) {
-  const Splat* sorted = reinterpret_cast<const Splat*>(ws + L.sorted);
+  const Splat* vsplats = reinterpret_cast<const Splat*>(ws + L.vsplats);
+  const uint32_t* lists = reinterpret_cast<const uint32_t*>(ws + L.pvals[0]);   // final tile-sorted ranks
   const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.ranges);
   const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + L.order);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
-  cudaError_t e = fwd_class<8>(tab, plan, sorted, ranges, order, hdr, count, s);
-  if (e == cudaSuccess) e = fwd_class<16>(tab, plan, sorted, ranges, order, hdr, count, s);
-  if (e == cudaSuccess) e = fwd_class<32>(tab, plan, sorted, ranges, order, hdr, count, s);
+  cudaError_t e = fwd_class<8>(tab, plan, vsplats, lists, ranges, order, hdr, count, s);
+  if (e == cudaSuccess) e = fwd_class<16>(tab, plan, vsplats, lists, ranges, order, hdr, count, s);
+  if (e == cudaSuccess) e = fwd_class<32>(tab, plan, vsplats, lists, ranges, order, hdr, count, s);
   return e;
 }
 
 cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool abs,
                                   cudaStream_t s) {
-  const Splat* sorted = reinterpret_cast<const Splat*>(ws + L.sorted);
+  const Splat* vsplats = reinterpret_cast<const Splat*>(ws + L.vsplats);
+  const uint32_t* lists = reinterpret_cast<const uint32_t*>(ws + L.pvals[0]);   // final tile-sorted ranks
   const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.ranges);
   const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + L.order);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
@@ -572,9 +588,9 @@ cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, co
   note_launches(2);
   const uint32_t* d0 = reinterpret_cast<const uint32_t*>(ws + L.vvals[0]);
   const uint32_t* d1 = reinterpret_cast<const uint32_t*>(ws + L.vvals[1]);
-  cudaError_t e = bwd_class<8>(tab, plan, sorted, ranges, order, g2d, d0, d1, hdr, abs, s);
-  if (e == cudaSuccess) e = bwd_class<16>(tab, plan, sorted, ranges, order, g2d, d0, d1, hdr, abs, s);
-  if (e == cudaSuccess) e = bwd_class<32>(tab, plan, sorted, ranges, order, g2d, d0, d1, hdr, abs, s);
+  cudaError_t e = bwd_class<8>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, s);
+  if (e == cudaSuccess) e = bwd_class<16>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, s);
+  if (e == cudaSuccess) e = bwd_class<32>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, s);
   return e;
 }
 

@@ -143,18 +143,28 @@ __device__ __forceinline__ int find_view(const DevTables* __restrict__ t, int ti
 }
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kDepthItems = 4;                          // depth sort: 1024-key partitions (V is small)
+constexpr int kTileItems = 16;                          // tile sort: 4096-key partitions
+constexpr int kDepthTile = kSortThreads * kDepthItems;
+constexpr int kTileTile = kSortThreads * kTileItems;
 constexpr int kMaxSortBlocks = 1024;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxPasses = 4;                           // 32-bit keys
+
+// Digit histograms and partition counters of the two sorts (0: depth, 1: tile); cleared at the
+// start of every render.
+struct SortCtl {
+  unsigned hist[2][kMaxPasses][kRadix];
+  unsigned next_part[2][kMaxPasses];
+};
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 // Offsets (bytes) of the regions of one render workspace (any number of views / segments).
 struct Layout {
-  size_t header, tables, splats, rects, touched, dkey, vis_ids, vkeys[2], vvals[2], pkeys[2], pvals[2], sorted,
-      ranges, order, buckets, hist, blocksums, slices, g2d, total;
+  size_t header, sortctl, tables, splats, rects, touched, dkey, vis_ids, vkeys[2], vvals[2], pkeys[2], pvals[2],
+      vsplats, ranges, order, buckets, blocksums, status[2], g2d, total;
 };
 Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t pair_capacity);
 

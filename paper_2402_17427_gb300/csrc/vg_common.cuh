@@ -11,8 +11,8 @@ namespace vg {
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kMaxChunk = 256;
 
-// One projected 2D Gaussian as the blend kernels consume it (48 bytes, 16-byte aligned so a
-// run of records can be moved by one bulk copy).
+// One projected 2D Gaussian as the blend kernels consume it (48 bytes, 16-byte aligned: three
+// 16-byte asynchronous copies move it to shared memory).
 //  - (u + ulo, v + vlo): the projected mean.  (u, v) is the FP32 value nearest to the mean's
 //    projection computed in FP64, and (ulo, vlo) (binary16) the remainder, so pixel offsets
 //    dx = (px - u) - ulo are accurate to ~1e-7 px even 2000 px from the origin.
@@ -67,59 +67,29 @@ __device__ __forceinline__ float splat_power2(float cc, float e0, float e1, floa
 }
 
 // ------------------------------------------------------------------------------------------
-// mbarrier + bulk-copy (TMA) helpers, CTA scope.  Waits are bounded: after `limit` polls they
-// give up and return false so the caller can flag the failure and leave cleanly.
+// Asynchronous global -> shared copies (16 bytes each, tracked per thread in commit groups).
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+// dst (shared) and src (global) 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
-               ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// Global -> shared bulk copy completing on `bar`.  dst, src 16-byte aligned; bytes % 16 == 0.
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-  return ok != 0;
+// Waits until at most N of this thread's most recent commit groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ uint64_t global_timer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-// Wait on phase `parity` of `bar`, giving up after `timeout_ns` of wall time (default 1 s).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns = 1000000000ull) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_timer_ns();
-  for (;;) {
-    for (int i = 0; i < 32; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (global_timer_ns() - t0 > timeout_ns) return false;
-  }
 }
 
 __device__ __forceinline__ void red_add_f32(float* addr, float v) {
