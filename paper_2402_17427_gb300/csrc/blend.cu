@@ -258,28 +258,28 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
           splat_col(f0.z, f0.w, __fsub_rn(__fsub_rn(pxc, f0.x), half_lo(f2.z)), e0, e1);
           // the thread's pixels are consecutive rows: dy of row p is dy0 + p
           const float dy0 = __fsub_rn(__fsub_rn(py[0], f0.y), half_hi(f2.z));
+          // branch-free over the thread's pixels (selects instead of skips), so the compiler can
+          // interleave the pixels' independent chains; a pixel that does not blend keeps C, T
+          // and last bit for bit (w = 0 adds an exact zero)
+          const uint32_t pos1 = (uint32_t)(k * ch + j + 1);
 #pragma unroll
           for (int p = 0; p < S::kPPT; ++p) {
-            if (done[p]) continue;
-            if (COUNT) ++ev;
+            if (COUNT) ev += done[p] ? 0 : 1;
             const float p2 = splat_power2(f1.x, e0, e1, __fadd_rn(dy0, (float)p));
             const float q = __fadd_rn(p2, f1.y);
-            if (p2 > 0.f || q < lamin) continue;
+            const bool ok = !done[p] && !(p2 > 0.f || q < lamin);
             const float a = fminf(amax, ex2_approx(q));
             const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
-            const bool stop = Tn < tmin;
-            if (stop && rule0) {
-              done[p] = true;
-              continue;
-            }
-            const float w = __fmul_rn(a, T[p]);
+            const bool stop = ok && Tn < tmin;
+            const bool blend = ok && !(stop && rule0);
+            const float w = blend ? __fmul_rn(a, T[p]) : 0.f;
             C[p][0] = __fmaf_rn(f1.z, w, C[p][0]);
             C[p][1] = __fmaf_rn(f1.w, w, C[p][1]);
             C[p][2] = __fmaf_rn(f2.x, w, C[p][2]);
-            T[p] = Tn;
-            last[p] = (uint32_t)(k * ch + j + 1);
-            if (COUNT) ++bl;
-            if (stop) done[p] = true;
+            T[p] = blend ? Tn : T[p];
+            last[p] = blend ? pos1 : last[p];
+            if (COUNT) bl += blend ? 1 : 0;
+            done[p] = done[p] || stop;
           }
         }
         if (COUNT) {
@@ -445,16 +445,17 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
           for (int f = 0; f < 10; ++f) v[f] = 0.f;
           float S0 = 0.f, S1 = 0.f, S2 = 0.f;
           bool any = false;
+          // branch-free over the thread's pixels: a pixel this Gaussian does not reach gets
+          // alpha = 0, which leaves B and the sums unchanged, and keeps its T by a select
 #pragma unroll
           for (int p = 0; p < S::kPPT; ++p) {
-            if (pos >= lastp[p]) continue;
             const float dy = __fadd_rn(dy0, (float)p);
             const float p2 = splat_power2(f1.x, e0, e1, dy);
             const float q = __fadd_rn(p2, f1.y);
-            if (p2 > 0.f || q < lamin) continue;
+            const bool ok = pos < lastp[p] && !(p2 > 0.f || q < lamin);
             const float araw = ex2_approx(q);
-            const float a = fminf(amax, araw);
-            any = true;
+            const float a = ok ? fminf(amax, araw) : 0.f;
+            any = any || ok;
             const float rom = rcp_approx(1.f - a);
             const float Tb = T[p] * rom;              // transmittance in front of this Gaussian
             const float aT = a * Tb;
@@ -464,9 +465,9 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
             const float cg = f1.z * G[p][0] + f1.w * G[p][1] + f2.x * G[p][2];
             const float dal = Tb * cg - B[p] * rom;
             B[p] = fmaf(cg, aT, B[p]);
-            T[p] = Tb;
+            T[p] = ok ? Tb : T[p];
             // where alpha is clamped to alpha_max it does not depend on the power
-            const float dpow = araw < amax ? dal * a : 0.f;
+            const float dpow = ok && araw < amax ? dal * a : 0.f;
             const float dpy = dpow * dy;
             S0 += dpow;
             S1 += dpy;
