@@ -51,6 +51,29 @@ __device__ __forceinline__ float half_hi(float bits) {
   return __half2float(__ushort_as_half((unsigned short)(__float_as_uint(bits) >> 16)));
 }
 
+// Whether some pixel of the block [cx -+ hw] x [cy -+ hh] may reach alpha >= alpha_min for a
+// splat: the maximum of its (concave) power2 over the block's rectangle is 0 if the rectangle
+// holds the mean, else it lies on an edge, at the 1D optimum of that edge clamped to the edge.
+// A splat is culled only if that maximum is below log2(alpha_min) - lo by a margin of 1/16 (in
+// log2 units, 4% in alpha), far above the rounding of the per-pixel evaluation, so no pixel that
+// would blend is ever skipped.
+__device__ __forceinline__ bool may_reach(const Splat& sp, float lamin, float cx, float cy, float hw, float hh) {
+  const float ulo = __half2float(__ushort_as_half((unsigned short)(sp.uvlo & 0xFFFFu)));
+  const float vlo = __half2float(__ushort_as_half((unsigned short)(sp.uvlo >> 16)));
+  const float x0 = (cx - hw - sp.u) - ulo, x1 = (cx + hw - sp.u) - ulo;
+  const float y0 = (cy - hh - sp.v) - vlo, y1 = (cy + hh - sp.v) - vlo;
+  if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
+  const float ca = sp.ca, cb = sp.cb, cc = sp.cc;     // ca, cc < 0 (positive-definite conic)
+  // edge optima dy = kx dx, dx = ky dy (approximate: an error there lowers the edge maximum only
+  // to second order, far inside the margin)
+  const float kx = -0.5f * cb * rcp_approx(cc), ky = -0.5f * cb * rcp_approx(ca);
+  auto pw = [&](float dx, float dy) { return fmaf(dy, fmaf(cc, dy, cb * dx), ca * dx * dx); };
+  const float d0 = fminf(fmaxf(kx * x0, y0), y1), d1 = fminf(fmaxf(kx * x1, y0), y1);
+  const float e0 = fminf(fmaxf(ky * y0, x0), x1), e1 = fminf(fmaxf(ky * y1, x0), x1);
+  const float best = fmaxf(fmaxf(pw(x0, d0), pw(x1, d1)), fmaxf(pw(e0, y0), pw(e1, y1)));
+  return best >= lamin - sp.lo - 0.0625f;
+}
+
 // Pixel block of the calling warp inside tile (tx, ty): centre and half extents.
 template <int TS, bool BWD>
 __device__ __forceinline__ void warp_block(int tx, int ty, float& cx, float& cy, float& hw, float& hh) {
@@ -233,7 +256,8 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
           if (jl < cnt) {
             const float4 g0 = *reinterpret_cast<const float4*>(&cb[jl].u);
             const float hxy = __uint_as_float(cb[jl].hxy);
-            pass = fabsf(g0.x - wcx) <= half_lo(hxy) + whw && fabsf(g0.y - wcy) <= half_hi(hxy) + whh;
+            pass = fabsf(g0.x - wcx) <= half_lo(hxy) + whw && fabsf(g0.y - wcy) <= half_hi(hxy) + whh &&
+                   may_reach(cb[jl], lamin, wcx, wcy, whw, whh);
           }
           live = __ballot_sync(0xffffffffu, pass);
         }
@@ -422,7 +446,8 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
           if (jl < cnt) {
             const float4 g0 = *reinterpret_cast<const float4*>(&cb[jl].u);
             const float hxy = __uint_as_float(cb[jl].hxy);
-            pass = fabsf(g0.x - wcx) <= half_lo(hxy) + whw && fabsf(g0.y - wcy) <= half_hi(hxy) + whh;
+            pass = fabsf(g0.x - wcx) <= half_lo(hxy) + whw && fabsf(g0.y - wcy) <= half_hi(hxy) + whh &&
+                   may_reach(cb[jl], lamin, wcx, wcy, whw, whh);
           }
           live = __ballot_sync(0xffffffffu, pass);
         }

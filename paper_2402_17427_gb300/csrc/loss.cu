@@ -7,7 +7,9 @@
 // and dL/dx(q) = l1' + (w * a)(q) + 2 x(q) (w * b)(q) + y(q) (w * c)(q), where a, b, c are
 // dL/dS times dS/dmx, dS/dexx, dS/dexy at every pixel (the window is symmetric, so correlation
 // with it is its own adjoint).  Two kernels: moments -> (a, b, c) maps + partial sums, then the
-// transposed convolution of the maps.  32x32 output tiles, halo 5, separable passes in smem.
+// transposed convolution of the maps.  32x32 output tiles, halo 5, separable passes in shared
+// memory, each thread sliding an 11-tap window along 8 outputs so every staged value is read
+// once per pass.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -19,6 +21,11 @@ namespace vg {
 namespace {
 
 constexpr int LT = 32, HALO = 5, LTH = LT + 2 * HALO;
+constexpr int kLossThreads = 128;
+constexpr int G = 8;                 // consecutive outputs per thread in each separable pass
+constexpr int SPX = LTH + 1;         // odd row pitches: lanes on different rows hit different banks
+constexpr int SPH = LT + 1;
+constexpr int kStage = (LTH * LTH + kLossThreads - 1) / kLossThreads;   // staged values per thread
 
 struct Win {
   float w[11];
@@ -37,71 +44,104 @@ __device__ __forceinline__ double block_sum(float v, double* sm) {
   return t;
 }
 
-__global__ void __launch_bounds__(256) ssim_forward_kernel(const float* __restrict__ x, const float* __restrict__ y,
-                                                           int W, int H, Win win, float dLdS,
-                                                           float* __restrict__ maps, double* __restrict__ partials) {
-  __shared__ float sx[LTH][LTH + 1], sy[LTH][LTH + 1];
-  __shared__ float hs[5][LTH][LT + 1];
-  __shared__ double red[8];
+// One separable 11-tap pass over G consecutive outputs: out[f][j] = sum_k w[k] in[f](j + k), the
+// G + 10 inputs read once each (sliding window in registers), taps accumulated in increasing k.
+template <int F, typename Load>
+__device__ __forceinline__ void window_pass(const Win& win, Load load, float (&out)[F][G]) {
+#pragma unroll
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int j = 0; j < G; ++j) out[f][j] = 0.f;
+#pragma unroll
+  for (int i = 0; i < G + 10; ++i) {
+    float v[F];
+    load(i, v);
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      const int k = i - j;
+      if (k >= 0 && k <= 10) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) out[f][j] = fmaf(win.w[k], v[f], out[f][j]);
+      }
+    }
+  }
+}
+
+// Moments of a 32x32 output tile: x, y staged with a 5-pixel zero-padded halo; the horizontal
+// pass (42 rows x 4 groups of 8 columns) and the vertical pass (32 columns x 4 groups of 8 rows)
+// each slide an 11-tap window along G outputs per thread.
+__global__ void __launch_bounds__(kLossThreads) ssim_forward_kernel(const float* __restrict__ x,
+                                                                    const float* __restrict__ y, int W, int H,
+                                                                    Win win, float dLdS, float* __restrict__ maps,
+                                                                    double* __restrict__ partials) {
+  __shared__ float sx[LTH][SPX], sy[LTH][SPX];
+  __shared__ float hs[5][LTH][SPH];
+  __shared__ double red[kLossThreads / 32];
   const int c = blockIdx.z;
   const int ox = blockIdx.x * LT, oy = blockIdx.y * LT;
   const size_t plane = (size_t)W * H;
   const float* X = x + c * plane;
   const float* Y = y + c * plane;
-  for (int i = threadIdx.x; i < LTH * LTH; i += blockDim.x) {
-    const int r = i / LTH, q = i % LTH;
-    const int gy = oy - HALO + r, gx = ox - HALO + q;
-    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-    sx[r][q] = in ? X[(size_t)gy * W + gx] : 0.f;
-    sy[r][q] = in ? Y[(size_t)gy * W + gx] : 0.f;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < LTH * LT; i += blockDim.x) {
-    const int r = i / LT, q = i % LT;
-    float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+  // staging: all copies in flight at once (asynchronous, zero-filled outside the image)
 #pragma unroll
-    for (int t = 0; t < 11; ++t) {
-      const float vx = sx[r][q + t], vy = sy[r][q + t], w = win.w[t];
-      a0 = fmaf(w, vx, a0);
-      a1 = fmaf(w, vy, a1);
-      a2 = fmaf(w, vx * vx, a2);
-      a3 = fmaf(w, vy * vy, a3);
-      a4 = fmaf(w, vx * vy, a4);
+  for (int k = 0; k < kStage; ++k) {
+    const int i = threadIdx.x + k * kLossThreads;
+    if (i < LTH * LTH) {
+      const int r = i / LTH, q = i % LTH;
+      const int gy = oy - HALO + r, gx = ox - HALO + q;
+      const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+      const size_t off = in ? (size_t)gy * W + gx : 0;
+      cp_async4_zfill(&sx[r][q], X + off, in);
+      cp_async4_zfill(&sy[r][q], Y + off, in);
     }
-    hs[0][r][q] = a0; hs[1][r][q] = a1; hs[2][r][q] = a2; hs[3][r][q] = a3; hs[4][r][q] = a4;
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int t = threadIdx.x; t < (LT / G) * LTH; t += kLossThreads) {
+    const int g = t / LTH, r = t % LTH;
+    float a[5][G];
+    window_pass<5>(win, [&](int i, float (&v)[5]) {
+      const float vx = sx[r][g * G + i], vy = sy[r][g * G + i];
+      v[0] = vx; v[1] = vy; v[2] = vx * vx; v[3] = vy * vy; v[4] = vx * vy;
+    }, a);
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+#pragma unroll
+      for (int j = 0; j < G; ++j) hs[f][r][g * G + j] = a[f][j];
   }
   __syncthreads();
   const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-  float ssum = 0.f, l1sum = 0.f;     // at most 4 pixels per thread; the block sum is in FP64
-  for (int i = threadIdx.x; i < LT * LT; i += blockDim.x) {
-    const int r = i / LT, q = i % LT;
-    const int gx = ox + q, gy = oy + r;
-    if (gx >= W || gy >= H) continue;
-    float mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+  float ssum = 0.f, l1sum = 0.f;
+  {
+    const int q = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * G;
+    float m[5][G];
+    window_pass<5>(win, [&](int i, float (&v)[5]) {
 #pragma unroll
-    for (int t = 0; t < 11; ++t) {
-      const float w = win.w[t];
-      mx = fmaf(w, hs[0][r + t][q], mx);
-      my = fmaf(w, hs[1][r + t][q], my);
-      exx = fmaf(w, hs[2][r + t][q], exx);
-      eyy = fmaf(w, hs[3][r + t][q], eyy);
-      exy = fmaf(w, hs[4][r + t][q], exy);
+      for (int f = 0; f < 5; ++f) v[f] = hs[f][r0 + i][q];
+    }, m);
+    const int gx = ox + q;
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      const int gy = oy + r0 + j;
+      if (gx >= W || gy >= H) continue;
+      l1sum += fabsf(sx[HALO + r0 + j][HALO + q] - sy[HALO + r0 + j][HALO + q]);
+      const float mx = m[0][j], my = m[1][j], exx = m[2][j], eyy = m[3][j], exy = m[4][j];
+      const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+      const float N1 = 2.f * mx * my + C1, N2 = 2.f * sxy + C2;
+      const float D1 = mx * mx + my * my + C1, D2 = sxx + syy + C2;
+      const float iD1 = __frcp_rn(D1), iD2 = __frcp_rn(D2);
+      const float iD = iD1 * iD2;
+      const float S = N1 * N2 * iD;
+      const float dS_dmx = 2.f * my * (N2 - N1) * iD - 2.f * mx * S * (iD1 - iD2);
+      const float dS_dexx = -S * iD2;
+      const float dS_dexy = 2.f * N1 * iD;
+      const size_t pix = (size_t)gy * W + gx;
+      maps[(0 * 3 + c) * plane + pix] = dLdS * dS_dmx;
+      maps[(1 * 3 + c) * plane + pix] = dLdS * dS_dexx;
+      maps[(2 * 3 + c) * plane + pix] = dLdS * dS_dexy;
+      ssum += S;
     }
-    const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-    const float N1 = 2.f * mx * my + C1, N2 = 2.f * sxy + C2;
-    const float D1 = mx * mx + my * my + C1, D2 = sxx + syy + C2;
-    const float iD1 = __frcp_rn(D1), iD2 = __frcp_rn(D2);
-    const float iD = iD1 * iD2;
-    const float S = N1 * N2 * iD;
-    const float dS_dmx = 2.f * my * (N2 - N1) * iD - 2.f * mx * S * (iD1 - iD2);
-    const float dS_dexx = -S * iD2;
-    const float dS_dexy = 2.f * N1 * iD;
-    const size_t pix = (size_t)gy * W + gx;
-    maps[(0 * 3 + c) * plane + pix] = dLdS * dS_dmx;
-    maps[(1 * 3 + c) * plane + pix] = dLdS * dS_dexx;
-    maps[(2 * 3 + c) * plane + pix] = dLdS * dS_dexy;
-    ssum += S;
-    l1sum += fabsf(sx[r + HALO][q + HALO] - sy[r + HALO][q + HALO]);
   }
   const double ts = block_sum(ssum, red);
   const double tl = block_sum(l1sum, red);
@@ -135,53 +175,62 @@ __global__ void __launch_bounds__(1024) loss_finalize(const double* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(256) ssim_backward_kernel(const float* __restrict__ x, const float* __restrict__ y,
-                                                            const float* __restrict__ maps, int W, int H, Win win,
-                                                            float l1_scale, float* __restrict__ grad) {
-  __shared__ float sm[3][LTH][LTH + 1];
-  __shared__ float hs[3][LTH][LT + 1];
+// dL/dx: the three maps correlated with the window (same staging and passes as the moments),
+// combined with x, y and the L1 sign at each output pixel.
+__global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float* __restrict__ x,
+                                                                     const float* __restrict__ y,
+                                                                     const float* __restrict__ maps, int W, int H,
+                                                                     Win win, float l1_scale,
+                                                                     float* __restrict__ grad) {
+  __shared__ float sm[3][LTH][SPX];
+  __shared__ float hs[3][LTH][SPH];
   const int c = blockIdx.z;
   const int ox = blockIdx.x * LT, oy = blockIdx.y * LT;
   const size_t plane = (size_t)W * H;
-  for (int i = threadIdx.x; i < LTH * LTH; i += blockDim.x) {
-    const int r = i / LTH, q = i % LTH;
-    const int gy = oy - HALO + r, gx = ox - HALO + q;
-    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-    const size_t pix = (size_t)gy * W + gx;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) sm[m][r][q] = in ? maps[(m * 3 + c) * plane + pix] : 0.f;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < LTH * LT; i += blockDim.x) {
-    const int r = i / LT, q = i % LT;
-    float a0 = 0, a1 = 0, a2 = 0;
+  for (int k = 0; k < kStage; ++k) {
+    const int i = threadIdx.x + k * kLossThreads;
+    if (i < LTH * LTH) {
+      const int r = i / LTH, q = i % LTH;
+      const int gy = oy - HALO + r, gx = ox - HALO + q;
+      const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+      const size_t pix = in ? (size_t)gy * W + gx : 0;
 #pragma unroll
-    for (int t = 0; t < 11; ++t) {
-      const float w = win.w[t];
-      a0 = fmaf(w, sm[0][r][q + t], a0);
-      a1 = fmaf(w, sm[1][r][q + t], a1);
-      a2 = fmaf(w, sm[2][r][q + t], a2);
+      for (int f = 0; f < 3; ++f) cp_async4_zfill(&sm[f][r][q], maps + (f * 3 + c) * plane + pix, in);
     }
-    hs[0][r][q] = a0; hs[1][r][q] = a1; hs[2][r][q] = a2;
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int t = threadIdx.x; t < (LT / G) * LTH; t += kLossThreads) {
+    const int g = t / LTH, r = t % LTH;
+    float a[3][G];
+    window_pass<3>(win, [&](int i, float (&v)[3]) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) v[f] = sm[f][r][g * G + i];
+    }, a);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int j = 0; j < G; ++j) hs[f][r][g * G + j] = a[f][j];
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < LT * LT; i += blockDim.x) {
-    const int r = i / LT, q = i % LT;
-    const int gx = ox + q, gy = oy + r;
+  const int q = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * G;
+  float cm[3][G];
+  window_pass<3>(win, [&](int i, float (&v)[3]) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) v[f] = hs[f][r0 + i][q];
+  }, cm);
+  const int gx = ox + q;
+#pragma unroll
+  for (int j = 0; j < G; ++j) {
+    const int gy = oy + r0 + j;
     if (gx >= W || gy >= H) continue;
-    float ca = 0, cb = 0, cc = 0;
-#pragma unroll
-    for (int t = 0; t < 11; ++t) {
-      const float w = win.w[t];
-      ca = fmaf(w, hs[0][r + t][q], ca);
-      cb = fmaf(w, hs[1][r + t][q], cb);
-      cc = fmaf(w, hs[2][r + t][q], cc);
-    }
     const size_t pix = c * plane + (size_t)gy * W + gx;
     const float xv = x[pix], yv = y[pix];
     const float d = xv - yv;
     const float l1g = d > 0.f ? l1_scale : (d < 0.f ? -l1_scale : 0.f);
-    grad[pix] = l1g + ca + 2.f * xv * cb + yv * cc;
+    grad[pix] = l1g + cm[0][j] + 2.f * xv * cm[1][j] + yv * cm[2][j];
   }
 }
 
@@ -220,10 +269,10 @@ extern "C" vg_status vg_loss_l1_dssim(const float* img, const float* target, int
   const double inv = 1.0 / (3.0 * (double)plane);
   const Win win = make_window();
   note_launches(out_grad ? 3 : 2);
-  ssim_forward_kernel<<<grid, 256, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
+  ssim_forward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
   loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
   if (out_grad)
-    ssim_backward_kernel<<<grid, 256, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
+    ssim_backward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
   return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;
 }
 
@@ -289,9 +338,9 @@ extern "C" vg_status vg_loss_l1_dssim_noalloc(const float* img, const float* tar
   note_launches(out_grad ? 3 : 2);
   // every map entry and partial these kernels read is written earlier in the same call, so the
   // scratch needs no clearing between calls
-  ssim_forward_kernel<<<grid, 256, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
+  ssim_forward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
   loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
   if (out_grad)
-    ssim_backward_kernel<<<grid, 256, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
+    ssim_backward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
   return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;
 }
