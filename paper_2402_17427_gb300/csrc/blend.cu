@@ -503,8 +503,9 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
             const float dal = Tb * cg - B[p] * rom;
             B[p] = fmaf(cg, aT, B[p]);
             T[p] = ok ? Tb : T[p];
-            // where alpha is clamped to alpha_max it does not depend on the power
-            const float dpow = ok && araw < amax ? dal * a : 0.f;
+            // where alpha is clamped to alpha_max it does not depend on the power (a pixel
+            // this Gaussian does not reach has a = 0, hence dal * a = 0)
+            const float dpow = araw < amax ? dal * a : 0.f;
             const float dpy = dpow * dy;
             S0 += dpow;
             S1 += dpy;
