@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -295,6 +296,18 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
   return cuda_status(cudaGetLastError());
 }
 
+// One non-blocking helper stream per device for work forked off the caller's stream.
+cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
+}
+
 // Backward pass of a prepared call (the table carries dL, final T, last and the gradient outputs).
 vg_status run_backward(Call& c, const vg_raster_opts* opts0, void* workspace, size_t workspace_bytes,
                        int64_t pair_capacity, bool abs, cudaStream_t s) {
@@ -307,17 +320,36 @@ vg_status run_backward(Call& c, const vg_raster_opts* opts0, void* workspace, si
   const vg_stage_events* ev = opts0->events;
   if (cudaMemcpyAsync(ws + L.tables, c.table.data(), c.table.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return VG_ERR_CUDA;
+  const bool accumulate = (opts0->flags & VG_FLAG_ACCUMULATE_GRADS) != 0;
   stage_event(ev, VG_STAGE_BLEND_BACKWARD, true, s);
   cudaError_t e = launch_blend_backward(tab, c.plan, L, ws, abs, s);
-  if (e != cudaSuccess) return VG_ERR_CUDA;
   stage_event(ev, VG_STAGE_BLEND_BACKWARD, false, s);
+  if (e != cudaSuccess) return VG_ERR_CUDA;
   stage_event(ev, VG_STAGE_PROJECT_BACKWARD, true, s);
-  e = launch_preprocess_backward(tab, c.total_n, c.degree, reinterpret_cast<const Splat*>(ws + L.splats),
-                                 reinterpret_cast<const uint32_t*>(ws + L.touched),
-                                 reinterpret_cast<const uint32_t*>(ws + L.vis_ids),
-                                 reinterpret_cast<const WsHeader*>(ws + L.header),
-                                 reinterpret_cast<const float*>(ws + L.g2d),
-                                 (opts0->flags & VG_FLAG_ACCUMULATE_GRADS) != 0, s);
+  // The dense zeroing of the culled Gaussians' gradients (HBM-bound) runs on a side stream beside
+  // the adjoint of the visible ones (latency-bound); it is forked from s here and joined back into
+  // s before the call returns.
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (!accumulate && c.total_n > 0) {
+    cudaStream_t side = side_stream();
+    if (!side || cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)
+      return VG_ERR_CUDA;
+    cudaEventRecord(fork, s);
+    cudaStreamWaitEvent(side, fork, 0);
+    e = launch_zero_culled(tab, c.total_n, c.degree, reinterpret_cast<const uint32_t*>(ws + L.touched), side);
+    cudaEventRecord(join, side);
+  }
+  if (e == cudaSuccess)
+    e = launch_preprocess_backward(tab, c.total_n, c.degree, reinterpret_cast<const Splat*>(ws + L.splats),
+                                   reinterpret_cast<const uint32_t*>(ws + L.vis_ids),
+                                   reinterpret_cast<const WsHeader*>(ws + L.header),
+                                   reinterpret_cast<const float*>(ws + L.g2d), accumulate, s);
+  if (join) {
+    cudaStreamWaitEvent(s, join, 0);   // always joined, so no work of the call outlives it on s
+    cudaEventDestroy(fork);            // released once the recorded work completes
+    cudaEventDestroy(join);
+  }
   stage_event(ev, VG_STAGE_PROJECT_BACKWARD, false, s);
   return cuda_status(e);
 }

@@ -189,9 +189,14 @@ struct HostPlan {
 // ---- launchers (each returns the first CUDA error it hits) ----
 cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Splat* splats, uint2* rects,
                               uint32_t* touched, uint32_t* dkey, WsHeader* hdr, cudaStream_t s);
+// Adjoint of the projection for the visible Gaussians (gradients of the culled ones are left
+// to launch_zero_culled, or untouched when accumulating).
 cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int degree, const Splat* splats,
-                                       const uint32_t* touched, const uint32_t* vis_ids, const WsHeader* hdr,
-                                       const float* g2d, bool accumulate, cudaStream_t s);
+                                       const uint32_t* vis_ids, const WsHeader* hdr, const float* g2d,
+                                       bool accumulate, cudaStream_t s);
+// Zero gradients of every culled Gaussian (dense gradient outputs).
+cudaError_t launch_zero_culled(const DevTables* tab, int total_n, int degree, const uint32_t* touched,
+                               cudaStream_t s);
 
 // Depth order of the visible Gaussians, pair generation, tile sort, ranges, the tile-ordered copy
 // of the splats and the largest-first order of the tiles.

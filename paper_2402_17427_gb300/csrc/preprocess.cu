@@ -561,30 +561,32 @@ cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Spl
   return cudaGetLastError();
 }
 
+cudaError_t launch_zero_culled(const DevTables* tab, int total_n, int degree, const uint32_t* touched,
+                               cudaStream_t s) {
+  if (total_n == 0) return cudaSuccess;
+  const int zb = (total_n + 255) / 256;
+  note_launches(1);
+  switch (degree) {
+    case 0: zero_culled_grads<0><<<zb, 256, 0, s>>>(tab, total_n, touched); break;
+    case 1: zero_culled_grads<1><<<zb, 256, 0, s>>>(tab, total_n, touched); break;
+    case 2: zero_culled_grads<2><<<zb, 256, 0, s>>>(tab, total_n, touched); break;
+    default: zero_culled_grads<3><<<zb, 256, 0, s>>>(tab, total_n, touched); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int degree, const Splat* splats,
-                                       const uint32_t* touched, const uint32_t* vis_ids, const WsHeader* hdr,
-                                       const float* g2d, bool accumulate, cudaStream_t s) {
+                                       const uint32_t* vis_ids, const WsHeader* hdr, const float* g2d,
+                                       bool accumulate, cudaStream_t s) {
   if (total_n == 0) return cudaSuccess;
   const int acc = accumulate ? 1 : 0;
-  const int zb = (total_n + 255) / 256, blocks = (total_n + 127) / 128;
-  note_launches(accumulate ? 1 : 2);
+  const int blocks = (total_n + 127) / 128;
+  note_launches(1);
   switch (degree) {
-    case 0:
-      if (!accumulate) zero_culled_grads<0><<<zb, 256, 0, s>>>(tab, total_n, touched);
-      preprocess_backward_kernel<0><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc);
-      break;
-    case 1:
-      if (!accumulate) zero_culled_grads<1><<<zb, 256, 0, s>>>(tab, total_n, touched);
-      preprocess_backward_kernel<1><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc);
-      break;
-    case 2:
-      if (!accumulate) zero_culled_grads<2><<<zb, 256, 0, s>>>(tab, total_n, touched);
-      preprocess_backward_kernel<2><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc);
-      break;
-    default:
-      if (!accumulate) zero_culled_grads<3><<<zb, 256, 0, s>>>(tab, total_n, touched);
-      preprocess_backward_kernel<3><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc);
-      break;
+    case 0: preprocess_backward_kernel<0><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc); break;
+    case 1: preprocess_backward_kernel<1><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc); break;
+    case 2: preprocess_backward_kernel<2><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc); break;
+    default: preprocess_backward_kernel<3><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc); break;
   }
   return cudaGetLastError();
 }
