@@ -231,7 +231,16 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     }
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-      const uint32_t peers = __match_any_sync(0xffffffffu, dig[k]);
+      // lanes holding the same digit: one ballot per digit bit (plus one for validity)
+      const bool valid = dig[k] != 0xFFFFFFFFu;
+      const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+      uint32_t peers = valid ? vm : ~vm;
+#pragma unroll
+      for (int b = 0; b < kRadixBits; ++b) {
+        const bool bit = (dig[k] >> b) & 1u;
+        const uint32_t bm = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bm : ~bm;
+      }
       unsigned before = 0;
       if (dig[k] != 0xFFFFFFFFu) before = s_cnt[w][dig[k]];
       rnk[k] = before + __popc(peers & lt);
