@@ -281,7 +281,7 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
   stage_event(ev, VG_STAGE_PROJECT, true, s);
   cudaError_t e = launch_preprocess(tab, c.total_n, c.degree, reinterpret_cast<Splat*>(ws + L.splats),
                                     reinterpret_cast<uint2*>(ws + L.rects), reinterpret_cast<uint32_t*>(ws + L.touched),
-                                    reinterpret_cast<uint32_t*>(ws + L.dkey), hdr, s);
+                                    make_compact(L, ws, c.total_n), hdr, s);
   if (e != cudaSuccess) return VG_ERR_CUDA;
   stage_event(ev, VG_STAGE_PROJECT, false, s);
   stage_event(ev, VG_STAGE_SORT, true, s);

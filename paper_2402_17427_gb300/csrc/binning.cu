@@ -3,16 +3,15 @@
 // The result is, per tile, the list of Gaussians whose tile rectangle contains it, ordered by
 // (FP32 depth bits, Gaussian index): exactly the order of a stable sort of the 64-bit keys
 // (tile << 32 | depth bits) emitted in index order.  It is produced in two cheaper steps:
-//   1. the visible Gaussians are compacted (index order kept) and stably radix-sorted by depth
-//      (key minus the minimum key, only the significant bits: V elements, not P);
-//   2. pairs are emitted in that depth order and stably radix-sorted by tile id only
-//      (ceil(log2 tiles) bits), which keeps the depth order inside every tile.
+//   1. the visible Gaussians, compacted in index order by the projection kernel, are stably
+//      radix-sorted by depth (V elements, not P; only the bits in which the keys differ);
+//   2. pairs (tile, depth rank) are emitted in that depth order and stably radix-sorted by tile
+//      id only (ceil(log2 tiles) bits), which keeps the depth order inside every tile.
 // Both sorts are least-significant-digit radix sorts with 8-bit digits and one kernel per
 // digit pass: the digit histograms of all passes are accumulated by the kernel that produces
-// the keys, and every pass finds the output offset of each 4096-key partition by a decoupled
-// look-back over the partitions before it (each partition publishes its digit counts as soon as
-// it has ranked its keys, then its inclusive prefix).  The last tile pass writes the 48-byte
-// splat records in tile order directly.
+// the keys, and every pass finds the output offset of each partition by a decoupled look-back
+// over the partitions before it (each partition publishes its digit counts as soon as it has
+// ranked its keys, then its inclusive prefix).
 // Every kernel takes its element count from device memory, so the whole forward pass is
 // enqueued without a host synchronisation; kernels with no work for this render return early.
 #include <cuda_runtime.h>
@@ -34,50 +33,9 @@ __device__ __forceinline__ void segment(unsigned n, unsigned& begin, unsigned& e
   end = min(n, begin + seg);
 }
 
-// Exclusive block scan over 256 threads (T = unsigned or unsigned long long).
-template <typename T>
-__device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* sm /*[8]*/) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  T x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sm[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    T t = lane < 8 ? sm[lane] : T(0);
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      T y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    if (lane < 8) sm[lane] = t;
-  }
-  __syncthreads();
-  T base = w > 0 ? sm[w - 1] : T(0);
-  *total = sm[7];
-  __syncthreads();
-  return base + x - v;
-}
-
 // ---- look-back sort helpers ------------------------------------------------------------------
 
-constexpr unsigned long long kFlagAggregate = 1ull << 62;   // the partition's own digit count
-constexpr unsigned long long kFlagPrefix = 1ull << 63;      // count of this and all earlier partitions
-constexpr unsigned long long kCountMask = 0xFFFFFFFFull;
 constexpr int kLookback = 8;                                 // status rows read per look-back step
-
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 
 // Adds the digits of `key` for passes [0, passes) to the block histograms h[pass][digit];
 // lanes with the same digit are merged first (match.any), so one shared atomic per distinct
@@ -98,85 +56,6 @@ __device__ __forceinline__ void zero_status(unsigned long long* status, unsigned
     status[i] = 0ull;
 }
 
-// ---- 1. compaction of the visible Gaussians (index order preserved) -------------------------
-
-__global__ void __launch_bounds__(256) compact_count(const uint32_t* __restrict__ dkey, unsigned n,
-                                                     unsigned* __restrict__ blocksums) {
-  unsigned begin, end;
-  segment(n, begin, end, 1024);
-  unsigned c = 0;
-  for (unsigned i = begin + threadIdx.x; i < end; i += blockDim.x) c += dkey[i] != 0xFFFFFFFFu;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  __shared__ unsigned sm[8];
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned t = 0;
-    for (int k = 0; k < 8; ++k) t += sm[k];
-    blocksums[blockIdx.x] = t;
-  }
-}
-
-// Single block: exclusive scan of the per-block counts; V, the significant depth bits and the
-// tile-key bits go to the header.
-__global__ void __launch_bounds__(256) compact_scan(unsigned* __restrict__ blocksums, int B, WsHeader* hdr,
-                                                    unsigned tile_bits) {
-  __shared__ unsigned sm[8];
-  unsigned run = 0;
-  for (int b0 = 0; b0 < B; b0 += 256) {
-    const int b = b0 + threadIdx.x;
-    unsigned v = b < B ? blocksums[b] : 0u, tot;
-    unsigned ex = block_exclusive_scan(v, &tot, sm);
-    if (b < B) blocksums[b] = run + ex;
-    run += tot;
-  }
-  if (threadIdx.x == 0) {
-    hdr->visible = run;
-    const unsigned lo = hdr->dmin, hi = hdr->dmax;
-    hdr->depth_bits = (run > 1 && hi > lo) ? 32u - __clz(hi - lo) : 0u;
-    hdr->tile_bits = tile_bits;
-  }
-}
-
-// Writes the visible Gaussians' keys (depth key - min) and ids in index order, accumulates the
-// digit histograms of the depth-sort passes and clears the first pass's look-back rows.
-__global__ void __launch_bounds__(256) compact_scatter(const uint32_t* __restrict__ dkey, unsigned n,
-                                                       const unsigned* __restrict__ blocksums,
-                                                       const WsHeader* __restrict__ hdr,
-                                                       uint32_t* __restrict__ vkeys, uint32_t* __restrict__ vvals,
-                                                       uint32_t* __restrict__ vis_ids, unsigned* __restrict__ hist,
-                                                       unsigned long long* __restrict__ status0) {
-  __shared__ unsigned sm[8];
-  __shared__ unsigned h[kMaxPasses][kRadix];
-#pragma unroll
-  for (int p = 0; p < kMaxPasses; ++p) h[p][threadIdx.x] = 0;
-  __syncthreads();
-  unsigned begin, end;
-  segment(n, begin, end, 1024);
-  unsigned run = blocksums[blockIdx.x];
-  const unsigned lo = hdr->dmin;
-  const int passes = (int)(hdr->depth_bits + kRadixBits - 1) / kRadixBits;
-  for (unsigned t0 = begin; t0 < end; t0 += 256) {
-    const unsigned i = t0 + threadIdx.x;
-    const uint32_t k = i < end ? dkey[i] : 0xFFFFFFFFu;
-    const unsigned f = k != 0xFFFFFFFFu;
-    unsigned tot;
-    const unsigned ex = block_exclusive_scan(f, &tot, sm);
-    if (f) {
-      vkeys[run + ex] = k - lo;
-      vvals[run + ex] = i;
-      vis_ids[run + ex] = i;     // kept in index order for the adjoint of the projection
-    }
-    histogram_add(h, k - lo, f != 0, passes);
-    run += tot;
-  }
-  __syncthreads();
-  for (int p = 0; p < passes; ++p)
-    if (h[p][threadIdx.x]) atomicAdd(&hist[p * kRadix + threadIdx.x], h[p][threadIdx.x]);
-  zero_status(status0, (hdr->visible + kDepthTile - 1) / kDepthTile);
-}
-
 // ---- radix sort passes (8-bit digits, stable, one kernel per pass, decoupled look-back) -------
 
 // One stable digit pass.  Blocks are persistent and take partitions in increasing order from an
@@ -189,11 +68,17 @@ __global__ void __launch_bounds__(256) compact_scatter(const uint32_t* __restric
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, const unsigned* n_ptr, unsigned cap, const unsigned* bits_ptr, int shift,
+    uint32_t* __restrict__ vout, const unsigned* n_ptr, unsigned cap, bool depth, int shift,
     const unsigned* __restrict__ hist, unsigned* next_part, unsigned long long* status_cur,
     unsigned long long* __restrict__ status_next, WsHeader* hdr) {
   constexpr int TILE = kSortThreads * ITEMS;
-  if (bits_ptr && (unsigned)shift >= *bits_ptr) return;
+  if (depth) {
+    // the depth keys agree above bit 32 - clz(dmin ^ dmax): only the passes below it run
+    const unsigned lo = hdr->dmin, hi = hdr->dmax;
+    const unsigned bits = (*n_ptr > 1 && hi > lo) ? 32u - __clz(lo ^ hi) : 0u;
+    if (shift == 0 && blockIdx.x == 0 && threadIdx.x == 0) hdr->depth_bits = bits;   // for depth_order()
+    if ((unsigned)shift >= bits) return;
+  }
   const unsigned n = min(*n_ptr, cap);
   const unsigned nparts = (n + TILE - 1) / TILE;
   constexpr int WARPS = kSortThreads / 32;
@@ -529,6 +414,30 @@ __global__ void __launch_bounds__(256) order_scatter(const DevTables* __restrict
   }
 }
 
+// The same order built by one block in shared memory (for up to kOrderSmallTiles tiles): one
+// launch instead of count + scan + scatter and a memset.
+constexpr int kOrderSmallTiles = 1 << 16;
+
+__global__ void __launch_bounds__(1024) order_small(const DevTables* __restrict__ tab,
+                                                    const uint2* __restrict__ ranges, int tiles,
+                                                    uint32_t* __restrict__ order) {
+  __shared__ unsigned cnt[kBuckets];
+  for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) cnt[k] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&cnt[tile_bucket(tab, ranges, t)], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int k = 0; k < kBuckets; ++k) {
+      const unsigned c = cnt[k];
+      cnt[k] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) order[atomicAdd(&cnt[tile_bucket(tab, ranges, t)], 1u)] = (uint32_t)t;
+}
+
 int ceil_log2(unsigned x) {
   int b = 0;
   while ((1u << b) < x) ++b;
@@ -561,7 +470,6 @@ Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
   L.splats = take(N * 48);
   L.rects = take(N * 8);
   L.touched = take(N * 4);
-  L.dkey = take(N * 4);
   L.vis_ids = take(N * 4);
   L.vkeys[0] = take(N * 4); L.vkeys[1] = take(N * 4);
   L.vvals[0] = take(N * 4); L.vvals[1] = take(N * 4);
@@ -579,6 +487,20 @@ Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
   L.g2d = take(N * 9 * 4);
   L.total = o;
   return L;
+}
+
+Compact make_compact(const Layout& L, char* ws, int total_n) {
+  Compact c;
+  c.vkeys = reinterpret_cast<uint32_t*>(ws + L.vkeys[0]);
+  c.vvals = reinterpret_cast<uint32_t*>(ws + L.vvals[0]);
+  c.vis_ids = reinterpret_cast<uint32_t*>(ws + L.vis_ids);
+  SortCtl* ctl = reinterpret_cast<SortCtl*>(ws + L.sortctl);
+  c.hist = ctl->hist[0][0];
+  c.ticket = &ctl->ticket;
+  c.status = reinterpret_cast<unsigned long long*>(ws + L.status[1]);
+  c.zero = reinterpret_cast<unsigned long long*>(ws + L.status[0]);
+  c.zero_words = (size_t)((total_n + kDepthTile - 1) / kDepthTile) * kRadix;
+  return c;
 }
 
 // Resident blocks of a look-back pass on this device (persistent grid).
@@ -604,7 +526,6 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   auto S64 = [&](int k) { return reinterpret_cast<unsigned long long*>(ws + L.status[k]); };
   Splat* splats = reinterpret_cast<Splat*>(ws + L.splats);
   Splat* vsplats = reinterpret_cast<Splat*>(ws + L.vsplats);
-  unsigned* bsum = U(L.blocksums);
   unsigned long long* bsum64 = reinterpret_cast<unsigned long long*>(ws + L.blocksums);
   const unsigned cap = (unsigned)(capacity > 0xFFFFFFFFll ? 0xFFFFFFFFll : capacity);
   const unsigned tile_bits = (unsigned)ceil_log2((unsigned)tiles);
@@ -612,19 +533,16 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   const int OBD = std::max(1, std::min(onesweep_blocks<kDepthItems>(), (n + kDepthTile - 1) / kDepthTile));
   const int OBT = (int)std::max<int64_t>(1, std::min<int64_t>(onesweep_blocks<kTileItems>(), ((int64_t)cap + kTileTile - 1) / kTileTile));
 
-  // 1. compaction + depth sort (passes beyond the significant bits return at once; the result
-  //    sits in the buffer depth_order() names)
-  compact_count<<<B, 256, 0, s>>>(U(L.dkey), (unsigned)n, bsum);
-  compact_scan<<<1, 256, 0, s>>>(bsum, B, hdr, tile_bits);
-  const int tpasses = std::max(1, ((int)tile_bits + kRadixBits - 1) / kRadixBits);
-  compact_scatter<<<B, 256, 0, s>>>(U(L.dkey), (unsigned)n, bsum, hdr, U(L.vkeys[0]), U(L.vvals[0]), U(L.vis_ids),
-                                    ctl->hist[0][0], S64(0));
+  // 1. depth sort of the visible Gaussians (compacted by the projection kernel); passes beyond
+  //    the bits the keys differ in return at once, and the result sits in the buffer
+  //    depth_order() names
   for (int pass = 0; pass < kMaxPasses; ++pass) {
     const int src = pass & 1, dst = src ^ 1;
     onesweep_pass<kDepthItems><<<OBD, kSortThreads, 0, s>>>(U(L.vkeys[src]), U(L.vvals[src]), U(L.vkeys[dst]), U(L.vvals[dst]),
-                                              &hdr->visible, 0xFFFFFFFFu, &hdr->depth_bits, pass * kRadixBits,
+                                              &hdr->visible, 0xFFFFFFFFu, true, pass * kRadixBits,
                                               ctl->hist[0][pass], &ctl->next_part[0][pass], S64(src), S64(dst), hdr);
   }
+  const int tpasses = std::max(1, ((int)tile_bits + kRadixBits - 1) / kRadixBits);
   // 2. pairs in depth order, written where the tile sort's passes leave the result in buffer 0
   const int p0 = tpasses & 1;
   const int BP = kMaxSortBlocks < 6 * B / 2 ? kMaxSortBlocks : 6 * B / 2;   // 6 blocks per SM
@@ -637,21 +555,27 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   for (int pass = 0; pass < tpasses; ++pass) {
     const int src = (p0 + pass) & 1, dst = src ^ 1;
     onesweep_pass<kTileItems><<<OBT, kSortThreads, 0, s>>>(U(L.pkeys[src]), U(L.pvals[src]), U(L.pkeys[dst]), U(L.pvals[dst]),
-                                              &hdr->pair_n, cap, nullptr, pass * kRadixBits, ctl->hist[1][pass],
+                                              &hdr->pair_n, cap, false, pass * kRadixBits, ctl->hist[1][pass],
                                               &ctl->next_part[1][pass], S64(pass & 1),
                                               pass + 1 < tpasses ? S64((pass + 1) & 1) : nullptr, hdr);
   }
-  note_launches(3 + kMaxPasses + 4 + tpasses + 4);
+  note_launches(kMaxPasses + 4 + tpasses + 1);
   uint2* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
   cudaMemsetAsync(ranges, 0, (size_t)tiles * sizeof(uint2), s);
   tile_ranges<<<B * 4, 256, 0, s>>>(U(L.pkeys[0]), hdr, (unsigned)tiles, ranges);
   // 4. largest-first tile order
-  unsigned* buckets = U(L.buckets);
-  cudaMemsetAsync(buckets, 0, kBuckets * sizeof(unsigned), s);
-  const int tgrid = (tiles + 255) / 256;
-  order_count<<<tgrid, 256, 0, s>>>(tab, ranges, tiles, buckets);
-  order_scan<<<1, 32, 0, s>>>(buckets);
-  order_scatter<<<tgrid, 256, 0, s>>>(tab, ranges, tiles, buckets, U(L.order));
+  if (tiles <= kOrderSmallTiles) {
+    order_small<<<1, 1024, 0, s>>>(tab, ranges, tiles, U(L.order));
+    note_launches(1);
+  } else {
+    unsigned* buckets = U(L.buckets);
+    cudaMemsetAsync(buckets, 0, kBuckets * sizeof(unsigned), s);
+    const int tgrid = (tiles + 255) / 256;
+    order_count<<<tgrid, 256, 0, s>>>(tab, ranges, tiles, buckets);
+    order_scan<<<1, 32, 0, s>>>(buckets);
+    order_scatter<<<tgrid, 256, 0, s>>>(tab, ranges, tiles, buckets, U(L.order));
+    note_launches(3);
+  }
   return cudaGetLastError();
 }
 

@@ -108,9 +108,9 @@ struct WsHeader {
   unsigned int visible;         // V
   unsigned int status;          // VG_STATUS_* bits
   unsigned int dmin, dmax;      // min / max depth key over visible Gaussians
-  unsigned int depth_bits;      // significant bits of (key - dmin)
+  unsigned int depth_bits;      // bits the depth keys differ in: 32 - clz(dmin ^ dmax)
   unsigned int pair_n;          // min(pairs, capacity): pairs actually sorted
-  unsigned int tile_bits;       // bits of the tile key
+  unsigned int tile_bits;       // unused (kept for the header layout)
   unsigned int work_fwd[kTileClasses];   // persistent-blend work queues (next item)
   unsigned int work_bwd[kTileClasses];
   unsigned int pad[3];
@@ -157,13 +157,14 @@ constexpr int kMaxPasses = 4;                           // 32-bit keys
 struct SortCtl {
   unsigned hist[2][kMaxPasses][kRadix];
   unsigned next_part[2][kMaxPasses];
+  unsigned ticket;                 // block tickets of the projection kernel's compaction
 };
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 // Offsets (bytes) of the regions of one render workspace (any number of views / segments).
 struct Layout {
-  size_t header, sortctl, tables, splats, rects, touched, dkey, vis_ids, vkeys[2], vvals[2], pkeys[2], pvals[2],
+  size_t header, sortctl, tables, splats, rects, touched, vis_ids, vkeys[2], vvals[2], pkeys[2], pvals[2],
       vsplats, ranges, order, buckets, blocksums, status[2], g2d, total;
 };
 Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t pair_capacity);
@@ -187,8 +188,20 @@ struct HostPlan {
 };
 
 // ---- launchers (each returns the first CUDA error it hits) ----
+// Outputs of the compaction fused into the projection kernel.
+struct Compact {
+  uint32_t* vkeys;                 // depth keys (FP32 bits) of the visible Gaussians, index order
+  uint32_t* vvals;                 // their ids (the depth sort's values)
+  uint32_t* vis_ids;               // their ids again (kept in index order for the adjoint)
+  unsigned* hist;                  // [kMaxPasses][kRadix] digit histograms of the depth keys
+  unsigned* ticket;                // block ticket counter (cleared per render)
+  unsigned long long* status;      // one look-back word per block (cleared by the launcher)
+  unsigned long long* zero;        // look-back rows of the first depth pass, cleared here
+  size_t zero_words;
+};
 cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Splat* splats, uint2* rects,
-                              uint32_t* touched, uint32_t* dkey, WsHeader* hdr, cudaStream_t s);
+                              uint32_t* touched, const Compact& cp, WsHeader* hdr, cudaStream_t s);
+Compact make_compact(const Layout& L, char* ws, int total_n);   // regions of the workspace
 // Adjoint of the projection for the visible Gaussians (gradients of the culled ones are left
 // to launch_zero_culled, or untouched when accumulating).
 cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int degree, const Splat* splats,

@@ -238,85 +238,107 @@ __device__ __forceinline__ void project(const KGauss& g, const KCam& cm, const K
 template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __restrict__ tab, int total_n,
                                                          Splat* __restrict__ splats, uint2* __restrict__ rects,
-                                                         uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey,
+                                                         uint32_t* __restrict__ touched, const Compact cp,
                                                          WsHeader* __restrict__ hdr) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // blocks take their Gaussians in ticket order, so the look-back below only ever waits on
+  // blocks that are already running
+  __shared__ unsigned s_blk, s_base;
+  __shared__ unsigned s_sm[8];
+  __shared__ unsigned s_h[kMaxPasses][kRadix];
+  if (threadIdx.x == 0) s_blk = atomicAdd(cp.ticket, 1u);
+#pragma unroll
+  for (int p = 0; p < kMaxPasses; ++p) s_h[p][threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned blk = s_blk;
+  const int i = (int)(blk * blockDim.x + threadIdx.x);
   uint32_t key = 0xFFFFFFFFu, lo_key = 0xFFFFFFFFu, hi_key = 0u;
+  // 1. projection, tile rectangle and visibility
+  const KSeg* sg = nullptr;
+  int li = 0;
+  Proj P;
+  P.valid = false;
+  bool vis = false;
   if (i < total_n) {
-    const KSeg& sg = tseg(tab, find_seg(tab, i));
-    const KView& vw = tview(tab, sg.view);
-    const KCam cm = vw.cam;
-    const KOpts op = vw.op;
-    const int li = i - sg.offset;
-    Proj P;
-    project(sg.g, cm, op, li, P);
+    sg = &tseg(tab, find_seg(tab, i));
+    const KView& vw = tview(tab, sg->view);
+    li = i - sg->offset;
+    project(sg->g, vw.cam, vw.op, li, P);
     uint32_t cnt = 0;
     if (P.valid) {
-      const int T = op.tile;
-      int xlo = rect_lo(P.u, P.r, cm.W), xhi = rect_hi(P.u, P.r, cm.W);
-      int ylo = rect_lo(P.v, P.r, cm.H), yhi = rect_hi(P.v, P.r, cm.H);
+      const int T = vw.op.tile;
+      int xlo = rect_lo(P.u, P.r, vw.cam.W), xhi = rect_hi(P.u, P.r, vw.cam.W);
+      int ylo = rect_lo(P.v, P.r, vw.cam.H), yhi = rect_hi(P.v, P.r, vw.cam.H);
       if (xlo <= xhi && ylo <= yhi) {
         const int tx0 = xlo / T, tx1 = xhi / T, ty0 = ylo / T, ty1 = yhi / T;
         cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
         rects[i] = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
-        // colour from spherical harmonics along the viewing direction
-        constexpr int K = (DEG + 1) * (DEG + 1);
-        float d0 = P.m[0] - cm.cam_pos[0], d1 = P.m[1] - cm.cam_pos[1], d2 = P.m[2] - cm.cam_pos[2];
-        const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-        d0 *= il; d1 *= il; d2 *= il;
-        float Y[16], c[3 * K];
-        sh_basis<DEG>(d0, d1, d2, Y);
-        load_sh<DEG>(sg.g.sh, li, c);
-        float rgb[3];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          float acc = 0.5f;
-#pragma unroll
-          for (int k = 0; k < K; ++k) acc = fmaf(c[3 * k + ch], Y[k], acc);
-          rgb[ch] = fmaxf(0.f, acc);
-        }
-        const float o = 1.f / (1.f + expf(-__ldg(sg.g.logits + li)));
-        // the mean's projection for blending, as a double-float (see df_dot3)
-        float xh, xl, yh, yl, zh, zl;
-        df_dot3(cm.R, cm.t[0], P.m, xh, xl);
-        df_dot3(cm.R + 3, cm.t[1], P.m, yh, yl);
-        df_dot3(cm.R + 6, cm.t[2], P.m, zh, zl);
-        float uh, ul, vh, vl;
-        df_project(xh, xl, zh, zl, cm.fx, cm.cx, uh, ul);
-        df_project(yh, yl, zh, zl, cm.fy, cm.cy, vh, vl);
-        Splat s;
-        s.u = uh;
-        s.v = vh;
-        s.uvlo = (uint32_t)__half_as_ushort(__float2half_rn(ul)) | ((uint32_t)__half_as_ushort(__float2half_rn(vl)) << 16);
-        s.ca = -0.5f * kLog2e * P.ca;
-        s.cb = -kLog2e * P.cb;
-        s.cc = -0.5f * kLog2e * P.cc;
-        s.lo = log2f(o);
-        s.r = rgb[0]; s.g = rgb[1]; s.b = rgb[2];
-        s.rank = 0;
-        // alpha >= alpha_min  <=>  power2 >= tg = log2(alpha_min) - lo;  that region is the
-        // ellipse d^T Sigma2^-1 d <= k2, k2 = 2 ln(opacity / alpha_min), whose bounding box has
-        // half-extents k sqrt(A), k sqrt(C)
-        const float tg = log2f(op.alpha_min) - s.lo;
-        float hx = -65504.f, hy = -65504.f;
-        if (tg <= 0.f) {
-          const float k2 = -2.0f * 0.69314718f * tg;
-          hx = sqrtf(k2 * P.A) * 1.001f + 0.01f;
-          hy = sqrtf(k2 * P.C) * 1.001f + 0.01f;
-        }
-        s.hxy = (uint32_t)__half_as_ushort(__float2half_ru(hx)) |
-                ((uint32_t)__half_as_ushort(__float2half_ru(hy)) << 16);
-        float4* dst = reinterpret_cast<float4*>(splats + i);
-        const float4* src = reinterpret_cast<const float4*>(&s);
-        dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
+        vis = true;
         key = __float_as_uint(P.depth);
         lo_key = hi_key = key;
       }
     }
     touched[i] = cnt;
-    dkey[i] = key;
   }
-  // min / max depth key over visible Gaussians (for trimming the depth sort)
+  // 2. the block's visible count, published before the heavy per-Gaussian work so that later
+  //    blocks rarely wait in their look-back
+  unsigned tot;
+  const unsigned ex = block_exclusive_scan((unsigned)vis, &tot, s_sm);
+  if (threadIdx.x == 0) st_relaxed(cp.status + blk, (blk == 0 ? kFlagPrefix : kFlagAggregate) | tot);
+  // 3. the splat record: colour from spherical harmonics along the viewing direction, opacity,
+  //    the accurate blending position and the alpha >= alpha_min box
+  if (vis) {
+    const KView& vw = tview(tab, sg->view);
+    const KCam& cm = vw.cam;
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float d0 = P.m[0] - cm.cam_pos[0], d1 = P.m[1] - cm.cam_pos[1], d2 = P.m[2] - cm.cam_pos[2];
+    const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    d0 *= il; d1 *= il; d2 *= il;
+    float Y[16], c[3 * K];
+    sh_basis<DEG>(d0, d1, d2, Y);
+    load_sh<DEG>(sg->g.sh, li, c);
+    float rgb[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float acc = 0.5f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc = fmaf(c[3 * k + ch], Y[k], acc);
+      rgb[ch] = fmaxf(0.f, acc);
+    }
+    const float o = 1.f / (1.f + expf(-__ldg(sg->g.logits + li)));
+    // the mean's projection for blending, as a double-float (see df_dot3)
+    float xh, xl, yh, yl, zh, zl;
+    df_dot3(cm.R, cm.t[0], P.m, xh, xl);
+    df_dot3(cm.R + 3, cm.t[1], P.m, yh, yl);
+    df_dot3(cm.R + 6, cm.t[2], P.m, zh, zl);
+    float uh, ul, vh, vl;
+    df_project(xh, xl, zh, zl, cm.fx, cm.cx, uh, ul);
+    df_project(yh, yl, zh, zl, cm.fy, cm.cy, vh, vl);
+    Splat sp;
+    sp.u = uh;
+    sp.v = vh;
+    sp.uvlo = (uint32_t)__half_as_ushort(__float2half_rn(ul)) | ((uint32_t)__half_as_ushort(__float2half_rn(vl)) << 16);
+    sp.ca = -0.5f * kLog2e * P.ca;
+    sp.cb = -kLog2e * P.cb;
+    sp.cc = -0.5f * kLog2e * P.cc;
+    sp.lo = log2f(o);
+    sp.r = rgb[0]; sp.g = rgb[1]; sp.b = rgb[2];
+    sp.rank = 0;
+    // alpha >= alpha_min  <=>  power2 >= tg = log2(alpha_min) - lo;  that region is the
+    // ellipse d^T Sigma2^-1 d <= k2, k2 = 2 ln(opacity / alpha_min), whose bounding box has
+    // half-extents k sqrt(A), k sqrt(C)
+    const float tg = log2f(vw.op.alpha_min) - sp.lo;
+    float hx = -65504.f, hy = -65504.f;
+    if (tg <= 0.f) {
+      const float k2 = -2.0f * 0.69314718f * tg;
+      hx = sqrtf(k2 * P.A) * 1.001f + 0.01f;
+      hy = sqrtf(k2 * P.C) * 1.001f + 0.01f;
+    }
+    sp.hxy = (uint32_t)__half_as_ushort(__float2half_ru(hx)) | ((uint32_t)__half_as_ushort(__float2half_ru(hy)) << 16);
+    float4* dst = reinterpret_cast<float4*>(splats + i);
+    const float4* src = reinterpret_cast<const float4*>(&sp);
+    dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
+  }
+  // min / max depth key over visible Gaussians (they fix the bits the depth sort needs)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     lo_key = min(lo_key, __shfl_xor_sync(0xffffffffu, lo_key, o));
@@ -326,6 +348,57 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __rest
     atomicMin(&hdr->dmin, lo_key);
     atomicMax(&hdr->dmax, hi_key);
   }
+  // 4. stable compaction of the visible Gaussians (index order): offsets within the block from
+  //    the scan above, the block's offset by a decoupled look-back over the blocks before it
+  if (vis) {
+#pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p) atomicAdd(&s_h[p][(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+  }
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    unsigned excl = 0;
+    if (blk > 0) {
+      // 32 predecessors per step; rows below 0 read as an empty prefix
+      long long p = (long long)blk - 1;
+      const uint64_t start = global_timer_ns();
+      for (;;) {
+        const unsigned long long v = p - lane >= 0 ? ld_relaxed(cp.status + (p - lane)) : kFlagPrefix;
+        const unsigned pre = __ballot_sync(0xffffffffu, (v & kFlagPrefix) != 0);
+        const unsigned nr = __ballot_sync(0xffffffffu, (v & (kFlagPrefix | kFlagAggregate)) == 0);
+        const int first_pre = pre ? __ffs(pre) - 1 : 32, first_nr = nr ? __ffs(nr) - 1 : 32;
+        const bool done = first_pre < first_nr;
+        const int take = done ? first_pre + 1 : first_nr;       // rows consumed this step
+        unsigned part = lane < take ? (unsigned)(v & kCountMask) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        excl += part;
+        if (done) break;
+        p -= take;
+        if (take == 0 && global_timer_ns() - start > 1000000000ull) {   // a predecessor never published
+          if (lane == 0) atomicOr(&hdr->status, (unsigned)VG_STATUS_WAIT_TIMEOUT);
+          break;
+        }
+      }
+      if (lane == 0) st_relaxed(cp.status + blk, kFlagPrefix | (excl + tot));
+    }
+    if (lane == 0) {
+      s_base = excl;
+      if (blk == gridDim.x - 1) hdr->visible = excl + tot;
+    }
+  }
+  __syncthreads();
+  if (vis) {
+    const unsigned at = s_base + ex;
+    cp.vkeys[at] = key;
+    cp.vvals[at] = (uint32_t)i;
+    cp.vis_ids[at] = (uint32_t)i;     // index order, for the adjoint of the projection
+  }
+#pragma unroll
+  for (int p = 0; p < kMaxPasses; ++p)
+    if (s_h[p][threadIdx.x]) atomicAdd(&cp.hist[p * kRadix + threadIdx.x], s_h[p][threadIdx.x]);
+  // clear the look-back rows of the first depth-sort pass
+  for (size_t z = (size_t)blk * blockDim.x + threadIdx.x; z < cp.zero_words; z += (size_t)gridDim.x * blockDim.x)
+    cp.zero[z] = 0ull;
 }
 
 // Zero gradients of the Gaussians that touch no tile (skipped when accumulating).  A warp owns
@@ -548,15 +621,18 @@ __global__ void __launch_bounds__(128, 4) preprocess_backward_kernel(
 }  // namespace
 
 cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Splat* splats, uint2* rects,
-                              uint32_t* touched, uint32_t* dkey, WsHeader* hdr, cudaStream_t s) {
+                              uint32_t* touched, const Compact& cp, WsHeader* hdr, cudaStream_t s) {
   if (total_n == 0) return cudaSuccess;
   note_launches(1);
   const int blocks = (total_n + 255) / 256;
+  // the compaction's look-back words (one per block) start cleared
+  if (cudaMemsetAsync(cp.status, 0, (size_t)blocks * sizeof(unsigned long long), s) != cudaSuccess)
+    return cudaGetLastError();
   switch (degree) {
-    case 0: preprocess_kernel<0><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, dkey, hdr); break;
-    case 1: preprocess_kernel<1><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, dkey, hdr); break;
-    case 2: preprocess_kernel<2><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, dkey, hdr); break;
-    default: preprocess_kernel<3><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, dkey, hdr); break;
+    case 0: preprocess_kernel<0><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, cp, hdr); break;
+    case 1: preprocess_kernel<1><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, cp, hdr); break;
+    case 2: preprocess_kernel<2><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, cp, hdr); break;
+    default: preprocess_kernel<3><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, cp, hdr); break;
   }
   return cudaGetLastError();
 }

@@ -108,4 +108,50 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// ------------------------------------------------------------------------------------------
+// Scans and decoupled look-back.
+// ------------------------------------------------------------------------------------------
+// Exclusive block scan over 256 threads (T = unsigned or unsigned long long).
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* sm /*[8]*/) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    T t = lane < 8 ? sm[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < 8) sm[lane] = t;
+  }
+  __syncthreads();
+  T base = w > 0 ? sm[w - 1] : T(0);
+  *total = sm[7];
+  __syncthreads();
+  return base + x - v;
+}
+
+// Look-back status words: flag bits over a 32-bit count.
+constexpr unsigned long long kFlagAggregate = 1ull << 62;   // the partition's own digit count
+constexpr unsigned long long kFlagPrefix = 1ull << 63;      // count of this and all earlier partitions
+constexpr unsigned long long kCountMask = 0xFFFFFFFFull;
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 }  // namespace vg
