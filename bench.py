@@ -324,6 +324,7 @@ def main():
     torch.cuda.synchronize()
     cnt = ras.counters.cpu().numpy()
     evals_f, blends_f = int(cnt[B.VG_CNT_EVALS]), int(cnt[B.VG_CNT_BLENDS])
+    evals_run_f = int(cnt[B.VG_CNT_EVALS_RUN])
     evals_b = int(last.to(torch.int64).sum().item())
     P, V = int(cnt[B.VG_CNT_PAIRS]), int(cnt[B.VG_CNT_VISIBLE])
     ras.settings.count_blends = False
@@ -448,6 +449,7 @@ def main():
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2070 MHz (nominal max clock)"},
         "stage_ms": stage_ms,
         "blends": {"evals_fwd": evals_f, "blends_fwd": blends_f, "evals_bwd": evals_b,
+                   "evals_run_fwd": evals_run_f,
                    "fwd_evals_per_s": evals_f / (stage_ms["blend"] * 1e-3),
                    "bwd_evals_per_s": evals_b / (stage_ms["blend_backward"] * 1e-3),
                    "fwd_tops": kern["blend"], "bwd_tops": kern["blend_backward"]},

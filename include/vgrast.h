@@ -60,6 +60,8 @@ enum {
   VG_CNT_DEPTH_BITS = 3, /* significant depth-key bits the depth sort used                 */
   VG_CNT_EVALS = 4,    /* (pixel, Gaussian) evaluations, when VG_FLAG_COUNT_BLENDS is set   */
   VG_CNT_BLENDS = 5,   /* evaluations that were composited, same flag                       */
+  VG_CNT_EVALS_RUN = 6, /* pixel slots the forward pass actually evaluated after its exact  */
+                       /* warp-level culling (a culled splat costs a warp nothing), same flag */
   VG_CNT_LEN = 8
 };
 

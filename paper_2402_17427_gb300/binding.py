@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libvgrast.so")
 VG_OK, VG_ERR_INVALID, VG_ERR_CAPACITY, VG_ERR_CUDA, VG_ERR_TIMEOUT, VG_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 VG_STATUS_PAIR_OVERFLOW = 1
 VG_STATUS_WAIT_TIMEOUT = 2
-VG_CNT_PAIRS, VG_CNT_VISIBLE, VG_CNT_STATUS, VG_CNT_DEPTH_BITS, VG_CNT_EVALS, VG_CNT_BLENDS = range(6)
+VG_CNT_PAIRS, VG_CNT_VISIBLE, VG_CNT_STATUS, VG_CNT_DEPTH_BITS, VG_CNT_EVALS, VG_CNT_BLENDS, VG_CNT_EVALS_RUN = range(7)
 VG_CNT_LEN = 8
 VG_FLAG_ACCUMULATE_GRADS = 1
 VG_FLAG_COUNT_BLENDS = 2

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(256) init_header(WsHeader* hdr, SortCtl* ctl) 
   hdr->pairs = 0;
   hdr->evals = 0;
   hdr->blends = 0;
+  hdr->evals_run = 0;
   hdr->visible = 0;
   hdr->status = 0;
   hdr->dmin = 0xFFFFFFFFu;
@@ -39,7 +40,7 @@ __global__ void publish_counters(const WsHeader* hdr, int64_t* c) {
   c[VG_CNT_DEPTH_BITS] = (int64_t)hdr->depth_bits;
   c[VG_CNT_EVALS] = (int64_t)hdr->evals;
   c[VG_CNT_BLENDS] = (int64_t)hdr->blends;
-  c[6] = 0;
+  c[VG_CNT_EVALS_RUN] = (int64_t)hdr->evals_run;
   c[7] = 0;
 }
 

@@ -187,7 +187,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
   using S = TileShape<TS, false>;
   __shared__ __align__(128) Splat buf[2][kCh];
   __shared__ int s_item;
-  unsigned long long ev = 0, bl = 0;
+  unsigned long long ev = 0, bl = 0, xr = 0;
   const int lane = threadIdx.x & 31;
   for (;;) {
     const int item = next_item(&hdr->work_fwd[S::kClass], item_count, &s_item);
@@ -292,6 +292,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
           // interleave the pixels' independent chains; a pixel that does not blend keeps C, T
           // and last bit for bit (w = 0 adds an exact zero)
           const uint32_t pos1 = (uint32_t)(k * ch + j + 1);
+          if (COUNT) xr += S::kPPT;
 #pragma unroll
           for (int p = 0; p < S::kPPT; ++p) {
             if (COUNT) ev += done[p] ? 0 : 1;
@@ -342,10 +343,12 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
     for (int o = 16; o > 0; o >>= 1) {
       ev += __shfl_xor_sync(0xffffffffu, ev, o);
       bl += __shfl_xor_sync(0xffffffffu, bl, o);
+      xr += __shfl_xor_sync(0xffffffffu, xr, o);
     }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&hdr->evals, ev);
       atomicAdd(&hdr->blends, bl);
+      atomicAdd(&hdr->evals_run, xr);
     }
   }
 }

@@ -105,6 +105,7 @@ struct WsHeader {
   unsigned long long pairs;     // pairs required
   unsigned long long evals;     // (pixel, Gaussian) evaluations (optional count)
   unsigned long long blends;    // composited evaluations (optional count)
+  unsigned long long evals_run; // pixel slots evaluated after culling (optional count)
   unsigned int visible;         // V
   unsigned int status;          // VG_STATUS_* bits
   unsigned int dmin, dmax;      // min / max depth key over visible Gaussians
