@@ -43,9 +43,9 @@ OPS_EVAL, OPS_BLEND_FWD, OPS_BLEND_BWD = 11, 7, 37
 TRAFFIC_SOURCES = ("paper_2402_17427_gb300/csrc/blend.cu", "paper_2402_17427_gb300/csrc/vg_common.cuh",
                    "paper_2402_17427_gb300/csrc/internal.h")
 PROFILED_TRAFFIC = {
-    "sources_sha256": "7dfefd2746bc2e1a8b61c1eea5305cf0d50d1890f1010df86553cc8d3e1dd628",
-    "blend": 18662656 + 1377792,
-    "blend_backward": 67452928 + 1243392,
+    "sources_sha256": "7b7b5801f340c5b3b173dea8d01f15ec2acdca994cf36b25c6ddcbdc38761e3e",
+    "blend": 18667008 + 1918208,
+    "blend_backward": 67442176 + 1484544,
 }
 
 
