@@ -43,7 +43,7 @@ OPS_EVAL, OPS_BLEND_FWD, OPS_BLEND_BWD = 11, 7, 37
 TRAFFIC_SOURCES = ("paper_2402_17427_gb300/csrc/blend.cu", "paper_2402_17427_gb300/csrc/vg_common.cuh",
                    "paper_2402_17427_gb300/csrc/internal.h")
 PROFILED_TRAFFIC = {
-    "sources_sha256": "7b7b5801f340c5b3b173dea8d01f15ec2acdca994cf36b25c6ddcbdc38761e3e",
+    "sources_sha256": "af228e7697c0223836b06dc2f6cf84de9f1224aca6a538be818ccd67621f9ca7",
     "blend": 18667008 + 1918208,
     "blend_backward": 67442176 + 1484544,
 }

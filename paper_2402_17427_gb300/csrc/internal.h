@@ -212,8 +212,8 @@ cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int de
 cudaError_t launch_zero_culled(const DevTables* tab, int total_n, int degree, const uint32_t* touched,
                                cudaStream_t s);
 
-// Depth order of the visible Gaussians, pair generation, tile sort, ranges, the tile-ordered copy
-// of the splats and the largest-first order of the tiles.
+// Depth order of the visible Gaussians, pair generation (with the depth-ordered splat records),
+// tile sort, ranges and the largest-first order of the tiles.
 cudaError_t launch_binning(const DevTables* tab, int total_n, int total_tiles, int64_t capacity, const Layout& L,
                            char* ws, cudaStream_t s);
 
