@@ -50,7 +50,7 @@ typedef enum {
 
 /* Bits of counters[VG_CNT_STATUS], set on the device. */
 #define VG_STATUS_PAIR_OVERFLOW 1u  /* pairs required > pair_capacity: outputs are invalid   */
-#define VG_STATUS_WAIT_TIMEOUT 2u   /* a bounded shared-memory copy wait gave up              */
+#define VG_STATUS_WAIT_TIMEOUT 2u   /* a bounded device wait (a sort look-back) gave up       */
 
 /* Layout of the int64 `counters` array every render call fills (device memory, >= 8 entries). */
 enum {

@@ -23,7 +23,9 @@ VG_FLAG_COUNT_BLENDS = 2
 EXPORTED = ("vg_default_opts", "vg_status_string", "vg_kernel_launches", "vg_workspace_bytes", "vg_rasterize_forward",
             "vg_rasterize_backward", "vg_read_render_state", "vg_loss_workspace_bytes", "vg_loss_l1_dssim",
             "vg_batch_workspace_bytes", "vg_render_batch", "vg_render_batch_backward",
-            "vg_views_workspace_bytes", "vg_render_views", "vg_loss_l1_dssim_noalloc")
+            "vg_views_workspace_bytes", "vg_render_views", "vg_loss_l1_dssim_noalloc",
+            "vg_airspace_boxes", "vg_visibility_workspace_bytes", "vg_camera_visibility", "vg_merge_workspace_bytes",
+            "vg_merge_cells")
 VG_LOSS_NOALLOC_MAX_PIXELS = 1024 * 1024
 
 
@@ -123,6 +125,18 @@ def lib():
                                   ctypes.POINTER(vg_raster_opts), ctypes.c_int32, _P, ctypes.c_size_t,
                                   ctypes.c_int64, _PP, _PP, _PP, _P, _P, _P]
     L.vg_render_views.restype = ctypes.c_int
+    L.vg_airspace_boxes.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.c_float, _P, _P]
+    L.vg_airspace_boxes.restype = ctypes.c_int
+    L.vg_visibility_workspace_bytes.argtypes = [ctypes.c_int32]
+    L.vg_visibility_workspace_bytes.restype = ctypes.c_size_t
+    L.vg_camera_visibility.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(vg_camera), ctypes.c_int32, ctypes.c_float,
+                                       _P, ctypes.c_size_t, _P, _P, _P]
+    L.vg_camera_visibility.restype = ctypes.c_int
+    L.vg_merge_workspace_bytes.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32]
+    L.vg_merge_workspace_bytes.restype = ctypes.c_size_t
+    L.vg_merge_cells.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.POINTER(ctypes.c_float), ctypes.c_int32, _P,
+                                 ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _P]
+    L.vg_merge_cells.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -263,3 +277,39 @@ def vg_loss_l1_dssim_noalloc(img: int, target: int, width: int, height: int, lam
     """Eq. 1 loss without a caller workspace (scratch compiled into the library; see vgrast.h)."""
     _check(lib().vg_loss_l1_dssim_noalloc(img, target, width, height, lam, out_loss, out_grad, stream),
            "vg_loss_l1_dssim_noalloc")
+
+
+# ------------------------------------------------------------------ scene partition (vgpartition.h)
+
+def vg_airspace_boxes(points: int, cell_offsets, ground_y: float, out_boxes: int, stream: int) -> None:
+    """Airspace box of each cell; cell_offsets is a host sequence of n_cells + 1 int64."""
+    n = len(cell_offsets) - 1
+    off = (ctypes.c_int64 * (n + 1))(*[int(v) for v in cell_offsets])
+    _check(lib().vg_airspace_boxes(points, off, n, ground_y, out_boxes, stream), "vg_airspace_boxes")
+
+
+def vg_visibility_workspace_bytes(n_cams: int) -> int:
+    return int(lib().vg_visibility_workspace_bytes(n_cams))
+
+
+def vg_camera_visibility(boxes: int, n_cells: int, cams, threshold: float, workspace: int, workspace_bytes: int,
+                         out_visibility: int | None, out_selected: int | None, stream: int) -> None:
+    n = len(cams)
+    C = (vg_camera * n)(*cams)
+    _check(lib().vg_camera_visibility(boxes, n_cells, C, n, threshold, workspace, workspace_bytes, out_visibility,
+                                      out_selected, stream), "vg_camera_visibility")
+
+
+def vg_merge_workspace_bytes(cells) -> int:
+    n = len(cells)
+    G = (vg_gaussians * n)(*cells)
+    return int(lib().vg_merge_workspace_bytes(G, n))
+
+
+def vg_merge_cells(cells, regions, workspace: int, workspace_bytes: int, out_means: int, out_log_scales: int,
+                   out_quats: int, out_logits: int, out_sh: int, out_n: int, stream: int) -> None:
+    n = len(cells)
+    G = (vg_gaussians * n)(*cells)
+    R = (ctypes.c_float * (4 * n))(*[float(v) for r in regions for v in r])
+    _check(lib().vg_merge_cells(G, R, n, workspace, workspace_bytes, out_means, out_log_scales, out_quats, out_logits,
+                                out_sh, out_n, stream), "vg_merge_cells")

@@ -1,4 +1,4 @@
-"""The C-ABI library: it builds, loads, exports every symbol include/vgrast.h declares, and
+"""The C-ABI library: it builds, loads, exports every symbol include/*.h declares, and
 rejects invalid arguments on the host (no GPU needed: nothing here launches a kernel)."""
 import ctypes
 import os
@@ -17,16 +17,21 @@ def vg():
 
 
 def declared_functions():
-    txt = open(os.path.join(ROOT, "include", "vgrast.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(vg_[a-z0-9_]+)\s*\(", txt, flags=re.M)
-    return sorted(set(names))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(vg_[a-z0-9_]+)\s*\(", txt, flags=re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("vg_rasterize_forward", "vg_rasterize_backward", "vg_render_batch", "vg_render_batch_backward",
-                 "vg_loss_l1_dssim", "vg_workspace_bytes", "vg_read_render_state"):
+                 "vg_loss_l1_dssim", "vg_workspace_bytes", "vg_read_render_state", "vg_airspace_boxes",
+                 "vg_camera_visibility", "vg_merge_cells"):
         assert must in names
 
 
