@@ -265,6 +265,71 @@ def batch_pattern(dev, steps=10, warmup=3):
             "tiles": [s.tile_size for s in settings], "chunks": [s.chunk for s in settings]}
 
 
+def _time_cuda(fn, reps=10, warmup=3):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def partition_pattern(dev, hbm_gbs):
+    """Scene partition on the device (Sec. 4.1, 4.3): airspace boxes of 16 cells (20M points),
+    visibility of those boxes in 4000 cameras, and the seamless merge of 16 cells whose Gaussians
+    (1.25M each, SH3) cover their 20%-expanded rectangles.  Inputs are drawn on the device from a
+    fixed seed."""
+    import math
+    import torch
+    from paper_2402_17427_gb300 import partition as PT, scenes
+    g = torch.Generator(device=dev)
+    g.manual_seed(6000)
+    n_cells, per, cell = 16, 1_250_000, 250.0
+    cells, regions, offs = [], [], [0]
+    for k in range(n_cells):
+        x0, z0 = cell * (k % 4), cell * (k // 4)
+        lo = torch.tensor([x0 - 0.1 * cell, 0.0, z0 - 0.1 * cell], device=dev)
+        ext = torch.tensor([1.2 * cell, 60.0, 1.2 * cell], device=dev)
+        means = lo + ext * torch.rand((per, 3), device=dev, generator=g)
+        cells.append((means, torch.randn((per, 3), device=dev, generator=g) - 2.0,
+                      torch.randn((per, 4), device=dev, generator=g), torch.randn((per,), device=dev, generator=g),
+                      torch.randn((per, 16, 3), device=dev, generator=g)))
+        regions.append((x0, x0 + cell, z0, z0 + cell))
+        offs.append(offs[-1] + per)
+    points = torch.cat([c[0] for c in cells]).contiguous()
+    t_box = _time_cuda(lambda: PT.airspace_boxes(points, offs, 0.0))
+    boxes = PT.airspace_boxes(points, offs, 0.0)
+    rng = np.random.default_rng(6001)
+    cams = []
+    for i in range(4000):
+        W, H = scenes.RESOLUTIONS[i % 3]
+        yaw, pitch = rng.uniform(0, 2 * math.pi), math.radians(rng.uniform(-90, -30))
+        eye = (rng.uniform(0, 1000), rng.uniform(20, 150), rng.uniform(0, 1000))
+        cams.append(scenes.camera_from_forward(eye, scenes.yaw_pitch_forward(yaw, pitch), W, H))
+    table = PT.camera_table(cams)      # marshalled once; the timed call is the C-ABI call
+    t_vis = _time_cuda(lambda: PT.camera_visibility(boxes, table))
+    vis, sel = PT.camera_visibility(boxes, table)
+    t_merge = _time_cuda(lambda: PT.merge_cells(cells, regions, 3), reps=5, warmup=2)
+    merged = PT.merge_cells(cells, regions, 3)
+    m, total = int(merged[0].shape[0]), n_cells * per
+    # algorithmic bytes: every mean read (12 B), the 236 B of each kept Gaussian read and written
+    merge_bytes = 12 * total + 2 * 236 * m
+    box_bytes = 12 * total
+    return {"workload": "16 cells x 1.25M Gaussians (SH3) over 20%-expanded 250 m cells; 4000 cameras "
+                        "(720p/1080p/4K, 20-150 m, pitch -90..-30 deg)",
+            "airspace_boxes_ms": t_box, "airspace_boxes_gbs": box_bytes / (t_box * 1e-3) / 1e9,
+            "visibility_ms": t_vis, "visibility_pairs_per_s": 4000 * n_cells / (t_vis * 1e-3),
+            "cameras_selected_per_cell_mean": float(sel.float().sum(0).mean()),
+            "merge_ms": t_merge, "merged": m, "merge_gbs": merge_bytes / (t_merge * 1e-3) / 1e9,
+            "merge_hbm_frac": merge_bytes / (t_merge * 1e-3) / 1e9 / hbm_gbs,
+            "note": "times include each call's argument marshalling and output allocation"}
+
+
 def serving_pattern(dev, seconds=30.0):
     """The merged 20M-Gaussian city (16 cells) served under a 200 req/s Poisson stream."""
     from paper_2402_17427_gb300 import scenes, serving
@@ -433,7 +498,8 @@ def main():
     patterns = None
     if not args.no_patterns and ws == 1:
         try:
-            patterns = {"batched_cells": batch_pattern(dev), "serving": serving_pattern(dev, args.serve_seconds)}
+            patterns = {"batched_cells": batch_pattern(dev), "serving": serving_pattern(dev, args.serve_seconds),
+                        "partition": partition_pattern(dev, hbm)}
         except Exception as e:  # report, never lose the main number
             patterns = {"error": repr(e)}
     line = {

@@ -295,7 +295,7 @@ def vg_visibility_workspace_bytes(n_cams: int) -> int:
 def vg_camera_visibility(boxes: int, n_cells: int, cams, threshold: float, workspace: int, workspace_bytes: int,
                          out_visibility: int | None, out_selected: int | None, stream: int) -> None:
     n = len(cams)
-    C = (vg_camera * n)(*cams)
+    C = cams if isinstance(cams, ctypes.Array) else (vg_camera * n)(*cams)
     _check(lib().vg_camera_visibility(boxes, n_cells, C, n, threshold, workspace, workspace_bytes, out_visibility,
                                       out_selected, stream), "vg_camera_visibility")
 

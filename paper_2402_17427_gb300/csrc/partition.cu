@@ -32,7 +32,17 @@ __device__ __forceinline__ float ord2f(unsigned o) {
   return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
-constexpr int kBoxChunk = 1 << 16;
+constexpr int kBoxChunk = 1 << 14;     // points per block
+constexpr int kBoxCellsPerLaunch = 256;
+
+// Chunk table of one launch: cell c of the launch owns blocks [chunk[c], chunk[c+1]) and points
+// [first[c], first[c] + count[c]).
+struct BoxJob {
+  int n;
+  int chunk[kBoxCellsPerLaunch + 1];
+  long long first[kBoxCellsPerLaunch];
+  long long count[kBoxCellsPerLaunch];
+};
 
 __global__ void box_init(unsigned* ob, int n_cells) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,14 +53,22 @@ __global__ void box_init(unsigned* ob, int n_cells) {
   }
 }
 
-__global__ void __launch_bounds__(256) box_reduce(const float* __restrict__ pts, long long n, unsigned* ob) {
+__global__ void __launch_bounds__(256) box_reduce(const float* __restrict__ pts, const BoxJob job, unsigned* ob) {
   __shared__ unsigned sm[6][8];
+  int lo_c = 0, hi_c = job.n - 1;   // this block's cell: the last c with chunk[c] <= blockIdx.x
+  while (lo_c < hi_c) {
+    const int mid = (lo_c + hi_c + 1) >> 1;
+    if (job.chunk[mid] <= (int)blockIdx.x) lo_c = mid; else hi_c = mid - 1;
+  }
+  const int c = lo_c;
   unsigned v[6] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u};
-  const long long lo = (long long)blockIdx.x * kBoxChunk, hi = lo + kBoxChunk < n ? lo + kBoxChunk : n;
+  const long long lo = (long long)(blockIdx.x - job.chunk[c]) * kBoxChunk;
+  const long long hi = lo + kBoxChunk < job.count[c] ? lo + kBoxChunk : job.count[c];
+  const float* p = pts + 3 * job.first[c];
   for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const unsigned o = f2ord(__ldg(pts + 3 * i + a));
+      const unsigned o = f2ord(__ldg(p + 3 * i + a));
       v[a] = min(v[a], o);
       v[3 + a] = max(v[3 + a], o);
     }
@@ -71,7 +89,8 @@ __global__ void __launch_bounds__(256) box_reduce(const float* __restrict__ pts,
     const int a = threadIdx.x;
     unsigned r = sm[a][0];
     for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = a < 3 ? min(r, sm[a][k]) : max(r, sm[a][k]);
-    if (a < 3) atomicMin(ob + a, r); else atomicMax(ob + a, r);
+    unsigned* dst = ob + 6 * (size_t)c;
+    if (a < 3) atomicMin(dst + a, r); else atomicMax(dst + a, r);
   }
 }
 
@@ -94,7 +113,7 @@ __global__ void box_finish(unsigned* ob, int n_cells, float ground_y) {
 
 // ---------------------------------------------------------------- visibility
 
-constexpr int kMaxPoly = 48;   // >= 2 x 20 (the hull stack) and >= 20 + 4 (four clips of a convex hull)
+constexpr int kMaxPoly = 32;   // >= 2 x 16 (the hull stack) and >= 16 + 4 (four clips of a convex hull)
 
 struct D2 {
   double x, y;
@@ -104,7 +123,7 @@ __device__ __forceinline__ double cross3(const D2& o, const D2& a, const D2& b) 
   return (a.x - o.x) * (b.y - o.y) - (a.y - o.y) * (b.x - o.x);
 }
 
-// Convex hull of p[0..n) (n <= 20) by the monotone chain, counter-clockwise, into h; returns its size.
+// Convex hull of p[0..n) (n <= 16) by the monotone chain, counter-clockwise, into h; returns its size.
 __device__ int hull(D2* p, int n, D2* h) {
   for (int i = 1; i < n; ++i) {   // insertion sort by (x, y)
     const D2 q = p[i];
@@ -161,8 +180,9 @@ __device__ double box_visibility(const float* box, const vg_camera& cam) {
     for (int r = 0; r < 3; ++r) c[k][r] = R[3 * r] * w[0] + R[3 * r + 1] * w[1] + R[3 * r + 2] * w[2] + t[r];
   }
   const double near = (double)cam.near_plane;
-  // the box clipped to z >= near: its inside corners and its edges' crossings of the plane
-  double q[20][3];
+  // the box clipped to z >= near: its inside corners and its edges' crossings of the plane (a
+  // plane crosses at most 6 edges of a box, and then at most 7 corners are inside: <= 13 points)
+  double q[16][3];
   int nq = 0;
   for (int k = 0; k < 8; ++k)
     if (c[k][2] >= near) {
@@ -180,7 +200,7 @@ __device__ double box_visibility(const float* box, const vg_camera& cam) {
     }
   }
   if (nq == 0) return 0.0;
-  D2 p[20], h[kMaxPoly], g[kMaxPoly];
+  D2 p[16], h[kMaxPoly], g[kMaxPoly];
   const double fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
   for (int k = 0; k < nq; ++k) p[k] = D2{fx * q[k][0] / q[k][2] + cx, fy * q[k][1] / q[k][2] + cy};
   int n = hull(p, nq, h);
@@ -359,11 +379,21 @@ extern "C" vg_status vg_airspace_boxes(const float* points, const int64_t* cell_
   unsigned* ob = reinterpret_cast<unsigned*>(out_boxes);
   box_init<<<(n_cells + 127) / 128, 128, 0, s>>>(ob, n_cells);
   int launches = 2;
-  for (int k = 0; k < n_cells; ++k) {
-    const long long n = cell_offsets[k + 1] - cell_offsets[k];
-    if (n == 0) continue;
-    const long long blocks = (n + kBoxChunk - 1) / kBoxChunk;
-    box_reduce<<<(unsigned)blocks, 256, 0, s>>>(points + 3 * cell_offsets[k], n, ob + 6 * k);
+  // one launch per group of up to 256 cells; a block reduces 16K points of one cell
+  for (int k0 = 0; k0 < n_cells; k0 += kBoxCellsPerLaunch) {
+    BoxJob job{};
+    job.n = n_cells - k0 < kBoxCellsPerLaunch ? n_cells - k0 : kBoxCellsPerLaunch;
+    long long blocks = 0;
+    for (int c = 0; c < job.n; ++c) {
+      job.chunk[c] = (int)blocks;
+      job.first[c] = cell_offsets[k0 + c];
+      job.count[c] = cell_offsets[k0 + c + 1] - cell_offsets[k0 + c];
+      blocks += (job.count[c] + kBoxChunk - 1) / kBoxChunk;
+    }
+    job.chunk[job.n] = (int)blocks;
+    if (blocks == 0) continue;
+    if (blocks > 0x7FFFFFFFll) return VG_ERR_INVALID;
+    box_reduce<<<(unsigned)blocks, 256, 0, s>>>(points, job, ob + 6 * (size_t)k0);
     ++launches;
   }
   box_finish<<<(n_cells + 127) / 128, 128, 0, s>>>(ob, n_cells, ground_y);

@@ -10,6 +10,8 @@
 """
 from __future__ import annotations
 
+import ctypes
+
 import torch
 
 from . import binding as B
@@ -27,12 +29,18 @@ def airspace_boxes(points: torch.Tensor, cell_offsets, ground_y: float) -> torch
     return out
 
 
+def camera_table(cameras):
+    """The cameras marshalled once for repeated visibility calls."""
+    cams = [camera_c(c) for c in cameras]
+    return (B.vg_camera * len(cams))(*cams)
+
+
 def camera_visibility(boxes: torch.Tensor, cameras, threshold: float = VISIBILITY_THRESHOLD):
-    """boxes: CUDA float32 [n_cells, 6]; cameras: scenes.Camera list.  Returns (visibility
-    float32 [n_cams, n_cells], selected bool [n_cams, n_cells])."""
+    """boxes: CUDA float32 [n_cells, 6]; cameras: scenes.Camera list or a camera_table.  Returns
+    (visibility float32 [n_cams, n_cells], selected bool [n_cams, n_cells])."""
     boxes = boxes.contiguous()
     n_cells = int(boxes.shape[0])
-    cams = [camera_c(c) for c in cameras]
+    cams = cameras if isinstance(cameras, ctypes.Array) else camera_table(cameras)
     need = B.vg_visibility_workspace_bytes(len(cams))
     ws = torch.empty(need, dtype=torch.uint8, device=boxes.device)
     vis = torch.empty((len(cams), n_cells), dtype=torch.float32, device=boxes.device)
