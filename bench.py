@@ -330,6 +330,25 @@ def partition_pattern(dev, hbm_gbs):
             "note": "times include each call's argument marshalling and output allocation"}
 
 
+def evaluation_pattern(dev, hbm_gbs):
+    """Colour-corrected PSNR / SSIM (Sec. 5.1) of a 1920x1080 rendering against its target."""
+    import torch
+    from paper_2402_17427_gb300 import rasterize as R
+    g = torch.Generator(device=dev)
+    g.manual_seed(7000)
+    y = torch.rand((3, 1080, 1920), device=dev, generator=g)
+    x = (0.8 * y + 0.1 + 0.05 * torch.randn((3, 1080, 1920), device=dev, generator=g)).clamp(0, 1)
+    t = _time_cuda(lambda: R.color_corrected_metrics(x, y), reps=20, warmup=3)
+    out = R.color_corrected_metrics(x, y).cpu().tolist()
+    # algorithmic bytes: both images read by the two fitting passes and the correction, the
+    # corrected image written, then read with the target by the SSIM pass
+    px = 1920 * 1080
+    nbytes = (3 * 2 + 1 + 2) * 3 * 4 * px
+    return {"workload": "1920x1080 rendering vs target (affine colour shift + noise)", "ms": t,
+            "images_per_s": 1000.0 / t, "psnr": out[0], "ssim": out[1],
+            "gbs": nbytes / (t * 1e-3) / 1e9, "hbm_frac": nbytes / (t * 1e-3) / 1e9 / hbm_gbs}
+
+
 def serving_pattern(dev, seconds=30.0):
     """The merged 20M-Gaussian city (16 cells) served under a 200 req/s Poisson stream."""
     from paper_2402_17427_gb300 import scenes, serving
@@ -499,7 +518,7 @@ def main():
     if not args.no_patterns and ws == 1:
         try:
             patterns = {"batched_cells": batch_pattern(dev), "serving": serving_pattern(dev, args.serve_seconds),
-                        "partition": partition_pattern(dev, hbm)}
+                        "partition": partition_pattern(dev, hbm), "evaluation": evaluation_pattern(dev, hbm)}
         except Exception as e:  # report, never lose the main number
             patterns = {"error": repr(e)}
     line = {

@@ -215,6 +215,25 @@ vg_status vg_loss_l1_dssim_noalloc(const float* img, const float* target, int32_
                                    float lambda, float* out_loss, float* out_grad, vg_stream stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Evaluation with colour correction (Sec. 5.1, "Metrics"): before PSNR and SSIM are measured,
+ * the rendering is aligned to the ground truth by a per-image least-squares fit of an affine
+ * colour map y ~ A x + b (A 3x3, b 3) over all pixels, solved in centred form: Cov(x) A^T =
+ * Cov(x, y), b = mean(y) - A mean(x) (moments accumulated in FP64, Cholesky in FP64).  The
+ * corrected image A x + b is clipped to [0, 1]; PSNR = -10 log10(MSE) with peak 1, SSIM as in
+ * the loss above (11x11 Gaussian window, mean over 3HW).
+ *   img, target   device float [3, H, W]
+ *   workspace     device, >= vg_eval_workspace_bytes(width, height), 256-byte aligned
+ *   out           device float [14]: PSNR, SSIM, A (row-major 3x3), b (3).  A colour direction
+ *                 whose Cholesky pivot is below 1e-10 of the covariance trace (a rendering
+ *                 whose colours do not span 3D, e.g. constant) gets coefficient 0; the fitted
+ *                 values, hence the metrics, are those of every least-squares solution.
+ * Errors: VG_ERR_INVALID (NULL, sizes), VG_ERR_CAPACITY (workspace).
+ * ------------------------------------------------------------------------------------------ */
+size_t vg_eval_workspace_bytes(int32_t width, int32_t height);
+vg_status vg_eval_color_corrected(const float* img, const float* target, int32_t width, int32_t height,
+                                  void* workspace, size_t workspace_bytes, float* out, vg_stream stream);
+
+/* ------------------------------------------------------------------------------------------
  * Batched cells (Sec. 4.1: cells are optimised independently, in parallel): n_cells
  * (Gaussian set, camera) pairs rendered by one launch per stage — one projection launch over
  * all cells, one sort, one persistent blend launch whose blocks pull (cell, tile) work items

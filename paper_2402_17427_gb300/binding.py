@@ -25,7 +25,7 @@ EXPORTED = ("vg_default_opts", "vg_status_string", "vg_kernel_launches", "vg_wor
             "vg_batch_workspace_bytes", "vg_render_batch", "vg_render_batch_backward",
             "vg_views_workspace_bytes", "vg_render_views", "vg_loss_l1_dssim_noalloc",
             "vg_airspace_boxes", "vg_visibility_workspace_bytes", "vg_camera_visibility", "vg_merge_workspace_bytes",
-            "vg_merge_cells")
+            "vg_merge_cells", "vg_eval_workspace_bytes", "vg_eval_color_corrected")
 VG_LOSS_NOALLOC_MAX_PIXELS = 1024 * 1024
 
 
@@ -137,6 +137,10 @@ def lib():
     L.vg_merge_cells.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.POINTER(ctypes.c_float), ctypes.c_int32, _P,
                                  ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _P]
     L.vg_merge_cells.restype = ctypes.c_int
+    L.vg_eval_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    L.vg_eval_workspace_bytes.restype = ctypes.c_size_t
+    L.vg_eval_color_corrected.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P, _P]
+    L.vg_eval_color_corrected.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -313,3 +317,15 @@ def vg_merge_cells(cells, regions, workspace: int, workspace_bytes: int, out_mea
     R = (ctypes.c_float * (4 * n))(*[float(v) for r in regions for v in r])
     _check(lib().vg_merge_cells(G, R, n, workspace, workspace_bytes, out_means, out_log_scales, out_quats, out_logits,
                                 out_sh, out_n, stream), "vg_merge_cells")
+
+
+# ------------------------------------------------------------------ evaluation (Sec. 5.1 metrics)
+
+def vg_eval_workspace_bytes(width: int, height: int) -> int:
+    return int(lib().vg_eval_workspace_bytes(width, height))
+
+
+def vg_eval_color_corrected(img: int, target: int, width: int, height: int, workspace: int, workspace_bytes: int,
+                            out: int, stream: int) -> None:
+    _check(lib().vg_eval_color_corrected(img, target, width, height, workspace, workspace_bytes, out, stream),
+           "vg_eval_color_corrected")

@@ -227,3 +227,16 @@ def l1_dssim_loss(img, target, lam: float = 0.2, lossobj: LossL1DSSIM | None = N
 def to_device(g, device="cuda"):
     """Gaussian parameter tensors (float32, contiguous) on the device."""
     return [torch.from_numpy(np.ascontiguousarray(a)).to(device) for a in g.arrays()]
+
+
+def color_corrected_metrics(img: torch.Tensor, target: torch.Tensor):
+    """PSNR and SSIM of a rendering after the per-image least-squares colour correction of the
+    evaluation protocol (Sec. 5.1).  img, target: CUDA float32 [3, H, W].  Returns a CUDA float32
+    [14] tensor: PSNR, SSIM, A (3x3, row-major), b (3)."""
+    img, target = img.contiguous(), target.contiguous()
+    H, W = int(img.shape[1]), int(img.shape[2])
+    need = B.vg_eval_workspace_bytes(W, H)
+    ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    out = torch.empty(14, dtype=torch.float32, device=img.device)
+    B.vg_eval_color_corrected(img.data_ptr(), target.data_ptr(), W, H, ws.data_ptr(), need, out.data_ptr(), _stream())
+    return out
