@@ -25,8 +25,24 @@ EXPORTED = ("vg_default_opts", "vg_status_string", "vg_kernel_launches", "vg_wor
             "vg_batch_workspace_bytes", "vg_render_batch", "vg_render_batch_backward",
             "vg_views_workspace_bytes", "vg_render_views", "vg_loss_l1_dssim_noalloc",
             "vg_airspace_boxes", "vg_visibility_workspace_bytes", "vg_camera_visibility", "vg_merge_workspace_bytes",
-            "vg_merge_cells", "vg_eval_workspace_bytes", "vg_eval_color_corrected")
+            "vg_merge_cells", "vg_eval_workspace_bytes", "vg_eval_color_corrected", "vg_adam_step",
+            "vg_densify_accumulate", "vg_densify_workspace_bytes", "vg_densify")
 VG_LOSS_NOALLOC_MAX_PIXELS = 1024 * 1024
+
+
+class vg_param_ptrs(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class vg_adam_opts(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 6), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
+
+
+class vg_densify_opts(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("percent_dense", ctypes.c_float),
+                ("scene_extent", ctypes.c_float), ("min_opacity", ctypes.c_float), ("max_world_scale", ctypes.c_float)]
 
 
 class vg_camera(ctypes.Structure):
@@ -141,6 +157,18 @@ def lib():
     L.vg_eval_workspace_bytes.restype = ctypes.c_size_t
     L.vg_eval_color_corrected.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P, _P]
     L.vg_eval_color_corrected.restype = ctypes.c_int
+    L.vg_adam_step.argtypes = [vg_param_ptrs, ctypes.POINTER(vg_gaussians), vg_param_ptrs, vg_param_ptrs,
+                               ctypes.POINTER(vg_adam_opts), _P]
+    L.vg_adam_step.restype = ctypes.c_int
+    L.vg_densify_accumulate.argtypes = [_P, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int64, ctypes.POINTER(vg_raster_opts), _P, _P, _P]
+    L.vg_densify_accumulate.restype = ctypes.c_int
+    L.vg_densify_workspace_bytes.argtypes = [ctypes.c_int64]
+    L.vg_densify_workspace_bytes.restype = ctypes.c_size_t
+    L.vg_densify.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.POINTER(vg_gaussians), ctypes.POINTER(vg_gaussians),
+                             _P, _P, _P, ctypes.POINTER(vg_densify_opts), _P, ctypes.c_size_t, vg_param_ptrs,
+                             vg_param_ptrs, vg_param_ptrs, _P, _P]
+    L.vg_densify.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -329,3 +357,28 @@ def vg_eval_color_corrected(img: int, target: int, width: int, height: int, work
                             out: int, stream: int) -> None:
     _check(lib().vg_eval_color_corrected(img, target, width, height, workspace, workspace_bytes, out, stream),
            "vg_eval_color_corrected")
+
+
+# ------------------------------------------------------------------ optimiser step (vgoptim.h)
+
+def vg_adam_step(params: vg_param_ptrs, grads: vg_gaussians, m: vg_param_ptrs, v: vg_param_ptrs,
+                 opts: vg_adam_opts, stream: int) -> None:
+    _check(lib().vg_adam_step(params, ctypes.byref(grads), m, v, ctypes.byref(opts), stream), "vg_adam_step")
+
+
+def vg_densify_accumulate(workspace: int, workspace_bytes: int, n: int, width: int, height: int, pair_capacity: int,
+                          opts: vg_raster_opts, accum: int, count: int, stream: int) -> None:
+    _check(lib().vg_densify_accumulate(workspace, workspace_bytes, n, width, height, pair_capacity, ctypes.byref(opts),
+                                       accum, count, stream), "vg_densify_accumulate")
+
+
+def vg_densify_workspace_bytes(n: int) -> int:
+    return int(lib().vg_densify_workspace_bytes(n))
+
+
+def vg_densify(inp: vg_gaussians, m_in: vg_gaussians, v_in: vg_gaussians, accum: int, count: int, normals: int,
+               opts: vg_densify_opts, workspace: int, workspace_bytes: int, out: vg_param_ptrs, m_out: vg_param_ptrs,
+               v_out: vg_param_ptrs, out_n: int, stream: int) -> None:
+    _check(lib().vg_densify(ctypes.byref(inp), ctypes.byref(m_in), ctypes.byref(v_in), accum, count, normals,
+                            ctypes.byref(opts), workspace, workspace_bytes, out, m_out, v_out, out_n, stream),
+           "vg_densify")
