@@ -330,6 +330,51 @@ def partition_pattern(dev, hbm_gbs):
             "note": "times include each call's argument marshalling and output allocation"}
 
 
+def optimiser_pattern(dev, hbm_gbs):
+    """The optimiser step at the benchmark cell's size (1M Gaussians, SH3): one fused Adam update
+    of every parameter, and one clone / split / prune pass with a mix of decisions."""
+    import torch
+    from paper_2402_17427_gb300 import optim as OP
+    n, K = 1_000_000, 16
+    g = torch.Generator(device=dev)
+    g.manual_seed(8000)
+    shapes = [(n, 3), (n, 3), (n, 4), (n,), (n, K, 3)]
+    params = [torch.randn(sh, device=dev, generator=g) for sh in shapes]
+    params[1] = params[1] * 0.8 + math.log(0.05)
+    params[3] = params[3] * 3.0
+    grads = [torch.randn(sh, device=dev, generator=g) * 1e-2 for sh in shapes]
+    adam = OP.Adam(params)
+    t_adam = _time_cuda(lambda: adam.step(params, grads, 3), reps=20, warmup=3)
+    # each parameter scalar: p, g, m, v read and p, m, v written
+    scalars = n * (3 + 3 + 4 + 1 + 3 * K)
+    adam_bytes = 7 * 4 * scalars
+    acc = torch.empty(n, device=dev).exponential_(1.0 / 3e-4, generator=g)
+    cnt = torch.randint(0, 4, (n,), device=dev, generator=g, dtype=torch.int32)
+    normals = torch.randn((n, 2, 3), device=dev, generator=g)
+    ds = OP.DensifySettings(scene_extent=10.0)
+    state = {}
+
+    def one():
+        a = OP.Adam.__new__(OP.Adam)
+        a.m, a.v = adam.m, adam.v
+        st = OP.DensifyStats.__new__(OP.DensifyStats)
+        st.accum, st.count = acc, cnt
+        state["new"] = OP.densify_with(params, a, st, 3, ds, normals)
+
+    t_dens = _time_cuda(one, reps=5, warmup=2)
+    m = int(state["new"][0].shape[0])
+    # read: every Gaussian's decision inputs and its parameters + moments (3 x 236 B) once;
+    # written: 3 x 236 B per emitted Gaussian
+    dens_bytes = n * (12 + 4 + 4 + 4) + 3 * 236 * (n + m)
+    return {"workload": "1M Gaussians, SH3 (59 floats each); densify with random statistics "
+                        "(prune / keep / clone / split mix)",
+            "adam_ms": t_adam, "adam_gbs": adam_bytes / (t_adam * 1e-3) / 1e9,
+            "adam_hbm_frac": adam_bytes / (t_adam * 1e-3) / 1e9 / hbm_gbs,
+            "densify_ms": t_dens, "densify_out": m, "densify_gbs": dens_bytes / (t_dens * 1e-3) / 1e9,
+            "densify_hbm_frac": dens_bytes / (t_dens * 1e-3) / 1e9 / hbm_gbs,
+            "note": "densify time includes its output allocation"}
+
+
 def evaluation_pattern(dev, hbm_gbs):
     """Colour-corrected PSNR / SSIM (Sec. 5.1) of a 1920x1080 rendering against its target."""
     import torch
@@ -518,7 +563,8 @@ def main():
     if not args.no_patterns and ws == 1:
         try:
             patterns = {"batched_cells": batch_pattern(dev), "serving": serving_pattern(dev, args.serve_seconds),
-                        "partition": partition_pattern(dev, hbm), "evaluation": evaluation_pattern(dev, hbm)}
+                        "partition": partition_pattern(dev, hbm), "evaluation": evaluation_pattern(dev, hbm),
+                        "optimiser": optimiser_pattern(dev, hbm)}
         except Exception as e:  # report, never lose the main number
             patterns = {"error": repr(e)}
     line = {

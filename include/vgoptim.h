@@ -82,6 +82,7 @@ size_t vg_densify_workspace_bytes(int64_t n);
  *   out, m_out, v_out  device arrays with room for 2 n Gaussians
  *   out_n            device int64: the new count (-1 if a bounded device wait gave up)
  * The statistics of the new model restart at 0 (the caller clears new accum / count arrays).
+ * quats (and sh for degrees 1 and 3) of every array set must be 16-byte aligned.
  * Errors: VG_ERR_INVALID (NULL, sizes, alignment), VG_ERR_CAPACITY (workspace). */
 vg_status vg_densify(const vg_gaussians* in, const vg_gaussians* m_in, const vg_gaussians* v_in, const float* accum,
                      const int32_t* count, const float* normals, const vg_densify_opts* opts, void* workspace,

@@ -130,7 +130,14 @@ __device__ void copy_gaussian(const vg_gaussians& src, long long i, const vg_par
   reinterpret_cast<float4*>(dst.quats)[o] =
       zero ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(reinterpret_cast<const float4*>(src.quats) + i);
   dst.opacity_logits[o] = zero ? 0.f : __ldg(src.opacity_logits + i);
-  for (int w = 0; w < F; ++w) dst.sh[o * F + w] = zero ? 0.f : __ldg(src.sh + i * F + w);
+  if constexpr (F % 4 == 0) {   // 16-byte rows (checked on the host for degrees 1 and 3)
+    const float4* sv = reinterpret_cast<const float4*>(src.sh + i * F);
+    float4* dv = reinterpret_cast<float4*>(dst.sh + o * F);
+#pragma unroll
+    for (int w = 0; w < F / 4; ++w) dv[w] = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(sv + w);
+  } else {
+    for (int w = 0; w < F; ++w) dst.sh[o * F + w] = zero ? 0.f : __ldg(src.sh + i * F + w);
+  }
 }
 
 template <int F>
@@ -338,6 +345,11 @@ extern "C" vg_status vg_densify(const vg_gaussians* in, const vg_gaussians* m_in
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (n == 0) return cudaMemsetAsync(out_n, 0, sizeof(int64_t), s) == cudaSuccess ? VG_OK : VG_ERR_CUDA;
   if (!accum || !count || !normals || !valid_ptrs(out) || !valid_ptrs(m_out) || !valid_ptrs(v_out)) return VG_ERR_INVALID;
+  if (in->sh_degree == 1 || in->sh_degree == 3) {   // SH rows are copied as 16-byte words
+    const void* shs[6] = {in->sh, m_in->sh, v_in->sh, out.sh, m_out.sh, v_out.sh};
+    for (const void* q : shs)
+      if (!aligned16(q)) return VG_ERR_INVALID;
+  }
   DensIn d{*in, *m_in, *v_in, accum, reinterpret_cast<const int*>(count), normals,
            opts->grad_threshold, (float)std::log((double)opts->percent_dense * (double)opts->scene_extent),
            (float)std::log((double)opts->min_opacity / (1.0 - (double)opts->min_opacity)),
