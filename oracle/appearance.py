@@ -54,27 +54,42 @@ def pool32_adj(g, H, W):
 
 
 def conv(x, w, b):
-    """3x3, zero padding 1: y[o, y, x] = b[o] + sum_{c, i, j} w[o, c, i, j] x[c, y + i - 1, x + j - 1]."""
+    """3x3, zero padding 1: y[o, y, x] = b[o] + sum_{c, i, j} w[o, c, i, j] x[c, y + i - 1, x + j - 1].
+
+    Evaluated on the padded image flattened with row pitch P = W + 2: output (y, x) and tap (i, j)
+    read flat element (y + i) P + x + j, so each tap is one matrix product over a contiguous
+    window; the two extra columns of every output row are computed and dropped."""
     C, H, W = x.shape
-    xp = np.pad(x, ((0, 0), (1, 1), (1, 1)))
-    y = np.broadcast_to(b[:, None, None], (w.shape[0], H, W)).copy()
+    P = W + 2
+    xp = np.pad(x, ((0, 0), (1, 2), (1, 1))).reshape(C, (H + 3) * P)
+    y = np.empty((w.shape[0], H * P))
+    y[:] = b[:, None]
     for i in range(3):
         for j in range(3):
-            y += np.einsum("oc,chw->ohw", w[:, :, i, j], xp[:, i:i + H, j:j + W])
-    return y
+            o = i * P + j
+            y += w[:, :, i, j] @ xp[:, o:o + H * P]
+    return np.ascontiguousarray(y.reshape(-1, H, P)[:, :, :W])
 
 
 def conv_adj(x, w, g):
-    """Adjoints of conv: (dL/dx, dL/dw, dL/db) from g = dL/dy."""
+    """Adjoints of conv: (dL/dx, dL/dw, dL/db) from g = dL/dy (same flat windows as conv, with g
+    zero in the dropped columns)."""
     C, H, W = x.shape
-    xp = np.pad(x, ((0, 0), (1, 1), (1, 1)))
-    gxp = np.zeros_like(xp)
-    dw = np.zeros_like(w)
+    P = W + 2
+    O = g.shape[0]
+    xp = np.pad(x, ((0, 0), (1, 2), (1, 1))).reshape(C, (H + 3) * P)
+    ge = np.zeros((O, H, P))
+    ge[:, :, :W] = g
+    ge = ge.reshape(O, H * P)
+    gxp = np.zeros((C, (H + 3) * P))
+    dw = np.empty_like(w)
     for i in range(3):
         for j in range(3):
-            dw[:, :, i, j] = np.einsum("ohw,chw->oc", g, xp[:, i:i + H, j:j + W])
-            gxp[:, i:i + H, j:j + W] += np.einsum("oc,ohw->chw", w[:, :, i, j], g)
-    return gxp[:, 1:1 + H, 1:1 + W], dw, g.sum(axis=(1, 2))
+            o = i * P + j
+            dw[:, :, i, j] = ge @ xp[:, o:o + H * P].T
+            gxp[:, o:o + H * P] += w[:, :, i, j].T @ ge
+    gx = gxp.reshape(C, H + 3, P)[:, 1:H + 1, 1:W + 1]
+    return np.ascontiguousarray(gx), dw, g.sum(axis=(1, 2))
 
 
 def shuffle(x):
