@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for the CPU baseline")
     ap.add_argument("--no-patterns", action="store_true", help="skip the batched-cells and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--only-pattern", choices=["appearance", "evaluation", "optimiser", "partition"],
+                    help="run one pattern measurement on one GPU, print its JSON and exit (no step line)")
     return ap.parse_args()
 
 
@@ -394,6 +396,37 @@ def evaluation_pattern(dev, hbm_gbs):
             "gbs": nbytes / (t * 1e-3) / 1e9, "hbm_frac": nbytes / (t * 1e-3) / 1e9 / hbm_gbs}
 
 
+def appearance_pattern(dev, bf16_tflops):
+    """The appearance loss of Eq. 3 (Sec. 4.2) on one 1920x1080 training view, forward and
+    backward: pooling, the CNN and its adjoint, the map, L1 and D-SSIM, every gradient."""
+    import torch
+    from paper_2402_17427_gb300 import appearance as AP
+    g = torch.Generator(device=dev)
+    g.manual_seed(9000)
+    H, W = 1080, 1920
+    y = torch.rand((3, H, W), device=dev, generator=g)
+    x = (0.9 * y + 0.05 + 0.05 * torch.randn((3, H, W), device=dev, generator=g)).clamp(0, 1)
+    model = AP.AppearanceModel(4, seed=9001, device=dev)
+    t_full = _time_cuda(lambda: model.loss(x, y, 1), reps=20, warmup=3)
+    t_fwd = _time_cuda(lambda: model.loss(x, y, 1, grad=False), reps=20, warmup=3)
+    # algorithmic FLOPs of the network as defined (dense 3x3 convolutions), forward; the backward
+    # pass costs two such products per layer (input gradient, weight gradient)
+    h, w = H // 32, W // 32
+    fwd = 0
+    for k, (c, o) in enumerate(AP.LAYERS):
+        px = (h << min(k, 4)) * (w << min(k, 4)) if k < 5 else H * W
+        fwd += 2 * px * o * 9 * c
+    tf32_peak = bf16_tflops * 1.1 / 2.25      # dense TF32 / BF16 nominal ratio
+    return {"workload": "1920x1080 view, 64-float embedding, CNN 67->256->...->16 at 528x960, "
+                        "bilinear to 1080p, 16->16->3 head; lambda 0.2",
+            "fwd_bwd_ms": t_full, "fwd_ms": t_fwd, "views_per_s": 1000.0 / t_full,
+            "gflop_fwd_bwd": 3 * fwd / 1e9,
+            "tflops_fwd_bwd": 3 * fwd / (t_full * 1e-3) / 1e12,
+            "tf32_frac": 3 * fwd / (t_full * 1e-3) / 1e12 / tf32_peak,
+            "tf32_peak_tflops": tf32_peak,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops x 1.1 / 2.25 (nominal TF32 / BF16)"}
+
+
 def serving_pattern(dev, seconds=30.0):
     """The merged 20M-Gaussian city (16 cells) served under a 200 req/s Poisson stream."""
     from paper_2402_17427_gb300 import scenes, serving
@@ -427,6 +460,20 @@ def main():
     from paper_2402_17427_gb300 import _build, binding as B, rasterize as R, scenes
     if rank == 0:
         _build.build()
+    if args.only_pattern:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        dev = torch.device("cuda", local)
+        fn = {"appearance": lambda: appearance_pattern(dev, float(peaks.get("bf16_tflops", 1900.0))),
+              "evaluation": lambda: evaluation_pattern(dev, float(peaks.get("hbm_gbs", 6800.0))),
+              "optimiser": lambda: optimiser_pattern(dev, float(peaks.get("hbm_gbs", 6800.0))),
+              "partition": lambda: partition_pattern(dev, float(peaks.get("hbm_gbs", 6800.0)))}[args.only_pattern]
+        if rank == 0:
+            print(json.dumps({"pattern": args.only_pattern, **fn()}), flush=True)
+        return
     if pg:
         pg.barrier()
     g, cam, target = scenes.blob_cell_1080p()
@@ -548,6 +595,7 @@ def main():
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
     F = 11 + 3 * 16
     N, px = g.n, cam.width * cam.height
     step_bytes = N * (4 * F + 12) + V * (8 * F + 156) + 116 * P + 76 * px
@@ -564,7 +612,8 @@ def main():
         try:
             patterns = {"batched_cells": batch_pattern(dev), "serving": serving_pattern(dev, args.serve_seconds),
                         "partition": partition_pattern(dev, hbm), "evaluation": evaluation_pattern(dev, hbm),
-                        "optimiser": optimiser_pattern(dev, hbm)}
+                        "optimiser": optimiser_pattern(dev, hbm),
+                        "appearance": appearance_pattern(dev, bf16_peak)}
         except Exception as e:  # report, never lose the main number
             patterns = {"error": repr(e)}
     line = {

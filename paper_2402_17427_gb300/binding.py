@@ -26,7 +26,8 @@ EXPORTED = ("vg_default_opts", "vg_status_string", "vg_kernel_launches", "vg_wor
             "vg_views_workspace_bytes", "vg_render_views", "vg_loss_l1_dssim_noalloc",
             "vg_airspace_boxes", "vg_visibility_workspace_bytes", "vg_camera_visibility", "vg_merge_workspace_bytes",
             "vg_merge_cells", "vg_eval_workspace_bytes", "vg_eval_color_corrected", "vg_adam_step",
-            "vg_densify_accumulate", "vg_densify_workspace_bytes", "vg_densify")
+            "vg_densify_accumulate", "vg_densify_workspace_bytes", "vg_densify", "vg_appearance_param_count",
+            "vg_appearance_workspace_bytes", "vg_appearance_loss")
 VG_LOSS_NOALLOC_MAX_PIXELS = 1024 * 1024
 
 
@@ -169,6 +170,13 @@ def lib():
                              _P, _P, _P, ctypes.POINTER(vg_densify_opts), _P, ctypes.c_size_t, vg_param_ptrs,
                              vg_param_ptrs, vg_param_ptrs, _P, _P]
     L.vg_densify.restype = ctypes.c_int
+    L.vg_appearance_param_count.argtypes = []
+    L.vg_appearance_param_count.restype = ctypes.c_int64
+    L.vg_appearance_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    L.vg_appearance_workspace_bytes.restype = ctypes.c_size_t
+    L.vg_appearance_loss.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_float, _P,
+                                     ctypes.c_size_t, _P, _P, _P, _P, _P, _P]
+    L.vg_appearance_loss.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -382,3 +390,21 @@ def vg_densify(inp: vg_gaussians, m_in: vg_gaussians, v_in: vg_gaussians, accum:
     _check(lib().vg_densify(ctypes.byref(inp), ctypes.byref(m_in), ctypes.byref(v_in), accum, count, normals,
                             ctypes.byref(opts), workspace, workspace_bytes, out, m_out, v_out, out_n, stream),
            "vg_densify")
+
+
+# ------------------------------------------------------------------ appearance model (vgappearance.h)
+
+def vg_appearance_param_count() -> int:
+    return int(lib().vg_appearance_param_count())
+
+
+def vg_appearance_workspace_bytes(width: int, height: int) -> int:
+    return int(lib().vg_appearance_workspace_bytes(width, height))
+
+
+def vg_appearance_loss(img: int, target: int, width: int, height: int, embedding: int, params: int, lam: float,
+                       workspace: int, workspace_bytes: int, out_loss: int, out_map: int, grad_img: int,
+                       grad_embedding: int, grad_params: int, stream: int) -> None:
+    _check(lib().vg_appearance_loss(img, target, width, height, embedding, params, lam, workspace, workspace_bytes,
+                                    out_loss, out_map, grad_img, grad_embedding, grad_params, stream),
+           "vg_appearance_loss")

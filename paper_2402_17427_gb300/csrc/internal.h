@@ -222,4 +222,14 @@ cudaError_t launch_blend_forward(const DevTables* tab, const HostPlan& plan, con
 cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool abs,
                                   cudaStream_t s);
 
+// SSIM half of the loss (loss.cu), for the appearance loss of Eq. 3: the moment pass (maps
+// [9][H][W], partials [ssim_partials][2] = (sum S, sum |x - y|) per block) and the gradient pass
+// that adds the SSIM term, the 32 x 32 block-mean gradient and the value already in grad.
+size_t ssim_maps_floats(int W, int H);
+int ssim_partials(int W, int H);
+cudaError_t launch_ssim_moments(const float* x, const float* y, int W, int H, float lambda, float* maps,
+                                double* partials, cudaStream_t s);
+cudaError_t launch_ssim_grad_appearance(const float* x, const float* y, const float* maps, int W, int H,
+                                        const float* pool_grad, int pw, int ph, float* grad, cudaStream_t s);
+
 }  // namespace vg

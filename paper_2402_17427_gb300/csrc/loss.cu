@@ -176,12 +176,18 @@ __global__ void __launch_bounds__(1024) loss_finalize(const double* __restrict__
 }
 
 // dL/dx: the three maps correlated with the window (same staging and passes as the moments),
-// combined with x, y and the L1 sign at each output pixel.
+// combined with x, y and the L1 sign at each output pixel.  kAppear (the loss of Eq. 3): no L1
+// term here; instead the value already in grad (the L1 term through the transformation map) and
+// the gradient of the 32 x 32 block mean the pixel belongs to (pool_grad [ph][pw][3], divided by
+// 1024) are added.
+template <bool kAppear>
 __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float* __restrict__ x,
                                                                      const float* __restrict__ y,
                                                                      const float* __restrict__ maps, int W, int H,
                                                                      Win win, float l1_scale,
-                                                                     float* __restrict__ grad) {
+                                                                     float* __restrict__ grad,
+                                                                     const float* __restrict__ pool_grad = nullptr,
+                                                                     int pw = 0, int ph = 0) {
   __shared__ float sm[3][LTH][SPX];
   __shared__ float hs[3][LTH][SPH];
   const int c = blockIdx.z;
@@ -228,9 +234,16 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
     if (gx >= W || gy >= H) continue;
     const size_t pix = c * plane + (size_t)gy * W + gx;
     const float xv = x[pix], yv = y[pix];
-    const float d = xv - yv;
-    const float l1g = d > 0.f ? l1_scale : (d < 0.f ? -l1_scale : 0.f);
-    grad[pix] = l1g + cm[0][j] + 2.f * xv * cm[1][j] + yv * cm[2][j];
+    if constexpr (kAppear) {
+      float add = grad[pix];
+      const int bx = gx >> 5, by = gy >> 5;
+      if (bx < pw && by < ph) add += pool_grad[(by * pw + bx) * 3 + c] * (1.f / 1024.f);
+      grad[pix] = add + cm[0][j] + 2.f * xv * cm[1][j] + yv * cm[2][j];
+    } else {
+      const float d = xv - yv;
+      const float l1g = d > 0.f ? l1_scale : (d < 0.f ? -l1_scale : 0.f);
+      grad[pix] = l1g + cm[0][j] + 2.f * xv * cm[1][j] + yv * cm[2][j];
+    }
   }
 }
 
@@ -243,6 +256,28 @@ Win make_window() {
 }
 
 }  // namespace
+
+size_t ssim_maps_floats(int W, int H) { return 9 * (size_t)W * H; }
+int ssim_partials(int W, int H) { return ((W + LT - 1) / LT) * ((H + LT - 1) / LT) * 3; }
+
+cudaError_t launch_ssim_moments(const float* x, const float* y, int W, int H, float lambda, float* maps,
+                                double* partials, cudaStream_t s) {
+  const dim3 grid((W + LT - 1) / LT, (H + LT - 1) / LT, 3);
+  const double inv = 1.0 / (3.0 * (double)W * H);
+  note_launches(1);
+  ssim_forward_kernel<<<grid, kLossThreads, 0, s>>>(x, y, W, H, make_window(), (float)(-lambda * inv), maps, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ssim_grad_appearance(const float* x, const float* y, const float* maps, int W, int H,
+                                        const float* pool_grad, int pw, int ph, float* grad, cudaStream_t s) {
+  const dim3 grid((W + LT - 1) / LT, (H + LT - 1) / LT, 3);
+  note_launches(1);
+  ssim_backward_kernel<true><<<grid, kLossThreads, 0, s>>>(x, y, maps, W, H, make_window(), 0.f, grad, pool_grad,
+                                                           pw, ph);
+  return cudaGetLastError();
+}
+
 }  // namespace vg
 
 using namespace vg;
@@ -272,7 +307,7 @@ extern "C" vg_status vg_loss_l1_dssim(const float* img, const float* target, int
   ssim_forward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
   loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
   if (out_grad)
-    ssim_backward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
+    ssim_backward_kernel<false><<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
   return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;
 }
 
@@ -341,6 +376,6 @@ extern "C" vg_status vg_loss_l1_dssim_noalloc(const float* img, const float* tar
   ssim_forward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
   loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
   if (out_grad)
-    ssim_backward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
+    ssim_backward_kernel<false><<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
   return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;
 }

@@ -1,0 +1,152 @@
+"""GPU parity of the decoupled appearance model (paper Sec. 4.2, Eq. 3, and the CNN of the
+supplementary material) against the FP64 appearance oracle, through the C ABI.
+
+Tolerances follow from the arithmetic.  The convolutions after the first run on TF32 inputs (10
+explicit mantissa bits, unit roundoff u = 2^-11, rounded to nearest) with FP32 accumulation: the
+GPU computes the exact network of slightly perturbed operands.  The map M is held to 2e-3 of its
+range (about 4 u).  A weight gradient is a sum over every pixel whose terms can cancel (with 1 x 2
+pooled cells the first layers' gradients are differences of near-equal terms), so its bound comes
+from the oracle itself: the relative change of that gradient when the tensor-core layers' weights
+are rounded to TF32 (one of the perturbations the GPU applies, the activations' roundings being of
+the same size) is its sensitivity s, and the GPU must agree within max(3e-3, 4 s).  The L1 term's
+sign is a decision taken in floating point: where |I_r M - I| is within the map's error bound the
+two sides may legitimately differ, so element-wise gradient checks skip those pixels.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import appearance as OA
+from paper_2402_17427_gb300 import appearance as AP
+from paper_2402_17427_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2402_17427_gb300 import _build
+    _build.build()
+    oracle.build()
+    assert torch.cuda.is_available()
+
+
+def _case(W, H, seed):
+    """Seeded inputs: a smooth rendering with noise, an independent target, an embedding and a
+    fan-in scaled CNN whose last bias is near 1 (so M stays near 1, as in training)."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.meshgrid(np.linspace(0, 1, H), np.linspace(0, 1, W), indexing="ij")
+    base = np.stack([0.5 + 0.3 * np.sin(6 * xx + c) * np.cos(4 * yy - c) for c in range(3)])
+    img = np.clip(base + 0.1 * rng.standard_normal((3, H, W)), 0, 1).astype(np.float32)
+    target = np.clip(base * 0.9 + 0.05 + 0.1 * rng.standard_normal((3, H, W)), 0, 1).astype(np.float32)
+    emb = rng.normal(0, 1, 64).astype(np.float32)
+    weights = OA.init_weights(rng)
+    weights[6] = (weights[6][0] * 0.5, 1.0 + 0.05 * rng.standard_normal(3))
+    weights = [(w.astype(np.float32), b.astype(np.float32)) for w, b in weights]
+    return img, target, emb, weights
+
+
+def _flat(weights):
+    return np.concatenate([np.concatenate([w.ravel(), b]) for w, b in weights]).astype(np.float32)
+
+
+def _gpu(img, target, emb, weights, lam, grad=True):
+    model = AP.AppearanceModel(1)
+    model.params.copy_(torch.from_numpy(_flat(weights)))
+    model.embeddings[0].copy_(torch.from_numpy(emb))
+    out = model.loss(torch.from_numpy(img).cuda(), torch.from_numpy(target).cuda(), 0, lam, grad=grad, want_map=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _tf32(x):
+    """Round to the TF32 format (10 explicit mantissa bits, to nearest, ties away from zero)."""
+    a = np.asarray(x, np.float32).copy()
+    bits = a.view(np.uint32)
+    bits[:] = (bits + np.uint32(0x1000)) & np.uint32(0xFFFFE000)
+    return a.astype(np.float64)
+
+
+def _compare(W, H, seed, lam=0.2):
+    img, target, emb, weights = _case(W, H, seed)
+    g = _gpu(img, target, emb, weights, lam)
+    w64 = [(w.astype(np.float64), b.astype(np.float64)) for w, b in weights]
+    e64 = emb.astype(np.float64)
+    L, M, gi, ge, gw = OA.loss_and_grads(img, target, e64, w64, lam)
+    # sensitivity of every gradient to TF32 rounding of the tensor-core layers' weights
+    wt = [w64[0]] + [(_tf32(w), b) for w, b in w64[1:]]
+    _, _, _, ge_t, gw_t = OA.loss_and_grads(img, target, e64, wt, lam)
+    tol = lambda ref, pert: max(3e-3, 4 * _rel(pert, ref))
+    # the map and the loss
+    span = M.max() - M.min()
+    assert np.abs(g["map"] - M).max() <= 2e-3 * span, np.abs(g["map"] - M).max() / span
+    assert g["loss"][0] == pytest.approx(L, rel=1e-4)
+    # the gradient of the image, element-wise where the L1 sign is settled
+    d = img.astype(np.float64) * M - target
+    settled = np.abs(d) > 4e-3 * span
+    scale = np.abs(gi).max()
+    assert np.abs(g["grad_img"] - gi)[settled].max() <= 2e-3 * scale
+    assert _rel(g["grad_img"], gi) <= 1e-2
+    # the embedding and every layer's weight and bias gradients
+    assert _rel(g["grad_embedding"], ge) <= tol(ge, ge_t)
+    views = AP.layer_views(torch.from_numpy(g["grad_params"]))
+    for k, ((gw_gpu, gb_gpu), (dw, db), (dw_t, db_t)) in enumerate(zip(views, gw, gw_t)):
+        assert _rel(gw_gpu.numpy(), dw) <= tol(dw, dw_t), k
+        assert _rel(gb_gpu.numpy(), db) <= tol(db, db_t), k
+    return g
+
+
+@pytest.mark.parametrize("W,H,seed", [(100, 70, 0), (330, 200, 1), (64, 32, 2)])
+def test_appearance_matches_oracle(W, H, seed):
+    # (100, 70): 3 x 2 pooled cells, 6 rows and 4 columns outside them, ragged 16 x 16 head tiles;
+    # (330, 200): 10 x 6 cells, 21 x 13 head tiles; (64, 32): the smallest shapes (1 x 2 cells)
+    _compare(W, H, seed)
+
+
+def test_appearance_full_size_matches_oracle():
+    # the 1920 x 1080 training view the benchmark times
+    _compare(1920, 1080, 3)
+
+
+def test_forward_only_and_identity_map():
+    img, target, emb, weights = _case(200, 96, 4)
+    full = _gpu(img, target, emb, weights, 0.2)
+    fwd = _gpu(img, target, emb, weights, 0.2, grad=False)
+    assert np.array_equal(full["map"], fwd["map"]) and full["loss"][0] == fwd["loss"][0]
+    # M = 1 (last convolution zero, bias 1): Eq. 3 is Eq. 1, and dL/dI_r is Eq. 1's gradient
+    weights[6] = (np.zeros_like(weights[6][0]), np.ones(3, np.float32))
+    g = _gpu(img, target, emb, weights, 0.2)
+    assert np.array_equal(g["map"], np.ones_like(g["map"]))
+    H, W = img.shape[1:]
+    need = B.vg_loss_workspace_bytes(W, H)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    grad = torch.empty(3, H, W, device="cuda")
+    x, y = torch.from_numpy(img).cuda(), torch.from_numpy(target).cuda()
+    B.vg_loss_l1_dssim(x.data_ptr(), y.data_ptr(), W, H, 0.2, ws.data_ptr(), need, loss.data_ptr(), grad.data_ptr(),
+                       torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert g["loss"][0] == pytest.approx(loss.item(), rel=1e-6)
+    assert np.array_equal(g["grad_img"], grad.cpu().numpy())
+    assert not g["grad_embedding"].any()
+    assert not g["grad_params"][:AP.param_count() - (3 * 16 * 9 + 3)].any()
+
+
+def test_appearance_rejects_bad_arguments():
+    assert B.vg_appearance_workspace_bytes(31, 100) == 0 and B.vg_appearance_workspace_bytes(100, 16385) == 0
+    assert B.vg_appearance_param_count() == AP.param_count() == 255539
+    dev = torch.zeros(16, device="cuda")
+    p = dev.data_ptr()
+    with pytest.raises(B.VGError):      # image too small
+        B.vg_appearance_loss(p, p, 16, 64, p, p, 0.2, p, 1 << 30, p, None, None, None, None, 0)
+    with pytest.raises(B.VGError):      # gradient pointers partly given
+        B.vg_appearance_loss(p, p, 64, 64, p, p, 0.2, p, 1 << 30, p, None, p, None, p, 0)
+    with pytest.raises(B.VGError):      # workspace too small
+        B.vg_appearance_loss(p, p, 64, 64, p, p, 0.2, p, 16, p, None, None, None, None, 0)
+    with pytest.raises(B.VGError):      # lambda outside [0, 1]
+        B.vg_appearance_loss(p, p, 64, 64, p, p, 1.5, p, 1 << 30, p, None, None, None, None, 0)
