@@ -298,6 +298,8 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
 }
 
 // One non-blocking helper stream per device for work forked off the caller's stream.
+}  // namespace
+
 cudaStream_t side_stream() {
   static std::mutex mu;
   static cudaStream_t streams[64] = {nullptr};
@@ -308,6 +310,8 @@ cudaStream_t side_stream() {
     streams[dev] = nullptr;
   return streams[dev];
 }
+
+namespace {
 
 // Backward pass of a prepared call (the table carries dL, final T, last and the gradient outputs).
 vg_status run_backward(Call& c, const vg_raster_opts* opts0, void* workspace, size_t workspace_bytes,

@@ -29,6 +29,7 @@
 //  * the SSIM half and the block-mean gradient reuse the loss kernels of Eq. 1.
 // The backward pass works in units of c = (1 - lambda) / (3 H W) (dL/dI_a = c sign(I_a - I)),
 // multiplying by c where results leave the head.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -83,37 +84,64 @@ __device__ __forceinline__ float2 ldg2(const float* p, int i) { return __ldg(rei
 //
 // A GEMM's B operand (K x N) is stored in fragment order: for k-step s, n-tile j and lane
 // (g, t) the pair (B[8s + t][8j + g], B[8s + t + 4][8j + g]) at float2 index (s N/8 + j) 32 + lane,
-// rounded to TF32.  A forward convolution has B[tap C + c][o] = W[o][c][tap]; the input-gradient
-// convolution (input = output gradient, O channels) has B[tap O + o][c] = W[o][c][8 - tap].
+// rounded to TF32.  K is tap-major with tapc channels a tap (tapc >= the input's channels; the
+// extra ones are zero).  A forward convolution has B[tap tapc + c][o] = W[o][c][tap]; the
+// input-gradient convolution (input = output gradient, O channels) has
+// B[tap tapc + o][c] = W[o][c][8 - tap].
 
 struct PackJob {
-  int layer, dgrad, kpad, npad, offset;
+  int layer, dgrad, tapc, kpad, npad, f16, offset;   // offset in elements of the job's type
 };
 constexpr int kPackJobs = 12;
 struct PackTable {
   PackJob job[kPackJobs];
-  int begin[kPackJobs + 1];
+  int begin[kPackJobs + 1];   // first element index of each job in the launch's index space
 };
 
-__global__ void pack_kernel(const float* __restrict__ params, float* __restrict__ packed, const PackTable tab) {
+// Magnitudes beyond FP16's largest finite value are clamped (never rounded to infinity).
+__device__ __forceinline__ __half to_half(float x) { return __float2half_rn(fminf(fmaxf(x, -65504.f), 65504.f)); }
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
+  const __half2 h = __halves2half2(to_half(lo), to_half(hi));
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// TF32 jobs (m16n8k8): element (k-step s, n-tile j, lane, e) = B[8s + t + 4e][8j + g].
+// FP16 jobs (m16n8k16): element (s, j, lane, r, h) = B[16s + 2t + h + 8r][8j + g], so that each
+// lane reads its two B registers as one 8-byte word.
+__global__ void pack_kernel(const float* __restrict__ params, void* __restrict__ packed, const PackTable tab) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= tab.begin[kPackJobs]) return;
   int jb = 0;
   while (i >= tab.begin[jb + 1]) ++jb;
   const PackJob J = tab.job[jb];
   const int local = i - tab.begin[jb];
-  const int e = local & 1, lane = (local >> 1) & 31, rest = local >> 6;
-  const int nt = J.npad / 8, jn = rest % nt, s = rest / nt;
-  const int k = 8 * s + (lane & 3) + 4 * e, n = 8 * jn + (lane >> 2);
+  const int nt = J.npad / 8;
+  int k, n, rest, lane;
+  if (J.f16) {
+    const int h = local & 1, r = (local >> 1) & 1;
+    lane = (local >> 2) & 31;
+    rest = local >> 7;
+    k = 16 * (rest / nt) + 2 * (lane & 3) + h + 8 * r;
+  } else {
+    const int e = local & 1;
+    lane = (local >> 1) & 31;
+    rest = local >> 6;
+    k = 8 * (rest / nt) + (lane & 3) + 4 * e;
+  }
+  n = 8 * (rest % nt) + (lane >> 2);
   const int C = layer_c(J.layer), O = layer_o(J.layer);
   const float* W = params + w_off(J.layer);
+  const int tap = k / J.tapc, c = k % J.tapc;
   float v = 0.f;
   if (!J.dgrad) {
-    if (k < 9 * C && n < O) v = W[(n * C + k % C) * 9 + k / C];
+    if (tap < 9 && c < C && n < O) v = W[(n * C + c) * 9 + tap];
   } else {
-    if (k < 9 * O && n < C) v = W[((k % O) * C + n) * 9 + 8 - k / O];
+    if (tap < 9 && c < O && n < C) v = W[(c * C + n) * 9 + 8 - tap];
   }
-  packed[J.offset + local] = tf32r(v);
+  if (J.f16)
+    static_cast<__half*>(packed)[J.offset + local] = to_half(v);
+  else
+    static_cast<float*>(packed)[J.offset + local] = tf32r(v);
 }
 
 // E[tap][o] = sum_c W0[o][3 + c][tap] l[c]: the embedding's share of conv0 at each tap.
@@ -161,11 +189,12 @@ __global__ void __launch_bounds__(256) pool_kernel(const float* __restrict__ img
 }
 
 // A0[y][x][o] = b0[o] + sum over in-image taps of (E[tap][o] + sum_{c < 3} W0[o][c][tap] P[y'][x'][c]).
-// One block per low-resolution row, one thread per output channel.
+// One thread per output channel; each block takes kConv0FwdPx consecutive low-resolution pixels.
+constexpr int kConv0FwdPx = 8;
 __global__ void __launch_bounds__(256) conv0_kernel(const float* __restrict__ P, const float* __restrict__ E,
                                                     const float* __restrict__ params, int ph, int pw,
                                                     float* __restrict__ A0) {
-  const int o = threadIdx.x, y = blockIdx.x;
+  const int o = threadIdx.x;
   float wt[27], e[9];
   const float* W = params + w_off(0) + (size_t)o * 67 * 9;
 #pragma unroll
@@ -173,65 +202,96 @@ __global__ void __launch_bounds__(256) conv0_kernel(const float* __restrict__ P,
 #pragma unroll
   for (int k = 0; k < 9; ++k) e[k] = E[k * 256 + o];
   const float b = params[b_off(0) + o];
-  for (int x = 0; x < pw; ++x) {
+  const int p1 = min(ph * pw, (blockIdx.x + 1) * kConv0FwdPx);
+  for (int p = blockIdx.x * kConv0FwdPx; p < p1; ++p) {
+    const int y = p / pw, x = p % pw;
     float acc = b;
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
       if (yy < 0 || yy >= ph || xx < 0 || xx >= pw) continue;
-      const float* p = P + (yy * pw + xx) * 3;
+      const float* q = P + (yy * pw + xx) * 3;
       acc += e[tap];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc = fmaf(wt[c * 9 + tap], p[c], acc);
+      for (int c = 0; c < 3; ++c) acc = fmaf(wt[c * 9 + tap], q[c], acc);
     }
-    A0[((size_t)y * pw + x) * 256 + o] = acc;
+    A0[(size_t)p * 256 + o] = acc;
   }
 }
 
 // ---------------------------------------------------------------- blocks 1..4: implicit GEMM
-//
+
+// Stages the logical (pixel-shuffled) input of a block, rows [Y0, Y0 + SH) x columns [X0, X0 + SW)
+// at resolution (Hr, Wr) with C channels, into dst (pixel pitch P), rounded to TF32 and zero
+// outside the image.  Aprev is [Hr/2][Wr/2][4C]: native channels 4c..4c+3 of native pixel
+// (Yn, Xn) are channel c of the logical pixels (2Yn + i, 2Xn + j), so each float4 load feeds four
+// staged pixels.
+template <int C, int P>
+__device__ __forceinline__ void stage_shuffled(float* dst, const float* __restrict__ Aprev, int Y0, int X0, int SH,
+                                               int SW, int Hr, int Wr) {
+  const int Hn = Hr >> 1, Wn = Wr >> 1;
+  const int yn0 = Y0 >> 1, xn0 = X0 >> 1;
+  const int nxn = ((X0 + SW - 1) >> 1) - xn0 + 1, n = (((Y0 + SH - 1) >> 1) - yn0 + 1) * nxn;
+  for (int i = threadIdx.x; i < n * C; i += blockDim.x) {
+    const int c = i % C, px = i / C;
+    const int yn = yn0 + px / nxn, xn = xn0 + px % nxn;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (yn >= 0 && yn < Hn && xn >= 0 && xn < Wn)
+      v = __ldg(reinterpret_cast<const float4*>(Aprev + ((size_t)yn * Wn + xn) * (4 * C)) + c);
+    const float q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = 2 * yn + (k >> 1) - Y0, s = 2 * xn + (k & 1) - X0;
+      if (r >= 0 && r < SH && s >= 0 && s < SW) dst[(r * SW + s) * P + c] = tf32r(q[k]);
+    }
+  }
+}
+
+// Stages rows [Y0, Y0 + SH) x columns [X0, X0 + SW) of g [Hr][Wr][C] (times [act > 0] when MASK)
+// into dst (pixel pitch P), rounded to TF32 and zero outside the image.
+template <int C, int P, bool MASK>
+__device__ __forceinline__ void stage_plain(float* dst, const float* __restrict__ g, const float* __restrict__ act,
+                                            int Y0, int X0, int SH, int SW, int Hr, int Wr) {
+  for (int i = threadIdx.x; i < SH * SW * (C / 4); i += blockDim.x) {
+    const int v = i % (C / 4), px = i / (C / 4);
+    const int Y = Y0 + px / SW, X = X0 + px % SW;
+    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (Y >= 0 && Y < Hr && X >= 0 && X < Wr) {
+      const size_t e = ((size_t)Y * Wr + X) * C + 4 * v;
+      z = __ldg(reinterpret_cast<const float4*>(g + e));
+      if constexpr (MASK) {
+        const float4 av = __ldg(reinterpret_cast<const float4*>(act + e));
+        z = make_float4(av.x > 0.f ? z.x : 0.f, av.y > 0.f ? z.y : 0.f, av.z > 0.f ? z.z : 0.f, av.w > 0.f ? z.w : 0.f);
+      }
+    }
+    *reinterpret_cast<float4*>(dst + px * P + 4 * v) = make_float4(tf32r(z.x), tf32r(z.y), tf32r(z.z), tf32r(z.w));
+  }
+}
+
 // One block computes MT rows x 16 columns of output pixels and all O channels.  The input tile
 // ((MT + 2) x 18 pixels x C channels, pitch C + 4 so that the 8 x 4 lanes of a fragment load hit
-// distinct banks) is staged once, rounded to TF32.  Warps form WM x (8 / WM): each owns MT / WM
-// pixel rows (m-tiles) and O / 8 / (8 / WM) n-tiles.
-//  forward (DGRAD false): input = shuffle(Aprev) with Aprev [Hr/2][Wr/2][4C]; output
-//    ReLU(acc + b) -> out [Hr][Wr][O].
-//  input gradient (DGRAD true): input = gA * [A > 0] with gA, A [Hr][Wr][C]; output (the
-//    gradient of the shuffled input, O channels) -> out in Aprev's layout [Hr/2][Wr/2][4 O].
-template <int C, int O, int MT, int WM, bool DGRAD>
+// distinct banks) is staged once.  Warps form WM x (8 / WM): each owns MT / WM pixel rows
+// (m-tiles) and O / 8 / (8 / WM) n-tiles.
+//  forward (DGRAD false): input = shuffle(in) with in [Hr/2][Wr/2][4C]; output ReLU(acc + b) ->
+//    out [Hr][Wr][O].
+//  input gradient (DGRAD true): input = in [Hr][Wr][C], the output gradient of the block (times
+//    [act > 0] when MASK_IN; otherwise already masked); output = the gradient of the shuffled input
+//    (O channels), written in the previous layer's layout [Hr/2][Wr/2][4 O] and, when MASK_OUT,
+//    times [aout > 0] (that layer's ReLU).
+template <int C, int O, int MT, int WM, bool DGRAD, bool MASK_IN, bool MASK_OUT>
 __global__ void __launch_bounds__(256) conv_mma_kernel(const float* __restrict__ in, const float* __restrict__ act,
                                                        const float* __restrict__ wpk, const float* __restrict__ bias,
-                                                       float* __restrict__ out, int Hr, int Wr) {
+                                                       const float* __restrict__ aout, float* __restrict__ out, int Hr,
+                                                       int Wr) {
   constexpr int NT = O / 8, WN = 8 / WM, NTW = NT / WN, MTW = MT / WM;
   constexpr int PITCH = C + 4, SW = 18, SHT = MT + 2;
   static_assert(NT % WN == 0 && MT % WM == 0 && C % 8 == 0, "tiling");
   extern __shared__ __align__(16) float smem[];
   const int ox = blockIdx.x * 16, oy = blockIdx.y * MT;
-  if constexpr (DGRAD) {
-    for (int i = threadIdx.x; i < SHT * SW * (C / 4); i += 256) {
-      const int v = i % (C / 4), px = i / (C / 4);
-      const int Y = oy - 1 + px / SW, X = ox - 1 + px % SW;
-      float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (Y >= 0 && Y < Hr && X >= 0 && X < Wr) {
-        const size_t e = ((size_t)Y * Wr + X) * C + 4 * v;
-        const float4 gv = __ldg(reinterpret_cast<const float4*>(in + e));
-        const float4 av = __ldg(reinterpret_cast<const float4*>(act + e));
-        z = make_float4(av.x > 0.f ? gv.x : 0.f, av.y > 0.f ? gv.y : 0.f, av.z > 0.f ? gv.z : 0.f,
-                        av.w > 0.f ? gv.w : 0.f);
-      }
-      *reinterpret_cast<float4*>(smem + px * PITCH + 4 * v) = make_float4(tf32r(z.x), tf32r(z.y), tf32r(z.z), tf32r(z.w));
-    }
-  } else {
-    const int Wp = Wr >> 1;
-    for (int i = threadIdx.x; i < SHT * SW * C; i += 256) {
-      const int c = i % C, px = i / C;
-      const int Y = oy - 1 + px / SW, X = ox - 1 + px % SW;
-      float z = 0.f;
-      if (Y >= 0 && Y < Hr && X >= 0 && X < Wr)
-        z = __ldg(in + ((size_t)(Y >> 1) * Wp + (X >> 1)) * (4 * C) + 4 * c + 2 * (Y & 1) + (X & 1));
-      smem[px * PITCH + c] = tf32r(z);
-    }
-  }
+  if constexpr (DGRAD)
+    stage_plain<C, PITCH, MASK_IN>(smem, in, act, oy - 1, ox - 1, SHT, SW, Hr, Wr);
+  else
+    stage_shuffled<C, PITCH>(smem, in, oy - 1, ox - 1, SHT, SW, Hr, Wr);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
   const int wm = warp % WM, wn = warp / WM;
@@ -273,9 +333,14 @@ __global__ void __launch_bounds__(256) conv_mma_kernel(const float* __restrict__
         if (X >= Wr) continue;
         const float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
         if constexpr (DGRAD) {
-          float* d = out + ((size_t)(Y >> 1) * (Wr >> 1) + (X >> 1)) * (4 * O) + 2 * (Y & 1) + (X & 1);
-          d[4 * o] = v0;
-          d[4 * o + 4] = v1;
+          const size_t e = ((size_t)(Y >> 1) * (Wr >> 1) + (X >> 1)) * (4 * O) + 2 * (Y & 1) + (X & 1) + 4 * o;
+          if constexpr (MASK_OUT) {
+            out[e] = __ldg(aout + e) > 0.f ? v0 : 0.f;
+            out[e + 4] = __ldg(aout + e + 4) > 0.f ? v1 : 0.f;
+          } else {
+            out[e] = v0;
+            out[e + 4] = v1;
+          }
         } else {
           *reinterpret_cast<float2*>(out + ((size_t)Y * Wr + X) * O + o) =
               make_float2(fmaxf(v0 + __ldg(bias + o), 0.f), fmaxf(v1 + __ldg(bias + o + 1), 0.f));
@@ -286,11 +351,13 @@ __global__ void __launch_bounds__(256) conv_mma_kernel(const float* __restrict__
 }
 
 // Weight gradient of block k: dW^T[(tap, c)][o] = sum_p X(p + tap)[c] gZ(p)[o] with X =
-// shuffle(Aprev) and gZ = gA * [A > 0]; db[o] = sum_p gZ(p)[o].  GEMM M = 9 C (rows past 9 C are
-// padding), N = O, K = pixels.  Block (x, y) owns m-tiles [4 y, 4 y + 4) and a run of pixel
-// tiles (TY x 16); warp w owns m-tile w % 4 and n-tiles [(w / 4) NT / 2, ...).  Row pitches are
-// 8 or 24 mod 32 floats (pixel along t, channel along g in both fragments: distinct banks).
-template <int C, int O, int TY>
+// shuffle(Aprev) and gZ the block's masked output gradient (gA * [A > 0], masked here when
+// MASK_IN); db[o] = sum_p gZ(p)[o].  GEMM M = 9 C (rows past 9 C are padding), N = O, K = pixels.
+// Block (x, y) owns m-tiles [4 y, 4 y + 4) and a run of pixel tiles (TY x 16); warp w owns m-tile
+// w % 4 and n-tiles [(w / 4) NT / 2, ...).  The pixels of a k-step are taken in the order x0 + 2t
+// (k = t), x0 + 2t + 1 (k = t + 4): with row pitches of 8 or 24 mod 32 floats the scalar fragment
+// loads (pixel along t, channel along g) then hit distinct banks.
+template <int C, int O, int TY, bool MASK_IN>
 __global__ void __launch_bounds__(256) wgrad_kernel(const float* __restrict__ Aprev, const float* __restrict__ gA,
                                                     const float* __restrict__ A, float* __restrict__ dW,
                                                     float* __restrict__ db, int Hr, int Wr, int tiles_x, int tiles,
@@ -316,32 +383,12 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const float* __restrict__ Ap
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
   float dbs = 0.f;
-  const int Wp = Wr >> 1;
   const int tile_end = min(tiles, (blockIdx.x + 1) * per_block);
   for (int tile = blockIdx.x * per_block; tile < tile_end; ++tile) {
     const int oy = (tile / tiles_x) * TY, ox = (tile % tiles_x) * 16;
     __syncthreads();
-    for (int i = threadIdx.x; i < (TY + 2) * SW * C; i += 256) {
-      const int c = i % C, px = i / C;
-      const int Y = oy - 1 + px / SW, X = ox - 1 + px % SW;
-      float z = 0.f;
-      if (Y >= 0 && Y < Hr && X >= 0 && X < Wr)
-        z = __ldg(Aprev + ((size_t)(Y >> 1) * Wp + (X >> 1)) * (4 * C) + 4 * c + 2 * (Y & 1) + (X & 1));
-      sX[px * PX + c] = tf32r(z);
-    }
-    for (int i = threadIdx.x; i < TY * 16 * (O / 4); i += 256) {
-      const int v = i % (O / 4), px = i / (O / 4);
-      const int Y = oy + px / 16, X = ox + px % 16;
-      float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (Y < Hr && X < Wr) {
-        const size_t e = ((size_t)Y * Wr + X) * O + 4 * v;
-        const float4 gv = __ldg(reinterpret_cast<const float4*>(gA + e));
-        const float4 av = __ldg(reinterpret_cast<const float4*>(A + e));
-        z = make_float4(av.x > 0.f ? gv.x : 0.f, av.y > 0.f ? gv.y : 0.f, av.z > 0.f ? gv.z : 0.f,
-                        av.w > 0.f ? gv.w : 0.f);
-      }
-      *reinterpret_cast<float4*>(sZ + px * PZ + 4 * v) = z;
-    }
+    stage_shuffled<C, PX>(sX, Aprev, oy - 1, ox - 1, TY + 2, SW, Hr, Wr);
+    stage_plain<O, PZ, MASK_IN>(sZ, gA, A, oy, ox, TY, 16, Hr, Wr);
     __syncthreads();
     if (blockIdx.y == 0 && threadIdx.x < O)
       for (int p = 0; p < TY * 16; ++p) dbs += sZ[p * PZ + threadIdx.x];
@@ -349,14 +396,14 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const float* __restrict__ Ap
 #pragma unroll 2
       for (int s = 0; s < 2 * TY; ++s) {
         const int ty = s >> 1, x0 = (s & 1) * 8;
-        const int pxA = (ty * SW + x0 + t) * PX;     // X at pixel (ty, x0 + t) + tap offsets below
-        const float a[4] = {v0 ? sX[pxA + xo0] : 0.f, v1 ? sX[pxA + xo1] : 0.f,
-                            v0 ? sX[pxA + 4 * PX + xo0] : 0.f, v1 ? sX[pxA + 4 * PX + xo1] : 0.f};
-        const float* zb = sZ + (ty * 16 + x0 + t) * PZ + g;
+        const int pxA = (ty * SW + x0 + 2 * t) * PX;     // X at pixel (ty, x0 + 2t); tap offsets in xo
+        const float a[4] = {v0 ? sX[pxA + xo0] : 0.f, v1 ? sX[pxA + xo1] : 0.f, v0 ? sX[pxA + PX + xo0] : 0.f,
+                            v1 ? sX[pxA + PX + xo1] : 0.f};
+        const float* zb = sZ + (ty * 16 + x0 + 2 * t) * PZ + g;
 #pragma unroll
         for (int j = 0; j < NTW; ++j) {
           const int n = (nt0 + j) * 8;
-          mma8(acc[j], a, zb[n], zb[4 * PZ + n]);
+          mma8(acc[j], a, zb[n], zb[PZ + n]);
         }
       }
     }
@@ -383,27 +430,30 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const float* __restrict__ Ap
 // gA0 is dL/dA0 (no ReLU on conv0).  Per output channel o and tap:
 //   G[tap][o] = sum over pixels p with p + tap inside of gA0(p)[o]   (the embedding's share)
 //   dW0[o][c][tap] = sum_p gA0(p)[o] P(p + tap)[c] for c < 3;  db0[o] = sum_p gA0(p)[o]
-// One block per low-resolution row; atomics across rows.
+// Each block takes kConv0Px consecutive low-resolution pixels; atomics across blocks.
+constexpr int kConv0Px = 16;
 __global__ void __launch_bounds__(256) conv0_wgrad_kernel(const float* __restrict__ gA0, const float* __restrict__ P,
                                                           int ph, int pw, float* __restrict__ G,
                                                           float* __restrict__ gparams) {
-  const int o = threadIdx.x, y = blockIdx.x;
+  const int o = threadIdx.x;
   float gs[9], dw[27], dbs = 0.f;
 #pragma unroll
   for (int k = 0; k < 9; ++k) gs[k] = 0.f;
 #pragma unroll
   for (int k = 0; k < 27; ++k) dw[k] = 0.f;
-  for (int x = 0; x < pw; ++x) {
-    const float gv = gA0[((size_t)y * pw + x) * 256 + o];
+  const int p1 = min(ph * pw, (blockIdx.x + 1) * kConv0Px);
+  for (int p = blockIdx.x * kConv0Px; p < p1; ++p) {
+    const int y = p / pw, x = p % pw;
+    const float gv = gA0[(size_t)p * 256 + o];
     dbs += gv;
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
       if (yy < 0 || yy >= ph || xx < 0 || xx >= pw) continue;
       gs[tap] += gv;
-      const float* p = P + (yy * pw + xx) * 3;
+      const float* q = P + (yy * pw + xx) * 3;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) dw[c * 9 + tap] = fmaf(gv, p[c], dw[c * 9 + tap]);
+      for (int c = 0; c < 3; ++c) dw[c * 9 + tap] = fmaf(gv, q[c], dw[c * 9 + tap]);
     }
   }
 #pragma unroll
@@ -471,21 +521,39 @@ __global__ void __launch_bounds__(256) conv0_embed_grad_kernel(const float* __re
 
 // ---------------------------------------------------------------- full-resolution head
 //
-// Regions around the 16 x 16 output tile T at (oy, ox): R_k = T grown by k pixels.  Shared memory:
-//   sU  U over R4 (24 x 24 pixels, pitch 20 floats), TF32
-//   sH  Hh = ReLU(Z5) over R3 (22 x 22), later overwritten by gZ5' over R1
-//   sG  gM' = sign(I_a - I) I_r over R2 (20 x 20, pitch 4)
-//   sF  F4 footprint of R4 (<= 14 x 14 low-res pixels, 16 channels); later the accumulator of
-//       dL/dF4 over the footprint of T
+// One persistent block per SM pair of 16 x 16 output tiles T at (oy, ox); R_k = T grown by k
+// pixels.  The head's GEMMs run as mma.sync m16n8k16 with FP16 operands (10-bit mantissa like
+// TF32, rounded to nearest, magnitudes clamped to FP16's range) and FP32 accumulation; every
+// operand comes from shared memory through ldmatrix (.trans for the weight gradients, whose K is
+// pixels).  Shared memory (FP16 rows of 48 bytes, so any 8 consecutive pixels of an ldmatrix
+// hit distinct banks):
+//   sU  U over R4 (24 x 24 pixels x 16 channels), copied with cp.async from the up-sampled image
+//       (computed once by upsample_kernel) while the previous tile finishes
+//   sH  Hh = ReLU(Z5) over R3 (22 x 22)
+//   sZ  gZ5' = (conv6 adjoint of gM') * [Hh > 0] over R1 (18 x 18)
+//   sG  gM' = sign(I_a - I) I_r over R2 (20 x 20, 16-byte rows, channels 3..7 zero)
+//   sI  I_r and I over R2 (FP32 planes, zero outside the image), fetched with cp.async at the
+//       start of the tile
+//   tables: bilinear taps (first, second source row / column, weight of the second) of R4's
+//       rows and columns, -1 outside the image
+// After the GEMMs, sH and sZ hold dL/dU over T and its column-reduced form (FP32) for the
+// bilinear adjoint's two gather passes.
 constexpr int HT = 16;
 constexpr int R4 = HT + 8, R3 = HT + 6, R2 = HT + 4, R1 = HT + 2;
-constexpr int UPITCH = 20;
-constexpr int FP = 14;
+constexpr int HP = 24;                // halves per pixel in sU / sH / sZ
+constexpr int GP = 8;                 // halves per pixel in sG
+constexpr int FT = 10;                // dL/dF4 footprint side of T
 constexpr int kHeadThreads = 256;
-constexpr int kHeadSmemFloats = R4 * R4 * UPITCH + R3 * R3 * UPITCH + R2 * R2 * 4 + FP * FP * 16;
+constexpr int kBU = R4 * R4 * HP * 2, kBH = R3 * R3 * HP * 2, kBZ = R1 * R1 * HP * 2, kBG = R2 * R2 * GP * 2;
+constexpr int kBI = 2 * 3 * R2 * R2 * 4, kBT = 6 * R4 * 4;
+constexpr int kHeadSmemBytes = kBU + kBH + kBZ + kBG + kBI + kBT;
+static_assert(HT * HT * 16 * 4 <= kBH && HT * FT * 16 * 4 <= kBZ, "bilinear adjoint buffers fit");
+static_assert(kBU % 16 == 0 && kBH % 16 == 0 && kBZ % 16 == 0 && kBG % 16 == 0 && kBI % 16 == 0, "alignment");
 
 struct HeadArgs {
-  const float *img, *target, *f4, *w5f, *w5d, *w6f, *w6d, *b5, *b6;
+  const float *img, *target, *b5, *b6;
+  const __half* u;                          // the up-sampled F4, [H][W][16]
+  const uint2 *w5f, *w5d, *w6f, *w6d;       // FP16 B fragments
   float *gimg, *map, *gf4, *dw5, *db5, *dw6, *db6;
   double* partials;
   int H, W, h4, w4, tiles_x, tiles;
@@ -513,98 +581,173 @@ __device__ __forceinline__ Tap up_tap(int y, int n_in, int n_out) {
   return r;
 }
 
+// U = F4 [h4][w4][16] up-sampled bilinearly to [H][W][16], stored in FP16 (magnitudes clamped to
+// its range): the head's conv5 input, computed once rather than once per overlapping head tile.
+// A thread produces 8 channels of one pixel.
+__global__ void __launch_bounds__(256) upsample_kernel(const float* __restrict__ f4, int h4, int w4, int H, int W,
+                                                       __half* __restrict__ U) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= H * W * 2) return;
+  const int hv = i & 1, px = i >> 1, y = px / W, x = px % W;
+  const Tap ty = up_tap(y, h4, H), tx = up_tap(x, w4, W);
+  const float fy = ty.f, fx = tx.f, gy = 1.f - fy, gx = 1.f - fx;
+  const float4* f00 = reinterpret_cast<const float4*>(f4 + ((size_t)ty.i0 * w4 + tx.i0) * 16 + 8 * hv);
+  const float4* f01 = reinterpret_cast<const float4*>(f4 + ((size_t)ty.i0 * w4 + tx.i1) * 16 + 8 * hv);
+  const float4* f10 = reinterpret_cast<const float4*>(f4 + ((size_t)ty.i1 * w4 + tx.i0) * 16 + 8 * hv);
+  const float4* f11 = reinterpret_cast<const float4*>(f4 + ((size_t)ty.i1 * w4 + tx.i1) * 16 + 8 * hv);
+  float u[8];
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    const float4 p = __ldg(f00 + v), q = __ldg(f01 + v), r = __ldg(f10 + v), t = __ldg(f11 + v);
+    u[4 * v + 0] = gy * (gx * p.x + fx * q.x) + fy * (gx * r.x + fx * t.x);
+    u[4 * v + 1] = gy * (gx * p.y + fx * q.y) + fy * (gx * r.y + fx * t.y);
+    u[4 * v + 2] = gy * (gx * p.z + fx * q.z) + fy * (gx * r.z + fx * t.z);
+    u[4 * v + 3] = gy * (gx * p.w + fx * q.w) + fy * (gx * r.w + fx * t.w);
+  }
+  *reinterpret_cast<uint4*>(U + (size_t)px * 16 + 8 * hv) =
+      make_uint4(pack_half2(u[0], u[1]), pack_half2(u[2], u[3]), pack_half2(u[4], u[5]), pack_half2(u[6], u[7]));
+}
+
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+// D += A B for one m16n8k16 FP16 tile: a = {A[g][2t..], A[g+8][2t..], A[g][2t+8..], A[g+8][2t+8..]},
+// b = {B[2t..][g], B[2t+8..][g]} (two halves a register), d as for m16n8k8.
+__device__ __forceinline__ void mma16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Four 8 x 8 FP16 matrices: lane l gives the 16-byte row address of matrix l / 8, row l % 8.
+// Without .trans a lane receives (row g, columns 2t, 2t + 1) of each matrix, with .trans
+// (rows 2t, 2t + 1, column g).
+__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr) : "memory");
+}
+__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr) : "memory");
+}
+__device__ __forceinline__ void ldsm2t(uint32_t& r0, uint32_t& r1, uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r0), "=r"(r1) : "r"(addr) : "memory");
+}
+
+__device__ __forceinline__ float2 half2_to_float2(uint32_t v) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&v));
+}
+
 template <bool BWD>
 __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a) {
-  extern __shared__ __align__(16) float sm[];
-  float* sU = sm;
-  float* sH = sU + R4 * R4 * UPITCH;
-  float* sG = sH + R3 * R3 * UPITCH;
-  float* sF = sG + R2 * R2 * 4;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __half* sU = reinterpret_cast<__half*>(smraw);
+  __half* sH = reinterpret_cast<__half*>(smraw + kBU);
+  __half* sZ = reinterpret_cast<__half*>(smraw + kBU + kBH);
+  __half* sG = reinterpret_cast<__half*>(smraw + kBU + kBH + kBZ);
+  float* sI = reinterpret_cast<float*>(smraw + kBU + kBH + kBZ + kBG);   // [2][3][R2][R2]
+  int* tY0 = reinterpret_cast<int*>(smraw + kBU + kBH + kBZ + kBG + kBI);
+  int* tY1 = tY0 + R4;
+  float* tFY = reinterpret_cast<float*>(tY1 + R4);
+  int* tX0 = reinterpret_cast<int*>(tFY + R4);
+  int* tX1 = tX0 + R4;
+  float* tFX = reinterpret_cast<float*>(tX1 + R4);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  // ldmatrix rows: lrow / lq for A (pixel rows, channel halves) and for the weight-gradient B
+  // operands; tp / tc for the transposed weight-gradient A operands (pixel, channel half)
+  const int lrow = (lane & 7) + (lane & 8), lq = lane >> 4;
+  const int tp = (lane & 7) + ((lane >> 4) << 3), tc = (lane >> 3) & 1;
+  const uint32_t uU = smem_u32(sU), uH = smem_u32(sH), uZ = smem_u32(sZ), uG = smem_u32(sG);
   const size_t HW = (size_t)a.H * a.W;
   float l1 = 0.f;
-  // weight-gradient accumulators kept across tiles: dW6 units (tap warp; warp 7 also tap 8),
-  // dW5 units (tap, n-tile) = u >> 1, u & 1 for u = warp, warp + 8 and, for warps 0 and 1, 16 + warp
-  float acc6[2][4], acc5[3][4], db5[2][2], db6[2];
+  // weight-gradient accumulators kept across tiles, for this warp's taps (warp; warp 7 also 8)
+  float acc5[2][2][4], acc6[2][4], db5[2][2], db6[3];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
+    acc5[0][0][q] = acc5[0][1][q] = acc5[1][0][q] = acc5[1][1][q] = 0.f;
     acc6[0][q] = acc6[1][q] = 0.f;
-    acc5[0][q] = acc5[1][q] = acc5[2][q] = 0.f;
   }
-  db5[0][0] = db5[0][1] = db5[1][0] = db5[1][1] = db6[0] = db6[1] = 0.f;
-  const int n4 = warp == 7 ? 2 : 1;
-  const int n6 = warp < 2 ? 3 : 2;
+  db5[0][0] = db5[0][1] = db5[1][0] = db5[1][1] = db6[0] = db6[1] = db6[2] = 0.f;
+  // U over R4 around a tile, zero outside the image
+  auto fetch_u = [&](int tile) {
+    if (tile < a.tiles) {
+      const int oy = (tile / a.tiles_x) * HT, ox = (tile % a.tiles_x) * HT;
+      for (int i = threadIdx.x; i < R4 * R4 * 2; i += kHeadThreads) {
+        const int px = i >> 1, hv = i & 1;
+        const int y = oy - 4 + px / R4, x = ox - 4 + px % R4;
+        const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
+        cp_async16_zfill(sU + px * HP + 8 * hv, a.u + (in ? ((size_t)y * a.W + x) * 16 + 8 * hv : 0), in);
+      }
+    }
+    cp_async_commit();
+  };
+  fetch_u(blockIdx.x);
 
   for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
     const int oy = (tile / a.tiles_x) * HT, ox = (tile % a.tiles_x) * HT;
     __syncthreads();
-    // S0: the F4 footprint of R4
-    const int fy0 = up_tap(max(oy - 4, 0), a.h4, a.H).i0, fy1 = up_tap(min(oy + HT + 3, a.H - 1), a.h4, a.H).i1;
-    const int fx0 = up_tap(max(ox - 4, 0), a.w4, a.W).i0, fx1 = up_tap(min(ox + HT + 3, a.W - 1), a.w4, a.W).i1;
-    const int nfx = fx1 - fx0 + 1, nff = (fy1 - fy0 + 1) * nfx;
-    for (int i = threadIdx.x; i < nff * 4; i += kHeadThreads) {
-      const int v = i & 3, px = i >> 2, r = px / nfx, q = px % nfx;
-      *reinterpret_cast<float4*>(sF + (r * FP + q) * 16 + 4 * v) =
-          __ldg(reinterpret_cast<const float4*>(a.f4 + ((size_t)(fy0 + r) * a.w4 + fx0 + q) * 16) + v);
-    }
-    __syncthreads();
-    // S1: U over R4 (zero outside the image: conv5's padding)
-    for (int px = threadIdx.x; px < R4 * R4; px += kHeadThreads) {
-      const int y = oy - 4 + px / R4, x = ox - 4 + px % R4;
-      float4* dst = reinterpret_cast<float4*>(sU + px * UPITCH);
-      if (y < 0 || y >= a.H || x < 0 || x >= a.W) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) dst[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-        continue;
+    // S0: tap tables (for the bilinear adjoint); gM' cleared; I_r and I over R2 in flight; U
+    // fetched during the last tile
+    if (threadIdx.x < 2 * R4) {
+      const bool col = threadIdx.x >= R4;
+      const int k = col ? threadIdx.x - R4 : threadIdx.x;
+      const int v = (col ? ox : oy) - 4 + k, n = col ? a.W : a.H, nin = col ? a.w4 : a.h4;
+      int i0 = -1, i1 = -1;
+      float f = 0.f;
+      if (v >= 0 && v < n) {
+        const Tap tq = up_tap(v, nin, n);
+        i0 = tq.i0;
+        i1 = tq.i1;
+        f = tq.f;
       }
-      const Tap ty = up_tap(y, a.h4, a.H), tx = up_tap(x, a.w4, a.W);
-      const float4* f00 = reinterpret_cast<const float4*>(sF + ((ty.i0 - fy0) * FP + tx.i0 - fx0) * 16);
-      const float4* f01 = reinterpret_cast<const float4*>(sF + ((ty.i0 - fy0) * FP + tx.i1 - fx0) * 16);
-      const float4* f10 = reinterpret_cast<const float4*>(sF + ((ty.i1 - fy0) * FP + tx.i0 - fx0) * 16);
-      const float4* f11 = reinterpret_cast<const float4*>(sF + ((ty.i1 - fy0) * FP + tx.i1 - fx0) * 16);
-      const float gy = 1.f - ty.f, gx = 1.f - tx.f;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const float4 p = f00[v], q = f01[v], r = f10[v], s = f11[v];
-        const float4 top = make_float4(gx * p.x + tx.f * q.x, gx * p.y + tx.f * q.y, gx * p.z + tx.f * q.z, gx * p.w + tx.f * q.w);
-        const float4 bot = make_float4(gx * r.x + tx.f * s.x, gx * r.y + tx.f * s.y, gx * r.z + tx.f * s.z, gx * r.w + tx.f * s.w);
-        dst[v] = make_float4(tf32r(gy * top.x + ty.f * bot.x), tf32r(gy * top.y + ty.f * bot.y),
-                             tf32r(gy * top.z + ty.f * bot.z), tf32r(gy * top.w + ty.f * bot.w));
-      }
+      (col ? tX0 : tY0)[k] = i0;
+      (col ? tX1 : tY1)[k] = i1;
+      (col ? tFX : tFY)[k] = f;
     }
+    for (int i = threadIdx.x; i < 2 * 3 * R2 * R2; i += kHeadThreads) {
+      const int px = i % (R2 * R2), plane = i / (R2 * R2), c = plane % 3;
+      const int y = oy - 2 + px / R2, x = ox - 2 + px % R2;
+      const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
+      const float* src = (plane < 3 ? a.img : a.target) + (in ? (size_t)c * HW + (size_t)y * a.W + x : 0);
+      cp_async4_zfill(sI + i, src, in);
+    }
+    cp_async_commit();
+    if constexpr (BWD)
+      for (int i = threadIdx.x; i < R2 * R2 * GP / 8; i += kHeadThreads)
+        reinterpret_cast<uint4*>(sG)[i] = make_uint4(0u, 0u, 0u, 0u);
+    cp_async_wait<1>();    // U (the older group)
     __syncthreads();
     // S2: Hh = ReLU(conv5 U + b5) over R3, zero outside the image.  M = 484 pixels (31 m-tiles),
-    // N = 16, K = 144 (tap-major, 16 channels a tap).
+    // N = 16, K = 9 taps x 16 channels (one k-step a tap).
     {
-      if constexpr (BWD)
-        for (int i = threadIdx.x; i < FP * FP * 4; i += kHeadThreads)
-          reinterpret_cast<float4*>(sF)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       constexpr int NM = (R3 * R3 + 15) / 16;
       const int nmt = (NM - warp + 7) / 8;
-      int base[4][2];
+      uint32_t abase[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int m = min((warp + 8 * i) * 16 + g + 8 * h, R3 * R3 - 1);
-          base[i][h] = ((m / R3) * R4 + m % R3) * UPITCH + t;
-        }
+      for (int i = 0; i < 4; ++i) {
+        const int m = min((warp + 8 * i) * 16 + lrow, R3 * R3 - 1);
+        abase[i] = uU + (((m / R3) * R4 + m % R3) * HP + 8 * lq) * 2;
+      }
       float acc[4][2][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[i][0][q] = acc[i][1][q] = 0.f;
 #pragma unroll
-      for (int s = 0; s < 18; ++s) {
-        const int tap = s >> 1, off = ((tap / 3) * R4 + tap % 3) * UPITCH + (s & 1) * 8;
-        const float2 b0 = ldg2(a.w5f, (s * 2 + 0) * 32 + lane), b1 = ldg2(a.w5f, (s * 2 + 1) * 32 + lane);
+      for (int s = 0; s < 9; ++s) {
+        const uint32_t off = (((s / 3) * R4 + s % 3) * HP) * 2;
+        const uint2 b0 = __ldg(a.w5f + (s * 2 + 0) * 32 + lane), b1 = __ldg(a.w5f + (s * 2 + 1) * 32 + lane);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
           if (i < nmt) {
-            const float av[4] = {sU[base[i][0] + off], sU[base[i][1] + off], sU[base[i][0] + off + 4],
-                                 sU[base[i][1] + off + 4]};
-            mma8(acc[i][0], av, b0);
-            mma8(acc[i][1], av, b1);
+            uint32_t av[4];
+            ldsm4(av, abase[i] + off);
+            mma16(acc[i][0], av, b0.x, b0.y);
+            mma16(acc[i][1], av, b1.x, b1.y);
           }
       }
 #pragma unroll
@@ -621,149 +764,128 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
             const int o = 8 * j + 2 * t;
             const float v0 = in ? fmaxf(acc[i][j][2 * h] + __ldg(a.b5 + o), 0.f) : 0.f;
             const float v1 = in ? fmaxf(acc[i][j][2 * h + 1] + __ldg(a.b5 + o + 1), 0.f) : 0.f;
-            *reinterpret_cast<float2*>(sH + m * UPITCH + o) = make_float2(tf32r(v0), tf32r(v1));
+            *reinterpret_cast<uint32_t*>(sH + m * HP + o) = pack_half2(v0, v1);
           }
         }
       }
+    }
+    if constexpr (BWD) {
+      cp_async_wait<0>();    // I_r and I
+    } else {
+      __syncthreads();       // every warp is past S2, the last reader of U
+      fetch_u(tile + gridDim.x);
+      cp_async_wait<1>();    // I_r and I (older than the next U)
     }
     __syncthreads();
     // S3: M = conv6 Hh + b6 over R2 (N = 8, channels 0..2 used); the L1 term and gM' over R2.
     {
       constexpr int NM = R2 * R2 / 16;
       const int nmt = (NM - warp + 7) / 8;
-      int base[4][2];
+      uint32_t abase[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int m = min((warp + 8 * i) * 16 + g + 8 * h, R2 * R2 - 1);
-          base[i][h] = ((m / R2) * R3 + m % R2) * UPITCH + t;
-        }
+      for (int i = 0; i < 4; ++i) {
+        const int m = min((warp + 8 * i) * 16 + lrow, R2 * R2 - 1);
+        abase[i] = uH + (((m / R2) * R3 + m % R2) * HP + 8 * lq) * 2;
+      }
       float acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
 #pragma unroll
-      for (int s = 0; s < 18; ++s) {
-        const int tap = s >> 1, off = ((tap / 3) * R3 + tap % 3) * UPITCH + (s & 1) * 8;
-        const float2 b = ldg2(a.w6f, s * 32 + lane);
+      for (int s = 0; s < 9; ++s) {
+        const uint32_t off = (((s / 3) * R3 + s % 3) * HP) * 2;
+        const uint2 b = __ldg(a.w6f + s * 32 + lane);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
           if (i < nmt) {
-            const float av[4] = {sH[base[i][0] + off], sH[base[i][1] + off], sH[base[i][0] + off + 4],
-                                 sH[base[i][1] + off + 4]};
-            mma8(acc[i], av, b);
+            uint32_t av[4];
+            ldsm4(av, abase[i] + off);
+            mma16(acc[i], av, b.x, b.y);
           }
       }
-      if (t < 2) {
+      // the quad's six (pixel, channel) items: t = 0 takes (g, 0), (g, 1); t = 1 (g, 2), (g + 8, 2);
+      // t = 2 (g + 8, 0) and t = 3 (g + 8, 1), fetched from t = 0
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if (i >= nmt) break;
+      for (int i = 0; i < 4; ++i) {
+        if (i >= nmt) break;
+        const float v2 = __shfl_sync(0xffffffffu, acc[i][2], lane & ~3);
+        const float v3 = __shfl_sync(0xffffffffu, acc[i][3], lane & ~3);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int m = (warp + 8 * i) * 16 + g + 8 * h;
-            const int r = m / R2, q = m % R2;
-            const int y = oy - 2 + r, x = ox - 2 + q;
-            const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
-            const bool inT = in && r >= 2 && r < 2 + HT && q >= 2 && q < 2 + HT;
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const int o = 2 * t + e;
-              if (o >= 3) continue;
-              float gm = 0.f;
-              if (in) {
-                const size_t pix = (size_t)o * HW + (size_t)y * a.W + x;
-                const float Mv = acc[i][2 * h + e] + __ldg(a.b6 + o);
-                const float iv = __ldg(a.img + pix), tv = __ldg(a.target + pix);
-                const float d = iv * Mv - tv;
-                const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-                gm = sgn * iv;
-                if (inT) {
-                  l1 += fabsf(d);
-                  if (a.map) a.map[pix] = Mv;
-                  if constexpr (BWD) {
-                    a.gimg[pix] = a.cscale * sgn * Mv;
-                    db6[e] += gm;
-                  }
-                }
-              }
-              if constexpr (BWD) sG[m * 4 + o] = tf32r(gm);
+        for (int k = 0; k < 2; ++k) {
+          if (k == 1 && t >= 2) break;
+          const int h = t == 0 ? 0 : (t == 1 ? k : 1);
+          const int o = t == 0 ? k : (t == 1 ? 2 : t - 2);
+          const float av = t == 0 ? acc[i][k] : (t == 1 ? acc[i][2 * k] : (t == 2 ? v2 : v3));
+          const int m = (warp + 8 * i) * 16 + g + 8 * h;
+          const int r = m / R2, q = m % R2;
+          const int y = oy - 2 + r, x = ox - 2 + q;
+          if (y < 0 || y >= a.H || x < 0 || x >= a.W) continue;
+          const bool inT = r >= 2 && r < 2 + HT && q >= 2 && q < 2 + HT;
+          const size_t pix = (size_t)o * HW + (size_t)y * a.W + x;
+          const float Mv = av + __ldg(a.b6 + o);
+          const float iv = sI[o * R2 * R2 + m], tv = sI[(3 + o) * R2 * R2 + m];
+          const float d = iv * Mv - tv;
+          const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+          const float gm = sgn * iv;
+          if (inT) {
+            l1 += fabsf(d);
+            if (a.map) a.map[pix] = Mv;
+            if constexpr (BWD) {
+              a.gimg[pix] = a.cscale * sgn * Mv;
+              db6[0] += o == 0 ? gm : 0.f;
+              db6[1] += o == 1 ? gm : 0.f;
+              db6[2] += o == 2 ? gm : 0.f;
             }
           }
+          if constexpr (BWD) sG[m * GP + o] = to_half(gm);
         }
       }
     }
     if constexpr (BWD) {
       __syncthreads();
-      // S4: dW6^T[(tap, ci)][o] += sum_{p in T} Hh(p + tap)[ci] gM'(p)[o]; K = 256 pixels of T.
-#pragma unroll 2
-      for (int s = 0; s < 2 * HT; ++s) {
-        const int ty = s >> 1, x0 = (s & 1) * 8;
-        const int pg = ((ty + 2) * R2 + x0 + t + 2) * 4 + g;
-        const float b0 = g < 3 ? sG[pg] : 0.f, b1 = g < 3 ? sG[pg + 16] : 0.f;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (u >= n4) break;
-          const int tap = u == 0 ? warp : 8;
-          const int ph = ((ty + tap / 3 + 2) * R3 + x0 + t + tap % 3 + 2) * UPITCH + g;
-          const float av[4] = {sH[ph], sH[ph + 8], sH[ph + 4 * UPITCH], sH[ph + 4 * UPITCH + 8]};
-          mma8(acc6[u], av, b0, b1);
-        }
-      }
-      __syncthreads();
-      // S5: gZ5' = (conv6 adjoint of gM') * [Hh > 0] over R1, written over Hh.  M = 324 pixels
-      // (21 m-tiles), N = 16, K = 27 -> 32 (k = flipped tap * 3 + output channel).
+      // S5: gZ5' = (conv6 adjoint of gM') * [Hh > 0] over R1.  M = 324 pixels (21 m-tiles), N = 16,
+      // K = 9 flipped taps x 8 channels (3 used) -> 80: k-step s covers taps 2s and 2s + 1.
       {
         constexpr int NM = (R1 * R1 + 15) / 16;
         const int nmt = (NM - warp + 7) / 8;
-        int koff[4][2];
+        uint2 bw[5][2];
 #pragma unroll
-        for (int s = 0; s < 4; ++s)
+        for (int s = 0; s < 5; ++s)
 #pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int k = 8 * s + t + 4 * e;
-            const int tp = k / 3, o = k % 3;
-            koff[s][e] = k < 27 ? ((tp / 3) * R2 + tp % 3) * 4 + o : -1;
-          }
-        float2 bw[4][2];
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) bw[s][j] = ldg2(a.w6d, (s * 2 + j) * 32 + lane);
+          for (int j = 0; j < 2; ++j) bw[s][j] = __ldg(a.w6d + (s * 2 + j) * 32 + lane);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           if (i >= nmt) break;
-          const int m0 = (warp + 8 * i) * 16 + g, m1 = m0 + 8;
-          const int mc0 = min(m0, R1 * R1 - 1), mc1 = min(m1, R1 * R1 - 1);
-          const int base0 = ((mc0 / R1) * R2 + mc0 % R1) * 4, base1 = ((mc1 / R1) * R2 + mc1 % R1) * 4;
+          const int mr = min((warp + 8 * i) * 16 + lrow, R1 * R1 - 1);
+          const uint32_t base = uG + ((mr / R1) * R2 + mr % R1) * GP * 2;
           float acc[2][4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[0][q] = acc[1][q] = 0.f;
 #pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            const int k0 = koff[s][0], k1 = koff[s][1];
-            const float av[4] = {k0 >= 0 ? sG[base0 + k0] : 0.f, k0 >= 0 ? sG[base1 + k0] : 0.f,
-                                 k1 >= 0 ? sG[base0 + k1] : 0.f, k1 >= 0 ? sG[base1 + k1] : 0.f};
-            mma8(acc[0], av, bw[s][0]);
-            mma8(acc[1], av, bw[s][1]);
+          for (int s = 0; s < 5; ++s) {
+            const int tap = min(2 * s + lq, 8);      // tap 9 is padding (zero weights)
+            uint32_t av[4];
+            ldsm4(av, base + ((tap / 3) * R2 + tap % 3) * GP * 2);
+            mma16(acc[0], av, bw[s][0].x, bw[s][0].y);
+            mma16(acc[1], av, bw[s][1].x, bw[s][1].y);
           }
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int m = h ? m1 : m0;
+            const int m = (warp + 8 * i) * 16 + g + 8 * h;
             if (m >= R1 * R1) continue;
             const int r = m / R1, q = m % R1;
             const int y = oy - 1 + r, x = ox - 1 + q;
             const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
             const bool inT = in && r >= 1 && r <= HT && q >= 1 && q <= HT;
-            float* hp = sH + ((r + 2) * R3 + q + 2) * UPITCH;
+            const __half* hp = sH + ((r + 2) * R3 + q + 2) * HP;
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
               const int o = 8 * j + 2 * t;
-              const float2 hv = *reinterpret_cast<const float2*>(hp + o);
+              const float2 hv = half2_to_float2(*reinterpret_cast<const uint32_t*>(hp + o));
               const float z0 = (in && hv.x > 0.f) ? acc[j][2 * h] : 0.f;
               const float z1 = (in && hv.y > 0.f) ? acc[j][2 * h + 1] : 0.f;
-              *reinterpret_cast<float2*>(hp + o) = make_float2(tf32r(z0), tf32r(z1));
+              *reinterpret_cast<uint32_t*>(sZ + m * HP + o) = pack_half2(z0, z1);
               if (inT) {
                 db5[j][0] += z0;
                 db5[j][1] += z1;
@@ -773,107 +895,123 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
         }
       }
       __syncthreads();
-      // S6: dW5^T[(tap, ci)][o] += sum_{p in T} U(p + tap)[ci] gZ5'(p)[o]; K = 256 pixels of T.
+      // S4 + S6, one k-step per row of T (16 pixels); warp w takes tap w over every row and tap 8
+      // over rows 2w and 2w + 1:
+      //   dW6^T[(tap, ci)][o] += sum_p Hh(p + tap)[ci] gM'(p)[o]   (A = Hh, transposed loads)
+      //   dW5[o][(tap, ci)]   += sum_p gZ5'(p)[o] U(p + tap)[ci]   (A = gZ5', transposed loads)
 #pragma unroll 2
-      for (int s = 0; s < 2 * HT; ++s) {
-        const int ty = s >> 1, x0 = (s & 1) * 8;
-        const int pz = ((ty + 3) * R3 + x0 + t + 3) * UPITCH + g;
+      for (int ty = 0; ty < HT; ++ty) {
+        uint32_t agz[4], bgm0, bgm1;
+        ldsm4t(agz, uZ + (((ty + 1) * R1 + tp + 1) * HP + 8 * tc) * 2);
+        ldsm2t(bgm0, bgm1, uG + ((ty + 2) * R2 + lrow + 2) * GP * 2);
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          if (u >= n6) break;
-          const int unit = u < 2 ? warp + 8 * u : 16 + warp;
-          const int tap = unit >> 1, jn = unit & 1;
-          const float b0 = sH[pz + 8 * jn], b1 = sH[pz + 4 * UPITCH + 8 * jn];
-          const int pu = ((ty + tap / 3 + 3) * R4 + x0 + t + tap % 3 + 3) * UPITCH + g;
-          const float av[4] = {sU[pu], sU[pu + 8], sU[pu + 4 * UPITCH], sU[pu + 4 * UPITCH + 8]};
-          mma8(acc5[u], av, b0, b1);
+        for (int u = 0; u < 2; ++u) {
+          if (u == 1 && (ty >> 1) != warp) break;
+          const int tap = u == 0 ? warp : 8, ti = tap / 3, tj = tap % 3;
+          uint32_t bu[4], ah[4];
+          ldsm4t(bu, uU + (((ty + ti + 3) * R4 + lrow + tj + 3) * HP + 8 * lq) * 2);
+          mma16(acc5[u][0], agz, bu[0], bu[1]);
+          mma16(acc5[u][1], agz, bu[2], bu[3]);
+          ldsm4t(ah, uH + (((ty + ti + 2) * R3 + tp + tj + 2) * HP + 8 * tc) * 2);
+          mma16(acc6[u], ah, bgm0, bgm1);
         }
       }
-      // S7: gU'(p) = (conv5 adjoint of gZ5')(p) over T (rows warp and warp + 8), scattered into
-      // sF by the bilinear adjoint.  N = 16, K = 144 (flipped tap * 16 + channel).
-      {
-        float acc[2][2][4];
+      // S7: gU'(p) = (conv5 adjoint of gZ5')(p) over T (rows warp and warp + 8).  N = 16, K = 9
+      // flipped taps x 16 channels.
+      float acc7[2][2][4];
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < 2; ++i)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[i][0][q] = acc[i][1][q] = 0.f;
+        for (int q = 0; q < 4; ++q) acc7[i][0][q] = acc7[i][1][q] = 0.f;
 #pragma unroll
-        for (int s = 0; s < 18; ++s) {
-          const int tap = s >> 1, off = ((tap / 3) * R3 + tap % 3) * UPITCH + (s & 1) * 8;
-          const float2 b0 = ldg2(a.w5d, (s * 2 + 0) * 32 + lane), b1 = ldg2(a.w5d, (s * 2 + 1) * 32 + lane);
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const int base = ((warp + 8 * i + 2) * R3 + g + 2) * UPITCH + t + off;
-            const float av[4] = {sH[base], sH[base + 8 * UPITCH], sH[base + 4], sH[base + 8 * UPITCH + 4]};
-            mma8(acc[i][0], av, b0);
-            mma8(acc[i][1], av, b1);
-          }
-        }
+      for (int s = 0; s < 9; ++s) {
+        const uint2 b0 = __ldg(a.w5d + (s * 2 + 0) * 32 + lane), b1 = __ldg(a.w5d + (s * 2 + 1) * 32 + lane);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-          const int y = oy + warp + 8 * i;
-          if (y >= a.H) continue;
-          const Tap ty = up_tap(y, a.h4, a.H);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int x = ox + g + 8 * h;
-            if (x >= a.W) continue;
-            const Tap tx = up_tap(x, a.w4, a.W);
-            const float gy = 1.f - ty.f, gx = 1.f - tx.f;
-            float* c00 = sF + ((ty.i0 - fy0) * FP + tx.i0 - fx0) * 16;
-            float* c01 = sF + ((ty.i0 - fy0) * FP + tx.i1 - fx0) * 16;
-            float* c10 = sF + ((ty.i1 - fy0) * FP + tx.i0 - fx0) * 16;
-            float* c11 = sF + ((ty.i1 - fy0) * FP + tx.i1 - fx0) * 16;
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-              for (int e = 0; e < 2; ++e) {
-                const int ci = 8 * j + 2 * t + e;
-                const float v = acc[i][j][2 * h + e];
-                atomicAdd(c00 + ci, gy * gx * v);
-                atomicAdd(c01 + ci, gy * tx.f * v);
-                atomicAdd(c10 + ci, ty.f * gx * v);
-                atomicAdd(c11 + ci, ty.f * tx.f * v);
-              }
-          }
+          uint32_t av[4];
+          ldsm4(av, uZ + (((warp + 8 * i + s / 3) * R1 + lrow + s % 3) * HP + 8 * lq) * 2);
+          mma16(acc7[i][0], av, b0.x, b0.y);
+          mma16(acc7[i][1], av, b1.x, b1.y);
         }
       }
+      __syncthreads();   // every warp is past S4, S6 and S7 (the last readers of U, Hh and gZ5')
+      fetch_u(tile + gridDim.x);
+      // dL/dU over T -> sH as FP32 [row][column][16]; then the bilinear adjoint as two gathers:
+      // columns (into sZ as [row][footprint column][16]) and rows (straight into dL/dF4).
+      float* sGU = reinterpret_cast<float*>(sH);
+      float* sX = reinterpret_cast<float*>(sZ);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+            *reinterpret_cast<float2*>(sGU + (((warp + 8 * i) * HT + g + 8 * h) * 16) + 8 * j + 2 * t) =
+                make_float2(acc7[i][j][2 * h], acc7[i][j][2 * h + 1]);
+      const int bx0 = tX0[4], bx1 = tX1[min(HT + 3, a.W - 1 - ox + 4)];
+      const int by0 = tY0[4], by1 = tY1[min(HT + 3, a.H - 1 - oy + 4)];
+      const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1;
+      const int ncx = min(HT, a.W - ox), ncy = min(HT, a.H - oy);
       __syncthreads();
-      // flush the footprint of T into dL/dF4
-      {
-        const int ty0 = up_tap(oy, a.h4, a.H).i0, ty1 = up_tap(min(oy + HT - 1, a.H - 1), a.h4, a.H).i1;
-        const int tx0 = up_tap(ox, a.w4, a.W).i0, tx1 = up_tap(min(ox + HT - 1, a.W - 1), a.w4, a.W).i1;
-        const int ntx = tx1 - tx0 + 1, n = (ty1 - ty0 + 1) * ntx;
-        for (int i = threadIdx.x; i < n * 4; i += kHeadThreads) {
-          const int v = i & 3, px = i >> 2, r = px / ntx, q = px % ntx;
-          const float4 s = *reinterpret_cast<const float4*>(sF + ((ty0 - fy0 + r) * FP + tx0 - fx0 + q) * 16 + 4 * v);
-          atomicAdd(reinterpret_cast<float4*>(a.gf4 + ((size_t)(ty0 + r) * a.w4 + tx0 + q) * 16 + 4 * v),
-                    make_float4(a.cscale * s.x, a.cscale * s.y, a.cscale * s.z, a.cscale * s.w));
+      // contributors of footprint column b: the T columns whose taps (first, second) include b, a
+      // contiguous run because the taps are monotone; likewise for rows
+      for (int it = threadIdx.x; it < HT * nbx * 4; it += kHeadThreads) {
+        const int v = it & 3, rest = it >> 2, jb = rest % nbx, r = rest / nbx;
+        const int b = bx0 + jb;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        int x = 0;
+        while (x < ncx && tX1[x + 4] < b) ++x;
+        for (; x < ncx && tX0[x + 4] <= b; ++x) {
+          const float fx = tFX[x + 4];
+          const float w = (tX0[x + 4] == b ? 1.f - fx : 0.f) + (tX1[x + 4] == b ? fx : 0.f);
+          const float4 gu = *reinterpret_cast<const float4*>(sGU + (r * HT + x) * 16 + 4 * v);
+          s.x = fmaf(w, gu.x, s.x);
+          s.y = fmaf(w, gu.y, s.y);
+          s.z = fmaf(w, gu.z, s.z);
+          s.w = fmaf(w, gu.w, s.w);
         }
+        *reinterpret_cast<float4*>(sX + (r * FT + jb) * 16 + 4 * v) = s;
+      }
+      __syncthreads();
+      for (int it = threadIdx.x; it < nby * nbx * 4; it += kHeadThreads) {
+        const int v = it & 3, rest = it >> 2, jb = rest % nbx, ja = rest / nbx;
+        const int b = by0 + ja;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        int r = 0;
+        while (r < ncy && tY1[r + 4] < b) ++r;
+        for (; r < ncy && tY0[r + 4] <= b; ++r) {
+          const float fy = tFY[r + 4];
+          const float w = (tY0[r + 4] == b ? 1.f - fy : 0.f) + (tY1[r + 4] == b ? fy : 0.f);
+          const float4 gx = *reinterpret_cast<const float4*>(sX + (r * FT + jb) * 16 + 4 * v);
+          s.x = fmaf(w, gx.x, s.x);
+          s.y = fmaf(w, gx.y, s.y);
+          s.z = fmaf(w, gx.z, s.z);
+          s.w = fmaf(w, gx.w, s.w);
+        }
+        atomicAdd(reinterpret_cast<float4*>(a.gf4 + ((size_t)b * a.w4 + bx0 + jb) * 16 + 4 * v),
+                  make_float4(a.cscale * s.x, a.cscale * s.y, a.cscale * s.z, a.cscale * s.w));
       }
     }
   }
+  cp_async_wait<0>();      // the (empty) last prefetch group
   if constexpr (BWD) {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      if (u >= n4) break;
       const int tap = u == 0 ? warp : 8;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
+        // dW6^T: rows ci = g (+ 8), columns o = 2t (+ 1)
         const int ci = g + 8 * (e >> 1), o = 2 * t + (e & 1);
         if (o < 3) atomicAdd(a.dw6 + (o * 16 + ci) * 9 + tap, a.cscale * acc6[u][e]);
       }
-    }
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      if (u >= n6) break;
-      const int unit = u < 2 ? warp + 8 * u : 16 + warp;
-      const int tap = unit >> 1, jn = unit & 1;
+      for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int ci = g + 8 * (e >> 1), o = 8 * jn + 2 * t + (e & 1);
-        atomicAdd(a.dw5 + (o * 16 + ci) * 9 + tap, a.cscale * acc5[u][e]);
-      }
+        for (int e = 0; e < 4; ++e) {
+          // dW5: rows o = g (+ 8), columns ci = 8j + 2t (+ 1)
+          const int o = g + 8 * (e >> 1), ci = 8 * j + 2 * t + (e & 1);
+          atomicAdd(a.dw5 + (o * 16 + ci) * 9 + tap, a.cscale * acc5[u][j][e]);
+        }
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j)
@@ -886,12 +1024,9 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
         if (g == 0) atomicAdd(a.db5 + 8 * j + 2 * t + e, a.cscale * v);
       }
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      float v = db6[e];
-      v += __shfl_xor_sync(0xffffffffu, v, 4);
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 16);
-      if (g == 0 && 2 * t + e < 3) atomicAdd(a.db6 + 2 * t + e, a.cscale * v);
+    for (int o = 0; o < 3; ++o) {
+      const float v = warp_sum(db6[o]);
+      if (lane == 0) atomicAdd(a.db6 + o, a.cscale * v);
     }
   }
   // the block's L1 sum (FP32 per warp, FP64 across warps)
@@ -938,7 +1073,7 @@ __global__ void __launch_bounds__(256) appearance_finalize(const double* __restr
 
 // Workspace regions (floats unless noted), for an H x W image with (h, w) = (H / 32, W / 32).
 struct AppLayout {
-  size_t E, G, P, gP, A[5], gA[5], packed, maps, ssim_part, head_part, total;
+  size_t E, G, P, gP, A[5], gA[5], U, packed, maps, ssim_part, head_part, total;
   int pack_off[kPackJobs];
   PackTable tab;
 };
@@ -964,25 +1099,32 @@ AppLayout make_app_layout(int W, int H) {
     L.A[k] = take(n);
     L.gA[k] = take(n);
   }
-  // packed B operands: forward and input-gradient GEMMs of blocks 1..4, conv5, conv6
+  // packed B operands: forward and input-gradient GEMMs of blocks 1..4 (TF32), conv5 and conv6 of
+  // the head (FP16)
   const int jobs[kPackJobs][2] = {{1, 0}, {2, 0}, {3, 0}, {4, 0}, {1, 1}, {2, 1},
                                   {3, 1}, {4, 1}, {5, 0}, {5, 1}, {6, 0}, {6, 1}};
-  int pos = 0;      // every packed size (kpad npad, both multiples of 8) is a multiple of 64 floats
+  int pos = 0, idx = 0;   // pos: floats of the buffer used; idx: elements of the launch's index space
   for (int j = 0; j < kPackJobs; ++j) {
     const int l = jobs[j][0], dg = jobs[j][1];
     const int kin = dg ? layer_o(l) : layer_c(l), n = dg ? layer_c(l) : layer_o(l);
     PackJob& J = L.tab.job[j];
     J.layer = l;
     J.dgrad = dg;
-    J.kpad = (9 * kin + 7) / 8 * 8;
+    J.f16 = l >= 5;
+    J.tapc = !J.f16 ? kin : (l == 6 && dg) ? 8 : 16;   // conv6's adjoint: 3 channels a tap, read as 8
+    const int kstep = J.f16 ? 16 : 8;
+    J.kpad = (9 * J.tapc + kstep - 1) / kstep * kstep;
     J.npad = (n + 7) / 8 * 8;
-    J.offset = pos;
-    L.tab.begin[j] = pos;
+    const int elems = J.kpad * J.npad;                  // a multiple of 64 (TF32) or 128 (FP16)
+    J.offset = J.f16 ? 2 * pos : pos;
     L.pack_off[j] = pos;
-    pos += J.kpad * J.npad;
+    L.tab.begin[j] = idx;
+    idx += elems;
+    pos += J.f16 ? elems / 2 : elems;
   }
-  L.tab.begin[kPackJobs] = pos;
+  L.tab.begin[kPackJobs] = idx;
   L.packed = take((size_t)pos * 4);
+  L.U = take((size_t)W * H * 16 * 2);          // FP16 [H][W][16]
   L.maps = take(ssim_maps_floats(W, H) * 4);
   L.ssim_part = take((size_t)ssim_partials(W, H) * 2 * 8);
   L.head_part = take((size_t)kMaxHeadBlocks * 8);
@@ -995,35 +1137,57 @@ cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int C, int O, int MT, int WM, bool DGRAD>
-cudaError_t launch_conv(const float* in, const float* act, const float* wpk, const float* bias, float* out, int Hr,
-                        int Wr, cudaStream_t s) {
+template <int C, int O, int MT, int WM, bool DGRAD, bool MASK_IN, bool MASK_OUT>
+cudaError_t launch_conv(const float* in, const float* act, const float* wpk, const float* bias, const float* aout,
+                        float* out, int Hr, int Wr, cudaStream_t s) {
   const size_t smem = (size_t)(MT + 2) * 18 * (C + 4) * sizeof(float);
-  auto k = conv_mma_kernel<C, O, MT, WM, DGRAD>;
+  auto k = conv_mma_kernel<C, O, MT, WM, DGRAD, MASK_IN, MASK_OUT>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((Wr + 15) / 16, (Hr + MT - 1) / MT);
   note_launches(1);
-  k<<<grid, 256, smem, s>>>(in, act, wpk, bias, out, Hr, Wr);
+  k<<<grid, 256, smem, s>>>(in, act, wpk, bias, aout, out, Hr, Wr);
   return cudaGetLastError();
 }
 
-template <int C, int O, int TY>
+template <int C, int O, int TY, bool MASK_IN>
 cudaError_t launch_wgrad(const float* Aprev, const float* gA, const float* A, float* dW, float* db, int Hr, int Wr,
                          int sms, cudaStream_t s) {
   constexpr int PX = C == 8 ? 8 : C + 8, PZ = O + 8, MTOT = (9 * C + 15) / 16;
   const size_t smem = ((size_t)(TY + 2) * 18 * PX + (size_t)TY * 16 * PZ) * sizeof(float);
-  auto k = wgrad_kernel<C, O, TY>;
+  auto k = wgrad_kernel<C, O, TY, MASK_IN>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   const int tiles_x = (Wr + 15) / 16, tiles = tiles_x * ((Hr + TY - 1) / TY);
   const int gy = (MTOT + 3) / 4;
-  const int want_x = std::max(1, std::min(tiles, (2 * sms + gy - 1) / gy));
+  const int want_x = std::max(1, std::min(tiles, (3 * sms + gy - 1) / gy));
   const int per = (tiles + want_x - 1) / want_x;
   const dim3 grid((tiles + per - 1) / per, gy);
   note_launches(1);
   k<<<grid, 256, smem, s>>>(Aprev, gA, A, dW, db, Hr, Wr, tiles_x, tiles, per);
   return cudaGetLastError();
+}
+
+// Events of one call's fork / join with the side stream, released at the end of the call (the
+// recorded work keeps them alive until it completes).
+struct Events {
+  cudaEvent_t ev[8] = {};
+  int n = 0;
+  cudaEvent_t make() {
+    if (n == 8 || cudaEventCreateWithFlags(&ev[n], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return ev[n++];
+  }
+  ~Events() {
+    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+  }
+};
+
+// Makes `to` wait for the work enqueued so far on `from`.
+cudaError_t link(Events& E, cudaStream_t from, cudaStream_t to) {
+  cudaEvent_t e = E.make();
+  if (!e) return cudaErrorMemoryAllocation;
+  cudaError_t r = cudaEventRecord(e, from);
+  return r == cudaSuccess ? cudaStreamWaitEvent(to, e, 0) : r;
 }
 
 }  // namespace
@@ -1072,6 +1236,15 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
     if (e == cudaSuccess) e = r;
     return e == cudaSuccess;
   };
+  // The SSIM moments run on the side stream beside the CNN's forward; in the backward pass the
+  // weight gradients (and conv0's) follow the input-gradient chain on the side stream.
+  cudaStream_t side = side_stream();
+  if (!side) return VG_ERR_CUDA;
+  Events E;
+  double* ssim_part = reinterpret_cast<double*>(ws + L.ssim_part);
+  double* head_part = reinterpret_cast<double*>(ws + L.head_part);
+  ok(link(E, s, side));
+  ok(launch_ssim_moments(img, target, W, H, lambda, F(L.maps), ssim_part, side));
   if (bwd) {
     ok(cudaMemsetAsync(grad_params, 0, (size_t)kParams * sizeof(float), s));
     ok(cudaMemsetAsync(gA[4], 0, (size_t)(ph << 4) * (pw << 4) * 16 * sizeof(float), s));
@@ -1080,28 +1253,28 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   // weights, embedding taps, pooling, conv0, blocks 1..4
   note_launches(4);
   const int npk = L.tab.begin[kPackJobs];
-  pack_kernel<<<(npk + 255) / 256, 256, 0, s>>>(params, packed, L.tab);
+  pack_kernel<<<(npk + 255) / 256, 256, 0, s>>>(params, static_cast<void*>(packed), L.tab);
   embed_taps_kernel<<<9, 256, 0, s>>>(params, embedding, F(L.E));
   pool_kernel<<<dim3(pw, ph), 256, 0, s>>>(img, W, H, pw, F(L.P));
-  conv0_kernel<<<ph, 256, 0, s>>>(F(L.P), F(L.E), params, ph, pw, A[0]);
+  conv0_kernel<<<(ph * pw + kConv0FwdPx - 1) / kConv0FwdPx, 256, 0, s>>>(F(L.P), F(L.E), params, ph, pw, A[0]);
   ok(cudaGetLastError());
   const float* bias[5] = {nullptr, params + b_off(1), params + b_off(2), params + b_off(3), params + b_off(4)};
-  ok(launch_conv<64, 128, 8, 2, false>(A[0], nullptr, wf[1], bias[1], A[1], ph << 1, pw << 1, s));
-  ok(launch_conv<32, 64, 8, 4, false>(A[1], nullptr, wf[2], bias[2], A[2], ph << 2, pw << 2, s));
-  ok(launch_conv<16, 32, 16, 8, false>(A[2], nullptr, wf[3], bias[3], A[3], ph << 3, pw << 3, s));
-  ok(launch_conv<8, 16, 16, 8, false>(A[3], nullptr, wf[4], bias[4], A[4], ph << 4, pw << 4, s));
-  // SSIM moments (D-SSIM term), then the head
-  double* ssim_part = reinterpret_cast<double*>(ws + L.ssim_part);
-  double* head_part = reinterpret_cast<double*>(ws + L.head_part);
-  ok(launch_ssim_moments(img, target, W, H, lambda, F(L.maps), ssim_part, s));
+  ok(launch_conv<64, 128, 8, 2, false, false, false>(A[0], nullptr, wf[1], bias[1], nullptr, A[1], ph << 1, pw << 1, s));
+  ok(launch_conv<32, 64, 8, 4, false, false, false>(A[1], nullptr, wf[2], bias[2], nullptr, A[2], ph << 2, pw << 2, s));
+  ok(launch_conv<16, 32, 16, 8, false, false, false>(A[2], nullptr, wf[3], bias[3], nullptr, A[3], ph << 3, pw << 3, s));
+  ok(launch_conv<8, 16, 16, 8, false, false, false>(A[3], nullptr, wf[4], bias[4], nullptr, A[4], ph << 4, pw << 4, s));
+  __half* U = reinterpret_cast<__half*>(ws + L.U);
+  note_launches(1);
+  upsample_kernel<<<(int)(((size_t)W * H * 2 + 255) / 256), 256, 0, s>>>(A[4], ph << 4, pw << 4, H, W, U);
+  // the head
   HeadArgs ha{};
   ha.img = img;
   ha.target = target;
-  ha.f4 = A[4];
-  ha.w5f = packed + L.pack_off[8];
-  ha.w5d = packed + L.pack_off[9];
-  ha.w6f = packed + L.pack_off[10];
-  ha.w6d = packed + L.pack_off[11];
+  ha.u = U;
+  ha.w5f = reinterpret_cast<const uint2*>(packed + L.pack_off[8]);
+  ha.w5d = reinterpret_cast<const uint2*>(packed + L.pack_off[9]);
+  ha.w6f = reinterpret_cast<const uint2*>(packed + L.pack_off[10]);
+  ha.w6d = reinterpret_cast<const uint2*>(packed + L.pack_off[11]);
   ha.b5 = params + b_off(5);
   ha.b6 = params + b_off(6);
   ha.gimg = grad_img;
@@ -1120,7 +1293,7 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   ha.tiles = ha.tiles_x * ((H + HT - 1) / HT);
   const double inv = 1.0 / (3.0 * (double)((size_t)W * H));
   ha.cscale = (float)((1.0 - lambda) * inv);     // the L1 scale of Eq. 1's kernel, bit for bit
-  const size_t head_smem = (size_t)kHeadSmemFloats * sizeof(float);
+  const size_t head_smem = (size_t)kHeadSmemBytes;
   const int grid = std::min(ha.tiles, std::min(kMaxHeadBlocks, 2 * sms));
   note_launches(2);
   if (bwd) {
@@ -1130,25 +1303,34 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
     ok(set_smem(head_kernel<false>, head_smem));
     head_kernel<false><<<grid, kHeadThreads, head_smem, s>>>(ha);
   }
+  ok(link(E, side, s));      // the SSIM partials and maps
   appearance_finalize<<<1, 256, 0, s>>>(ssim_part, ssim_partials(W, H), head_part, grid, inv, lambda, out_loss);
   ok(cudaGetLastError());
   if (!bwd) return e == cudaSuccess ? VG_OK : VG_ERR_CUDA;
-  // blocks 4..1 backward: weight gradient, then the gradient of the block's (shuffled) input
+  // blocks 4..1 backward: the input-gradient chain on s (each launch writes the next block's
+  // masked output gradient), the weight gradients on the side stream as their inputs are ready
   float* gp = grad_params;
-  ok(launch_wgrad<8, 16, 16>(A[3], gA[4], A[4], gp + w_off(4), gp + b_off(4), ph << 4, pw << 4, sms, s));
-  ok(launch_conv<16, 8, 16, 8, true>(gA[4], A[4], wd[4], nullptr, gA[3], ph << 4, pw << 4, s));
-  ok(launch_wgrad<16, 32, 16>(A[2], gA[3], A[3], gp + w_off(3), gp + b_off(3), ph << 3, pw << 3, sms, s));
-  ok(launch_conv<32, 16, 16, 8, true>(gA[3], A[3], wd[3], nullptr, gA[2], ph << 3, pw << 3, s));
-  ok(launch_wgrad<32, 64, 8>(A[1], gA[2], A[2], gp + w_off(2), gp + b_off(2), ph << 2, pw << 2, sms, s));
-  ok(launch_conv<64, 32, 16, 8, true>(gA[2], A[2], wd[2], nullptr, gA[1], ph << 2, pw << 2, s));
-  ok(launch_wgrad<64, 128, 8>(A[0], gA[1], A[1], gp + w_off(1), gp + b_off(1), ph << 1, pw << 1, sms, s));
-  ok(launch_conv<128, 64, 8, 4, true>(gA[1], A[1], wd[1], nullptr, gA[0], ph << 1, pw << 1, s));
-  // conv0 adjoint, then dL/dI_r = head term + block-mean term + SSIM term
+  ok(link(E, s, side));
+  ok(launch_wgrad<8, 16, 16, true>(A[3], gA[4], A[4], gp + w_off(4), gp + b_off(4), ph << 4, pw << 4, sms, side));
+  ok(launch_conv<16, 8, 16, 8, true, true, true>(gA[4], A[4], wd[4], nullptr, A[3], gA[3], ph << 4, pw << 4, s));
+  ok(link(E, s, side));
+  ok(launch_wgrad<16, 32, 16, false>(A[2], gA[3], nullptr, gp + w_off(3), gp + b_off(3), ph << 3, pw << 3, sms, side));
+  ok(launch_conv<32, 16, 16, 8, true, false, true>(gA[3], nullptr, wd[3], nullptr, A[2], gA[2], ph << 3, pw << 3, s));
+  ok(link(E, s, side));
+  ok(launch_wgrad<32, 64, 8, false>(A[1], gA[2], nullptr, gp + w_off(2), gp + b_off(2), ph << 2, pw << 2, sms, side));
+  ok(launch_conv<64, 32, 8, 8, true, false, true>(gA[2], nullptr, wd[2], nullptr, A[1], gA[1], ph << 2, pw << 2, s));
+  ok(link(E, s, side));
+  ok(launch_wgrad<64, 128, 4, false>(A[0], gA[1], nullptr, gp + w_off(1), gp + b_off(1), ph << 1, pw << 1, sms, side));
+  ok(launch_conv<128, 64, 8, 4, true, false, false>(gA[1], nullptr, wd[1], nullptr, nullptr, gA[0], ph << 1, pw << 1, s));
+  // conv0's adjoint: the input gradient on s, the weight and embedding gradients on the side
+  // stream; then dL/dI_r = head term + block-mean term + SSIM term
+  ok(link(E, s, side));
   note_launches(3);
-  conv0_wgrad_kernel<<<ph, 256, 0, s>>>(gA[0], F(L.P), ph, pw, F(L.G), gp);
+  conv0_wgrad_kernel<<<(ph * pw + kConv0Px - 1) / kConv0Px, 256, 0, side>>>(gA[0], F(L.P), ph, pw, F(L.G), gp);
+  conv0_embed_grad_kernel<<<kEmbed, 256, 0, side>>>(F(L.G), params, embedding, grad_embedding, gp);
   conv0_dgrad_kernel<<<ph * pw, 256, 0, s>>>(gA[0], params, ph, pw, F(L.gP));
-  conv0_embed_grad_kernel<<<kEmbed, 256, 0, s>>>(F(L.G), params, embedding, grad_embedding, gp);
   ok(cudaGetLastError());
   ok(launch_ssim_grad_appearance(img, target, F(L.maps), W, H, F(L.gP), pw, ph, grad_img, s));
+  ok(link(E, side, s));      // every launch of the call is ordered before later work on s
   return e == cudaSuccess ? VG_OK : VG_ERR_CUDA;
 }
