@@ -300,15 +300,15 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
 // One non-blocking helper stream per device for work forked off the caller's stream.
 }  // namespace
 
-cudaStream_t side_stream() {
+cudaStream_t side_stream(int k) {
   static std::mutex mu;
-  static cudaStream_t streams[64] = {nullptr};
+  static cudaStream_t streams[64][kSideStreams] = {};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (k < 0 || k >= kSideStreams || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
-  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
-    streams[dev] = nullptr;
-  return streams[dev];
+  if (!streams[dev][k] && cudaStreamCreateWithFlags(&streams[dev][k], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev][k] = nullptr;
+  return streams[dev][k];
 }
 
 namespace {

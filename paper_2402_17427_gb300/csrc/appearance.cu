@@ -270,8 +270,10 @@ __device__ __forceinline__ void stage_plain(float* dst, const float* __restrict_
 
 // One block computes MT rows x 16 columns of output pixels and all O channels.  The input tile
 // ((MT + 2) x 18 pixels x C channels, pitch C + 4 so that the 8 x 4 lanes of a fragment load hit
-// distinct banks) is staged once.  Warps form WM x (8 / WM): each owns MT / WM pixel rows
-// (m-tiles) and O / 8 / (8 / WM) n-tiles.
+// distinct banks) is staged once; the packed weights of one tap (C x O floats) at a time follow
+// it into shared memory with cp.async, double-buffered so that the next tap's copy overlaps the
+// current tap's MMAs.  Warps form WM x (8 / WM): each owns MT / WM pixel rows (m-tiles) and
+// O / 8 / (8 / WM) n-tiles.
 //  forward (DGRAD false): input = shuffle(in) with in [Hr/2][Wr/2][4C]; output ReLU(acc + b) ->
 //    out [Hr][Wr][O].
 //  input gradient (DGRAD true): input = in [Hr][Wr][C], the output gradient of the block (times
@@ -285,14 +287,22 @@ __global__ void __launch_bounds__(256) conv_mma_kernel(const float* __restrict__
                                                        int Wr) {
   constexpr int NT = O / 8, WN = 8 / WM, NTW = NT / WN, MTW = MT / WM;
   constexpr int PITCH = C + 4, SW = 18, SHT = MT + 2;
+  constexpr int TAPF = C * O;                      // packed weight floats of one tap
   static_assert(NT % WN == 0 && MT % WM == 0 && C % 8 == 0, "tiling");
   extern __shared__ __align__(16) float smem[];
+  float* wbuf = smem + SHT * SW * PITCH;           // [2][TAPF]
   const int ox = blockIdx.x * 16, oy = blockIdx.y * MT;
+  auto fetch_tap = [&](int tap) {
+    float* dst = wbuf + (tap & 1) * TAPF;
+    const float* src = wpk + (size_t)tap * TAPF;
+    for (int i = threadIdx.x; i < TAPF / 4; i += 256) cp_async16(dst + 4 * i, src + 4 * i);
+    cp_async_commit();
+  };
+  fetch_tap(0);
   if constexpr (DGRAD)
     stage_plain<C, PITCH, MASK_IN>(smem, in, act, oy - 1, ox - 1, SHT, SW, Hr, Wr);
   else
     stage_shuffled<C, PITCH>(smem, in, oy - 1, ox - 1, SHT, SW, Hr, Wr);
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
   const int wm = warp % WM, wn = warp / WM;
   float acc[MTW][NTW][4];
@@ -305,12 +315,19 @@ __global__ void __launch_bounds__(256) conv_mma_kernel(const float* __restrict__
 #pragma unroll 1
   for (int tap = 0; tap < 9; ++tap) {
     const int dy = tap / 3, dx = tap % 3;
+    if (tap + 1 < 9) {
+      fetch_tap(tap + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();                                 // this tap's weights (and, first, the input)
+    const float2* wt = reinterpret_cast<const float2*>(wbuf + (tap & 1) * TAPF);
 #pragma unroll
     for (int cb = 0; cb < C / 8; ++cb) {
-      const int s = tap * (C / 8) + cb;
       float2 b[NTW];
 #pragma unroll
-      for (int j = 0; j < NTW; ++j) b[j] = ldg2(wpk, (s * NT + wn * NTW + j) * 32 + lane);
+      for (int j = 0; j < NTW; ++j) b[j] = wt[(cb * NT + wn * NTW + j) * 32 + lane];
 #pragma unroll
       for (int i = 0; i < MTW; ++i) {
         const float* base = smem + ((wm + i * WM + dy) * SW + dx + g) * PITCH + cb * 8 + t;
@@ -319,6 +336,7 @@ __global__ void __launch_bounds__(256) conv_mma_kernel(const float* __restrict__
         for (int j = 0; j < NTW; ++j) mma8(acc[i][j], a, b[j]);
       }
     }
+    __syncthreads();                                 // the buffer is refilled two taps later
   }
 #pragma unroll
   for (int i = 0; i < MTW; ++i) {
@@ -353,35 +371,46 @@ __global__ void __launch_bounds__(256) conv_mma_kernel(const float* __restrict__
 // Weight gradient of block k: dW^T[(tap, c)][o] = sum_p X(p + tap)[c] gZ(p)[o] with X =
 // shuffle(Aprev) and gZ the block's masked output gradient (gA * [A > 0], masked here when
 // MASK_IN); db[o] = sum_p gZ(p)[o].  GEMM M = 9 C (rows past 9 C are padding), N = O, K = pixels.
-// Block (x, y) owns m-tiles [4 y, 4 y + 4) and a run of pixel tiles (TY x 16); warp w owns m-tile
-// w % 4 and n-tiles [(w / 4) NT / 2, ...).  The pixels of a k-step are taken in the order x0 + 2t
-// (k = t), x0 + 2t + 1 (k = t + 4): with row pitches of 8 or 24 mod 32 floats the scalar fragment
-// loads (pixel along t, channel along g) then hit distinct banks.
-template <int C, int O, int TY, bool MASK_IN>
+// Block (x, y) owns m-tiles [MB y, MB y + MB) and a run of pixel tiles (TY x 16).  Warps form
+// WM x (8 / WM); warp (wm, wn) owns MW = ceil(MB / WM) m-tiles and NT / (8 / WM) n-tiles, so each
+// A and B fragment is loaded once per k-step for all the MMAs that use it.  The pixels of a
+// k-step are taken in the order x0 + 2t (k = t), x0 + 2t + 1 (k = t + 4): with row pitches of 8
+// or 24 mod 32 floats the scalar fragment loads (pixel along t, channel along g) then hit
+// distinct banks.
+template <int C, int O, int TY, int MB, int WM, bool MASK_IN>
 __global__ void __launch_bounds__(256) wgrad_kernel(const float* __restrict__ Aprev, const float* __restrict__ gA,
                                                     const float* __restrict__ A, float* __restrict__ dW,
                                                     float* __restrict__ db, int Hr, int Wr, int tiles_x, int tiles,
                                                     int per_block) {
-  constexpr int NT = O / 8, NTW = NT / 2, MTOT = (9 * C + 15) / 16;
+  constexpr int NT = O / 8, WNn = 8 / WM, NW = NT / WNn, MW = (MB + WM - 1) / WM, MTOT = (9 * C + 15) / 16;
   constexpr int PX = C == 8 ? 8 : C + 8, PZ = O + 8, SW = 18;
-  static_assert(NT % 2 == 0, "tiling");
+  static_assert(NT % WNn == 0 && O >= 16, "tiling");
   extern __shared__ __align__(16) float smem[];
   float* sX = smem;
   float* sZ = smem + (TY + 2) * SW * PX;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  const int mt = blockIdx.y * 4 + (warp & 3);
-  const int nt0 = (warp >> 2) * NTW;
-  const bool active = mt < MTOT;
-  // rows g and g + 8 of the m-tile: (tap, channel), or padding
-  const int m0 = mt * 16 + g, m1 = m0 + 8;
-  const bool v0 = m0 < 9 * C, v1 = m1 < 9 * C;
-  const int tp0 = v0 ? m0 / C : 0, c0 = v0 ? m0 % C : 0, tp1 = v1 ? m1 / C : 0, c1 = v1 ? m1 % C : 0;
-  const int xo0 = ((tp0 / 3) * SW + tp0 % 3) * PX + c0, xo1 = ((tp1 / 3) * SW + tp1 % 3) * PX + c1;
-  float acc[NTW][4];
+  const int wm = warp % WM, wn = warp / WM;
+  const int nt0 = wn * NW;
+  // this warp's m-tiles: rows g and g + 8 of each as (tap, channel) offsets into sX, or padding
+  int xo[MW][2];
+  bool vr[MW][2];
 #pragma unroll
-  for (int j = 0; j < NTW; ++j)
+  for (int i = 0; i < MW; ++i)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+    for (int h = 0; h < 2; ++h) {
+      const int mt = blockIdx.y * MB + wm * MW + i;
+      const int m = mt * 16 + g + 8 * h;
+      vr[i][h] = (wm * MW + i) < MB && mt < MTOT && m < 9 * C;
+      const int tp = vr[i][h] ? m / C : 0, c = vr[i][h] ? m % C : 0;
+      xo[i][h] = ((tp / 3) * SW + tp % 3) * PX + c;
+    }
+  float acc[MW][NW][4];
+#pragma unroll
+  for (int i = 0; i < MW; ++i)
+#pragma unroll
+    for (int j = 0; j < NW; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
   float dbs = 0.f;
   const int tile_end = min(tiles, (blockIdx.x + 1) * per_block);
   for (int tile = blockIdx.x * per_block; tile < tile_end; ++tile) {
@@ -390,39 +419,49 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const float* __restrict__ Ap
     stage_shuffled<C, PX>(sX, Aprev, oy - 1, ox - 1, TY + 2, SW, Hr, Wr);
     stage_plain<O, PZ, MASK_IN>(sZ, gA, A, oy, ox, TY, 16, Hr, Wr);
     __syncthreads();
-    if (blockIdx.y == 0 && threadIdx.x < O)
-      for (int p = 0; p < TY * 16; ++p) dbs += sZ[p * PZ + threadIdx.x];
-    if (active) {
+    if (blockIdx.y == 0)     // db: thread -> channel tid % O, pixels tid / O + k (256 / O)
+      for (int p = threadIdx.x / O; p < TY * 16; p += 256 / O) dbs += sZ[p * PZ + threadIdx.x % O];
 #pragma unroll 2
-      for (int s = 0; s < 2 * TY; ++s) {
-        const int ty = s >> 1, x0 = (s & 1) * 8;
-        const int pxA = (ty * SW + x0 + 2 * t) * PX;     // X at pixel (ty, x0 + 2t); tap offsets in xo
-        const float a[4] = {v0 ? sX[pxA + xo0] : 0.f, v1 ? sX[pxA + xo1] : 0.f, v0 ? sX[pxA + PX + xo0] : 0.f,
-                            v1 ? sX[pxA + PX + xo1] : 0.f};
-        const float* zb = sZ + (ty * 16 + x0 + 2 * t) * PZ + g;
+    for (int s = 0; s < 2 * TY; ++s) {
+      const int ty = s >> 1, x0 = (s & 1) * 8;
+      const int pxA = (ty * SW + x0 + 2 * t) * PX;     // X at pixel (ty, x0 + 2t); tap offsets in xo
+      float a[MW][4];
 #pragma unroll
-        for (int j = 0; j < NTW; ++j) {
-          const int n = (nt0 + j) * 8;
-          mma8(acc[j], a, zb[n], zb[PZ + n]);
-        }
+      for (int i = 0; i < MW; ++i) {
+        a[i][0] = vr[i][0] ? sX[pxA + xo[i][0]] : 0.f;
+        a[i][1] = vr[i][1] ? sX[pxA + xo[i][1]] : 0.f;
+        a[i][2] = vr[i][0] ? sX[pxA + PX + xo[i][0]] : 0.f;
+        a[i][3] = vr[i][1] ? sX[pxA + PX + xo[i][1]] : 0.f;
+      }
+      const float* zb = sZ + (ty * 16 + x0 + 2 * t) * PZ + g;
+#pragma unroll
+      for (int j = 0; j < NW; ++j) {
+        const int n = (nt0 + j) * 8;
+        const float b0 = zb[n], b1 = zb[PZ + n];
+#pragma unroll
+        for (int i = 0; i < MW; ++i) mma8(acc[i][j], a[i], b0, b1);
       }
     }
   }
-  if (active) {
 #pragma unroll
-    for (int j = 0; j < NTW; ++j) {
-      const int o = (nt0 + j) * 8 + 2 * t;
-      if (v0) {
-        atomicAdd(dW + ((size_t)o * C + c0) * 9 + tp0, acc[j][0]);
-        atomicAdd(dW + ((size_t)(o + 1) * C + c0) * 9 + tp0, acc[j][1]);
-      }
-      if (v1) {
-        atomicAdd(dW + ((size_t)o * C + c1) * 9 + tp1, acc[j][2]);
-        atomicAdd(dW + ((size_t)(o + 1) * C + c1) * 9 + tp1, acc[j][3]);
+  for (int i = 0; i < MW; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!vr[i][h]) continue;
+      const int m = (blockIdx.y * MB + wm * MW + i) * 16 + g + 8 * h, tp = m / C, c = m % C;
+#pragma unroll
+      for (int j = 0; j < NW; ++j) {
+        const int o = (nt0 + j) * 8 + 2 * t;
+        atomicAdd(dW + ((size_t)o * C + c) * 9 + tp, acc[i][j][2 * h]);
+        atomicAdd(dW + ((size_t)(o + 1) * C + c) * 9 + tp, acc[i][j][2 * h + 1]);
       }
     }
+  if (blockIdx.y == 0) {
+    // lanes l and l + O (O <= 16) or the warp's other lanes hold the same channel
+#pragma unroll
+    for (int o = 16; o >= O && o < 32; o <<= 1) dbs += __shfl_xor_sync(0xffffffffu, dbs, o);
+    if ((threadIdx.x & 31) < O || O >= 32) atomicAdd(db + threadIdx.x % O, dbs);
   }
-  if (blockIdx.y == 0 && threadIdx.x < O) atomicAdd(db + threadIdx.x, dbs);
 }
 
 // ---------------------------------------------------------------- conv0 adjoint
@@ -545,7 +584,7 @@ constexpr int GP = 8;                 // halves per pixel in sG
 constexpr int FT = 10;                // dL/dF4 footprint side of T
 constexpr int kHeadThreads = 256;
 constexpr int kBU = R4 * R4 * HP * 2, kBH = R3 * R3 * HP * 2, kBZ = R1 * R1 * HP * 2, kBG = R2 * R2 * GP * 2;
-constexpr int kBI = 2 * 3 * R2 * R2 * 4, kBT = 6 * R4 * 4;
+constexpr int kBI = 2 * 3 * R2 * R2 * 4, kBT = 6 * R4 * 4 + 4 * FT * 4;
 constexpr int kHeadSmemBytes = kBU + kBH + kBZ + kBG + kBI + kBT;
 static_assert(HT * HT * 16 * 4 <= kBH && HT * FT * 16 * 4 <= kBZ, "bilinear adjoint buffers fit");
 static_assert(kBU % 16 == 0 && kBH % 16 == 0 && kBZ % 16 == 0 && kBG % 16 == 0 && kBI % 16 == 0, "alignment");
@@ -656,6 +695,8 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
   int* tX0 = reinterpret_cast<int*>(tFY + R4);
   int* tX1 = tX0 + R4;
   float* tFX = reinterpret_cast<float*>(tX1 + R4);
+  int2* rX = reinterpret_cast<int2*>(tFX + R4);     // contributor runs [first, end) of T's columns
+  int2* rY = rX + FT;                                // and rows, per footprint column / row
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
   // ldmatrix rows: lrow / lq for A (pixel rows, channel halves) and for the weight-gradient B
   // operands; tp / tc for the transposed weight-gradient A operands (pixel, channel half)
@@ -952,16 +993,27 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
       const int by0 = tY0[4], by1 = tY1[min(HT + 3, a.H - 1 - oy + 4)];
       const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1;
       const int ncx = min(HT, a.W - ox), ncy = min(HT, a.H - oy);
-      __syncthreads();
       // contributors of footprint column b: the T columns whose taps (first, second) include b, a
       // contiguous run because the taps are monotone; likewise for rows
+      if (threadIdx.x < 2 * FT) {
+        const bool row = threadIdx.x >= FT;
+        const int k = row ? threadIdx.x - FT : threadIdx.x, b = (row ? by0 : bx0) + k;
+        const int n = row ? ncy : ncx;
+        const int* t0 = row ? tY0 : tX0;
+        const int* t1 = row ? tY1 : tX1;
+        int first = 0, end = 0;
+        while (first < n && t1[first + 4] < b) ++first;
+        end = first;
+        while (end < n && t0[end + 4] <= b) ++end;
+        (row ? rY : rX)[k] = make_int2(first, end);
+      }
+      __syncthreads();
       for (int it = threadIdx.x; it < HT * nbx * 4; it += kHeadThreads) {
         const int v = it & 3, rest = it >> 2, jb = rest % nbx, r = rest / nbx;
         const int b = bx0 + jb;
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        int x = 0;
-        while (x < ncx && tX1[x + 4] < b) ++x;
-        for (; x < ncx && tX0[x + 4] <= b; ++x) {
+        const int2 run = rX[jb];
+        for (int x = run.x; x < run.y; ++x) {
           const float fx = tFX[x + 4];
           const float w = (tX0[x + 4] == b ? 1.f - fx : 0.f) + (tX1[x + 4] == b ? fx : 0.f);
           const float4 gu = *reinterpret_cast<const float4*>(sGU + (r * HT + x) * 16 + 4 * v);
@@ -977,9 +1029,8 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
         const int v = it & 3, rest = it >> 2, jb = rest % nbx, ja = rest / nbx;
         const int b = by0 + ja;
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        int r = 0;
-        while (r < ncy && tY1[r + 4] < b) ++r;
-        for (; r < ncy && tY0[r + 4] <= b; ++r) {
+        const int2 run = rY[ja];
+        for (int r = run.x; r < run.y; ++r) {
           const float fy = tFY[r + 4];
           const float w = (tY0[r + 4] == b ? 1.f - fy : 0.f) + (tY1[r + 4] == b ? fy : 0.f);
           const float4 gx = *reinterpret_cast<const float4*>(sX + (r * FT + jb) * 16 + 4 * v);
@@ -1039,6 +1090,17 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
     for (int k = 0; k < kHeadThreads / 32; ++k) s += red[k];
     a.partials[blockIdx.x] = s;
   }
+}
+
+// dL/dI_r += dL/dP / 1024 over the pixels of the complete 32 x 32 blocks (the pooled input's
+// adjoint), once conv0's adjoint has produced dL/dP [ph][pw][3].
+__global__ void __launch_bounds__(256) pool_grad_add_kernel(const float* __restrict__ gP, int W, int H, int pw,
+                                                            int ph, float* __restrict__ grad) {
+  const int Wp = 32 * pw, Hp = 32 * ph;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * Wp * Hp) return;
+  const int c = i / (Wp * Hp), r = i % (Wp * Hp), y = r / Wp, x = r % Wp;
+  grad[(size_t)c * W * H + (size_t)y * W + x] += gP[((y >> 5) * pw + (x >> 5)) * 3 + c] * (1.f / 1024.f);
 }
 
 // L = (1 - lambda) sum|I_a - I| / n + lambda (1 - sum S / n), n = 3 H W.
@@ -1140,7 +1202,7 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 template <int C, int O, int MT, int WM, bool DGRAD, bool MASK_IN, bool MASK_OUT>
 cudaError_t launch_conv(const float* in, const float* act, const float* wpk, const float* bias, const float* aout,
                         float* out, int Hr, int Wr, cudaStream_t s) {
-  const size_t smem = (size_t)(MT + 2) * 18 * (C + 4) * sizeof(float);
+  const size_t smem = ((size_t)(MT + 2) * 18 * (C + 4) + 2 * (size_t)C * O) * sizeof(float);
   auto k = conv_mma_kernel<C, O, MT, WM, DGRAD, MASK_IN, MASK_OUT>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1150,17 +1212,17 @@ cudaError_t launch_conv(const float* in, const float* act, const float* wpk, con
   return cudaGetLastError();
 }
 
-template <int C, int O, int TY, bool MASK_IN>
+template <int C, int O, int TY, int MB, int WM, bool MASK_IN>
 cudaError_t launch_wgrad(const float* Aprev, const float* gA, const float* A, float* dW, float* db, int Hr, int Wr,
                          int sms, cudaStream_t s) {
   constexpr int PX = C == 8 ? 8 : C + 8, PZ = O + 8, MTOT = (9 * C + 15) / 16;
   const size_t smem = ((size_t)(TY + 2) * 18 * PX + (size_t)TY * 16 * PZ) * sizeof(float);
-  auto k = wgrad_kernel<C, O, TY, MASK_IN>;
+  auto k = wgrad_kernel<C, O, TY, MB, WM, MASK_IN>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   const int tiles_x = (Wr + 15) / 16, tiles = tiles_x * ((Hr + TY - 1) / TY);
-  const int gy = (MTOT + 3) / 4;
-  const int want_x = std::max(1, std::min(tiles, (3 * sms + gy - 1) / gy));
+  const int gy = (MTOT + MB - 1) / MB;
+  const int want_x = std::max(1, std::min(tiles, (2 * sms + gy - 1) / gy));
   const int per = (tiles + want_x - 1) / want_x;
   const dim3 grid((tiles + per - 1) / per, gy);
   note_launches(1);
@@ -1171,10 +1233,10 @@ cudaError_t launch_wgrad(const float* Aprev, const float* gA, const float* A, fl
 // Events of one call's fork / join with the side stream, released at the end of the call (the
 // recorded work keeps them alive until it completes).
 struct Events {
-  cudaEvent_t ev[8] = {};
+  cudaEvent_t ev[16] = {};
   int n = 0;
   cudaEvent_t make() {
-    if (n == 8 || cudaEventCreateWithFlags(&ev[n], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    if (n == 16 || cudaEventCreateWithFlags(&ev[n], cudaEventDisableTiming) != cudaSuccess) return nullptr;
     return ev[n++];
   }
   ~Events() {
@@ -1236,10 +1298,13 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
     if (e == cudaSuccess) e = r;
     return e == cudaSuccess;
   };
-  // The SSIM moments run on the side stream beside the CNN's forward; in the backward pass the
-  // weight gradients (and conv0's) follow the input-gradient chain on the side stream.
-  cudaStream_t side = side_stream();
-  if (!side) return VG_ERR_CUDA;
+  // The SSIM moments run on a side stream beside the CNN's forward.  In the backward pass the
+  // input-gradient chain stays on s while the SSIM gradient and the weight gradients run on side
+  // streams as their inputs become ready.
+  cudaStream_t sd[kSideStreams];
+  for (int k = 0; k < kSideStreams; ++k)
+    if (!(sd[k] = side_stream(k))) return VG_ERR_CUDA;
+  cudaStream_t side = sd[0];
   Events E;
   double* ssim_part = reinterpret_cast<double*>(ws + L.ssim_part);
   double* head_part = reinterpret_cast<double*>(ws + L.head_part);
@@ -1259,7 +1324,7 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   conv0_kernel<<<(ph * pw + kConv0FwdPx - 1) / kConv0FwdPx, 256, 0, s>>>(F(L.P), F(L.E), params, ph, pw, A[0]);
   ok(cudaGetLastError());
   const float* bias[5] = {nullptr, params + b_off(1), params + b_off(2), params + b_off(3), params + b_off(4)};
-  ok(launch_conv<64, 128, 8, 2, false, false, false>(A[0], nullptr, wf[1], bias[1], nullptr, A[1], ph << 1, pw << 1, s));
+  ok(launch_conv<64, 128, 4, 2, false, false, false>(A[0], nullptr, wf[1], bias[1], nullptr, A[1], ph << 1, pw << 1, s));
   ok(launch_conv<32, 64, 8, 4, false, false, false>(A[1], nullptr, wf[2], bias[2], nullptr, A[2], ph << 2, pw << 2, s));
   ok(launch_conv<16, 32, 16, 8, false, false, false>(A[2], nullptr, wf[3], bias[3], nullptr, A[3], ph << 3, pw << 3, s));
   ok(launch_conv<8, 16, 16, 8, false, false, false>(A[3], nullptr, wf[4], bias[4], nullptr, A[4], ph << 4, pw << 4, s));
@@ -1307,30 +1372,35 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   appearance_finalize<<<1, 256, 0, s>>>(ssim_part, ssim_partials(W, H), head_part, grid, inv, lambda, out_loss);
   ok(cudaGetLastError());
   if (!bwd) return e == cudaSuccess ? VG_OK : VG_ERR_CUDA;
-  // blocks 4..1 backward: the input-gradient chain on s (each launch writes the next block's
-  // masked output gradient), the weight gradients on the side stream as their inputs are ready
+  // dL/dI_r's SSIM and L1 terms (the block-mean term is added at the end)
   float* gp = grad_params;
-  ok(link(E, s, side));
-  ok(launch_wgrad<8, 16, 16, true>(A[3], gA[4], A[4], gp + w_off(4), gp + b_off(4), ph << 4, pw << 4, sms, side));
+  ok(link(E, s, sd[0]));
+  ok(launch_ssim_grad_appearance(img, target, F(L.maps), W, H, nullptr, 0, 0, grad_img, sd[0]));
+  // blocks 4..1: the input-gradient chain on s (each launch writes the next block's masked output
+  // gradient); each weight gradient on a side stream once its output gradient exists
+  ok(link(E, s, sd[1]));
+  ok(launch_wgrad<8, 16, 16, 5, 4, true>(A[3], gA[4], A[4], gp + w_off(4), gp + b_off(4), ph << 4, pw << 4, sms, sd[1]));
   ok(launch_conv<16, 8, 16, 8, true, true, true>(gA[4], A[4], wd[4], nullptr, A[3], gA[3], ph << 4, pw << 4, s));
-  ok(link(E, s, side));
-  ok(launch_wgrad<16, 32, 16, false>(A[2], gA[3], nullptr, gp + w_off(3), gp + b_off(3), ph << 3, pw << 3, sms, side));
+  ok(link(E, s, sd[2]));
+  ok(launch_wgrad<16, 32, 16, 9, 4, false>(A[2], gA[3], nullptr, gp + w_off(3), gp + b_off(3), ph << 3, pw << 3, sms, sd[2]));
   ok(launch_conv<32, 16, 16, 8, true, false, true>(gA[3], nullptr, wd[3], nullptr, A[2], gA[2], ph << 3, pw << 3, s));
-  ok(link(E, s, side));
-  ok(launch_wgrad<32, 64, 8, false>(A[1], gA[2], nullptr, gp + w_off(2), gp + b_off(2), ph << 2, pw << 2, sms, side));
+  ok(link(E, s, sd[3]));
+  ok(launch_wgrad<32, 64, 8, 9, 4, false>(A[1], gA[2], nullptr, gp + w_off(2), gp + b_off(2), ph << 2, pw << 2, sms, sd[3]));
   ok(launch_conv<64, 32, 8, 8, true, false, true>(gA[2], nullptr, wd[2], nullptr, A[1], gA[1], ph << 2, pw << 2, s));
-  ok(link(E, s, side));
-  ok(launch_wgrad<64, 128, 4, false>(A[0], gA[1], nullptr, gp + w_off(1), gp + b_off(1), ph << 1, pw << 1, sms, side));
-  ok(launch_conv<128, 64, 8, 4, true, false, false>(gA[1], nullptr, wd[1], nullptr, nullptr, gA[0], ph << 1, pw << 1, s));
-  // conv0's adjoint: the input gradient on s, the weight and embedding gradients on the side
-  // stream; then dL/dI_r = head term + block-mean term + SSIM term
-  ok(link(E, s, side));
-  note_launches(3);
-  conv0_wgrad_kernel<<<(ph * pw + kConv0Px - 1) / kConv0Px, 256, 0, side>>>(gA[0], F(L.P), ph, pw, F(L.G), gp);
-  conv0_embed_grad_kernel<<<kEmbed, 256, 0, side>>>(F(L.G), params, embedding, grad_embedding, gp);
+  ok(link(E, s, sd[2]));
+  ok(launch_wgrad<64, 128, 4, 6, 2, false>(A[0], gA[1], nullptr, gp + w_off(1), gp + b_off(1), ph << 1, pw << 1, sms, sd[2]));
+  ok(launch_conv<128, 64, 4, 4, true, false, false>(gA[1], nullptr, wd[1], nullptr, nullptr, gA[0], ph << 1, pw << 1, s));
+  // conv0's adjoint: the input gradient on s, the weight and embedding gradients on a side stream;
+  // then the block-mean term of dL/dI_r
+  ok(link(E, s, sd[1]));
+  note_launches(4);
+  conv0_wgrad_kernel<<<(ph * pw + kConv0Px - 1) / kConv0Px, 256, 0, sd[1]>>>(gA[0], F(L.P), ph, pw, F(L.G), gp);
+  conv0_embed_grad_kernel<<<kEmbed, 256, 0, sd[1]>>>(F(L.G), params, embedding, grad_embedding, gp);
   conv0_dgrad_kernel<<<ph * pw, 256, 0, s>>>(gA[0], params, ph, pw, F(L.gP));
   ok(cudaGetLastError());
-  ok(launch_ssim_grad_appearance(img, target, F(L.maps), W, H, F(L.gP), pw, ph, grad_img, s));
-  ok(link(E, side, s));      // every launch of the call is ordered before later work on s
+  ok(link(E, sd[0], s));
+  pool_grad_add_kernel<<<(3 * 1024 * ph * pw + 255) / 256, 256, 0, s>>>(F(L.gP), W, H, pw, ph, grad_img);
+  ok(cudaGetLastError());
+  for (int k = 1; k < kSideStreams; ++k) ok(link(E, sd[k], s));   // every launch is ordered before later work on s
   return e == cudaSuccess ? VG_OK : VG_ERR_CUDA;
 }

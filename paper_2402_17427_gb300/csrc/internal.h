@@ -222,9 +222,10 @@ cudaError_t launch_blend_forward(const DevTables* tab, const HostPlan& plan, con
 cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool abs,
                                   cudaStream_t s);
 
-// A non-blocking stream per device (created on first use) for work that overlaps the caller's
-// stream; callers fork to it and join back with events within the same call.
-cudaStream_t side_stream();
+// Non-blocking streams per device (created on first use) for work that overlaps the caller's
+// stream; callers fork to them and join back with events within the same call.
+constexpr int kSideStreams = 4;
+cudaStream_t side_stream(int k = 0);
 
 // SSIM half of the loss (loss.cu), for the appearance loss of Eq. 3: the moment pass (maps
 // [9][H][W], partials [ssim_partials][2] = (sum S, sum |x - y|) per block) and the gradient pass
