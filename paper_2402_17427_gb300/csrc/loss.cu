@@ -46,25 +46,38 @@ __device__ __forceinline__ double block_sum(float v, double* sm) {
 
 // One separable 11-tap pass over G consecutive outputs: out[f][j] = sum_k w[k] in[f](j + k), the
 // G + 10 inputs read once each (sliding window in registers), taps accumulated in increasing k.
+// Outputs are updated in pairs with packed FP32 FMAs (two independent round-to-nearest FMAs an
+// instruction); a tap outside one output's window enters with weight 0, which leaves that sum
+// unchanged, so the result equals the scalar form bit for bit.
 template <int F, typename Load>
 __device__ __forceinline__ void window_pass(const Win& win, Load load, float (&out)[F][G]) {
+  static_assert(G % 2 == 0, "outputs are updated in pairs");
+  float2 acc[F][G / 2];
 #pragma unroll
   for (int f = 0; f < F; ++f)
 #pragma unroll
-    for (int j = 0; j < G; ++j) out[f][j] = 0.f;
+    for (int jp = 0; jp < G / 2; ++jp) acc[f][jp] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int i = 0; i < G + 10; ++i) {
     float v[F];
     load(i, v);
 #pragma unroll
-    for (int j = 0; j < G; ++j) {
-      const int k = i - j;
-      if (k >= 0 && k <= 10) {
+    for (int jp = 0; jp < G / 2; ++jp) {
+      const int k0 = i - 2 * jp, k1 = k0 - 1;       // taps of outputs 2 jp and 2 jp + 1
+      if (k0 >= 0 && k0 <= 11) {
+        const float2 w2 = make_float2(k0 <= 10 ? win.w[k0] : 0.f, k1 >= 0 ? win.w[k1] : 0.f);
 #pragma unroll
-        for (int f = 0; f < F; ++f) out[f][j] = fmaf(win.w[k], v[f], out[f][j]);
+        for (int f = 0; f < F; ++f) acc[f][jp] = __ffma2_rn(w2, make_float2(v[f], v[f]), acc[f][jp]);
       }
     }
   }
+#pragma unroll
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int jp = 0; jp < G / 2; ++jp) {
+      out[f][2 * jp] = acc[f][jp].x;
+      out[f][2 * jp + 1] = acc[f][jp].y;
+    }
 }
 
 // Moments of a 32x32 output tile: x, y staged with a 5-pixel zero-padded halo; the horizontal
@@ -193,6 +206,19 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
   const int c = blockIdx.z;
   const int ox = blockIdx.x * LT, oy = blockIdx.y * LT;
   const size_t plane = (size_t)W * H;
+  // this thread's output pixels' x and y, loaded now so that their latency overlaps the passes
+  const int q = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * G;
+  const int gx = ox + q;
+  float xs[G], ys[G], gs[G];
+#pragma unroll
+  for (int j = 0; j < G; ++j) {
+    const int gy = oy + r0 + j;
+    const bool in = gx < W && gy < H;
+    const size_t pix = c * plane + (in ? (size_t)gy * W + gx : 0);
+    xs[j] = __ldg(x + pix);
+    ys[j] = __ldg(y + pix);
+    if constexpr (kAppear) gs[j] = grad[pix];
+  }
 #pragma unroll
   for (int k = 0; k < kStage; ++k) {
     const int i = threadIdx.x + k * kLossThreads;
@@ -221,21 +247,19 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
       for (int j = 0; j < G; ++j) hs[f][r][g * G + j] = a[f][j];
   }
   __syncthreads();
-  const int q = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * G;
   float cm[3][G];
   window_pass<3>(win, [&](int i, float (&v)[3]) {
 #pragma unroll
     for (int f = 0; f < 3; ++f) v[f] = hs[f][r0 + i][q];
   }, cm);
-  const int gx = ox + q;
 #pragma unroll
   for (int j = 0; j < G; ++j) {
     const int gy = oy + r0 + j;
     if (gx >= W || gy >= H) continue;
     const size_t pix = c * plane + (size_t)gy * W + gx;
-    const float xv = x[pix], yv = y[pix];
+    const float xv = xs[j], yv = ys[j];
     if constexpr (kAppear) {
-      float add = grad[pix];
+      float add = gs[j];
       const int bx = gx >> 5, by = gy >> 5;
       if (bx < pw && by < ph) add += pool_grad[(by * pw + bx) * 3 + c] * (1.f / 1024.f);
       grad[pix] = add + cm[0][j] + 2.f * xv * cm[1][j] + yv * cm[2][j];
@@ -256,6 +280,23 @@ Win make_window() {
 }
 
 }  // namespace
+
+// The loss reduction reads only the moment pass's partial sums, so when the gradient pass follows
+// it runs on a side stream beside that pass, joined back to s before the call returns.
+cudaError_t finalize_beside(const double* partials, int nb, double inv, float lambda, float* out_loss, bool beside,
+                            cudaStream_t s, cudaEvent_t* fork, cudaEvent_t* join) {
+  cudaStream_t side = beside ? side_stream(1) : nullptr;
+  if (!side || cudaEventCreateWithFlags(fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(join, cudaEventDisableTiming) != cudaSuccess) {
+    loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
+    return cudaGetLastError();
+  }
+  cudaEventRecord(*fork, s);
+  cudaStreamWaitEvent(side, *fork, 0);
+  loss_finalize<<<1, 1024, 0, side>>>(partials, nb, inv, lambda, out_loss);
+  cudaEventRecord(*join, side);
+  return cudaGetLastError();
+}
 
 size_t ssim_maps_floats(int W, int H) { return 9 * (size_t)W * H; }
 int ssim_partials(int W, int H) { return ((W + LT - 1) / LT) * ((H + LT - 1) / LT) * 3; }
@@ -305,10 +346,15 @@ extern "C" vg_status vg_loss_l1_dssim(const float* img, const float* target, int
   const Win win = make_window();
   note_launches(out_grad ? 3 : 2);
   ssim_forward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
-  loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaError_t e = finalize_beside(partials, nb, inv, lambda, out_loss, out_grad != nullptr, s, &fork, &join);
   if (out_grad)
     ssim_backward_kernel<false><<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
-  return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;
+  if (join) cudaStreamWaitEvent(s, join, 0);   // nothing of the call outlives it on s
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e == cudaSuccess ? VG_OK : VG_ERR_CUDA;
 }
 
 // ----------------------------------------------------------------------------------------------
