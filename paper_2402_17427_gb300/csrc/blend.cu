@@ -293,24 +293,63 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
           // and last bit for bit (w = 0 adds an exact zero)
           const uint32_t pos1 = (uint32_t)(k * ch + j + 1);
           if (COUNT) xr += S::kPPT;
+          if constexpr (S::kPPT % 2 == 0) {
+            // pixel pairs: the arithmetic as packed FP32 (two independent round-to-nearest
+            // operations an instruction, so every value equals the scalar form's bit for bit)
 #pragma unroll
-          for (int p = 0; p < S::kPPT; ++p) {
-            if (COUNT) ev += done[p] ? 0 : 1;
-            const float p2 = splat_power2(f1.x, e0, e1, __fadd_rn(dy0, (float)p));
-            const float q = __fadd_rn(p2, f1.y);
-            const bool ok = !done[p] && !(p2 > 0.f || q < lamin);
-            const float a = fminf(amax, ex2_approx(q));
-            const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
-            const bool stop = ok && Tn < tmin;
-            const bool blend = ok && !(stop && rule0);
-            const float w = blend ? __fmul_rn(a, T[p]) : 0.f;
-            C[p][0] = __fmaf_rn(f1.z, w, C[p][0]);
-            C[p][1] = __fmaf_rn(f1.w, w, C[p][1]);
-            C[p][2] = __fmaf_rn(f2.x, w, C[p][2]);
-            T[p] = blend ? Tn : T[p];
-            last[p] = blend ? pos1 : last[p];
-            if (COUNT) bl += blend ? 1 : 0;
-            done[p] = done[p] || stop;
+            for (int p = 0; p < S::kPPT; p += 2) {
+              if (COUNT) ev += (done[p] ? 0 : 1) + (done[p + 1] ? 0 : 1);
+              const float2 dy = __fadd2_rn(make_float2(dy0, dy0), make_float2((float)p, (float)(p + 1)));
+              const float2 p2 = __ffma2_rn(dy, __ffma2_rn(make_float2(f1.x, f1.x), dy, make_float2(e1, e1)),
+                                           make_float2(e0, e0));
+              const float2 q = __fadd2_rn(p2, make_float2(f1.y, f1.y));
+              const bool ok0 = !done[p] && !(p2.x > 0.f || q.x < lamin);
+              const bool ok1 = !done[p + 1] && !(p2.y > 0.f || q.y < lamin);
+              const float2 a = make_float2(fminf(amax, ex2_approx(q.x)), fminf(amax, ex2_approx(q.y)));
+              const float2 Tp = make_float2(T[p], T[p + 1]);
+              const float2 Tn = __fmul2_rn(Tp, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a.x, -a.y)));
+              const bool stop0 = ok0 && Tn.x < tmin, stop1 = ok1 && Tn.y < tmin;
+              const bool blend0 = ok0 && !(stop0 && rule0), blend1 = ok1 && !(stop1 && rule0);
+              float2 w = __fmul2_rn(a, Tp);
+              w.x = blend0 ? w.x : 0.f;
+              w.y = blend1 ? w.y : 0.f;
+              const float2 c0 = __ffma2_rn(make_float2(f1.z, f1.z), w, make_float2(C[p][0], C[p + 1][0]));
+              const float2 c1 = __ffma2_rn(make_float2(f1.w, f1.w), w, make_float2(C[p][1], C[p + 1][1]));
+              const float2 c2 = __ffma2_rn(make_float2(f2.x, f2.x), w, make_float2(C[p][2], C[p + 1][2]));
+              C[p][0] = c0.x;
+              C[p + 1][0] = c0.y;
+              C[p][1] = c1.x;
+              C[p + 1][1] = c1.y;
+              C[p][2] = c2.x;
+              C[p + 1][2] = c2.y;
+              T[p] = blend0 ? Tn.x : T[p];
+              T[p + 1] = blend1 ? Tn.y : T[p + 1];
+              last[p] = blend0 ? pos1 : last[p];
+              last[p + 1] = blend1 ? pos1 : last[p + 1];
+              if (COUNT) bl += (blend0 ? 1 : 0) + (blend1 ? 1 : 0);
+              done[p] = done[p] || stop0;
+              done[p + 1] = done[p + 1] || stop1;
+            }
+          } else {
+#pragma unroll
+            for (int p = 0; p < S::kPPT; ++p) {
+              if (COUNT) ev += done[p] ? 0 : 1;
+              const float p2 = splat_power2(f1.x, e0, e1, __fadd_rn(dy0, (float)p));
+              const float q = __fadd_rn(p2, f1.y);
+              const bool ok = !done[p] && !(p2 > 0.f || q < lamin);
+              const float a = fminf(amax, ex2_approx(q));
+              const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
+              const bool stop = ok && Tn < tmin;
+              const bool blend = ok && !(stop && rule0);
+              const float w = blend ? __fmul_rn(a, T[p]) : 0.f;
+              C[p][0] = __fmaf_rn(f1.z, w, C[p][0]);
+              C[p][1] = __fmaf_rn(f1.w, w, C[p][1]);
+              C[p][2] = __fmaf_rn(f2.x, w, C[p][2]);
+              T[p] = blend ? Tn : T[p];
+              last[p] = blend ? pos1 : last[p];
+              if (COUNT) bl += blend ? 1 : 0;
+              done[p] = done[p] || stop;
+            }
           }
         }
         if (COUNT) {
@@ -486,7 +525,59 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
           float S0 = 0.f, S1 = 0.f, S2 = 0.f;
           bool any = false;
           // branch-free over the thread's pixels: a pixel this Gaussian does not reach gets
-          // alpha = 0, which leaves B and the sums unchanged, and keeps its T by a select
+          // alpha = 0, which leaves B and the sums unchanged, and keeps its T by a select.
+          // Pixel pairs run as packed FP32; the power and the decisions are formed exactly as in
+          // the forward pass (round-to-nearest in both lanes), the sums pairwise.
+          if constexpr (S::kPPT % 2 == 0 && !ABS) {
+            float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, w6 = s0, w7 = s0, w8 = s0;
+#pragma unroll
+            for (int p = 0; p < S::kPPT; p += 2) {
+              const float2 dy = __fadd2_rn(make_float2(dyb[p / FP], dyb[(p + 1) / FP]),
+                                           make_float2((float)(p % FP), (float)((p + 1) % FP)));
+              const float2 p2 = __ffma2_rn(dy, __ffma2_rn(make_float2(f1.x, f1.x), dy, make_float2(e1, e1)),
+                                           make_float2(e0, e0));
+              const float2 q = __fadd2_rn(p2, make_float2(f1.y, f1.y));
+              const bool ok0 = pos < lastp[p] && !(p2.x > 0.f || q.x < lamin);
+              const bool ok1 = pos < lastp[p + 1] && !(p2.y > 0.f || q.y < lamin);
+              const float2 araw = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+              const float2 a = make_float2(ok0 ? fminf(amax, araw.x) : 0.f, ok1 ? fminf(amax, araw.y) : 0.f);
+              any = any || ok0 || ok1;
+              const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a.x, -a.y));
+              const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+              const float2 Tp = make_float2(T[p], T[p + 1]), Bp = make_float2(B[p], B[p + 1]);
+              const float2 Tb = __fmul2_rn(Tp, rom);
+              const float2 aT = __fmul2_rn(a, Tb);
+              const float2 g0 = make_float2(G[p][0], G[p + 1][0]), g1 = make_float2(G[p][1], G[p + 1][1]),
+                           g2 = make_float2(G[p][2], G[p + 1][2]);
+              w6 = __ffma2_rn(aT, g0, w6);
+              w7 = __ffma2_rn(aT, g1, w7);
+              w8 = __ffma2_rn(aT, g2, w8);
+              const float2 cg = __ffma2_rn(make_float2(f2.x, f2.x), g2,
+                                           __ffma2_rn(make_float2(f1.w, f1.w), g1, __fmul2_rn(make_float2(f1.z, f1.z), g0)));
+              const float2 br = __fmul2_rn(Bp, rom);
+              const float2 dal = __ffma2_rn(Tb, cg, make_float2(-br.x, -br.y));
+              const float2 Bn = __ffma2_rn(cg, aT, Bp);
+              B[p] = Bn.x;
+              B[p + 1] = Bn.y;
+              T[p] = ok0 ? Tb.x : T[p];
+              T[p + 1] = ok1 ? Tb.y : T[p + 1];
+              // where alpha is clamped to alpha_max it does not depend on the power (a pixel
+              // this Gaussian does not reach has a = 0, hence dal * a = 0)
+              float2 dpow = __fmul2_rn(dal, a);
+              dpow.x = araw.x < amax ? dpow.x : 0.f;
+              dpow.y = araw.y < amax ? dpow.y : 0.f;
+              const float2 dpy = __fmul2_rn(dpow, dy);
+              s0 = __fadd2_rn(s0, dpow);
+              s1 = __fadd2_rn(s1, dpy);
+              s2 = __ffma2_rn(dpy, dy, s2);
+            }
+            S0 = s0.x + s0.y;
+            S1 = s1.x + s1.y;
+            S2 = s2.x + s2.y;
+            v[6] = w6.x + w6.y;
+            v[7] = w7.x + w7.y;
+            v[8] = w8.x + w8.y;
+          } else {
 #pragma unroll
           for (int p = 0; p < S::kPPT; ++p) {
             const float dy = __fadd_rn(dyb[p / FP], (float)(p % FP));
@@ -518,6 +609,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
               const float dv = kNegTwoLn2 * (0.5f * f0.w * dx * dpow + f1.x * dpy);
               v[9] += fabsf(du) + fabsf(dv);
             }
+          }
           }
           if (__any_sync(0xffffffffu, any)) {
             // fields: du, dv, d conic (a, b, c), d opacity, d rgb; with alpha = o G unclamped,
