@@ -43,9 +43,9 @@ OPS_EVAL, OPS_BLEND_FWD, OPS_BLEND_BWD = 11, 7, 37
 TRAFFIC_SOURCES = ("paper_2402_17427_gb300/csrc/blend.cu", "paper_2402_17427_gb300/csrc/vg_common.cuh",
                    "paper_2402_17427_gb300/csrc/internal.h")
 PROFILED_TRAFFIC = {
-    "sources_sha256": "af228e7697c0223836b06dc2f6cf84de9f1224aca6a538be818ccd67621f9ca7",
-    "blend": 18667008 + 1918208,
-    "blend_backward": 67442176 + 1484544,
+    "sources_sha256": "984ce675407e8db67d48b34e1c020bb7dd3e8788e1730636dc1be1adbe42e6ff",
+    "blend": 18659328 + 2043392,
+    "blend_backward": 67468800 + 1629696,
 }
 
 
