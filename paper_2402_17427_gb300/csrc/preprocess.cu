@@ -497,16 +497,28 @@ __global__ void __launch_bounds__(128, 4) preprocess_backward_kernel(
   {
     float G[16][3];
     sh_basis_grad<DEG>(d0, d1, dz, G);
+    auto term = [&](float c, int k, int ch) {
+      pre[ch] = fmaf(c, Y[k], pre[ch]);
+      D[ch][0] = fmaf(c, G[k][0], D[ch][0]);
+      D[ch][1] = fmaf(c, G[k][1], D[ch][1]);
+      D[ch][2] = fmaf(c, G[k][2], D[ch][2]);
+    };
+    if constexpr (F % 4 == 0) {   // 16-byte rows: one vector load per four coefficients, same order
+      const float4* p4 = reinterpret_cast<const float4*>(shp);
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        const float c = __ldg(shp + 3 * k + ch);
-        pre[ch] = fmaf(c, Y[k], pre[ch]);
-        D[ch][0] = fmaf(c, G[k][0], D[ch][0]);
-        D[ch][1] = fmaf(c, G[k][1], D[ch][1]);
-        D[ch][2] = fmaf(c, G[k][2], D[ch][2]);
+      for (int q = 0; q < F / 4; ++q) {
+        const float4 v = __ldg(p4 + q);
+        term(v.x, (4 * q) / 3, (4 * q) % 3);
+        term(v.y, (4 * q + 1) / 3, (4 * q + 1) % 3);
+        term(v.z, (4 * q + 2) / 3, (4 * q + 2) % 3);
+        term(v.w, (4 * q + 3) / 3, (4 * q + 3) % 3);
       }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) term(__ldg(shp + 3 * k + ch), k, ch);
+    }
   }
   float dpre[3];
 #pragma unroll
