@@ -558,7 +558,7 @@ def main():
         host = [t.cpu().pin_memory() for t in params]
         host_target = target_t.cpu().pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in host) + host_target.numel() * 4
-        dev = [params, [torch.empty_like(t) for t in params]]
+        dsets = [params, [torch.empty_like(t) for t in params]]
         dtg = [target_t, torch.empty_like(target_t)]
         comp, cs = torch.cuda.current_stream(), torch.cuda.Stream()
         ready = [torch.cuda.Event(), torch.cuda.Event()]
@@ -567,7 +567,7 @@ def main():
         def upload(b):
             with torch.cuda.stream(cs):
                 cs.wait_event(free[b])        # the step that last read input set b has finished
-                for d, h in zip(dev[b], host):
+                for d, h in zip(dsets[b], host):
                     d.copy_(h, non_blocking=True)
                 dtg[b].copy_(host_target, non_blocking=True)
                 ready[b].record(cs)
@@ -581,7 +581,7 @@ def main():
                 if i + 1 < n:
                     upload(1 - b)
                 comp.wait_event(ready[b])
-                L = step(prm=dev[b], tgt=dtg[b])[0]
+                L = step(prm=dsets[b], tgt=dtg[b])[0]
                 free[b].record(comp)
                 out[i].copy_(L.view(-1)[:1], non_blocking=True)   # the step's loss, device to host
 
