@@ -90,9 +90,9 @@ __device__ __forceinline__ float2 ldg2(const float* p, int i) { return __ldg(rei
 // B[tap tapc + o][c] = W[o][c][8 - tap].
 
 struct PackJob {
-  int layer, dgrad, tapc, kpad, npad, f16, offset;   // offset in elements of the job's type
+  int layer, dgrad, tapc, kpad, npad, f16, aop, offset;   // offset in elements of the job's type
 };
-constexpr int kPackJobs = 12;
+constexpr int kPackJobs = 13;
 struct PackTable {
   PackJob job[kPackJobs];
   int begin[kPackJobs + 1];   // first element index of each job in the launch's index space
@@ -107,7 +107,9 @@ __device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
 
 // TF32 jobs (m16n8k8): element (k-step s, n-tile j, lane, e) = B[8s + t + 4e][8j + g].
 // FP16 jobs (m16n8k16): element (s, j, lane, r, h) = B[16s + 2t + h + 8r][8j + g], so that each
-// lane reads its two B registers as one 8-byte word.
+// lane reads its two B registers as one 8-byte word.  FP16 A-operand jobs hold B transposed as an
+// m16n8k16 A operand (rows = B's columns): element (s, lane, r, h) = B[16s + 2t + h + 8 (r >> 1)]
+// [g + 8 (r & 1)], four registers a lane as one 16-byte word.
 __global__ void pack_kernel(const float* __restrict__ params, void* __restrict__ packed, const PackTable tab) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= tab.begin[kPackJobs]) return;
@@ -117,7 +119,12 @@ __global__ void pack_kernel(const float* __restrict__ params, void* __restrict__
   const int local = i - tab.begin[jb];
   const int nt = J.npad / 8;
   int k, n, rest, lane;
-  if (J.f16) {
+  if (J.aop) {
+    const int h = local & 1, r = (local >> 1) & 3;
+    lane = (local >> 3) & 31;
+    k = 16 * (local >> 8) + 2 * (lane & 3) + h + 8 * (r >> 1);
+    n = (lane >> 2) + 8 * (r & 1);
+  } else if (J.f16) {
     const int h = local & 1, r = (local >> 1) & 1;
     lane = (local >> 2) & 31;
     rest = local >> 7;
@@ -128,7 +135,7 @@ __global__ void pack_kernel(const float* __restrict__ params, void* __restrict__
     rest = local >> 6;
     k = 8 * (rest / nt) + (lane & 3) + 4 * e;
   }
-  n = 8 * (rest % nt) + (lane >> 2);
+  if (!J.aop) n = 8 * (rest % nt) + (lane >> 2);
   const int C = layer_c(J.layer), O = layer_o(J.layer);
   const float* W = params + w_off(J.layer);
   const int tap = k / J.tapc, c = k % J.tapc;
@@ -593,6 +600,7 @@ struct HeadArgs {
   const float *img, *target, *b5, *b6;
   const __half* u;                          // the up-sampled F4, [H][W][16]
   const uint2 *w5f, *w5d, *w6f, *w6d;       // FP16 B fragments
+  const uint4* w5da;                        // conv5's adjoint weights as FP16 A fragments
   float *gimg, *map, *gf4, *dw5, *db5, *dw6, *db6;
   double* partials;
   int H, W, h4, w4, tiles_x, tiles;
@@ -957,8 +965,11 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
           mma16(acc6[u], ah, bgm0, bgm1);
         }
       }
-      // S7: gU'(p) = (conv5 adjoint of gZ5')(p) over T (rows warp and warp + 8).  N = 16, K = 9
-      // flipped taps x 16 channels.
+      // S7: dL/dU over T, rows warp and warp + 8, computed transposed: gU^T[ci][p] = sum_k
+      // W5d^T[ci][k] gZ5'^T[k][p] with M = 16 input channels (A: the packed weights), N = the
+      // row's 16 pixels (B: gZ5' rows through ldmatrix), K = 9 flipped taps x 16 channels.  The
+      // accumulators of the two pixel halves then form exactly an m16n8k16 A operand, which the
+      // bilinear adjoint's column pass uses directly.
       float acc7[2][2][4];
 #pragma unroll
       for (int i = 0; i < 2; ++i)
@@ -966,63 +977,68 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
         for (int q = 0; q < 4; ++q) acc7[i][0][q] = acc7[i][1][q] = 0.f;
 #pragma unroll
       for (int s = 0; s < 9; ++s) {
-        const uint2 b0 = __ldg(a.w5d + (s * 2 + 0) * 32 + lane), b1 = __ldg(a.w5d + (s * 2 + 1) * 32 + lane);
+        const uint4 aw = __ldg(a.w5da + s * 32 + lane);
+        const uint32_t afr[4] = {aw.x, aw.y, aw.z, aw.w};
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-          uint32_t av[4];
-          ldsm4(av, uZ + (((warp + 8 * i + s / 3) * R1 + lrow + s % 3) * HP + 8 * lq) * 2);
-          mma16(acc7[i][0], av, b0.x, b0.y);
-          mma16(acc7[i][1], av, b1.x, b1.y);
+          uint32_t bz[4];
+          ldsm4(bz, uZ + (((warp + 8 * i + s / 3) * R1 + tp + s % 3) * HP + 8 * tc) * 2);
+          mma16(acc7[i][0], afr, bz[0], bz[1]);
+          mma16(acc7[i][1], afr, bz[2], bz[3]);
         }
       }
       __syncthreads();   // every warp is past S4, S6 and S7 (the last readers of U, Hh and gZ5')
       fetch_u(tile + gridDim.x);
-      // dL/dU over T -> sH as FP32 [row][column][16]; then the bilinear adjoint as two gathers:
-      // columns (into sZ as [row][footprint column][16]) and rows (straight into dL/dF4).
-      float* sGU = reinterpret_cast<float*>(sH);
+      // Bilinear adjoint, column pass on the tensor cores: X^T[ci][b] = sum_x gU^T[ci][x] Rx[x][b]
+      // for each of the warp's rows (K = the row's 16 pixels, N = footprint columns b in two
+      // n-tiles), Rx[x][b] = the weight of column x's taps on footprint column bx0 + b; then the
+      // row pass gathers sX [row][footprint column][16] straight into dL/dF4.
       float* sX = reinterpret_cast<float*>(sZ);
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int j = 0; j < 2; ++j)
-            *reinterpret_cast<float2*>(sGU + (((warp + 8 * i) * HT + g + 8 * h) * 16) + 8 * j + 2 * t) =
-                make_float2(acc7[i][j][2 * h], acc7[i][j][2 * h + 1]);
       const int bx0 = tX0[4], bx1 = tX1[min(HT + 3, a.W - 1 - ox + 4)];
       const int by0 = tY0[4], by1 = tY1[min(HT + 3, a.H - 1 - oy + 4)];
       const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1;
-      const int ncx = min(HT, a.W - ox), ncy = min(HT, a.H - oy);
-      // contributors of footprint column b: the T columns whose taps (first, second) include b, a
-      // contiguous run because the taps are monotone; likewise for rows
-      if (threadIdx.x < 2 * FT) {
-        const bool row = threadIdx.x >= FT;
-        const int k = row ? threadIdx.x - FT : threadIdx.x, b = (row ? by0 : bx0) + k;
-        const int n = row ? ncy : ncx;
-        const int* t0 = row ? tY0 : tX0;
-        const int* t1 = row ? tY1 : tX1;
-        int first = 0, end = 0;
-        while (first < n && t1[first + 4] < b) ++first;
-        end = first;
-        while (end < n && t0[end + 4] <= b) ++end;
-        (row ? rY : rX)[k] = make_int2(first, end);
-      }
-      __syncthreads();
-      for (int it = threadIdx.x; it < HT * nbx * 4; it += kHeadThreads) {
-        const int v = it & 3, rest = it >> 2, jb = rest % nbx, r = rest / nbx;
-        const int b = bx0 + jb;
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int2 run = rX[jb];
-        for (int x = run.x; x < run.y; ++x) {
-          const float fx = tFX[x + 4];
-          const float w = (tX0[x + 4] == b ? 1.f - fx : 0.f) + (tX1[x + 4] == b ? fx : 0.f);
-          const float4 gu = *reinterpret_cast<const float4*>(sGU + (r * HT + x) * 16 + 4 * v);
-          s.x = fmaf(w, gu.x, s.x);
-          s.y = fmaf(w, gu.y, s.y);
-          s.z = fmaf(w, gu.z, s.z);
-          s.w = fmaf(w, gu.w, s.w);
+      const int ncy = min(HT, a.H - oy);
+      {
+        uint32_t rx[2][2];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            float w2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int x = 2 * t + h + 8 * r + 4, b = bx0 + g + 8 * nt;   // x: R4 column of T column
+              const float fx = tFX[x];
+              w2[h] = (tX0[x] == b ? 1.f - fx : 0.f) + (tX1[x] == b ? fx : 0.f);
+            }
+            rx[nt][r] = pack_half2(w2[0], w2[1]);
+          }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const uint32_t ga[4] = {pack_half2(acc7[i][0][0], acc7[i][0][1]), pack_half2(acc7[i][0][2], acc7[i][0][3]),
+                                  pack_half2(acc7[i][1][0], acc7[i][1][1]), pack_half2(acc7[i][1][2], acc7[i][1][3])};
+          const int r = warp + 8 * i;
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            float xc[4] = {0.f, 0.f, 0.f, 0.f};
+            mma16(xc, ga, rx[nt][0], rx[nt][1]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int b = 8 * nt + 2 * t + (e & 1), ci = g + 8 * (e >> 1);
+              if (b < FT) sX[(r * FT + b) * 16 + ci] = xc[e];
+            }
+          }
         }
-        *reinterpret_cast<float4*>(sX + (r * FT + jb) * 16 + 4 * v) = s;
+      }
+      // contributors of footprint row b: the T rows whose taps (first, second) include b, a
+      // contiguous run because the taps are monotone
+      if (threadIdx.x < FT) {
+        const int b = by0 + threadIdx.x;
+        int first = 0;
+        while (first < ncy && tY1[first + 4] < b) ++first;
+        int end = first;
+        while (end < ncy && tY0[end + 4] <= b) ++end;
+        rY[threadIdx.x] = make_int2(first, end);
       }
       __syncthreads();
       for (int it = threadIdx.x; it < nby * nbx * 4; it += kHeadThreads) {
@@ -1164,7 +1180,7 @@ AppLayout make_app_layout(int W, int H) {
   // packed B operands: forward and input-gradient GEMMs of blocks 1..4 (TF32), conv5 and conv6 of
   // the head (FP16)
   const int jobs[kPackJobs][2] = {{1, 0}, {2, 0}, {3, 0}, {4, 0}, {1, 1}, {2, 1},
-                                  {3, 1}, {4, 1}, {5, 0}, {5, 1}, {6, 0}, {6, 1}};
+                                  {3, 1}, {4, 1}, {5, 0}, {5, 1}, {6, 0}, {6, 1}, {5, 1}};
   int pos = 0, idx = 0;   // pos: floats of the buffer used; idx: elements of the launch's index space
   for (int j = 0; j < kPackJobs; ++j) {
     const int l = jobs[j][0], dg = jobs[j][1];
@@ -1173,6 +1189,7 @@ AppLayout make_app_layout(int W, int H) {
     J.layer = l;
     J.dgrad = dg;
     J.f16 = l >= 5;
+    J.aop = j == 12;                                   // conv5's adjoint as an A operand
     J.tapc = !J.f16 ? kin : (l == 6 && dg) ? 8 : 16;   // conv6's adjoint: 3 channels a tap, read as 8
     const int kstep = J.f16 ? 16 : 8;
     J.kpad = (9 * J.tapc + kstep - 1) / kstep * kstep;
@@ -1340,6 +1357,7 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   ha.w5d = reinterpret_cast<const uint2*>(packed + L.pack_off[9]);
   ha.w6f = reinterpret_cast<const uint2*>(packed + L.pack_off[10]);
   ha.w6d = reinterpret_cast<const uint2*>(packed + L.pack_off[11]);
+  ha.w5da = reinterpret_cast<const uint4*>(packed + L.pack_off[12]);
   ha.b5 = params + b_off(5);
   ha.b6 = params + b_off(6);
   ha.gimg = grad_img;
