@@ -581,7 +581,8 @@ __global__ void __launch_bounds__(256) conv0_embed_grad_kernel(const float* __re
 //   sI  I_r and I over R2 (FP32 planes, zero outside the image), fetched with cp.async at the
 //       start of the tile
 //   tables: bilinear taps (first, second source row / column, weight of the second) of R4's
-//       rows and columns, -1 outside the image
+//       rows and columns, -1 outside the image; per footprint row, the run of T's rows that
+//       reach it
 // After the GEMMs, sH and sZ hold dL/dU over T and its column-reduced form (FP32) for the
 // bilinear adjoint's two gather passes.
 constexpr int HT = 16;
@@ -591,7 +592,7 @@ constexpr int GP = 8;                 // halves per pixel in sG
 constexpr int FT = 10;                // dL/dF4 footprint side of T
 constexpr int kHeadThreads = 256;
 constexpr int kBU = R4 * R4 * HP * 2, kBH = R3 * R3 * HP * 2, kBZ = R1 * R1 * HP * 2, kBG = R2 * R2 * GP * 2;
-constexpr int kBI = 2 * 3 * R2 * R2 * 4, kBT = 6 * R4 * 4 + 4 * FT * 4;
+constexpr int kBI = 2 * 3 * R2 * R2 * 4, kBT = 6 * R4 * 4 + 2 * FT * 4;
 constexpr int kHeadSmemBytes = kBU + kBH + kBZ + kBG + kBI + kBT;
 static_assert(HT * HT * 16 * 4 <= kBH && HT * FT * 16 * 4 <= kBZ, "bilinear adjoint buffers fit");
 static_assert(kBU % 16 == 0 && kBH % 16 == 0 && kBZ % 16 == 0 && kBG % 16 == 0 && kBI % 16 == 0, "alignment");
@@ -703,8 +704,7 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
   int* tX0 = reinterpret_cast<int*>(tFY + R4);
   int* tX1 = tX0 + R4;
   float* tFX = reinterpret_cast<float*>(tX1 + R4);
-  int2* rX = reinterpret_cast<int2*>(tFX + R4);     // contributor runs [first, end) of T's columns
-  int2* rY = rX + FT;                                // and rows, per footprint column / row
+  int2* rY = reinterpret_cast<int2*>(tFX + R4);     // contributor runs [first, end) of T's rows
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
   // ldmatrix rows: lrow / lq for A (pixel rows, channel halves) and for the weight-gradient B
   // operands; tp / tc for the transposed weight-gradient A operands (pixel, channel half)
