@@ -10,7 +10,8 @@ from the oracle itself: the relative change of that gradient when the tensor-cor
 are rounded to TF32 (one of the perturbations the GPU applies, the activations' roundings being of
 the same size) is its sensitivity s, and the GPU must agree within max(3e-3, 4 s).  The L1 term's
 sign is a decision taken in floating point: where |I_r M - I| is within the map's error bound the
-two sides may legitimately differ, so element-wise gradient checks skip those pixels.
+two sides may legitimately differ, so dL/dI_r must agree element-wise (within 2e-3 of its scale)
+everywhere except at such pixels.
 """
 import numpy as np
 import pytest
@@ -90,8 +91,9 @@ def _compare(W, H, seed, lam=0.2):
     d = img.astype(np.float64) * M - target
     settled = np.abs(d) > 4e-3 * span
     scale = np.abs(gi).max()
-    assert np.abs(g["grad_img"] - gi)[settled].max() <= 2e-3 * scale
-    assert _rel(g["grad_img"], gi) <= 1e-2
+    off = np.abs(g["grad_img"] - gi) > 2e-3 * scale
+    assert not (off & settled).any()           # any disagreement is at a pixel whose sign is unsettled
+    assert off.mean() <= (~settled).mean()
     # the embedding and every layer's weight and bias gradients
     assert _rel(g["grad_embedding"], ge) <= tol(ge, ge_t)
     views = AP.layer_views(torch.from_numpy(g["grad_params"]))
@@ -106,6 +108,15 @@ def test_appearance_matches_oracle(W, H, seed):
     # (100, 70): 3 x 2 pooled cells, 6 rows and 4 columns outside them, ragged 16 x 16 head tiles;
     # (330, 200): 10 x 6 cells, 21 x 13 head tiles; (64, 32): the smallest shapes (1 x 2 cells)
     _compare(W, H, seed)
+
+
+@pytest.mark.parametrize("lam", [0.0, 1.0])
+def test_appearance_lambda_extremes(lam):
+    # lambda = 0: L1 on I_a alone (no D-SSIM term); lambda = 1: D-SSIM on I_r alone, so the CNN
+    # receives no gradient at all
+    g = _compare(100, 70, 5, lam)
+    if lam == 1.0:
+        assert not g["grad_params"].any() and not g["grad_embedding"].any()
 
 
 def test_appearance_full_size_matches_oracle():
