@@ -384,8 +384,8 @@ __global__ void __launch_bounds__(256) conv_mma_kernel(const float* __restrict__
 // k-step are taken in the order x0 + 2t (k = t), x0 + 2t + 1 (k = t + 4): with row pitches of 8
 // or 24 mod 32 floats the scalar fragment loads (pixel along t, channel along g) then hit
 // distinct banks.
-template <int C, int O, int TY, int MB, int WM, bool MASK_IN>
-__global__ void __launch_bounds__(256) wgrad_kernel(const float* __restrict__ Aprev, const float* __restrict__ gA,
+template <int C, int O, int TY, int MB, int WM, bool MASK_IN, int PF>
+__global__ void __launch_bounds__(256, 2) wgrad_kernel(const float* __restrict__ Aprev, const float* __restrict__ gA,
                                                     const float* __restrict__ A, float* __restrict__ dW,
                                                     float* __restrict__ db, int Hr, int Wr, int tiles_x, int tiles,
                                                     int per_block) {
@@ -419,13 +419,89 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const float* __restrict__ Ap
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
   float dbs = 0.f;
-  const int tile_end = min(tiles, (blockIdx.x + 1) * per_block);
-  for (int tile = blockIdx.x * per_block; tile < tile_end; ++tile) {
+  // Staging: a tile's global data (X in the previous layer's native layout, the output gradient
+  // and, when MASK_IN, the activations) is loaded into registers, then written to shared memory
+  // (X scattered to its four logical pixels, TF32-rounded).  Where the registers allow (PF bit 0
+  // for X, bit 1 for the gradient) the loads of the next tile are issued before this tile's MMAs,
+  // so that they are in flight while it computes.  Tile origins are even, so the native extents
+  // are fixed: NYN x NXN native pixels of 4C floats cover the (TY + 2) x 18 logical tile.
+  constexpr int NYN = TY / 2 + 2, NXN = 10, SHT = TY + 2;
+  constexpr int XN = NYN * NXN * C, ZN = TY * 16 * (O / 4);
+  constexpr int XI = (XN + 255) / 256, ZI = (ZN + 255) / 256;
+  const int Hn = Hr >> 1, Wn = Wr >> 1;
+  float4 rx[XI], rz[ZI], ra[MASK_IN ? ZI : 1];
+  auto load_x = [&](int tile) {
+    const int oy = (tile / tiles_x) * TY, ox = (tile % tiles_x) * 16;
+    const int yn0 = (oy - 1) >> 1, xn0 = (ox - 1) >> 1;
+#pragma unroll
+    for (int q = 0; q < XI; ++q) {
+      const int i = threadIdx.x + 256 * q;
+      const int c = i % C, px = i / C, yn = yn0 + px / NXN, xn = xn0 + px % NXN;
+      rx[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < XN && yn >= 0 && yn < Hn && xn >= 0 && xn < Wn)
+        rx[q] = __ldg(reinterpret_cast<const float4*>(Aprev + ((size_t)yn * Wn + xn) * (4 * C)) + c);
+    }
+  };
+  auto load_z = [&](int tile) {
+    const int oy = (tile / tiles_x) * TY, ox = (tile % tiles_x) * 16;
+#pragma unroll
+    for (int q = 0; q < ZI; ++q) {
+      const int i = threadIdx.x + 256 * q;
+      const int v = i % (O / 4), px = i / (O / 4), Y = oy + px / 16, X = ox + px % 16;
+      rz[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < ZN && Y < Hr && X < Wr) {
+        const size_t e = ((size_t)Y * Wr + X) * O + 4 * v;
+        rz[q] = __ldg(reinterpret_cast<const float4*>(gA + e));
+        if constexpr (MASK_IN) ra[q] = __ldg(reinterpret_cast<const float4*>(A + e));
+      }
+    }
+  };
+  auto store_x = [&](int tile) {
+    const int oy = (tile / tiles_x) * TY, ox = (tile % tiles_x) * 16;
+    const int Y0 = oy - 1, X0 = ox - 1, yn0 = Y0 >> 1, xn0 = X0 >> 1;
+#pragma unroll
+    for (int q = 0; q < XI; ++q) {
+      const int i = threadIdx.x + 256 * q;
+      if (i >= XN) continue;
+      const int c = i % C, px = i / C, yn = yn0 + px / NXN, xn = xn0 + px % NXN;
+      const float v4[4] = {rx[q].x, rx[q].y, rx[q].z, rx[q].w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = 2 * yn + (k >> 1) - Y0, sx = 2 * xn + (k & 1) - X0;
+        if (r >= 0 && r < SHT && sx >= 0 && sx < SW) sX[(r * SW + sx) * PX + c] = tf32r(v4[k]);
+      }
+    }
+  };
+  auto store_z = [&]() {
+#pragma unroll
+    for (int q = 0; q < ZI; ++q) {
+      const int i = threadIdx.x + 256 * q;
+      if (i >= ZN) continue;
+      const int v = i % (O / 4), px = i / (O / 4);
+      float4 z = rz[q];
+      if constexpr (MASK_IN)
+        z = make_float4(ra[q].x > 0.f ? z.x : 0.f, ra[q].y > 0.f ? z.y : 0.f, ra[q].z > 0.f ? z.z : 0.f,
+                        ra[q].w > 0.f ? z.w : 0.f);
+      *reinterpret_cast<float4*>(sZ + px * PZ + 4 * v) = make_float4(tf32r(z.x), tf32r(z.y), tf32r(z.z), tf32r(z.w));
+    }
+  };
+  const int tile_begin = blockIdx.x * per_block, tile_end = min(tiles, (blockIdx.x + 1) * per_block);
+  if (tile_begin < tile_end) {
+    if constexpr ((PF & 1) != 0) load_x(tile_begin);
+    if constexpr ((PF & 2) != 0) load_z(tile_begin);
+  }
+  for (int tile = tile_begin; tile < tile_end; ++tile) {
     const int oy = (tile / tiles_x) * TY, ox = (tile % tiles_x) * 16;
     __syncthreads();
-    stage_shuffled<C, PX>(sX, Aprev, oy - 1, ox - 1, TY + 2, SW, Hr, Wr);
-    stage_plain<O, PZ, MASK_IN>(sZ, gA, A, oy, ox, TY, 16, Hr, Wr);
+    if constexpr ((PF & 1) != 0) store_x(tile);
+    else stage_shuffled<C, PX>(sX, Aprev, oy - 1, ox - 1, TY + 2, SW, Hr, Wr);
+    if constexpr ((PF & 2) != 0) store_z();
+    else stage_plain<O, PZ, MASK_IN>(sZ, gA, A, oy, ox, TY, 16, Hr, Wr);
     __syncthreads();
+    if (tile + 1 < tile_end) {      // in flight while this tile computes
+      if constexpr ((PF & 1) != 0) load_x(tile + 1);
+      if constexpr ((PF & 2) != 0) load_z(tile + 1);
+    }
     if (blockIdx.y == 0)     // db: thread -> channel tid % O, pixels tid / O + k (256 / O)
       for (int p = threadIdx.x / O; p < TY * 16; p += 256 / O) dbs += sZ[p * PZ + threadIdx.x % O];
 #pragma unroll 2
@@ -1229,12 +1305,12 @@ cudaError_t launch_conv(const float* in, const float* act, const float* wpk, con
   return cudaGetLastError();
 }
 
-template <int C, int O, int TY, int MB, int WM, bool MASK_IN>
+template <int C, int O, int TY, int MB, int WM, bool MASK_IN, int PF>
 cudaError_t launch_wgrad(const float* Aprev, const float* gA, const float* A, float* dW, float* db, int Hr, int Wr,
                          int sms, cudaStream_t s) {
   constexpr int PX = C == 8 ? 8 : C + 8, PZ = O + 8, MTOT = (9 * C + 15) / 16;
   const size_t smem = ((size_t)(TY + 2) * 18 * PX + (size_t)TY * 16 * PZ) * sizeof(float);
-  auto k = wgrad_kernel<C, O, TY, MB, WM, MASK_IN>;
+  auto k = wgrad_kernel<C, O, TY, MB, WM, MASK_IN, PF>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   const int tiles_x = (Wr + 15) / 16, tiles = tiles_x * ((Hr + TY - 1) / TY);
@@ -1397,16 +1473,16 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   // blocks 4..1: the input-gradient chain on s (each launch writes the next block's masked output
   // gradient); each weight gradient on a side stream once its output gradient exists
   ok(link(E, s, sd[1]));
-  ok(launch_wgrad<8, 16, 16, 5, 4, true>(A[3], gA[4], A[4], gp + w_off(4), gp + b_off(4), ph << 4, pw << 4, sms, sd[1]));
+  ok(launch_wgrad<8, 16, 16, 5, 4, true, 3>(A[3], gA[4], A[4], gp + w_off(4), gp + b_off(4), ph << 4, pw << 4, sms, sd[1]));
   ok(launch_conv<16, 8, 16, 8, true, true, true>(gA[4], A[4], wd[4], nullptr, A[3], gA[3], ph << 4, pw << 4, s));
   ok(link(E, s, sd[2]));
-  ok(launch_wgrad<16, 32, 16, 9, 4, false>(A[2], gA[3], nullptr, gp + w_off(3), gp + b_off(3), ph << 3, pw << 3, sms, sd[2]));
+  ok(launch_wgrad<16, 32, 16, 9, 4, false, 1>(A[2], gA[3], nullptr, gp + w_off(3), gp + b_off(3), ph << 3, pw << 3, sms, sd[2]));
   ok(launch_conv<32, 16, 16, 8, true, false, true>(gA[3], nullptr, wd[3], nullptr, A[2], gA[2], ph << 3, pw << 3, s));
   ok(link(E, s, sd[3]));
-  ok(launch_wgrad<32, 64, 8, 9, 4, false>(A[1], gA[2], nullptr, gp + w_off(2), gp + b_off(2), ph << 2, pw << 2, sms, sd[3]));
+  ok(launch_wgrad<32, 64, 8, 9, 4, false, 0>(A[1], gA[2], nullptr, gp + w_off(2), gp + b_off(2), ph << 2, pw << 2, sms, sd[3]));
   ok(launch_conv<64, 32, 8, 8, true, false, true>(gA[2], nullptr, wd[2], nullptr, A[1], gA[1], ph << 2, pw << 2, s));
   ok(link(E, s, sd[2]));
-  ok(launch_wgrad<64, 128, 4, 6, 2, false>(A[0], gA[1], nullptr, gp + w_off(1), gp + b_off(1), ph << 1, pw << 1, sms, sd[2]));
+  ok(launch_wgrad<64, 128, 4, 6, 2, false, 0>(A[0], gA[1], nullptr, gp + w_off(1), gp + b_off(1), ph << 1, pw << 1, sms, sd[2]));
   ok(launch_conv<128, 64, 4, 4, true, false, false>(gA[1], nullptr, wd[1], nullptr, nullptr, gA[0], ph << 1, pw << 1, s));
   // conv0's adjoint: the input gradient on s, the weight and embedding gradients on a side stream;
   // then the block-mean term of dL/dI_r
