@@ -8,8 +8,11 @@
 // dL/dS times dS/dmx, dS/dexx, dS/dexy at every pixel (the window is symmetric, so correlation
 // with it is its own adjoint).  Two kernels: moments -> (a, b, c) maps + partial sums, then the
 // transposed convolution of the maps.  32x32 output tiles, halo 5, separable passes in shared
-// memory, each thread sliding an 11-tap window along 8 outputs so every staged value is read
-// once per pass.
+// memory.  Each thread slides the 11-tap window along a run of outputs so that every staged value
+// is read once per pass, on packed FP32 instructions: the horizontal pass runs two rows at once
+// (the tile is staged as interleaved row pairs, so each packed operand is one load and the weight
+// a duplicated constant); the vertical pass, one column a lane, updates pairs of consecutive
+// outputs with shifted weight pairs.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -20,16 +23,36 @@
 namespace vg {
 namespace {
 
-constexpr int LT = 32, HALO = 5, LTH = LT + 2 * HALO;
+constexpr int LT = 32, HALO = 5, LTH = LT + 2 * HALO;   // output tile, window half-width, staged tile
 constexpr int kLossThreads = 128;
-constexpr int G = 8;                 // consecutive outputs per thread in each separable pass
-constexpr int SPX = LTH + 1;         // odd row pitches: lanes on different rows hit different banks
-constexpr int SPH = LT + 1;
-constexpr int kStage = (LTH * LTH + kLossThreads - 1) / kLossThreads;   // staged values per thread
+constexpr int NRP = LTH / 2;          // staged row pairs
+constexpr int QP = 52;                // pitch of a staged row pair, in remapped columns (see qcol)
+// Pitch of the gradient pass's staged row pairs.  Bank-conflict free like QP, and it brings the
+// kernel's shared memory to 46.4 KB, so that at most 4 blocks are resident on an SM: with 5 the
+// pass measured 62 us instead of 50 us at 1080p (shared-memory pipe contention).
+constexpr int QPB = 60;
+constexpr int GH = 8;                 // horizontal pass: outputs per thread along a row, two rows at once
+constexpr int NH = NRP * (LT / GH);   // horizontal items (row pair, group of GH columns)
+constexpr int GV = 8;                 // vertical pass: outputs per thread down a column
+static_assert(LT * (LT / GV) == kLossThreads, "one vertical item per thread");
+static_assert(NH <= kLossThreads && 3 * LTH <= kLossThreads, "one horizontal item, one staged column per thread");
 
+// Window weights as packed FP32 operands: w[k] = (w_k, w_k) for two lines at one output each,
+// ws[k] = (w_k, w_{k-1}) (zero outside 0..10) for two consecutive outputs of one line.
 struct Win {
-  float w[11];
+  float2 w[11];
+  float2 ws[12];
 };
+
+// Staged column q sits at q + q / 8.  Horizontal items run with the column group fastest across
+// the lanes, so the eight lanes of one 16-byte (or 8-byte) shared-load phase then fall on
+// distinct bank groups.
+__device__ __forceinline__ int qcol(int q) { return q + (q >> 3); }
+
+// The horizontal pass output hs[r][c] (LT floats a row) keeps column pair c / 2 at
+// (c / 2) ^ ((r / 2) & 3): a row read by the vertical pass is still one 128-byte line (a
+// permutation of it), and the horizontal pass's scalar stores spread over 16 banks.
+__device__ __forceinline__ int hs_at(int r, int c) { return r * LT + 2 * ((c >> 1) ^ ((r >> 1) & 3)) + (c & 1); }
 
 // Block sum: FP32 inside each warp (FP64 is slow on this part), FP64 across the warps.
 __device__ __forceinline__ double block_sum(float v, double* sm) {
@@ -44,117 +67,165 @@ __device__ __forceinline__ double block_sum(float v, double* sm) {
   return t;
 }
 
-// One separable 11-tap pass over G consecutive outputs: out[f][j] = sum_k w[k] in[f](j + k), the
-// G + 10 inputs read once each (sliding window in registers), taps accumulated in increasing k.
-// Outputs are updated in pairs with packed FP32 FMAs (two independent round-to-nearest FMAs an
-// instruction); a tap outside one output's window enters with weight 0, which leaves that sum
-// unchanged, so the result equals the scalar form bit for bit.
-template <int F, typename Load>
-__device__ __forceinline__ void window_pass(const Win& win, Load load, float (&out)[F][G]) {
-  static_assert(G % 2 == 0, "outputs are updated in pairs");
-  float2 acc[F][G / 2];
+// One separable 11-tap pass over G consecutive outputs, two independent lines at once (the two
+// lanes of a packed FP32 pair): out[f][j] = sum_k w[k] in[f](j + k).  load(i, v) gives input
+// position i of every quantity as a pair; it is read once and enters every output whose window
+// holds it.  Each output accumulates its taps in increasing k from zero with round-to-nearest
+// FMAs, exactly as the scalar definition does.
+template <int F, int G, typename Load>
+__device__ __forceinline__ void window_pairs(const Win& win, Load load, float2 (&acc)[F][G]) {
 #pragma unroll
   for (int f = 0; f < F; ++f)
 #pragma unroll
-    for (int jp = 0; jp < G / 2; ++jp) acc[f][jp] = make_float2(0.f, 0.f);
+    for (int j = 0; j < G; ++j) acc[f][j] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int i = 0; i < G + 10; ++i) {
+    float2 v[F];
+    load(i, v);
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      const int k = i - j;
+      if (k >= 0 && k <= 10) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) acc[f][j] = __ffma2_rn(win.w[k], v[f], acc[f][j]);
+      }
+    }
+  }
+}
+
+// One vertical pass over GV consecutive outputs of one line: out[f][j] = sum_k w[k] in[f](j + k),
+// outputs taken in pairs (2 jp, 2 jp + 1) on packed FP32 FMAs with the shifted weight pairs ws; a
+// tap outside one output's window enters with weight 0, which leaves that sum unchanged, so every
+// output accumulates exactly the scalar definition's FMAs in the same order.
+template <int F, typename Load>
+__device__ __forceinline__ void window_column(const Win& win, Load load, float (&out)[F][GV]) {
+  static_assert(GV % 2 == 0, "outputs are updated in pairs");
+  float2 acc[F][GV / 2];
+#pragma unroll
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int jp = 0; jp < GV / 2; ++jp) acc[f][jp] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < GV + 10; ++i) {
     float v[F];
     load(i, v);
 #pragma unroll
-    for (int jp = 0; jp < G / 2; ++jp) {
-      const int k0 = i - 2 * jp, k1 = k0 - 1;       // taps of outputs 2 jp and 2 jp + 1
+    for (int jp = 0; jp < GV / 2; ++jp) {
+      const int k0 = i - 2 * jp;      // tap of output 2 jp (output 2 jp + 1 takes k0 - 1)
       if (k0 >= 0 && k0 <= 11) {
-        const float2 w2 = make_float2(k0 <= 10 ? win.w[k0] : 0.f, k1 >= 0 ? win.w[k1] : 0.f);
 #pragma unroll
-        for (int f = 0; f < F; ++f) acc[f][jp] = __ffma2_rn(w2, make_float2(v[f], v[f]), acc[f][jp]);
+        for (int f = 0; f < F; ++f) acc[f][jp] = __ffma2_rn(win.ws[k0], make_float2(v[f], v[f]), acc[f][jp]);
       }
     }
   }
 #pragma unroll
   for (int f = 0; f < F; ++f)
 #pragma unroll
-    for (int jp = 0; jp < G / 2; ++jp) {
+    for (int jp = 0; jp < GV / 2; ++jp) {
       out[f][2 * jp] = acc[f][jp].x;
       out[f][2 * jp + 1] = acc[f][jp].y;
     }
 }
 
-// Moments of a 32x32 output tile: x, y staged with a 5-pixel zero-padded halo; the horizontal
-// pass (42 rows x 4 groups of 8 columns) and the vertical pass (32 columns x 4 groups of 8 rows)
-// each slide an 11-tap window along G outputs per thread.
+// Staging of F planes' (LTH x LTH) tile with a HALO-pixel zero-padded border, as row pairs:
+// thread t < 3 LTH takes staged column t % LTH of row pairs t / LTH + 3k; all its loads are issued
+// before the first store.  put(p, q, v) stores rows 2p, 2p + 1 of every plane at column q (v[f]
+// holds plane f's pair).
+template <int F, typename Put>
+__device__ __forceinline__ void stage_pairs(const float* const (&plane)[F], int W, int H, int ox, int oy, Put put) {
+  if (threadIdx.x >= 3 * LTH) return;
+  const int q = threadIdx.x % LTH, p0 = threadIdx.x / LTH;
+  const int gx = ox - HALO + q;
+  const bool colin = gx >= 0 && gx < W;
+  float2 v[F][NRP / 3];
+#pragma unroll
+  for (int k = 0; k < NRP / 3; ++k) {
+    const int gy = oy - HALO + 2 * (p0 + 3 * k);
+    const bool in0 = colin && gy >= 0 && gy < H, in1 = colin && gy + 1 >= 0 && gy + 1 < H;
+    const long long o = (long long)gy * W + gx;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      v[f][k].x = in0 ? __ldg(plane[f] + o) : 0.f;
+      v[f][k].y = in1 ? __ldg(plane[f] + o + W) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NRP / 3; ++k) {
+    float2 pr[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) pr[f] = v[f][k];
+    put(p0 + 3 * k, qcol(q), pr);
+  }
+}
+
+// Moments of a 32x32 output tile: x, y staged with a 5-pixel zero-padded halo as row pairs.  The
+// horizontal pass (21 row pairs x 4 groups of 8 columns) slides the window along a row for two
+// rows at once; the vertical pass (32 columns x 4 groups of 8 rows) slides it down a column.
 __global__ void __launch_bounds__(kLossThreads) ssim_forward_kernel(const float* __restrict__ x,
                                                                     const float* __restrict__ y, int W, int H,
                                                                     Win win, float dLdS, float* __restrict__ maps,
                                                                     double* __restrict__ partials) {
-  __shared__ float sx[LTH][SPX], sy[LTH][SPX];
-  __shared__ float hs[5][LTH][SPH];
+  __shared__ __align__(16) float4 s4[NRP][QP];   // (x row 2p, x row 2p + 1, y row 2p, y row 2p + 1)
+  __shared__ __align__(16) float hs[5][LTH * LT];
   __shared__ double red[kLossThreads / 32];
   const int c = blockIdx.z;
   const int ox = blockIdx.x * LT, oy = blockIdx.y * LT;
   const size_t plane = (size_t)W * H;
-  const float* X = x + c * plane;
-  const float* Y = y + c * plane;
-  // staging: all copies in flight at once (asynchronous, zero-filled outside the image)
-#pragma unroll
-  for (int k = 0; k < kStage; ++k) {
-    const int i = threadIdx.x + k * kLossThreads;
-    if (i < LTH * LTH) {
-      const int r = i / LTH, q = i % LTH;
-      const int gy = oy - HALO + r, gx = ox - HALO + q;
-      const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-      const size_t off = in ? (size_t)gy * W + gx : 0;
-      cp_async4_zfill(&sx[r][q], X + off, in);
-      cp_async4_zfill(&sy[r][q], Y + off, in);
-    }
+  {
+    const float* const src[2] = {x + c * plane, y + c * plane};
+    stage_pairs<2>(src, W, H, ox, oy, [&](int p, int q, const float2 (&v)[2]) {
+      s4[p][q] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    });
   }
-  cp_async_commit();
-  cp_async_wait<0>();
   __syncthreads();
-  for (int t = threadIdx.x; t < (LT / G) * LTH; t += kLossThreads) {
-    const int g = t / LTH, r = t % LTH;
-    float a[5][G];
-    window_pass<5>(win, [&](int i, float (&v)[5]) {
-      const float vx = sx[r][g * G + i], vy = sy[r][g * G + i];
-      v[0] = vx; v[1] = vy; v[2] = vx * vx; v[3] = vy * vy; v[4] = vx * vy;
+  if (threadIdx.x < NH) {
+    const int p = threadIdx.x >> 2, g = threadIdx.x & 3;
+    float2 a[5][GH];
+    window_pairs<5, GH>(win, [&](int i, float2 (&v)[5]) {
+      const float4 s = s4[p][qcol(GH * g + i)];
+      const float2 xv = make_float2(s.x, s.y), yv = make_float2(s.z, s.w);
+      v[0] = xv; v[1] = yv; v[2] = __fmul2_rn(xv, xv); v[3] = __fmul2_rn(yv, yv); v[4] = __fmul2_rn(xv, yv);
     }, a);
 #pragma unroll
     for (int f = 0; f < 5; ++f)
 #pragma unroll
-      for (int j = 0; j < G; ++j) hs[f][r][g * G + j] = a[f][j];
+      for (int j = 0; j < GH; ++j) {
+        hs[f][hs_at(2 * p, GH * g + j)] = a[f][j].x;
+        hs[f][hs_at(2 * p + 1, GH * g + j)] = a[f][j].y;
+      }
   }
   __syncthreads();
+  const int q = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * GV;   // column q, output rows r0 .. r0 + 7
+  float m[5][GV];
+  window_column<5>(win, [&](int i, float (&v)[5]) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) v[f] = hs[f][hs_at(r0 + i, q)];
+  }, m);
   const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
   float ssum = 0.f, l1sum = 0.f;
-  {
-    const int q = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * G;
-    float m[5][G];
-    window_pass<5>(win, [&](int i, float (&v)[5]) {
+  const float* sf = reinterpret_cast<const float*>(&s4[0][0]);
+  const int gx = ox + q;
 #pragma unroll
-      for (int f = 0; f < 5; ++f) v[f] = hs[f][r0 + i][q];
-    }, m);
-    const int gx = ox + q;
-#pragma unroll
-    for (int j = 0; j < G; ++j) {
-      const int gy = oy + r0 + j;
-      if (gx >= W || gy >= H) continue;
-      l1sum += fabsf(sx[HALO + r0 + j][HALO + q] - sy[HALO + r0 + j][HALO + q]);
-      const float mx = m[0][j], my = m[1][j], exx = m[2][j], eyy = m[3][j], exy = m[4][j];
-      const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-      const float N1 = 2.f * mx * my + C1, N2 = 2.f * sxy + C2;
-      const float D1 = mx * mx + my * my + C1, D2 = sxx + syy + C2;
-      const float iD1 = __frcp_rn(D1), iD2 = __frcp_rn(D2);
-      const float iD = iD1 * iD2;
-      const float S = N1 * N2 * iD;
-      const float dS_dmx = 2.f * my * (N2 - N1) * iD - 2.f * mx * S * (iD1 - iD2);
-      const float dS_dexx = -S * iD2;
-      const float dS_dexy = 2.f * N1 * iD;
-      const size_t pix = (size_t)gy * W + gx;
-      maps[(0 * 3 + c) * plane + pix] = dLdS * dS_dmx;
-      maps[(1 * 3 + c) * plane + pix] = dLdS * dS_dexx;
-      maps[(2 * 3 + c) * plane + pix] = dLdS * dS_dexy;
-      ssum += S;
-    }
+  for (int j = 0; j < GV; ++j) {
+    const int gy = oy + r0 + j, sr = r0 + j + HALO;
+    if (gx >= W || gy >= H) continue;
+    const float* cell = sf + ((sr >> 1) * QP + qcol(q + HALO)) * 4;
+    l1sum += fabsf(cell[sr & 1] - cell[2 + (sr & 1)]);
+    const float mx = m[0][j], my = m[1][j], exx = m[2][j], eyy = m[3][j], exy = m[4][j];
+    const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+    const float N1 = 2.f * mx * my + C1, N2 = 2.f * sxy + C2;
+    const float D1 = mx * mx + my * my + C1, D2 = sxx + syy + C2;
+    const float iD1 = __frcp_rn(D1), iD2 = __frcp_rn(D2);
+    const float iD = iD1 * iD2;
+    const float S = N1 * N2 * iD;
+    const float dS_dmx = 2.f * my * (N2 - N1) * iD - 2.f * mx * S * (iD1 - iD2);
+    const float dS_dexx = -S * iD2;
+    const float dS_dexy = 2.f * N1 * iD;
+    const size_t pix = (size_t)gy * W + gx;
+    maps[(0 * 3 + c) * plane + pix] = dLdS * dS_dmx;
+    maps[(1 * 3 + c) * plane + pix] = dLdS * dS_dexx;
+    maps[(2 * 3 + c) * plane + pix] = dLdS * dS_dexy;
+    ssum += S;
   }
   const double ts = block_sum(ssum, red);
   const double tl = block_sum(l1sum, red);
@@ -201,17 +272,18 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
                                                                      float* __restrict__ grad,
                                                                      const float* __restrict__ pool_grad = nullptr,
                                                                      int pw = 0, int ph = 0) {
-  __shared__ float sm[3][LTH][SPX];
-  __shared__ float hs[3][LTH][SPH];
+  __shared__ __align__(16) float2 s2[3][NRP][QPB];   // map f on rows 2p, 2p + 1
+  __shared__ __align__(16) float hs[3][LTH * LT];
   const int c = blockIdx.z;
   const int ox = blockIdx.x * LT, oy = blockIdx.y * LT;
   const size_t plane = (size_t)W * H;
-  // this thread's output pixels' x and y, loaded now so that their latency overlaps the passes
-  const int q = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * G;
+  // this thread's output pixels (column q, rows r0 .. r0 + 7): x, y (and the gradient already
+  // there) loaded now so that their latency overlaps the passes
+  const int q = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * GV;
   const int gx = ox + q;
-  float xs[G], ys[G], gs[G];
+  float xs[GV], ys[GV], gs[GV];
 #pragma unroll
-  for (int j = 0; j < G; ++j) {
+  for (int j = 0; j < GV; ++j) {
     const int gy = oy + r0 + j;
     const bool in = gx < W && gy < H;
     const size_t pix = c * plane + (in ? (size_t)gy * W + gx : 0);
@@ -219,41 +291,37 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
     ys[j] = __ldg(y + pix);
     if constexpr (kAppear) gs[j] = grad[pix];
   }
+  {
+    const float* const src[3] = {maps + (0 * 3 + c) * plane, maps + (1 * 3 + c) * plane, maps + (2 * 3 + c) * plane};
+    stage_pairs<3>(src, W, H, ox, oy, [&](int p, int q, const float2 (&v)[3]) {
 #pragma unroll
-  for (int k = 0; k < kStage; ++k) {
-    const int i = threadIdx.x + k * kLossThreads;
-    if (i < LTH * LTH) {
-      const int r = i / LTH, q = i % LTH;
-      const int gy = oy - HALO + r, gx = ox - HALO + q;
-      const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-      const size_t pix = in ? (size_t)gy * W + gx : 0;
-#pragma unroll
-      for (int f = 0; f < 3; ++f) cp_async4_zfill(&sm[f][r][q], maps + (f * 3 + c) * plane + pix, in);
-    }
+      for (int f = 0; f < 3; ++f) s2[f][p][q] = v[f];
+    });
   }
-  cp_async_commit();
-  cp_async_wait<0>();
   __syncthreads();
-  for (int t = threadIdx.x; t < (LT / G) * LTH; t += kLossThreads) {
-    const int g = t / LTH, r = t % LTH;
-    float a[3][G];
-    window_pass<3>(win, [&](int i, float (&v)[3]) {
+  if (threadIdx.x < NH) {
+    const int p = threadIdx.x >> 2, g = threadIdx.x & 3;
+    float2 a[3][GH];
+    window_pairs<3, GH>(win, [&](int i, float2 (&v)[3]) {
 #pragma unroll
-      for (int f = 0; f < 3; ++f) v[f] = sm[f][r][g * G + i];
+      for (int f = 0; f < 3; ++f) v[f] = s2[f][p][qcol(GH * g + i)];
     }, a);
 #pragma unroll
     for (int f = 0; f < 3; ++f)
 #pragma unroll
-      for (int j = 0; j < G; ++j) hs[f][r][g * G + j] = a[f][j];
+      for (int j = 0; j < GH; ++j) {
+        hs[f][hs_at(2 * p, GH * g + j)] = a[f][j].x;
+        hs[f][hs_at(2 * p + 1, GH * g + j)] = a[f][j].y;
+      }
   }
   __syncthreads();
-  float cm[3][G];
-  window_pass<3>(win, [&](int i, float (&v)[3]) {
+  float cm[3][GV];
+  window_column<3>(win, [&](int i, float (&v)[3]) {
 #pragma unroll
-    for (int f = 0; f < 3; ++f) v[f] = hs[f][r0 + i][q];
+    for (int f = 0; f < 3; ++f) v[f] = hs[f][hs_at(r0 + i, q)];
   }, cm);
 #pragma unroll
-  for (int j = 0; j < G; ++j) {
+  for (int j = 0; j < GV; ++j) {
     const int gy = oy + r0 + j;
     if (gx >= W || gy >= H) continue;
     const size_t pix = c * plane + (size_t)gy * W + gx;
@@ -275,7 +343,10 @@ Win make_window() {
   Win w;
   double v[11], s = 0;
   for (int i = 0; i < 11; ++i) { v[i] = exp(-((i - 5) * (i - 5)) / (2.0 * 1.5 * 1.5)); s += v[i]; }
-  for (int i = 0; i < 11; ++i) w.w[i] = (float)(v[i] / s);
+  float wf[11];
+  for (int i = 0; i < 11; ++i) wf[i] = (float)(v[i] / s);
+  for (int k = 0; k < 11; ++k) w.w[k] = make_float2(wf[k], wf[k]);
+  for (int k = 0; k < 12; ++k) w.ws[k] = make_float2(k <= 10 ? wf[k] : 0.f, k >= 1 ? wf[k - 1] : 0.f);
   return w;
 }
 
