@@ -204,7 +204,8 @@ cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Spl
                               uint32_t* touched, const Compact& cp, WsHeader* hdr, cudaStream_t s);
 Compact make_compact(const Layout& L, char* ws, int total_n);   // regions of the workspace
 // Adjoint of the projection for the visible Gaussians (gradients of the culled ones are left
-// to launch_zero_culled, or untouched when accumulating).
+// to launch_zero_culled, or untouched when accumulating).  Sized to leave launch_zero_culled
+// room to run beside it when not accumulating.
 cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int degree, const Splat* splats,
                                        const uint32_t* vis_ids, const WsHeader* hdr, const float* g2d,
                                        bool accumulate, cudaStream_t s);
