@@ -311,6 +311,25 @@ cudaStream_t side_stream(int k) {
   return streams[dev][k];
 }
 
+cudaStream_t side_stream_for(cudaStream_t caller) {
+  constexpr int kCallers = 32;
+  static std::mutex mu;
+  static cudaStream_t keys[64][kCallers] = {}, sides[64][kCallers] = {};
+  static int used[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < used[dev]; ++i)
+    if (keys[dev][i] == caller) return sides[dev][i];
+  if (used[dev] == kCallers) return nullptr;
+  cudaStream_t side = nullptr;
+  if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  keys[dev][used[dev]] = caller;
+  sides[dev][used[dev]] = side;
+  ++used[dev];
+  return side;
+}
+
 namespace {
 
 // Backward pass of a prepared call (the table carries dL, final T, last and the gradient outputs).

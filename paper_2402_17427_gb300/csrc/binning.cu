@@ -37,18 +37,6 @@ __device__ __forceinline__ void segment(unsigned n, unsigned& begin, unsigned& e
 
 constexpr int kLookback = 8;                                 // status rows read per look-back step
 
-// Adds the digits of `key` for passes [0, passes) to the block histograms h[pass][digit];
-// lanes with the same digit are merged first (match.any), so one shared atomic per distinct
-// digit.  All 32 lanes must call it; `valid` false contributes nothing.
-__device__ __forceinline__ void histogram_add(unsigned (*h)[kRadix], uint32_t key, bool valid, int passes) {
-  const uint32_t lt = lanemask_lt();
-  for (int p = 0; p < passes; ++p) {
-    const uint32_t d = valid ? (key >> (p * kRadixBits)) & (kRadix - 1) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (valid && (peers & lt) == 0) atomicAdd(&h[p][d], (unsigned)__popc(peers));
-  }
-}
-
 // Zeroes rows [0, nparts) of a look-back status array (grid-stride over the calling grid).
 __device__ __forceinline__ void zero_status(unsigned long long* status, unsigned nparts) {
   const size_t total = (size_t)nparts * kRadix;
@@ -257,8 +245,11 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
                                                   const unsigned long long* __restrict__ blocksums,
                                                   unsigned long long cap, uint32_t* __restrict__ pkeys,
                                                   uint32_t* __restrict__ pvals, Splat* __restrict__ splats,
-                                                  Splat* __restrict__ vsplats) {
+                                                  Splat* __restrict__ vsplats, unsigned long long* __restrict__ status0) {
   if (hdr->pair_n == 0) return;   // no pairs, or more than the capacity (nothing is sorted)
+  // with the tile counts known in advance (tile_prep), this kernel clears the first tile-sort
+  // pass's look-back rows
+  if (status0) zero_status(status0, (hdr->pair_n + kTileTile - 1) / kTileTile);
   const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
   __shared__ unsigned long long sm[8];
   __shared__ unsigned s_off[257];
@@ -414,28 +405,175 @@ __global__ void __launch_bounds__(256) order_scatter(const DevTables* __restrict
   }
 }
 
-// The same order built by one block in shared memory (for up to kOrderSmallTiles tiles): one
-// launch instead of count + scan + scatter and a memset.
-constexpr int kOrderSmallTiles = 1 << 16;
+// Per-tile pair counts as differences along each tile row: a Gaussian's pairs are the tiles of
+// its rectangle, so it adds 1 at the rectangle's first column and subtracts 1 after its last, in
+// every row it spans.  The visible Gaussians are taken in index order (neighbouring ids tend to be
+// neighbours in space), the lanes of a warp adding to the same word are merged first, and block b
+// adds into replica b % kCountCopies of the array (tdiff[kCountCopies][tiles]), which spreads the
+// atomics on the words many rectangles share.
+constexpr int kCountCopies = 8;
+__global__ void __launch_bounds__(256) tile_count(const DevTables* __restrict__ tab, const uint32_t* __restrict__ vis_ids,
+                                                  const uint32_t* __restrict__ touched, const uint2* __restrict__ rects,
+                                                  const WsHeader* __restrict__ hdr, unsigned* __restrict__ tdiff,
+                                                  int tiles) {
+  const unsigned nv = hdr->visible;
+  tdiff += (size_t)(blockIdx.x % kCountCopies) * tiles;
+  const uint32_t lt = lanemask_lt();
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned t0 = blockIdx.x * blockDim.x; t0 < nv; t0 += stride) {   // whole warps iterate together
+    const unsigned t = t0 + threadIdx.x;
+    int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1, base = 0, txn = 0;
+    if (t < nv) {
+      const uint32_t id = vis_ids[t];
+      if (touched[id]) {
+        const KView& vw = tview(tab, tseg(tab, find_seg(tab, (int)id)).view);
+        const uint2 rc = rects[id];
+        tx0 = (int)(rc.x & 0xFFFF); tx1 = (int)(rc.x >> 16);
+        ty0 = (int)(rc.y & 0xFFFF); ty1 = (int)(rc.y >> 16);
+        base = vw.tile_base; txn = vw.tiles_x;
+      }
+    }
+    for (int r = 0;; ++r) {
+      const bool act = ty0 + r <= ty1;
+      if (!__any_sync(0xffffffffu, act)) break;
+      const unsigned row = (unsigned)(base + (ty0 + r) * txn);
+      const unsigned a0 = act ? row + (unsigned)tx0 : 0xFFFFFFFFu;
+      const unsigned p0 = __match_any_sync(0xffffffffu, a0);
+      if (act && (p0 & lt) == 0) atomicAdd(tdiff + a0, (unsigned)__popc(p0));
+      const unsigned a1 = act && tx1 + 1 < txn ? row + (unsigned)(tx1 + 1) : 0xFFFFFFFFu;
+      const unsigned p1 = __match_any_sync(0xffffffffu, a1);
+      if (a1 != 0xFFFFFFFFu && (p1 & lt) == 0) atomicAdd(tdiff + a1, 0u - (unsigned)__popc(p1));   // -n, modulo 2^32
+    }
+  }
+}
 
-__global__ void __launch_bounds__(1024) order_small(const DevTables* __restrict__ tab,
-                                                    const uint2* __restrict__ ranges, int tiles,
-                                                    uint32_t* __restrict__ order) {
-  __shared__ unsigned cnt[kBuckets];
-  for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) cnt[k] = 0;
+// Tile ranges, the digit histograms of the tile-sort passes and the largest-first tile order,
+// all from the per-tile pair counts, which are known before the pairs are emitted.  One block,
+// with the counts in shared memory: a scan along every tile row turns tile_count's differences
+// into counts; an exclusive scan over the tile ids (the order the tile sort leaves the pairs in)
+// gives the ranges, [first, last + 1) for a tile with pairs and (0, 0) for one without; the
+// histograms and the order buckets (tile class, then list length as in tile_bucket) follow.
+// With nothing to sort (no pairs, or more than cap) every range is empty, as the sort leaves it.
+constexpr int kPrepThreads = 256;
+constexpr int kPrepTiles = 16384;        // tiles of a render that takes this path (two words each)
+
+__global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __restrict__ tab, int tiles, unsigned cap,
+                                                          int tpasses, const unsigned* __restrict__ tdiff,
+                                                          uint2* __restrict__ ranges, unsigned* __restrict__ hist,
+                                                          uint32_t* __restrict__ order) {
+  extern __shared__ unsigned s_c[];      // [tiles] counts, then [tiles] exclusive offsets
+  unsigned* s_x = s_c + tiles;
+  __shared__ unsigned s_h[kMaxPasses][kRadix];
+  __shared__ unsigned s_cnt[kBuckets];
+  __shared__ unsigned long long sm[8];
+  // the replicas of tile_count's differences, summed; eight loads in flight per thread
+  for (int t0 = 0; t0 < tiles; t0 += 8 * kPrepThreads) {
+    unsigned v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = 0u;
+#pragma unroll
+    for (int r = 0; r < kCountCopies; ++r)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * kPrepThreads + (int)threadIdx.x;
+        if (t < tiles) v[u] += tdiff[(size_t)r * tiles + t];
+      }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * kPrepThreads + (int)threadIdx.x;
+      if (t < tiles) s_c[t] = v[u];
+    }
+  }
+  for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) s_h[k / kRadix][k % kRadix] = 0;
+  for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) s_cnt[k] = 0;
   __syncthreads();
-  for (int t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&cnt[tile_bucket(tab, ranges, t)], 1u);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned run = 0;
-    for (int k = 0; k < kBuckets; ++k) {
-      const unsigned c = cnt[k];
-      cnt[k] = run;
-      run += c;
+  // 1. counts: an inclusive scan along every tile row of every view, a warp per row
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int v = 0; v < tab->h.n_views; ++v) {
+    const KView& vw = tview(tab, v);
+    const int txn = vw.tiles_x;
+    for (int ty = warp; ty < vw.tiles_y; ty += nwarps) {
+      unsigned* row = s_c + vw.tile_base + ty * txn;
+      unsigned carry = 0;
+      for (int x0 = 0; x0 < txn; x0 += 32) {
+        const int x = x0 + lane;
+        unsigned c = x < txn ? row[x] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, c, o);
+          if (lane >= o) c += y;
+        }
+        c += carry;
+        carry = __shfl_sync(0xffffffffu, c, 31);
+        if (x < txn) row[x] = c;
+      }
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < tiles; t += blockDim.x) order[atomicAdd(&cnt[tile_bucket(tab, ranges, t)], 1u)] = (uint32_t)t;
+  // 2. exclusive offsets over the tile ids, a block-wide scan per 256 tiles
+  unsigned long long run = 0;
+  for (int t0 = 0; t0 < tiles; t0 += kPrepThreads) {
+    const int t = t0 + threadIdx.x;
+    const unsigned c = t < tiles ? s_c[t] : 0u;
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan((unsigned long long)c, &tot, sm);
+    if (t < tiles) s_x[t] = (unsigned)(run + ex);
+    run += tot;
+  }
+  const bool any = run > 0 && run <= cap;
+  const uint32_t lt = lanemask_lt();
+  // 3. ranges, digit histograms, order buckets (view by view: the bucket needs the tile class);
+  //    lanes adding to the same shared counter are merged first
+  for (int v = 0; v < tab->h.n_views; ++v) {
+    const KView& vw = tview(tab, v);
+    const int cls = vw.tile_class, t_end = vw.tile_base + vw.tiles_x * vw.tiles_y;
+    for (int t0 = vw.tile_base; t0 < t_end; t0 += kPrepThreads) {   // whole warps iterate together
+      const int t = t0 + (int)threadIdx.x;
+      const bool in = t < t_end;
+      const unsigned c = in && any ? s_c[t] : 0u;
+      if (in) ranges[t] = c ? make_uint2(s_x[t], s_x[t] + c) : make_uint2(0u, 0u);
+      for (int p = 0; p < tpasses; ++p) {
+        // consecutive lanes hold consecutive tiles, so equal digits sit in runs of lanes: a
+        // segmented scan leaves each run's sum in its last lane, which adds it
+        const unsigned d = in ? ((unsigned)t >> (p * kRadixBits)) & (kRadix - 1) : 0xFFFFFFFFu;   // nondecreasing
+        unsigned sum = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, sum, o);
+          const unsigned dy = __shfl_up_sync(0xffffffffu, d, o);
+          if (lane >= o && dy == d) sum += y;
+        }
+        const unsigned dn = __shfl_down_sync(0xffffffffu, d, 1);
+        if (in && sum && (lane == 31 || dn != d)) atomicAdd(&s_h[p][d], sum);
+      }
+      const int bits = c == 0 ? 0 : 32 - __clz(c);
+      const unsigned bk = in ? (unsigned)(cls * 33 + (32 - bits)) : 0xFFFFFFFFu;
+      if (in) s_x[t] = bk;
+      const unsigned peers = __match_any_sync(0xffffffffu, bk);
+      if (in && (peers & lt) == 0) atomicAdd(&s_cnt[bk], (unsigned)__popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < tpasses * kRadix; k += blockDim.x) hist[k] = s_h[k / kRadix][k % kRadix];
+  if (threadIdx.x == 0) {
+    unsigned acc = 0;
+    for (int k = 0; k < kBuckets; ++k) {
+      const unsigned c = s_cnt[k];
+      s_cnt[k] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  for (int t0 = 0; t0 < tiles; t0 += kPrepThreads) {          // whole warps iterate together
+    const int t = t0 + (int)threadIdx.x;
+    const unsigned bk = t < tiles ? s_x[t] : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, bk);
+    const int leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if (bk != 0xFFFFFFFFu && (peers & lt) == 0) base = atomicAdd(&s_cnt[bk], (unsigned)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (bk != 0xFFFFFFFFu) order[base + __popc(peers & lt)] = (uint32_t)t;
+  }
 }
 
 int ceil_log2(unsigned x) {
@@ -479,6 +617,7 @@ Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
   L.ranges = take(tiles * 8);
   L.order = take(tiles * 4);
   L.buckets = take(2 * kBuckets * 4);
+  L.tcount = take(std::min<size_t>(tiles, kPrepTiles) * kCountCopies * 4);   // tile_count's replicas
   L.blocksums = take((size_t)kMaxSortBlocks * 8);
   // look-back rows of either sort
   const size_t parts = std::max((N + kDepthTile - 1) / kDepthTile, (P + kTileTile - 1) / kTileTile);
@@ -533,6 +672,39 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   const int OBD = std::max(1, std::min(onesweep_blocks<kDepthItems>(), (n + kDepthTile - 1) / kDepthTile));
   const int OBT = (int)std::max<int64_t>(1, std::min<int64_t>(onesweep_blocks<kTileItems>(), ((int64_t)cap + kTileTile - 1) / kTileTile));
 
+  const int tpasses = std::max(1, ((int)tile_bits + kRadixBits - 1) / kRadixBits);
+  // Renders with up to kPrepTiles tiles take their tile counts from the rectangles (tile_count)
+  // and their ranges, tile-digit histograms and tile order from one block (tile_prep), on a side
+  // stream beside the depth sort and the pair emission; larger ones take them from the sorted
+  // keys (tile_histogram, tile_ranges, order_*).
+  const bool prep = tiles <= kPrepTiles;
+  const uint2* rects = reinterpret_cast<const uint2*>(ws + L.rects);
+  uint2* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (prep) {
+    cudaStream_t side = side_stream_for(s);
+    if (side && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(fork, s);
+      cudaStreamWaitEvent(side, fork, 0);
+    } else {
+      side = s;
+    }
+    unsigned* tdiff = U(L.tcount);
+    const size_t smem = (size_t)2 * tiles * sizeof(unsigned);
+    static bool opted[64] = {};      // the shared-memory opt-in, once per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !opted[dev]) {
+      cudaFuncSetAttribute(tile_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * kPrepTiles * sizeof(unsigned)));
+      if (dev >= 0 && dev < 64) opted[dev] = true;
+    }
+    cudaMemsetAsync(tdiff, 0, (size_t)kCountCopies * tiles * sizeof(unsigned), side);
+    tile_count<<<2 * std::max(1, sort_blocks()), 256, 0, side>>>(tab, U(L.vis_ids), U(L.touched), rects, hdr, tdiff,
+                                                                tiles);
+    tile_prep<<<1, kPrepThreads, smem, side>>>(tab, tiles, cap, tpasses, tdiff, ranges, ctl->hist[1][0], U(L.order));
+    if (join) cudaEventRecord(join, side);
+  }
   // 1. depth sort of the visible Gaussians (compacted by the projection kernel); passes beyond
   //    the bits the keys differ in return at once, and the result sits in the buffer
   //    depth_order() names
@@ -542,15 +714,18 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
                                               &hdr->visible, 0xFFFFFFFFu, true, pass * kRadixBits,
                                               ctl->hist[0][pass], &ctl->next_part[0][pass], S64(src), S64(dst), hdr);
   }
-  const int tpasses = std::max(1, ((int)tile_bits + kRadixBits - 1) / kRadixBits);
   // 2. pairs in depth order, written where the tile sort's passes leave the result in buffer 0
   const int p0 = tpasses & 1;
   const int BP = kMaxSortBlocks < 6 * B / 2 ? kMaxSortBlocks : 6 * B / 2;   // 6 blocks per SM
   pairs_count<<<BP, 256, 0, s>>>(U(L.vvals[0]), U(L.vvals[1]), U(L.touched), hdr, bsum64);
   pairs_scan<<<1, 256, 0, s>>>(bsum64, BP, hdr, (unsigned long long)cap);
-  pairs_emit<<<BP, 256, 0, s>>>(tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), reinterpret_cast<const uint2*>(ws + L.rects),
-                               hdr, bsum64, (unsigned long long)cap, U(L.pkeys[p0]), U(L.pvals[p0]), splats, vsplats);
-  tile_histogram<<<B * 2, 256, 0, s>>>(U(L.pkeys[p0]), hdr, tpasses, ctl->hist[1][0], S64(0));
+  pairs_emit<<<BP, 256, 0, s>>>(tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), rects, hdr, bsum64,
+                               (unsigned long long)cap, U(L.pkeys[p0]), U(L.pvals[p0]), splats, vsplats,
+                               prep ? S64(0) : nullptr);
+  if (!prep) tile_histogram<<<B * 2, 256, 0, s>>>(U(L.pkeys[p0]), hdr, tpasses, ctl->hist[1][0], S64(0));
+  if (join) cudaStreamWaitEvent(s, join, 0);   // ranges, histograms and order ready
+  if (fork) cudaEventDestroy(fork);            // released once the recorded work completes
+  if (join) cudaEventDestroy(join);
   // 3. stable sort of the pairs by tile id
   for (int pass = 0; pass < tpasses; ++pass) {
     const int src = (p0 + pass) & 1, dst = src ^ 1;
@@ -559,15 +734,15 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
                                               &ctl->next_part[1][pass], S64(pass & 1),
                                               pass + 1 < tpasses ? S64((pass + 1) & 1) : nullptr, hdr);
   }
+  if (prep) {
+    note_launches(kMaxPasses + 3 + tpasses + 2);
+    return cudaGetLastError();
+  }
   note_launches(kMaxPasses + 4 + tpasses + 1);
-  uint2* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
   cudaMemsetAsync(ranges, 0, (size_t)tiles * sizeof(uint2), s);
   tile_ranges<<<B * 4, 256, 0, s>>>(U(L.pkeys[0]), hdr, (unsigned)tiles, ranges);
   // 4. largest-first tile order
-  if (tiles <= kOrderSmallTiles) {
-    order_small<<<1, 1024, 0, s>>>(tab, ranges, tiles, U(L.order));
-    note_launches(1);
-  } else {
+  {
     unsigned* buckets = U(L.buckets);
     cudaMemsetAsync(buckets, 0, kBuckets * sizeof(unsigned), s);
     const int tgrid = (tiles + 255) / 256;

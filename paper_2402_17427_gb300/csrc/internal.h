@@ -166,7 +166,7 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 // Offsets (bytes) of the regions of one render workspace (any number of views / segments).
 struct Layout {
   size_t header, sortctl, tables, splats, rects, touched, vis_ids, vkeys[2], vvals[2], pkeys[2], pvals[2],
-      vsplats, ranges, order, buckets, blocksums, status[2], g2d, total;
+      vsplats, ranges, order, buckets, tcount, blocksums, status[2], g2d, total;
 };
 Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t pair_capacity);
 
@@ -227,6 +227,10 @@ cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, co
 // stream; callers fork to them and join back with events within the same call.
 constexpr int kSideStreams = 4;
 cudaStream_t side_stream(int k = 0);
+// A side stream of the current device dedicated to work forked from `caller`, so that forks from
+// calls running concurrently on different streams do not queue behind one another (created on
+// first use; nullptr once 32 callers of this device have one, or if creation fails).
+cudaStream_t side_stream_for(cudaStream_t caller);
 
 // SSIM half of the loss (loss.cu), for the appearance loss of Eq. 3: the moment pass (maps
 // [9][H][W], partials [ssim_partials][2] = (sum S, sum |x - y|) per block) and the gradient pass
