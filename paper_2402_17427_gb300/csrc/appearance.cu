@@ -78,7 +78,6 @@ __device__ __forceinline__ void mma8(float (&d)[4], const float (&a)[4], float b
 }
 __device__ __forceinline__ void mma8(float (&d)[4], const float (&a)[4], float2 b) { mma8(d, a, b.x, b.y); }
 
-__device__ __forceinline__ float2 ldg2(const float* p, int i) { return __ldg(reinterpret_cast<const float2*>(p) + i); }
 
 // ---------------------------------------------------------------- weight packing
 //

@@ -265,23 +265,20 @@ __global__ void __launch_bounds__(1024) loss_finalize(const double* __restrict__
 // the gradient of the 32 x 32 block mean the pixel belongs to (pool_grad [ph][pw][3], divided by
 // 1024) are added.
 template <bool kAppear>
-__global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float* __restrict__ x,
-                                                                     const float* __restrict__ y,
-                                                                     const float* __restrict__ maps, int W, int H,
-                                                                     Win win, float l1_scale,
-                                                                     float* __restrict__ grad,
-                                                                     const float* __restrict__ pool_grad = nullptr,
-                                                                     int pw = 0, int ph = 0) {
+__device__ __forceinline__ void ssim_backward_body(const float* __restrict__ x, const float* __restrict__ y,
+                                                   const float* __restrict__ maps, int W, int H, Win win,
+                                                   float l1_scale, float* __restrict__ grad,
+                                                   const float* __restrict__ pool_grad, int pw, int ph) {
   __shared__ __align__(16) float2 s2[3][NRP][QPB];   // map f on rows 2p, 2p + 1
   __shared__ __align__(16) float hs[3][LTH * LT];
   const int c = blockIdx.z;
   const int ox = blockIdx.x * LT, oy = blockIdx.y * LT;
   const size_t plane = (size_t)W * H;
-  // this thread's output pixels (column q, rows r0 .. r0 + 7): x, y (and the gradient already
-  // there) loaded now so that their latency overlaps the passes
+  // this thread's output pixels (column q, rows r0 .. r0 + 7): x and y loaded now so that their
+  // latency overlaps the passes
   const int q = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * GV;
   const int gx = ox + q;
-  float xs[GV], ys[GV], gs[GV];
+  float xs[GV], ys[GV];
 #pragma unroll
   for (int j = 0; j < GV; ++j) {
     const int gy = oy + r0 + j;
@@ -289,7 +286,6 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
     const size_t pix = c * plane + (in ? (size_t)gy * W + gx : 0);
     xs[j] = __ldg(x + pix);
     ys[j] = __ldg(y + pix);
-    if constexpr (kAppear) gs[j] = grad[pix];
   }
   {
     const float* const src[3] = {maps + (0 * 3 + c) * plane, maps + (1 * 3 + c) * plane, maps + (2 * 3 + c) * plane};
@@ -320,6 +316,14 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
 #pragma unroll
     for (int f = 0; f < 3; ++f) v[f] = hs[f][hs_at(r0 + i, q)];
   }, cm);
+  float gs[GV];       // kAppear: the gradient already there, read late to keep the passes' registers
+  if constexpr (kAppear) {
+#pragma unroll
+    for (int j = 0; j < GV; ++j) {
+      const int gy = oy + r0 + j;
+      gs[j] = gx < W && gy < H ? grad[c * plane + (size_t)gy * W + gx] : 0.f;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < GV; ++j) {
     const int gy = oy + r0 + j;
@@ -337,6 +341,27 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
       grad[pix] = l1g + cm[0][j] + 2.f * xv * cm[1][j] + yv * cm[2][j];
     }
   }
+}
+
+template <bool kAppear>
+__global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float* __restrict__ x,
+                                                                     const float* __restrict__ y,
+                                                                     const float* __restrict__ maps, int W, int H,
+                                                                     Win win, float l1_scale,
+                                                                     float* __restrict__ grad) {
+  ssim_backward_body<kAppear>(x, y, maps, W, H, win, l1_scale, grad, nullptr, 0, 0);
+}
+
+// The gradient pass of Eq. 3's loss.  Held to 128 registers a thread (4 blocks an SM, as the
+// shared memory allows): left free, this variant's allocation grows to about 160 and 3 blocks.
+__global__ void __launch_bounds__(kLossThreads, 4) ssim_grad_appearance_kernel(const float* __restrict__ x,
+                                                                               const float* __restrict__ y,
+                                                                               const float* __restrict__ maps, int W,
+                                                                               int H, Win win,
+                                                                               float* __restrict__ grad,
+                                                                               const float* __restrict__ pool_grad,
+                                                                               int pw, int ph) {
+  ssim_backward_body<true>(x, y, maps, W, H, win, 0.f, grad, pool_grad, pw, ph);
 }
 
 Win make_window() {
@@ -385,8 +410,7 @@ cudaError_t launch_ssim_grad_appearance(const float* x, const float* y, const fl
                                         const float* pool_grad, int pw, int ph, float* grad, cudaStream_t s) {
   const dim3 grid((W + LT - 1) / LT, (H + LT - 1) / LT, 3);
   note_launches(1);
-  ssim_backward_kernel<true><<<grid, kLossThreads, 0, s>>>(x, y, maps, W, H, make_window(), 0.f, grad, pool_grad,
-                                                           pw, ph);
+  ssim_grad_appearance_kernel<<<grid, kLossThreads, 0, s>>>(x, y, maps, W, H, make_window(), grad, pool_grad, pw, ph);
   return cudaGetLastError();
 }
 

@@ -145,9 +145,10 @@ def test_empty_and_fully_culled_inputs():
 
 def test_pair_overflow_is_reported_and_recovered():
     g, cam, _ = scenes.tiny_scene(n=200, width=48, height=40, degree=2, seed=2)
-    _, _, out = run_forward(g, cam, capacity=8, check="defer")
+    r0, _, out = run_forward(g, cam, capacity=8, check="defer")
     assert out["counters"][B.VG_CNT_STATUS] & B.VG_STATUS_PAIR_OVERFLOW
     assert out["counters"][B.VG_CNT_PAIRS] > 8
+    assert not read_state(r0, g, cam)["ranges"].any()     # nothing sorted: every tile list is empty
     r, _, out2 = run_forward(g, cam, capacity=8, check="sync")
     assert out2["counters"][B.VG_CNT_STATUS] == 0 and r.ws.capacity >= out2["counters"][B.VG_CNT_PAIRS]
     orc = oracle.render(g, cam)
