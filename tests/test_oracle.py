@@ -193,6 +193,37 @@ def test_keys_sorted_ranges_and_ties(oracle_lib):
     assert np.array_equal(np.bincount(r.vals, minlength=g.n), area)
 
 
+def _ranges_from_rectangles(r):
+    """Tile ranges rebuilt from the visible Gaussians' tile rectangles alone: +1 / -1 at the ends
+    of every rectangle row (differences along the tile rows), a prefix sum along each row for the
+    per-tile counts, an exclusive scan over the tile ids for the starts; (0, 0) for an empty tile."""
+    tx, ty = r.tiles_x, r.tiles_y
+    diff = np.zeros((ty, tx + 1), np.int64)
+    rc = r.rec["rect"][r.rec["visible"]]
+    for tx0, tx1, ty0, ty1 in rc:
+        diff[ty0:ty1 + 1, tx0] += 1
+        diff[ty0:ty1 + 1, tx1 + 1] -= 1
+    counts = np.cumsum(diff[:, :tx], axis=1).ravel()
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    out = np.stack([starts, starts + counts], 1)
+    out[counts == 0] = 0
+    return out
+
+
+@pytest.mark.parametrize("case", ["tiny", "small"])
+def test_tile_ranges_follow_from_rectangles(oracle_lib, case):
+    # a Gaussian's pairs are exactly the tiles of its rectangle, so the ranges of the tile-sorted
+    # pair list are fixed before any sort: per-tile counts from the rectangles, scanned over the
+    # tile ids in order (what the GPU builds beside its depth sort)
+    if case == "tiny":
+        g, cam, _ = scenes.tiny_scene(n=300, width=100, height=70, degree=1, seed=11)
+    else:
+        g, cam, _ = scenes.small_cell(1)
+    r = oracle_lib.render(g, cam)
+    assert np.array_equal(_ranges_from_rectangles(r), r.ranges.astype(np.int64))
+    assert r.ranges[:, 1].max() == r.num_pairs
+
+
 # ------------------------------------------------------------------ invariants
 
 def test_transmittance_monotone_and_bounded(oracle_lib):
