@@ -8,10 +8,13 @@
 //   2. pairs (tile, depth rank) are emitted in that depth order and stably radix-sorted by tile
 //      id only (ceil(log2 tiles) bits), which keeps the depth order inside every tile.
 // Both sorts are least-significant-digit radix sorts with 8-bit digits and one kernel per
-// digit pass: the digit histograms of all passes are accumulated by the kernel that produces
-// the keys, and every pass finds the output offset of each partition by a decoupled look-back
-// over the partitions before it (each partition publishes its digit counts as soon as it has
-// ranked its keys, then its inclusive prefix).
+// digit pass: the digit histograms of all passes are known before the first pass (the
+// projection kernel accumulates the depth keys'; the tile keys' follow from the per-tile pair
+// counts, which the tile rectangles fix before any pair is emitted), and every pass finds the
+// output offset of each partition by a decoupled look-back over the partitions before it (each
+// partition publishes its digit counts as soon as it has ranked its keys, then its inclusive
+// prefix).  The same counts give the tile ranges and the largest-first tile order, built on a
+// side stream while the depth sort and the pair emission run.
 // Every kernel takes its element count from device memory, so the whole forward pass is
 // enqueued without a host synchronisation; kernels with no work for this render return early.
 #include <cuda_runtime.h>
