@@ -10,7 +10,8 @@
 // Both sorts are least-significant-digit radix sorts with 8-bit digits and one kernel per
 // digit pass: the digit histograms of all passes are known before the first pass (the
 // projection kernel accumulates the depth keys'; the tile keys' follow from the per-tile pair
-// counts, which the tile rectangles fix before any pair is emitted), and every pass finds the
+// counts, which the tile rectangles fix before any pair is emitted, or, for renders of more
+// tiles than one block holds, from the emitted keys), and every pass finds the
 // output offset of each partition by a decoupled look-back over the partitions before it (each
 // partition publishes its digit counts as soon as it has ranked its keys, then its inclusive
 // prefix).  The same counts give the tile ranges and the largest-first tile order, built on a
