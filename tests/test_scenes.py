@@ -75,3 +75,36 @@ def test_request_stream_mix_rate_and_cameras():
     assert [r.rid for r in reqs] == list(range(n))
     again = scenes.request_stream(seed=11, rate_hz=200.0, duration_s=20.0)
     assert [r.arrival_s for r in again] == list(t)
+
+
+def test_aerial_cells_grid_cameras_and_scales():
+    sizes = (3000, 5000, 8000, 12000, 15000, 20000, 25000, 30000)
+    cells = scenes.aerial_cells(step=5, sizes=sizes)
+    assert [c.gaussians.n for c in cells] == list(sizes)
+    for k, c in enumerate(cells):
+        x0, z0 = 250.0 * (k % 4), 500.0 * (k // 4)          # 4 x 2 grid of 250 x 500 m cells
+        m = c.gaussians.means
+        # ground points stay inside the cell; facade points at most half a footprint outside it
+        assert np.median(m[:, 0]) == pytest.approx(x0 + 125.0, abs=60.0)
+        assert np.median(m[:, 2]) == pytest.approx(z0 + 250.0, abs=120.0)
+        assert np.allclose(c.aabb, np.concatenate([m.min(0), m.max(0)]))
+        mu = math.log(0.5 * math.sqrt(250.0 * 500.0 / sizes[k]))
+        assert float(c.gaussians.log_scales.mean()) == pytest.approx(mu, abs=0.05)
+        cam = c.camera
+        _check_camera(cam, 1152, 864)
+        assert np.allclose(_forward(cam), [0.0, -1.0, 0.0], atol=1e-5)      # nadir
+        ground = float(scenes._heightfield(cam.cam_pos[0], cam.cam_pos[2]))
+        assert cam.cam_pos[1] - ground == pytest.approx(100.0, abs=1e-3)   # 100 m above ground
+        assert x0 < cam.cam_pos[0] < x0 + 250.0 and z0 < cam.cam_pos[2] < z0 + 500.0
+
+
+def test_merged_city_sizes_and_grid():
+    cells = scenes.merged_city(total_scale=0.01)
+    sizes = [c.gaussians.n for c in cells]
+    assert sizes == [int(round(500_000 * (1 + k / 5) * 0.01)) for k in range(16)]
+    slots = set()
+    for c in cells:
+        cx, cz = np.median(c.gaussians.means[:, 0]), np.median(c.gaussians.means[:, 2])
+        slots.add((int(cx // 250.0), int(cz // 250.0)))
+        assert c.camera is None
+    assert slots == {(i, j) for i in range(4) for j in range(4)}  # every grid slot holds one cell
