@@ -51,13 +51,69 @@ PROFILED_TRAFFIC = {
 }
 
 
-def profiled_traffic(kernel):
+# Warp instructions issued per launch (smsp__inst_executed.sum) of the compositing kernels on this
+# workload, from the same kind of ncu capture; held to the same source hash.
+PROFILED_INSTRUCTIONS = {
+    "sources_sha256": "",
+}
+
+
+def _sources_sha256():
     import hashlib
     h = hashlib.sha256()
     for rel in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
-    return PROFILED_TRAFFIC.get(kernel) if h.hexdigest() == PROFILED_TRAFFIC["sources_sha256"] else None
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel):
+    return PROFILED_TRAFFIC.get(kernel) if _sources_sha256() == PROFILED_TRAFFIC["sources_sha256"] else None
+
+
+def profiled_instructions(kernel):
+    return PROFILED_INSTRUCTIONS.get(kernel) if _sources_sha256() == PROFILED_INSTRUCTIONS["sources_sha256"] else None
+
+
+def alu_peaks(dev, local):
+    """Measured throughput of the FP32 FMA pipe (scalar and packed f32x2, lane operations) and of
+    the special-function unit's ex2.approx on this GPU, from the library's probe kernels: a grid of
+    8 blocks of 256 threads per SM, 8 independent chains a thread, best of 5 timed launches, with
+    the SM clock sampled meanwhile."""
+    import torch
+    from paper_2402_17427_gb300 import binding as B
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = sms * 8, 16384
+    scratch = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    out = {}
+    t_end = time.time() + 0.6          # long enough for a few clock samples
+    best = {0: 1e30, 1: 1e30, 2: 1e30}
+    while True:
+        for kind in (0, 1, 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            B.vg_alu_probe(kind, blocks, iters, scratch.data_ptr(), stream)
+            b.record()
+            torch.cuda.synchronize()
+            best[kind] = min(best[kind], a.elapsed_time(b))
+        if time.time() > t_end:
+            break
+    clk = clocks.stop()
+    ops = blocks * 256 * iters * 8
+    out["ffma_tops"] = ops / (best[0] * 1e-3) / 1e12
+    out["ffma2_lane_tops"] = 2 * ops / (best[1] * 1e-3) / 1e12
+    out["ex2_tops"] = ops / (best[2] * 1e-3) / 1e12
+    out["sm_mhz"] = clk["sm_mhz"] if clk else None
+    out["sms"] = sms
+    if clk and clk.get("sm_mhz"):
+        f = clk["sm_mhz"] * 1e6
+        out["ffma_per_sm_clk"] = out["ffma_tops"] * 1e12 / (sms * f)
+        out["ffma2_lanes_per_sm_clk"] = out["ffma2_lane_tops"] * 1e12 / (sms * f)
+        out["ex2_per_sm_clk"] = out["ex2_tops"] * 1e12 / (sms * f)
+    return out
 
 
 def parse():
@@ -71,7 +127,8 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for the CPU baseline")
     ap.add_argument("--no-patterns", action="store_true", help="skip the batched-cells and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
-    ap.add_argument("--only-pattern", choices=["appearance", "evaluation", "optimiser", "partition"],
+    ap.add_argument("--only-pattern", choices=["appearance", "evaluation", "optimiser", "partition", "memory_scale",
+                                               "batched_cells", "serving"],
                     help="run one pattern measurement on one GPU, print its JSON and exit (no step line)")
     return ap.parse_args()
 
@@ -446,6 +503,53 @@ def appearance_pattern(dev, bf16_tflops):
             "peak_source": "MEASURED_PEAKS.json bf16_tflops x 1.1 / 2.25 (nominal TF32 / BF16)"}
 
 
+def memory_scale_pattern(dev, steps=5, warmup=2):
+    """The differentiable cell at memory scale (pattern 3): 20M Gaussians (SH3) on urban facades
+    and ground, one 1920x1080 view, a training step through the torch.autograd.Functions (render,
+    Eq. 1 loss, backward from the stored final transmittance) with every gradient returned."""
+    import torch
+    from paper_2402_17427_gb300 import binding as B, rasterize as R, scenes
+    g, cam, target = scenes.urban_cell_20m()
+    params = [t.to(dev).requires_grad_(True) for t in R.to_device(g, "cpu")]
+    tgt = torch.from_numpy(target).to(dev)
+    ras = R.Rasterizer(device=dev, check="sync")
+    lossobj = R.LossL1DSSIM(0.2)
+
+    def step():
+        img = R.rasterize(*params, g.sh_degree, cam, ras)
+        L = R.l1_dssim_loss(img, tgt, 0.2, lossobj)
+        return torch.autograd.grad(L, params)
+
+    step()                         # sizes the pair list (one synchronous check)
+    torch.cuda.synchronize()
+    ras.check = "defer"
+    torch.cuda.reset_peak_memory_stats(dev)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = B.vg_kernel_launches()
+    e0.record()
+    for _ in range(steps):
+        grads = step()
+    e1.record()
+    torch.cuda.synchronize()
+    launches = (B.vg_kernel_launches() - launches0) / steps
+    ras.verify()
+    ms = e0.elapsed_time(e1) / steps
+    cnt = ras.counters.cpu().numpy()
+    assert all(bool(torch.isfinite(t).all()) for t in grads)
+    return {"workload": "urban cell: 20,000,000 Gaussians (SH3) on ~150 building facades and ground in "
+                        "500x500x60 m, one 1920x1080 view at 80 m pitched -45 deg; render + L1/D-SSIM + "
+                        "backward through torch.autograd, gradients of all 20M",
+            "ms_per_step": ms, "steps_per_s": 1000.0 / ms,
+            "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev)),
+            "parameter_bytes": int(sum(t.numel() * 4 for t in params)),
+            "workspace_bytes": int(ras.ws.buf.numel()), "pair_capacity": int(ras.ws.capacity),
+            "pairs": int(cnt[B.VG_CNT_PAIRS]), "visible": int(cnt[B.VG_CNT_VISIBLE]),
+            "library_launches_per_step": launches}
+
+
 def serving_pattern(dev, seconds=30.0):
     """The merged 20M-Gaussian city (16 cells) served under a 200 req/s Poisson stream."""
     from paper_2402_17427_gb300 import scenes, serving
@@ -489,7 +593,10 @@ def main():
         fn = {"appearance": lambda: appearance_pattern(dev, float(peaks.get("bf16_tflops", 1900.0))),
               "evaluation": lambda: evaluation_pattern(dev, float(peaks.get("hbm_gbs", 6800.0))),
               "optimiser": lambda: optimiser_pattern(dev, float(peaks.get("hbm_gbs", 6800.0))),
-              "partition": lambda: partition_pattern(dev, float(peaks.get("hbm_gbs", 6800.0)))}[args.only_pattern]
+              "partition": lambda: partition_pattern(dev, float(peaks.get("hbm_gbs", 6800.0))),
+              "memory_scale": lambda: memory_scale_pattern(dev),
+              "batched_cells": lambda: batch_pattern(dev),
+              "serving": lambda: serving_pattern(dev, args.serve_seconds)}[args.only_pattern]
         if rank == 0:
             print(json.dumps({"pattern": args.only_pattern, **fn()}), flush=True)
         return
@@ -524,6 +631,11 @@ def main():
     evals_run_f = int(cnt[B.VG_CNT_EVALS_RUN])
     evals_b = int(last.to(torch.int64).sum().item())
     P, V = int(cnt[B.VG_CNT_PAIRS]), int(cnt[B.VG_CNT_VISIBLE])
+    # the backward's executed pixel slots (same step's workspace, counting backward)
+    cnt_t = torch.empty(B.VG_CNT_LEN, dtype=torch.int64, device=dev)
+    B.vg_read_counters(ras.ws.buf.data_ptr(), ras.ws.buf.numel(), cnt_t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    evals_run_b = int(cnt_t[B.VG_CNT_EVALS_RUN_BWD].item())
     ras.settings.count_blends = False
 
     for _ in range(args.warmup):
@@ -622,12 +734,21 @@ def main():
 
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    peak_ops = sms * 128 * 2070e6 / 1e12          # FP32 lanes x max SM clock, Tops/s
+    alu = alu_peaks(dev, local)
+    peak_ops = alu["ffma_tops"]                   # measured FP32 FMA lane operations, Tops/s
     fwd_ops = OPS_EVAL * evals_f + OPS_BLEND_FWD * blends_f
     bwd_ops = OPS_EVAL * evals_b + OPS_BLEND_BWD * blends_f
+    # the same per-evaluation counts over the slots the kernels execute after their warp culling
+    fwd_ops_x = OPS_EVAL * evals_run_f + OPS_BLEND_FWD * blends_f
+    bwd_ops_x = OPS_EVAL * evals_run_b + OPS_BLEND_BWD * blends_f
     kern = {"blend": fwd_ops / (stage_ms["blend"] * 1e-3) / 1e12,
             "blend_backward": bwd_ops / (stage_ms["blend_backward"] * 1e-3) / 1e12}
+    kern_x = {"blend": fwd_ops_x / (stage_ms["blend"] * 1e-3) / 1e12,
+              "blend_backward": bwd_ops_x / (stage_ms["blend_backward"] * 1e-3) / 1e12}
     dom = max(("blend", "blend_backward"), key=lambda k: stage_ms[k])
+    clk_mhz = (clk or {}).get("sm_mhz") or alu.get("sm_mhz") or 2070.0
+    inst = profiled_instructions(dom)
+    issue_frac = (inst / (sms * 4 * clk_mhz * 1e6 * stage_ms[dom] * 1e-3)) if inst else None
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -650,6 +771,7 @@ def main():
     if not args.no_patterns and ws == 1:
         try:
             patterns = {"batched_cells": batch_pattern(dev), "serving": serving_pattern(dev, args.serve_seconds),
+                        "memory_scale": memory_scale_pattern(dev),
                         "partition": partition_pattern(dev, hbm), "evaluation": evaluation_pattern(dev, hbm),
                         "optimiser": optimiser_pattern(dev, hbm),
                         "appearance": appearance_pattern(dev, bf16_peak)}
@@ -665,10 +787,14 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": kern[dom], "peak": peak_ops,
                      "unit": "FP32 Tops/s", "frac": kern[dom] / peak_ops, "traffic": profiled_traffic(dom),
-                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2070 MHz (nominal max clock)"},
+                     "achieved_executed": kern_x[dom], "frac_executed": kern_x[dom] / peak_ops,
+                     "issue_frac": issue_frac,
+                     "peak_source": "measured: vg_alu_probe FP32 FMA lane rate on this GPU "
+                                    f"({sms} SMs, SM clock {alu.get('sm_mhz')} MHz during the probe)",
+                     "alu_probe": alu},
         "stage_ms": stage_ms,
         "blends": {"evals_fwd": evals_f, "blends_fwd": blends_f, "evals_bwd": evals_b,
-                   "evals_run_fwd": evals_run_f,
+                   "evals_run_fwd": evals_run_f, "evals_run_bwd": evals_run_b,
                    "fwd_evals_per_s": evals_f / (stage_ms["blend"] * 1e-3),
                    "bwd_evals_per_s": evals_b / (stage_ms["blend_backward"] * 1e-3),
                    "fwd_tops": kern["blend"], "bwd_tops": kern["blend_backward"]},

@@ -44,13 +44,16 @@ typedef enum {
   VG_ERR_INVALID = -1,     /* bad argument (null pointer, size, degree, tile size ...)      */
   VG_ERR_CAPACITY = -2,    /* workspace too small for the requested sizes                    */
   VG_ERR_CUDA = -3,        /* a CUDA launch or runtime call failed                           */
-  VG_ERR_TIMEOUT = -4,     /* reserved: a bounded device wait gave up (status word)          */
+  VG_ERR_TIMEOUT = -4,     /* a bounded device wait gave up (reported through the status
+                              word; wrappers that read it return or raise this code)          */
   VG_ERR_UNSUPPORTED = -5  /* valid request this build does not implement                    */
 } vg_status;
 
 /* Bits of counters[VG_CNT_STATUS], set on the device. */
 #define VG_STATUS_PAIR_OVERFLOW 1u  /* pairs required > pair_capacity: outputs are invalid   */
-#define VG_STATUS_WAIT_TIMEOUT 2u   /* a bounded device wait (a sort look-back) gave up       */
+#define VG_STATUS_WAIT_TIMEOUT 2u   /* a bounded device wait (a look-back) gave up; the
+                                       stages after it treat every tile list as empty and the
+                                       outputs are invalid                                   */
 
 /* Layout of the int64 `counters` array every render call fills (device memory, >= 8 entries). */
 enum {
@@ -62,6 +65,9 @@ enum {
   VG_CNT_BLENDS = 5,   /* evaluations that were composited, same flag                       */
   VG_CNT_EVALS_RUN = 6, /* pixel slots the forward pass actually evaluated after its exact  */
                        /* warp-level culling (a culled splat costs a warp nothing), same flag */
+  VG_CNT_EVALS_RUN_BWD = 7, /* pixel slots the last backward pass on this workspace evaluated
+                       after culling, when that backward call had VG_FLAG_COUNT_BLENDS set
+                       (read with vg_read_counters; a forward writes 0)                     */
   VG_CNT_LEN = 8
 };
 
@@ -115,10 +121,30 @@ typedef struct {
                                   blended; 1: it is blended, then the pixel stops            */
   int32_t flags;               /* VG_FLAG_* bits                                              */
   const vg_stage_events* events; /* optional stage timing events (host struct), may be NULL   */
+  float* key_inputs;           /* optional (NULL = not recorded), device float [n, 4]: for
+                                  every Gaussian, the FP32 values the forward pass decided its
+                                  tile rectangle and sort key from, (u, v, r, depth): u, v the
+                                  projected mean on the key path, r = 3 sqrt(lambda_max) of the
+                                  2D covariance, depth the view-space z whose bits form the key;
+                                  (0, 0, -1, 0) for a Gaussian culled before its rectangle (near
+                                  plane, zero quaternion, determinant <= 0).  Lets a test feed the
+                                  kernel's own FP32 decision inputs to an independent key
+                                  generator and sort and demand identical lists.  Batch and
+                                  multi-view calls use opts[0]'s pointer, indexed by the call's
+                                  global Gaussian index (cells concatenated in order; for
+                                  vg_render_views every (view, kept cell) segment).             */
 } vg_raster_opts;
 
 #define VG_FLAG_ACCUMULATE_GRADS 1  /* backward adds into the gradient arrays (else writes)  */
 #define VG_FLAG_COUNT_BLENDS 2      /* forward counts evaluations / blends into counters     */
+/* Diagnostic for tests of the bounded-wait error path, never set in normal use: the first block
+ * of the projection kernel's stream compaction withholds its look-back status, and that
+ * look-back's waits give up after 2 ms instead of 1 s.  The render then reports
+ * VG_STATUS_WAIT_TIMEOUT: every later stage of that render sees the status and treats every tile
+ * list as empty (image = background, final T = 1, last = 0), and a backward pass on its
+ * workspace writes no gradient of a visible Gaussian.  Nothing waits longer than the limit and
+ * nothing is read or written out of bounds; the next render on the same workspace is normal. */
+#define VG_FLAG_TEST_STALL_LOOKBACK 4
 
 void vg_default_opts(vg_raster_opts* opts);
 
@@ -186,6 +212,19 @@ vg_status vg_read_render_state(const void* workspace, size_t workspace_bytes, in
                                uint32_t* ranges, uint32_t* ids, float* projected, uint32_t* touched,
                                vg_stream stream);
 
+/* Copies the counters a render workspace holds now (the forward's, plus VG_CNT_EVALS_RUN_BWD of a
+ * backward pass run on it since) into counters (device int64 [VG_CNT_LEN]).  Any render workspace
+ * (single view, batch or multi-view); workspace 256-byte aligned, workspace_bytes >= 256. */
+vg_status vg_read_counters(const void* workspace, size_t workspace_bytes, int64_t* counters, vg_stream stream);
+
+/* Throughput probe of one GPU pipe, for roofline denominators measured on the GPU at hand
+ * (diagnostic; no part of a render).  kind 0: FP32 fma.rn, kind 1: packed fma.rn.f32x2, kind 2:
+ * ex2.approx (special-function unit).  Launches `blocks` blocks of 256 threads, each thread
+ * running 8 independent chains for `iters` steps; scratch: device float [blocks * 256], written.
+ * Lane operations done = blocks * 256 * iters * 8 (times 2 for kind 1); the caller times the
+ * launch with CUDA events. */
+vg_status vg_alu_probe(int32_t kind, int32_t blocks, int32_t iters, float* scratch, vg_stream stream);
+
 /* ------------------------------------------------------------------------------------------
  * Loss, Eq. 1:  L = (1 - lambda) mean|I - I_gt| + lambda (1 - mean SSIM(I, I_gt))
  * SSIM: 11x11 Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2, mean over
@@ -196,16 +235,30 @@ vg_status vg_loss_l1_dssim(const float* img, const float* target, int32_t width,
                            float lambda, void* workspace, size_t workspace_bytes,
                            float* out_loss, float* out_grad, vg_stream stream);
 
+/* The gradient half of vg_loss_l1_dssim, for callers that take the loss value first and its
+ * gradient later (an autograd backward pass): call vg_loss_l1_dssim with out_grad = NULL, then
+ * this with the same images, size, lambda and the workspace that call used, untouched in between
+ * (it holds the SSIM adjoint maps).  Writes scale * dL/dI into out_grad [3,H,W]; scale is a device
+ * float (the incoming gradient of the loss) or NULL for 1.  The result equals the out_grad of one
+ * vg_loss_l1_dssim call times the scale.  Errors: VG_ERR_INVALID (NULL, sizes, lambda outside
+ * [0, 1]), VG_ERR_CAPACITY (workspace smaller than vg_loss_workspace_bytes). */
+vg_status vg_loss_l1_dssim_grad(const float* img, const float* target, int32_t width, int32_t height,
+                                float lambda, const void* workspace, size_t workspace_bytes,
+                                const float* scale, float* out_grad, vg_stream stream);
+
 /* Allocation-free variant of vg_loss_l1_dssim (the paper has no counterpart; this is a library
  * convenience).  It computes exactly what vg_loss_l1_dssim computes, but keeps its scratch in one
  * device array compiled into this library (about 37.8 MB on every GPU that loads it, held until
  * the process exits) instead of a caller workspace, for callers that cannot allocate device
  * memory between steps: hosts that plan all device memory up front and latency-critical loops
  * where cudaMalloc could synchronise the device or fail near the memory limit.
- *  - Images of up to VG_LOSS_NOALLOC_MAX_PIXELS pixels (width, height <= 16384); larger ones
- *    return VG_ERR_CAPACITY without launching anything.
- *  - The first call on a device looks the array's address up (cudaGetSymbolAddress) with that
- *    device current; make that first call before capturing any stream.
+ *  - Images of up to VG_LOSS_NOALLOC_MAX_PIXELS pixels; more pixels return VG_ERR_CAPACITY
+ *    without launching anything.  As for every entry point, a width or height above 16384 (or
+ *    below 1) is an argument error, VG_ERR_INVALID, whatever the pixel count.
+ *  - The first call in each CUDA context of a device looks the array's address up
+ *    (cudaGetSymbolAddress) with that device current and caches it with the context's id; a
+ *    device reset or a new context makes the next call look it up again.  Make the first call
+ *    of every context before capturing any stream.
  *  - Every call uses the same array and leaves its contents behind; each call overwrites all it
  *    reads, so nothing needs clearing, but calls that overlap on the GPU (concurrent streams)
  *    race on the array and must be serialised by the caller.
@@ -249,6 +302,17 @@ vg_status vg_render_batch(const vg_gaussians* cells /* host array [n_cells] */, 
                           void* workspace, size_t workspace_bytes, int64_t pair_capacity,
                           float* const* out_rgb, float* const* out_final_T, uint32_t* const* out_last,
                           int64_t* counters, vg_stream stream);
+/* vg_read_render_state for a batch: copies state a vg_render_batch call left in `workspace` (same
+ * cells, cameras, options and capacity).  Tiles are numbered globally, cell by cell in order
+ * (cell c's tiles start after the tiles of cells 0 .. c-1, each row-major at its own tile size);
+ * Gaussians are numbered globally, cells concatenated in order.
+ *   ranges     uint32 [total tiles, 2]; ids uint32 [pair_capacity] (global Gaussian indices);
+ *   projected  float32 [total n, 12]; touched uint32 [total n] — as in vg_read_render_state. */
+vg_status vg_read_batch_state(const void* workspace, size_t workspace_bytes, const vg_gaussians* cells /* host */,
+                              int32_t n_cells, const vg_camera* cams /* host */, const vg_raster_opts* opts /* host */,
+                              int64_t pair_capacity, uint32_t* ranges, uint32_t* ids, float* projected,
+                              uint32_t* touched, vg_stream stream);
+
 /* Adjoint of vg_render_batch with the same cells, cameras, options and workspace.
  * dL_drgb[c], g_*[c]: host arrays of device pointers, one entry per cell. */
 vg_status vg_render_batch_backward(const vg_gaussians* cells, int32_t n_cells, const vg_camera* cams,

@@ -87,6 +87,11 @@ def lib():
             L.or_pixel_trace.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int32]
             L.or_backward.argtypes = [P, P, P, P, P, P, P, P]
             L.or_sh_basis.argtypes = [ctypes.c_int, P, P, P]
+            L.or_fd_directional.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_double, P, P]
+            L.or_fd_directional.restype = None
+            L.or_pairs_from_fp32.restype = ctypes.c_int64
+            L.or_pairs_from_fp32.argtypes = [ctypes.c_int64, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int64, P, P, P]
             L.or_ssim_map.restype = ctypes.c_double
             L.or_ssim_map.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P]
             L.or_loss_l1_dssim.restype = ctypes.c_double
@@ -228,6 +233,21 @@ class Render:
         n = self._L.or_pixel_trace(self.h, int(x), int(y), _ptr(T), _ptr(g), cap)
         return T[:min(n, cap)], g[:min(n, cap)]
 
+    def fd_directional(self, w, ids, dirs, eps: float = 1e-6):
+        """Central differences of L = sum(w * image) along dirs[k] (raw parameters of Gaussian
+        ids[k] in the layout mean 3, log-scale 3, quaternion 4, logit 1, SH 3K), re-rendering only
+        that Gaussian's tiles.  Returns (derivatives [m], flags [m]); flag 1 marks a perturbation
+        that changed a decision (not a derivative)."""
+        w = np.ascontiguousarray(np.asarray(w, np.float64))
+        ids = np.ascontiguousarray(np.asarray(ids, np.int64))
+        dirs = np.ascontiguousarray(np.asarray(dirs, np.float64).reshape(len(ids), -1))
+        assert dirs.shape[1] == 11 + 3 * self.scene.K
+        out = np.zeros(len(ids))
+        flags = np.zeros(len(ids), np.int32)
+        self._L.or_fd_directional(self.h, _ptr(w), len(ids), _ptr(ids), _ptr(dirs), float(eps), _ptr(out),
+                                  _ptr(flags))
+        return out, flags
+
     def backward(self, dL_dimg):
         """Gradients w.r.t. raw parameters, plus the per-Gaussian 2D gradients [n, 9]."""
         s = self.scene
@@ -242,6 +262,25 @@ class Render:
 def render(gaussians_or_scene, cam, opts: Options | None = None, tile_mask=None) -> Render:
     sc = gaussians_or_scene if isinstance(gaussians_or_scene, Scene64) else Scene64.of(gaussians_or_scene)
     return Render(sc, cam, opts or Options(), tile_mask)
+
+
+def pairs_from_fp32(uvrd, width: int, height: int, tile: int = 16):
+    """Keys, Gaussian ids and tile ranges of the stable (tile, depth) sort built from given FP32
+    decision inputs uvrd [n, 4] = (u, v, r, depth) per Gaussian (r < 0: culled), with the forward
+    pass's own rectangle rule, key layout and sort.  Returns (keys uint64 [P], ids uint32 [P],
+    ranges int32 [tiles, 2])."""
+    a = np.ascontiguousarray(np.asarray(uvrd, np.float32).reshape(-1, 4))
+    n = a.shape[0]
+    tiles = ((width + tile - 1) // tile) * ((height + tile - 1) // tile)
+    L = lib()
+    dummy = np.zeros(1, np.uint64)
+    P = int(L.or_pairs_from_fp32(n, _ptr(a), width, height, tile, 0, _ptr(dummy), _ptr(dummy), _ptr(dummy)))
+    keys = np.zeros(max(P, 1), np.uint64)
+    vals = np.zeros(max(P, 1), np.uint32)
+    ranges = np.zeros((tiles, 2), np.int32)
+    got = int(L.or_pairs_from_fp32(n, _ptr(a), width, height, tile, P, _ptr(keys), _ptr(vals), _ptr(ranges)))
+    assert got == P
+    return keys[:P], vals[:P], ranges
 
 
 def sh_basis(degree: int, d):

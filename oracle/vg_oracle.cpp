@@ -369,15 +369,18 @@ inline uint64_t mix(uint64_t h, uint64_t v) { h ^= v + 0x9e3779b97f4a7c15ULL + (
 // T before, G, clamped) for every blended Gaussian of pixel (tx_pix, ty_pix).
 struct Step { int32_t pos; uint32_t g; double alpha, Tb, G; bool clamped; };
 
+// `over`, when given, replaces the record of Gaussian `over_id` (finite differences re-project
+// one Gaussian and composite its tiles again with everything else unchanged).
 void render_pixel(const State& S, int x, int y, int tile, double* C, double* Tout, int32_t* lastout,
-                  bool* amb, int64_t* n_eval, int64_t* n_blend, uint64_t* h, std::vector<Step>* trace) {
+                  bool* amb, int64_t* n_eval, int64_t* n_blend, uint64_t* h, std::vector<Step>* trace,
+                  const Rec* over = nullptr, uint32_t over_id = 0xFFFFFFFFu) {
   const OrOpts& op = S.op;
   int32_t s0 = S.ranges[2 * tile], s1 = S.ranges[2 * tile + 1];
   double T = 1.0;
   C[0] = C[1] = C[2] = 0.0;
   int32_t last = 0;
   for (int32_t j = s0; j < s1; ++j) {
-    const Rec& g = S.rec[S.vals[j]];
+    const Rec& g = (over && S.vals[j] == over_id) ? *over : S.rec[S.vals[j]];
     ++*n_eval;
     double dx = x - g.u, dy = y - g.v;
     double qa = 0.5 * g.a * dx * dx, qc = 0.5 * g.c * dy * dy, qb = g.b * dx * dy;
@@ -407,6 +410,38 @@ void render_pixel(const State& S, int x, int y, int tile, double* C, double* Tou
   *lastout = last;
 }
 
+// Stable sort of the (key, Gaussian id) pairs by key, in emission order for equal keys, and the
+// range [first, last + 1) of every tile's run in the sorted keys ((0, 0) for a tile with none).
+void sort_keyed_pairs(std::vector<uint64_t>& keys, std::vector<uint32_t>& vals, int tiles,
+                      std::vector<int32_t>& ranges) {
+  std::vector<size_t> order(keys.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return keys[a] < keys[b]; });
+  std::vector<uint64_t> k2(order.size());
+  std::vector<uint32_t> v2(order.size());
+  for (size_t j = 0; j < order.size(); ++j) { k2[j] = keys[order[j]]; v2[j] = vals[order[j]]; }
+  keys.swap(k2);
+  vals.swap(v2);
+  ranges.assign(2 * (size_t)tiles, 0);
+  for (size_t j = 0; j < keys.size(); ++j) {
+    int t = (int)(keys[j] >> 32);
+    if (j == 0 || (int)(keys[j - 1] >> 32) != t) ranges[2 * t] = (int32_t)j;
+    ranges[2 * t + 1] = (int32_t)j + 1;
+  }
+}
+
+// One key per (Gaussian, tile of its rectangle): (tile id << 32) | FP32 depth bits, emitted in
+// Gaussian index order with the rectangle's tiles row-major.
+void emit_keys(std::vector<uint64_t>& keys, std::vector<uint32_t>& vals, uint32_t id, int tx0, int tx1, int ty0,
+               int ty1, int tiles_x, float depth32) {
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) {
+      uint64_t tile = (uint64_t)ty * tiles_x + tx;
+      keys.push_back((tile << 32) | float_bits(depth32));
+      vals.push_back(id);
+    }
+}
+
 void build_pairs(State& S) {
   int64_t n = S.sc.n;
   S.keys.clear();
@@ -414,28 +449,9 @@ void build_pairs(State& S) {
   for (int64_t i = 0; i < n; ++i) {
     const Rec& g = S.rec[i];
     if (!g.visible) continue;
-    for (int ty = g.ty0; ty <= g.ty1; ++ty)
-      for (int tx = g.tx0; tx <= g.tx1; ++tx) {
-        uint64_t tile = (uint64_t)ty * S.tiles_x + tx;
-        S.keys.push_back((tile << 32) | float_bits(g.depth32));
-        S.vals.push_back((uint32_t)i);
-      }
+    emit_keys(S.keys, S.vals, (uint32_t)i, g.tx0, g.tx1, g.ty0, g.ty1, S.tiles_x, g.depth32);
   }
-  std::vector<size_t> order(S.keys.size());
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return S.keys[a] < S.keys[b]; });
-  std::vector<uint64_t> k2(order.size());
-  std::vector<uint32_t> v2(order.size());
-  for (size_t j = 0; j < order.size(); ++j) { k2[j] = S.keys[order[j]]; v2[j] = S.vals[order[j]]; }
-  S.keys.swap(k2);
-  S.vals.swap(v2);
-  int tiles = S.tiles_x * S.tiles_y;
-  S.ranges.assign(2 * (size_t)tiles, 0);
-  for (size_t j = 0; j < S.keys.size(); ++j) {
-    int t = (int)(S.keys[j] >> 32);
-    if (j == 0 || (int)(S.keys[j - 1] >> 32) != t) S.ranges[2 * t] = (int32_t)j;
-    S.ranges[2 * t + 1] = (int32_t)j + 1;
-  }
+  sort_keyed_pairs(S.keys, S.vals, S.tiles_x * S.tiles_y, S.ranges);
 }
 
 void set_threads(const OrOpts& op) {
@@ -449,6 +465,35 @@ void set_threads(const OrOpts& op) {
 }  // namespace
 
 extern "C" {
+
+// Tile lists from given FP32 decision inputs: uvrd[i] = (u, v, r, depth) of Gaussian i, r < 0 for
+// a Gaussian culled before its rectangle.  The rectangle edges (closed box [u - r, u + r] x
+// [v - r, v + r] against the pixel samples inside a W x H image), the keys and the stable sort
+// are the forward pass's own (rect_lo / rect_hi, emit_keys, sort_keyed_pairs), so feeding another
+// implementation's FP32 (u, v, r, depth) checks its key generation, sort and ranges alone.
+// Returns the number of pairs P; keys [P], vals [P] and ranges [tiles, 2] are written only when
+// P <= cap.
+int64_t or_pairs_from_fp32(int64_t n, const float* uvrd, int W, int H, int tile, int64_t cap, uint64_t* keys_out,
+                           uint32_t* vals_out, int32_t* ranges_out) {
+  const int tiles_x = (W + tile - 1) / tile, tiles_y = (H + tile - 1) / tile;
+  std::vector<uint64_t> keys;
+  std::vector<uint32_t> vals;
+  for (int64_t i = 0; i < n; ++i) {
+    const float u = uvrd[4 * i], v = uvrd[4 * i + 1], r = uvrd[4 * i + 2], depth = uvrd[4 * i + 3];
+    if (!(r >= 0.0f)) continue;
+    int xlo = rect_lo(u, r, W), xhi = rect_hi(u, r, W), ylo = rect_lo(v, r, H), yhi = rect_hi(v, r, H);
+    if (xlo > xhi || ylo > yhi) continue;
+    emit_keys(keys, vals, (uint32_t)i, xlo / tile, xhi / tile, ylo / tile, yhi / tile, tiles_x, depth);
+  }
+  const int64_t P = (int64_t)keys.size();
+  if (P > cap) return P;
+  std::vector<int32_t> ranges;
+  sort_keyed_pairs(keys, vals, tiles_x * tiles_y, ranges);
+  std::memcpy(keys_out, keys.data(), keys.size() * sizeof(uint64_t));
+  std::memcpy(vals_out, vals.data(), vals.size() * sizeof(uint32_t));
+  std::memcpy(ranges_out, ranges.data(), ranges.size() * sizeof(int32_t));
+  return P;
+}
 
 int or_sh_basis(int degree, const double* d, double* Y, double* dY) {
   double dy[16][3];
@@ -584,6 +629,99 @@ void or_get_records(void* h, double* f64, float* f32, int32_t* i32, int32_t* are
       o[6] = g.rect_amb; o[7] = g.grad_amb; o[8] = 0;
     }
     if (arect) { arect[4 * i] = g.atx0; arect[4 * i + 1] = g.atx1; arect[4 * i + 2] = g.aty0; arect[4 * i + 3] = g.aty1; }
+  }
+}
+
+// Directional central differences of L = sum over channels and pixels of w[c, p] * I[c, p], one
+// Gaussian at a time (the adjoint's pin at memory scale).  Target k is Gaussian ids[k] of the
+// rendered state; its raw parameters move by +-eps * dirs[k] (dirs [m, F], F = 11 + 3K: mean 3,
+// log-scale 3, quaternion 4, logit 1, SH 3K, the layout of the raw parameters).  Only that Gaussian
+// is projected again and only the tiles of its rectangle are composited again: every other pixel
+// is unchanged by construction, so the difference of the two partial sums is the difference of
+// the full loss.  out[k] = (L(+) - L(-)) / (2 eps).  flags[k] = 1 when the perturbation changes a
+// decision (validity, tile rectangle, the Gaussian's position in any of its tile lists, a guard-band
+// or colour-clamp side, or any skip / clamp / stop decision of an affected pixel); a flagged sample
+// crosses a discontinuity and is not a derivative.  Runs targets in parallel.
+void or_fd_directional(void* h, const double* w, int64_t m, const int64_t* ids, const double* dirs, double eps,
+                       double* out, int32_t* flags) {
+  State* S = (State*)h;
+  const int K = S->K, F = 11 + 3 * K;
+  const int W = S->cam.width, H = S->cam.height, TS = S->op.tile;
+  const size_t plane = (size_t)W * H;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < m; ++k) {
+    const int64_t id = ids[k];
+    const Rec& g0 = S->rec[id];
+    out[k] = 0.0;
+    flags[k] = 0;
+    if (!g0.visible) { flags[k] = 1; continue; }
+    // composite the Gaussian's tiles with record `rec` for it; returns the partial loss and the
+    // decision hash of those pixels
+    auto partial = [&](const Rec* rec, uint64_t* hh) {
+      double L = 0.0;
+      int64_t ev = 0, bl = 0;
+      *hh = 0;
+      for (int ty = g0.ty0; ty <= g0.ty1; ++ty)
+        for (int tx = g0.tx0; tx <= g0.tx1; ++tx) {
+          const int t = ty * S->tiles_x + tx;
+          for (int y = ty * TS; y < std::min(H, (ty + 1) * TS); ++y)
+            for (int x = tx * TS; x < std::min(W, (tx + 1) * TS); ++x) {
+              double C[3], T;
+              int32_t last;
+              bool amb = false;
+              render_pixel(*S, x, y, t, C, &T, &last, &amb, &ev, &bl, hh, nullptr, rec, (uint32_t)id);
+              const size_t p = (size_t)y * W + x;
+              for (int ch = 0; ch < 3; ++ch) L += w[ch * plane + p] * (C[ch] + T * S->op.bg[ch]);
+            }
+        }
+      return L;
+    };
+    uint64_t h0 = 0;
+    partial(nullptr, &h0);
+    double Ls[2];
+    for (int sgn = 0; sgn < 2 && !flags[k]; ++sgn) {
+      const double e = sgn == 0 ? eps : -eps;
+      const double* d = dirs + (size_t)k * F;
+      std::vector<double> means(3), ls(3), q(4), lg(1), sh(3 * (size_t)K);
+      for (int c = 0; c < 3; ++c) means[c] = S->sc.means[3 * id + c] + e * d[c];
+      for (int c = 0; c < 3; ++c) ls[c] = S->sc.log_scales[3 * id + c] + e * d[3 + c];
+      for (int c = 0; c < 4; ++c) q[c] = S->sc.quats[4 * id + c] + e * d[6 + c];
+      lg[0] = S->sc.logits[id] + e * d[10];
+      for (int c = 0; c < 3 * K; ++c) sh[c] = S->sc.sh[(size_t)id * 3 * K + c] + e * d[11 + c];
+      State one;
+      one.sc = S->sc;
+      one.sc.n = 1;
+      one.sc.means = means.data(); one.sc.log_scales = ls.data(); one.sc.quats = q.data();
+      one.sc.logits = lg.data(); one.sc.sh = sh.data();
+      one.cam = S->cam;
+      one.op = S->op;
+      one.K = K;
+      one.tiles_x = S->tiles_x;
+      one.tiles_y = S->tiles_y;
+      one.rec.assign(1, Rec());
+      project(one, 0);
+      const Rec& g1 = one.rec[0];
+      bool same = g1.valid && g1.visible && g1.tx0 == g0.tx0 && g1.tx1 == g0.tx1 && g1.ty0 == g0.ty0 &&
+                  g1.ty1 == g0.ty1 && g1.clx == g0.clx && g1.cly == g0.cly;
+      for (int ch = 0; ch < 3 && same; ++ch) same = (g1.pre[ch] > 0) == (g0.pre[ch] > 0);
+      // the new key keeps the Gaussian's place in every list it is in
+      for (int ty = g0.ty0; ty <= g0.ty1 && same; ++ty)
+        for (int tx = g0.tx0; tx <= g0.tx1 && same; ++tx) {
+          const int t = ty * S->tiles_x + tx;
+          const int32_t s0 = S->ranges[2 * t], s1 = S->ranges[2 * t + 1];
+          int32_t j = s0;
+          while (j < s1 && S->vals[j] != (uint32_t)id) ++j;
+          if (j == s1) { same = false; break; }
+          const uint64_t key = ((uint64_t)t << 32) | float_bits(g1.depth32);
+          if (j > s0 && !(S->keys[j - 1] < key || (S->keys[j - 1] == key && S->vals[j - 1] < (uint32_t)id))) same = false;
+          if (j + 1 < s1 && !(key < S->keys[j + 1] || (key == S->keys[j + 1] && (uint32_t)id < S->vals[j + 1]))) same = false;
+        }
+      if (!same) { flags[k] = 1; break; }
+      uint64_t h1 = 0;
+      Ls[sgn] = partial(&g1, &h1);
+      if (h1 != h0) flags[k] = 1;
+    }
+    if (!flags[k]) out[k] = (Ls[0] - Ls[1]) / (2.0 * eps);
   }
 }
 

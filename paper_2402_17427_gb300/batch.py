@@ -55,17 +55,25 @@ class BatchRasterizer:
             self.buf = torch.empty(need, dtype=torch.uint8, device=self.device)
         return need
 
-    def forward(self, cells, degree, cameras, events=None):
-        """cells: list of (means, log_scales, quats, logits, sh) tensors.  Returns [(rgb, T, last)]."""
+    def forward(self, cells, degree, cameras, events=None, key_inputs=None):
+        """cells: list of (means, log_scales, quats, logits, sh) tensors.  Returns [(rgb, T, last)].
+        key_inputs: optional float32 CUDA tensor [total n, 4] receiving every Gaussian's FP32
+        (u, v, r, depth) decision inputs, cells concatenated in order (parity tests)."""
         gs = [gaussians_c(*c, degree) for c in cells]
         cams = [camera_c(c) for c in cameras]
         opts = self._opts(len(cells), events=events)
+        if key_inputs is not None:
+            total = sum(int(c[0].shape[0]) for c in cells)
+            if not (key_inputs.is_cuda and key_inputs.dtype == torch.float32 and key_inputs.is_contiguous()
+                    and key_inputs.numel() >= 4 * total):
+                raise ValueError("key_inputs must be a contiguous float32 CUDA tensor of total n x 4 entries")
+            opts[0].key_inputs = key_inputs.data_ptr()
         outs = []
         for cam in cameras:
             outs.append((torch.empty((3, cam.height, cam.width), dtype=torch.float32, device=self.device),
                          torch.empty((cam.height, cam.width), dtype=torch.float32, device=self.device),
                          torch.empty((cam.height, cam.width), dtype=torch.int32, device=self.device)))
-        counters = torch.zeros(B.VG_CNT_LEN, dtype=torch.int64, device=self.device)
+        counters = torch.empty(B.VG_CNT_LEN, dtype=torch.int64, device=self.device)   # every entry written by the call
         n_total = sum(int(c[0].shape[0]) for c in cells)
         for _ in range(4):
             nbytes = self._ensure(gs, cams, opts, n_total)
@@ -83,6 +91,24 @@ class BatchRasterizer:
             self.capacity = int(c[B.VG_CNT_PAIRS] * 1.25) + 1024
         self.counters = counters
         return outs
+
+    def read_state(self, cells, degree, cameras):
+        """Tile ranges [total tiles, 2] and Gaussian ids of every pair (global numbering, cells in
+        order) left by the last forward, as NumPy arrays."""
+        import numpy as np
+        gs = [gaussians_c(*c, degree) for c in cells]
+        cams = [camera_c(c) for c in cameras]
+        opts = self._opts(len(cells))
+        tiles = 0
+        for s, cam in zip(self.settings or [RasterSettings()] * len(cells), cameras):
+            ts = s.tile_size
+            tiles += ((cam.width + ts - 1) // ts) * ((cam.height + ts - 1) // ts)
+        ranges = torch.zeros((tiles, 2), dtype=torch.int32, device=self.device)
+        ids = torch.zeros(self.capacity, dtype=torch.int32, device=self.device)
+        B.vg_read_batch_state(self.buf.data_ptr(), self.buf.numel(), gs, cams, opts, self.capacity,
+                              ranges.data_ptr(), ids.data_ptr(), None, None, _stream())
+        torch.cuda.synchronize()
+        return ranges.cpu().numpy().astype(np.int64), ids.cpu().numpy().view(np.uint32)
 
     def verify(self):
         for c in self._pending:

@@ -15,15 +15,18 @@ LIB_PATH = os.path.join(_PKG, "libvgrast.so")
 VG_OK, VG_ERR_INVALID, VG_ERR_CAPACITY, VG_ERR_CUDA, VG_ERR_TIMEOUT, VG_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 VG_STATUS_PAIR_OVERFLOW = 1
 VG_STATUS_WAIT_TIMEOUT = 2
-VG_CNT_PAIRS, VG_CNT_VISIBLE, VG_CNT_STATUS, VG_CNT_DEPTH_BITS, VG_CNT_EVALS, VG_CNT_BLENDS, VG_CNT_EVALS_RUN = range(7)
+(VG_CNT_PAIRS, VG_CNT_VISIBLE, VG_CNT_STATUS, VG_CNT_DEPTH_BITS, VG_CNT_EVALS, VG_CNT_BLENDS, VG_CNT_EVALS_RUN,
+ VG_CNT_EVALS_RUN_BWD) = range(8)
 VG_CNT_LEN = 8
 VG_FLAG_ACCUMULATE_GRADS = 1
 VG_FLAG_COUNT_BLENDS = 2
+VG_FLAG_TEST_STALL_LOOKBACK = 4
 
 EXPORTED = ("vg_default_opts", "vg_status_string", "vg_kernel_launches", "vg_workspace_bytes", "vg_rasterize_forward",
             "vg_rasterize_backward", "vg_read_render_state", "vg_loss_workspace_bytes", "vg_loss_l1_dssim",
             "vg_batch_workspace_bytes", "vg_render_batch", "vg_render_batch_backward",
-            "vg_views_workspace_bytes", "vg_render_views", "vg_loss_l1_dssim_noalloc",
+            "vg_views_workspace_bytes", "vg_render_views", "vg_loss_l1_dssim_noalloc", "vg_read_batch_state",
+            "vg_loss_l1_dssim_grad", "vg_read_counters", "vg_alu_probe",
             "vg_airspace_boxes", "vg_visibility_workspace_bytes", "vg_camera_visibility", "vg_merge_workspace_bytes",
             "vg_merge_cells", "vg_eval_workspace_bytes", "vg_eval_color_corrected", "vg_adam_step",
             "vg_densify_accumulate", "vg_densify_workspace_bytes", "vg_densify", "vg_appearance_param_count",
@@ -71,7 +74,8 @@ class vg_raster_opts(ctypes.Structure):
     _fields_ = [("tile_size", ctypes.c_int32), ("chunk", ctypes.c_int32), ("bg", ctypes.c_float * 3),
                 ("dilation", ctypes.c_float), ("alpha_max", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("guard", ctypes.c_float), ("stop_rule", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("events", ctypes.POINTER(vg_stage_events))]
+                ("flags", ctypes.c_int32), ("events", ctypes.POINTER(vg_stage_events)),
+                ("key_inputs", ctypes.c_void_p)]
 
 
 class VGError(RuntimeError):
@@ -118,6 +122,13 @@ def lib():
     L.vg_loss_l1_dssim.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P, ctypes.c_size_t,
                                    _P, _P, _P]
     L.vg_loss_l1_dssim.restype = ctypes.c_int
+    L.vg_loss_l1_dssim_grad.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P, ctypes.c_size_t,
+                                        _P, _P, _P]
+    L.vg_loss_l1_dssim_grad.restype = ctypes.c_int
+    L.vg_read_counters.argtypes = [_P, ctypes.c_size_t, _P, _P]
+    L.vg_read_counters.restype = ctypes.c_int
+    L.vg_alu_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]
+    L.vg_alu_probe.restype = ctypes.c_int
     if hasattr(L, "vg_render_batch"):
         L.vg_batch_workspace_bytes.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32,
                                                ctypes.POINTER(vg_camera), ctypes.POINTER(vg_raster_opts),
@@ -127,6 +138,10 @@ def lib():
                                       ctypes.POINTER(vg_raster_opts), _P, ctypes.c_size_t, ctypes.c_int64,
                                       _PP, _PP, _PP, _P, _P]
         L.vg_render_batch.restype = ctypes.c_int
+        L.vg_read_batch_state.argtypes = [_P, ctypes.c_size_t, ctypes.POINTER(vg_gaussians), ctypes.c_int32,
+                                          ctypes.POINTER(vg_camera), ctypes.POINTER(vg_raster_opts), ctypes.c_int64,
+                                          _P, _P, _P, _P, _P]
+        L.vg_read_batch_state.restype = ctypes.c_int
         L.vg_render_batch_backward.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32,
                                                ctypes.POINTER(vg_camera), ctypes.POINTER(vg_raster_opts), _P,
                                                ctypes.c_size_t, ctypes.c_int64, _PP, _PP, _PP, _PP, _PP, _PP,
@@ -242,6 +257,20 @@ def vg_loss_l1_dssim(img: int, target: int, width: int, height: int, lam: float,
                                   stream), "vg_loss_l1_dssim")
 
 
+def vg_read_counters(workspace: int, workspace_bytes: int, counters: int, stream: int) -> None:
+    _check(lib().vg_read_counters(workspace, workspace_bytes, counters, stream), "vg_read_counters")
+
+
+def vg_alu_probe(kind: int, blocks: int, iters: int, scratch: int, stream: int) -> None:
+    _check(lib().vg_alu_probe(kind, blocks, iters, scratch, stream), "vg_alu_probe")
+
+
+def vg_loss_l1_dssim_grad(img: int, target: int, width: int, height: int, lam: float, workspace: int,
+                          workspace_bytes: int, scale: int | None, out_grad: int, stream: int) -> None:
+    _check(lib().vg_loss_l1_dssim_grad(img, target, width, height, lam, workspace, workspace_bytes, scale, out_grad,
+                                       stream), "vg_loss_l1_dssim_grad")
+
+
 def _ptr_array(ptrs):
     arr = (ctypes.c_void_p * len(ptrs))(*[p or None for p in ptrs])
     return ctypes.cast(arr, _PP), arr
@@ -266,6 +295,17 @@ def vg_render_batch(cells, cams, opts, workspace: int, workspace_bytes: int, pai
     c, _kc = _ptr_array(out_last)
     _check(lib().vg_render_batch(G, n, C, O, workspace, workspace_bytes, pair_capacity, a, b, c, counters, stream),
            "vg_render_batch")
+
+
+def vg_read_batch_state(workspace: int, workspace_bytes: int, cells, cams, opts, pair_capacity: int,
+                        ranges: int | None, ids: int | None, projected: int | None, touched: int | None,
+                        stream: int) -> None:
+    n = len(cells)
+    G = (vg_gaussians * n)(*cells)
+    C = (vg_camera * n)(*cams)
+    O = (vg_raster_opts * n)(*opts)
+    _check(lib().vg_read_batch_state(workspace, workspace_bytes, G, n, C, O, pair_capacity, ranges, ids, projected,
+                                     touched, stream), "vg_read_batch_state")
 
 
 def vg_render_batch_backward(cells, cams, opts, workspace: int, workspace_bytes: int, pair_capacity: int,

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(256) init_header(WsHeader* hdr, SortCtl* ctl) 
   hdr->depth_bits = 0;
   hdr->pair_n = 0;
   hdr->tile_bits = 0;
+  hdr->evals_run_bwd = 0;
   for (int k = 0; k < kTileClasses; ++k) hdr->work_fwd[k] = hdr->work_bwd[k] = 0;
 }
 
@@ -41,14 +42,14 @@ __global__ void publish_counters(const WsHeader* hdr, int64_t* c) {
   c[VG_CNT_EVALS] = (int64_t)hdr->evals;
   c[VG_CNT_BLENDS] = (int64_t)hdr->blends;
   c[VG_CNT_EVALS_RUN] = (int64_t)hdr->evals_run;
-  c[7] = 0;
+  c[VG_CNT_EVALS_RUN_BWD] = (int64_t)hdr->evals_run_bwd;
 }
 
 __global__ void read_state(const uint32_t* __restrict__ lists, const Splat* __restrict__ splats,
                            const uint32_t* __restrict__ touched_in, const WsHeader* __restrict__ hdr, int n,
                            const uint32_t* d0, const uint32_t* d1, uint32_t* __restrict__ ids,
                            float* __restrict__ proj, uint32_t* __restrict__ touched) {
-  const unsigned np = hdr->pair_n;
+  const unsigned np = render_dead(hdr) ? 0u : hdr->pair_n;   // lists of a render that gave up are not read
   const uint32_t* dorder = depth_order(hdr, d0, d1);
   const float k = -1.3862943611198906f;   // scaled conic -> inverse covariance
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < np || i < (unsigned)n; i += gridDim.x * blockDim.x) {
@@ -282,7 +283,7 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
   stage_event(ev, VG_STAGE_PROJECT, true, s);
   cudaError_t e = launch_preprocess(tab, c.total_n, c.degree, reinterpret_cast<Splat*>(ws + L.splats),
                                     reinterpret_cast<uint2*>(ws + L.rects), reinterpret_cast<uint32_t*>(ws + L.touched),
-                                    make_compact(L, ws, c.total_n), hdr, s);
+                                    make_compact(L, ws, c.total_n, opts0), hdr, s);
   if (e != cudaSuccess) return VG_ERR_CUDA;
   stage_event(ev, VG_STAGE_PROJECT, false, s);
   stage_event(ev, VG_STAGE_SORT, true, s);
@@ -346,7 +347,7 @@ vg_status run_backward(Call& c, const vg_raster_opts* opts0, void* workspace, si
     return VG_ERR_CUDA;
   const bool accumulate = (opts0->flags & VG_FLAG_ACCUMULATE_GRADS) != 0;
   stage_event(ev, VG_STAGE_BLEND_BACKWARD, true, s);
-  cudaError_t e = launch_blend_backward(tab, c.plan, L, ws, abs, s);
+  cudaError_t e = launch_blend_backward(tab, c.plan, L, ws, abs, (opts0->flags & VG_FLAG_COUNT_BLENDS) != 0, s);
   stage_event(ev, VG_STAGE_BLEND_BACKWARD, false, s);
   if (e != cudaSuccess) return VG_ERR_CUDA;
   stage_event(ev, VG_STAGE_PROJECT_BACKWARD, true, s);
@@ -578,5 +579,40 @@ extern "C" vg_status vg_read_render_state(const void* workspace, size_t workspac
                                   reinterpret_cast<const WsHeader*>(ws + L.header), (int)n,
                                   reinterpret_cast<const uint32_t*>(ws + L.vvals[0]),
                                   reinterpret_cast<const uint32_t*>(ws + L.vvals[1]), ids, projected, touched);
+  return cuda_status(cudaGetLastError());
+}
+
+extern "C" vg_status vg_read_batch_state(const void* workspace, size_t workspace_bytes, const vg_gaussians* cells,
+                                         int32_t n_cells, const vg_camera* cams, const vg_raster_opts* opts,
+                                         int64_t pair_capacity, uint32_t* ranges, uint32_t* ids, float* projected,
+                                         uint32_t* touched, vg_stream stream) {
+  if (!workspace || !cells || !cams || !opts || n_cells < 1 || n_cells > kMaxViews) return VG_ERR_INVALID;
+  if (pair_capacity < 1 || pair_capacity > 0xFFFFFFFFll) return VG_ERR_INVALID;
+  std::vector<int> sv(n_cells);
+  for (int i = 0; i < n_cells; ++i) sv[i] = i;
+  Call c;
+  const vg_status st = make_call(c, cells, n_cells, sv.data(), cams, opts, n_cells);
+  if (st != VG_OK) return st;
+  const Layout L = make_layout(c.total_n64, c.total_tiles64, pair_capacity);
+  if (workspace_bytes < L.total) return VG_ERR_CAPACITY;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const char* ws = static_cast<const char*>(workspace);
+  if (ranges && cudaMemcpyAsync(ranges, ws + L.ranges, (size_t)c.total_tiles * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return VG_ERR_CUDA;
+  note_launches(1);
+  read_state<<<1024, 256, 0, s>>>(reinterpret_cast<const uint32_t*>(ws + L.pvals[0]), reinterpret_cast<const Splat*>(ws + L.splats),
+                                  reinterpret_cast<const uint32_t*>(ws + L.touched),
+                                  reinterpret_cast<const WsHeader*>(ws + L.header), c.total_n,
+                                  reinterpret_cast<const uint32_t*>(ws + L.vvals[0]),
+                                  reinterpret_cast<const uint32_t*>(ws + L.vvals[1]), ids, projected, touched);
+  return cuda_status(cudaGetLastError());
+}
+
+extern "C" vg_status vg_read_counters(const void* workspace, size_t workspace_bytes, int64_t* counters,
+                                      vg_stream stream) {
+  if (!workspace || !counters || !aligned(workspace, 256) || workspace_bytes < 256) return VG_ERR_INVALID;
+  note_launches(1);
+  publish_counters<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(static_cast<const WsHeader*>(workspace),
+                                                                        counters);
   return cuda_status(cudaGetLastError());
 }

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     const unsigned* __restrict__ hist, unsigned* next_part, unsigned long long* status_cur,
     unsigned long long* __restrict__ status_next, WsHeader* hdr) {
   constexpr int TILE = kSortThreads * ITEMS;
+  if (render_dead(hdr)) return;   // an earlier look-back gave up: nothing later is sorted
   if (depth) {
     // the depth keys agree above bit 32 - clz(dmin ^ dmax): only the passes below it run
     const unsigned lo = hdr->dmin, hi = hdr->dmax;
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
 __global__ void __launch_bounds__(256) pairs_count(const uint32_t* order0, const uint32_t* order1,
                                                    const uint32_t* __restrict__ touched, const WsHeader* __restrict__ hdr,
                                                    unsigned long long* __restrict__ blocksums) {
+  if (render_dead(hdr)) return;   // pairs_scan then records no pairs
   const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
   unsigned begin, end;
   segment(hdr->visible, begin, end, 256);
@@ -220,6 +222,10 @@ __global__ void __launch_bounds__(256) pairs_count(const uint32_t* order0, const
 
 __global__ void __launch_bounds__(256) pairs_scan(unsigned long long* __restrict__ blocksums, int B, WsHeader* hdr,
                                                   unsigned long long cap) {
+  if (render_dead(hdr)) {          // the depth order may hold unwritten slots: emit nothing
+    if (threadIdx.x == 0) { hdr->pairs = 0; hdr->pair_n = 0; }
+    return;
+  }
   __shared__ unsigned long long sm[8];
   unsigned long long run = 0;
   for (int b0 = 0; b0 < B; b0 += 256) {
@@ -420,6 +426,7 @@ __global__ void __launch_bounds__(256) tile_count(const DevTables* __restrict__ 
                                                   const uint32_t* __restrict__ touched, const uint2* __restrict__ rects,
                                                   const WsHeader* __restrict__ hdr, unsigned* __restrict__ tdiff,
                                                   int tiles) {
+  if (render_dead(hdr)) return;   // every count stays 0: every tile list is empty
   const unsigned nv = hdr->visible;
   tdiff += (size_t)(blockIdx.x % kCountCopies) * tiles;
   const uint32_t lt = lanemask_lt();
@@ -632,8 +639,12 @@ Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
   return L;
 }
 
-Compact make_compact(const Layout& L, char* ws, int total_n) {
+Compact make_compact(const Layout& L, char* ws, int total_n, const vg_raster_opts* opts0) {
   Compact c;
+  c.key_inputs = reinterpret_cast<float4*>(opts0 ? opts0->key_inputs : nullptr);
+  const bool stall = opts0 && (opts0->flags & VG_FLAG_TEST_STALL_LOOKBACK) != 0;
+  c.stall_block = stall ? 0 : -1;
+  c.wait_ns = stall ? 2000000ull : 1000000000ull;
   c.vkeys = reinterpret_cast<uint32_t*>(ws + L.vkeys[0]);
   c.vvals = reinterpret_cast<uint32_t*>(ws + L.vvals[0]);
   c.vis_ids = reinterpret_cast<uint32_t*>(ws + L.vis_ids);

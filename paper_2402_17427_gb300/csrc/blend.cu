@@ -188,6 +188,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
   __shared__ __align__(128) Splat buf[2][kCh];
   __shared__ int s_item;
   unsigned long long ev = 0, bl = 0, xr = 0;
+  const bool dead = render_dead(hdr);   // a look-back gave up: every list counts as empty
   const int lane = threadIdx.x & 31;
   for (;;) {
     const int item = next_item(&hdr->work_fwd[S::kClass], item_count, &s_item);
@@ -202,7 +203,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
     const bool rule0 = vw.op.stop_rule == 0;
     float wcx, wcy, whw, whh;
     warp_block<TS, false>(tx, ty, wcx, wcy, whw, whh);
-    const uint2 rg = ranges[tile];
+    const uint2 rg = dead ? make_uint2(0u, 0u) : ranges[tile];
     const int n = (int)(rg.y - rg.x);
     const int ch = vw.op.chunk;
 
@@ -392,7 +393,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
   }
 }
 
-template <int TS, bool ABS>
+template <int TS, bool ABS, bool COUNT>
 __global__ void __launch_bounds__(TileShape<TS, true>::kThreads)
 blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ vsplats,
                       const uint32_t* __restrict__ lists, const uint2* __restrict__ ranges,
@@ -400,10 +401,12 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
                       const uint32_t* dorder0, const uint32_t* dorder1, WsHeader* __restrict__ hdr) {
   using S = TileShape<TS, true>;
   const uint32_t* __restrict__ dorder = depth_order(hdr, dorder0, dorder1);
+  const bool dead = render_dead(hdr);   // a look-back gave up: every list counts as empty
   __shared__ __align__(128) Splat buf[2][kCh];
   __shared__ int s_item;
   __shared__ unsigned s_maxlast;
   const int lane = threadIdx.x & 31;
+  unsigned long long xr = 0;   // pixel slots evaluated (COUNT)
   for (;;) {
     const int item = next_item(&hdr->work_bwd[S::kClass], item_count, &s_item);
     if (item < 0) break;
@@ -416,7 +419,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
     const float lamin = log2f(vw.op.alpha_min);
     float wcx, wcy, whw, whh;
     warp_block<TS, true>(tx, ty, wcx, wcy, whw, whh);
-    const uint2 rg = ranges[tile];
+    const uint2 rg = dead ? make_uint2(0u, 0u) : ranges[tile];
     const uint32_t list_len = rg.y - rg.x;
     const int ch = vw.op.chunk;
     // per pixel: T (transmittance, walked back to front), G (dL/dpixel colour) and
@@ -504,6 +507,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
           live &= ~(1u << bit);
           const int j = jb + bit;
           const uint32_t pos = (uint32_t)(lo + j);
+          if (COUNT) xr += S::kPPT;
           const float4 f0 = *reinterpret_cast<const float4*>(&cb[j].u);
           const float4 f2 = *reinterpret_cast<const float4*>(&cb[j].b);
           const float4 f1 = *reinterpret_cast<const float4*>(&cb[j].cc);
@@ -635,6 +639,11 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
       __syncthreads();
     }
   }
+  if (COUNT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) xr += __shfl_xor_sync(0xffffffffu, xr, o);
+    if (lane == 0) atomicAdd(&hdr->evals_run_bwd, xr);
+  }
 }
 
 __global__ void zero_g2d(float* __restrict__ g2d, const WsHeader* __restrict__ hdr) {
@@ -644,6 +653,7 @@ __global__ void zero_g2d(float* __restrict__ g2d, const WsHeader* __restrict__ h
 
 __global__ void reset_bwd_queues(WsHeader* hdr) {
   if (threadIdx.x < kTileClasses) hdr->work_bwd[threadIdx.x] = 0;
+  if (threadIdx.x == 0) hdr->evals_run_bwd = 0;
 }
 
 template <typename K>
@@ -675,22 +685,29 @@ cudaError_t fwd_class(const DevTables* tab, const HostPlan& plan, const Splat* v
   return cudaGetLastError();
 }
 
+template <int TS, bool ABS, bool COUNT>
+void bwd_launch(const DevTables* tab, const Splat* vsplats, const uint32_t* lists, const uint2* ranges,
+                const uint32_t* order, int begin, int items, float* g2d, const uint32_t* d0, const uint32_t* d1,
+                WsHeader* hdr, cudaStream_t s) {
+  using S = TileShape<TS, true>;
+  auto k = blend_backward_kernel<TS, ABS, COUNT>;
+  k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, g2d,
+                                                                 d0, d1, hdr);
+}
+
 template <int TS>
 cudaError_t bwd_class(const DevTables* tab, const HostPlan& plan, const Splat* vsplats, const uint32_t* lists,
                       const uint2* ranges, const uint32_t* order, float* g2d, const uint32_t* d0, const uint32_t* d1,
-                      WsHeader* hdr, bool abs, cudaStream_t s) {
+                      WsHeader* hdr, bool abs, bool count, cudaStream_t s) {
   using S = TileShape<TS, true>;
   const int items = plan.class_tiles[S::kClass];
   if (items == 0) return cudaSuccess;
   note_launches(1);
   const int begin = plan.class_begin[S::kClass];
-  if (abs) {
-    auto k = blend_backward_kernel<TS, true>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, g2d, d0, d1, hdr);
-  } else {
-    auto k = blend_backward_kernel<TS, false>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, g2d, d0, d1, hdr);
-  }
+  if (abs && count) bwd_launch<TS, true, true>(tab, vsplats, lists, ranges, order, begin, items, g2d, d0, d1, hdr, s);
+  else if (abs) bwd_launch<TS, true, false>(tab, vsplats, lists, ranges, order, begin, items, g2d, d0, d1, hdr, s);
+  else if (count) bwd_launch<TS, false, true>(tab, vsplats, lists, ranges, order, begin, items, g2d, d0, d1, hdr, s);
+  else bwd_launch<TS, false, false>(tab, vsplats, lists, ranges, order, begin, items, g2d, d0, d1, hdr, s);
   return cudaGetLastError();
 }
 
@@ -710,7 +727,7 @@ cudaError_t launch_blend_forward(const DevTables* tab, const HostPlan& plan, con
 }
 
 cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool abs,
-                                  cudaStream_t s) {
+                                  bool count, cudaStream_t s) {
   const Splat* vsplats = reinterpret_cast<const Splat*>(ws + L.vsplats);
   const uint32_t* lists = reinterpret_cast<const uint32_t*>(ws + L.pvals[0]);   // final tile-sorted ranks
   const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.ranges);
@@ -722,9 +739,9 @@ cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, co
   note_launches(2);
   const uint32_t* d0 = reinterpret_cast<const uint32_t*>(ws + L.vvals[0]);
   const uint32_t* d1 = reinterpret_cast<const uint32_t*>(ws + L.vvals[1]);
-  cudaError_t e = bwd_class<8>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, s);
-  if (e == cudaSuccess) e = bwd_class<16>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, s);
-  if (e == cudaSuccess) e = bwd_class<32>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, s);
+  cudaError_t e = bwd_class<8>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, count, s);
+  if (e == cudaSuccess) e = bwd_class<16>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, count, s);
+  if (e == cudaSuccess) e = bwd_class<32>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, count, s);
   return e;
 }
 

@@ -115,6 +115,7 @@ struct WsHeader {
   unsigned int work_fwd[kTileClasses];   // persistent-blend work queues (next item)
   unsigned int work_bwd[kTileClasses];
   unsigned int pad[3];
+  unsigned long long evals_run_bwd;  // pixel slots the backward pass evaluated (optional count)
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
@@ -199,10 +200,19 @@ struct Compact {
   unsigned long long* status;      // one look-back word per block (cleared by the launcher)
   unsigned long long* zero;        // look-back rows of the first depth pass, cleared here
   size_t zero_words;
+  float4* key_inputs;              // optional [total_n]: (u, v, r, depth) the keys were decided from
+  int stall_block;                 // block that withholds its look-back status (tests only), else -1
+  unsigned long long wait_ns;      // limit of each look-back wait
 };
+// Every kernel after the first look-back of a render checks this once: after a wait gave up the
+// compacted and sorted arrays may hold unwritten slots, so no stage may index with them.
+__device__ __forceinline__ bool render_dead(const WsHeader* hdr) {
+  return (*(volatile const unsigned*)&hdr->status & VG_STATUS_WAIT_TIMEOUT) != 0u;
+}
 cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Splat* splats, uint2* rects,
                               uint32_t* touched, const Compact& cp, WsHeader* hdr, cudaStream_t s);
-Compact make_compact(const Layout& L, char* ws, int total_n);   // regions of the workspace
+// Regions of the workspace; opts0 supplies the optional key-input record and the test stall.
+Compact make_compact(const Layout& L, char* ws, int total_n, const vg_raster_opts* opts0);
 // Adjoint of the projection for the visible Gaussians (gradients of the culled ones are left
 // to launch_zero_culled, or untouched when accumulating).  Sized to leave launch_zero_culled
 // room to run beside it when not accumulating.
@@ -221,7 +231,7 @@ cudaError_t launch_binning(const DevTables* tab, int total_n, int total_tiles, i
 cudaError_t launch_blend_forward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool count,
                                  cudaStream_t s);
 cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool abs,
-                                  cudaStream_t s);
+                                  bool count, cudaStream_t s);
 
 // Non-blocking streams per device (created on first use) for work that overlaps the caller's
 // stream; callers fork to them and join back with events within the same call.

@@ -268,7 +268,8 @@ template <bool kAppear>
 __device__ __forceinline__ void ssim_backward_body(const float* __restrict__ x, const float* __restrict__ y,
                                                    const float* __restrict__ maps, int W, int H, Win win,
                                                    float l1_scale, float* __restrict__ grad,
-                                                   const float* __restrict__ pool_grad, int pw, int ph) {
+                                                   const float* __restrict__ pool_grad, int pw, int ph,
+                                                   const float* __restrict__ scale = nullptr) {
   __shared__ __align__(16) float2 s2[3][NRP][QPB];   // map f on rows 2p, 2p + 1
   __shared__ __align__(16) float hs[3][LTH * LT];
   const int c = blockIdx.z;
@@ -316,6 +317,7 @@ __device__ __forceinline__ void ssim_backward_body(const float* __restrict__ x, 
 #pragma unroll
     for (int f = 0; f < 3; ++f) v[f] = hs[f][hs_at(r0 + i, q)];
   }, cm);
+  const float sc = scale ? __ldg(scale) : 1.f;   // the incoming gradient of the loss, if given
   float gs[GV];       // kAppear: the gradient already there, read late to keep the passes' registers
   if constexpr (kAppear) {
 #pragma unroll
@@ -338,7 +340,8 @@ __device__ __forceinline__ void ssim_backward_body(const float* __restrict__ x, 
     } else {
       const float d = xv - yv;
       const float l1g = d > 0.f ? l1_scale : (d < 0.f ? -l1_scale : 0.f);
-      grad[pix] = l1g + cm[0][j] + 2.f * xv * cm[1][j] + yv * cm[2][j];
+      const float gv = l1g + cm[0][j] + 2.f * xv * cm[1][j] + yv * cm[2][j];
+      grad[pix] = scale ? gv * sc : gv;
     }
   }
 }
@@ -348,8 +351,9 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
                                                                      const float* __restrict__ y,
                                                                      const float* __restrict__ maps, int W, int H,
                                                                      Win win, float l1_scale,
-                                                                     float* __restrict__ grad) {
-  ssim_backward_body<kAppear>(x, y, maps, W, H, win, l1_scale, grad, nullptr, 0, 0);
+                                                                     float* __restrict__ grad,
+                                                                     const float* __restrict__ scale = nullptr) {
+  ssim_backward_body<kAppear>(x, y, maps, W, H, win, l1_scale, grad, nullptr, 0, 0, scale);
 }
 
 // The gradient pass of Eq. 3's loss.  Held to 128 registers a thread (4 blocks an SM, as the
@@ -452,6 +456,23 @@ extern "C" vg_status vg_loss_l1_dssim(const float* img, const float* target, int
   return e == cudaSuccess ? VG_OK : VG_ERR_CUDA;
 }
 
+extern "C" vg_status vg_loss_l1_dssim_grad(const float* img, const float* target, int32_t width, int32_t height,
+                                           float lambda, const void* workspace, size_t workspace_bytes,
+                                           const float* scale, float* out_grad, vg_stream stream) {
+  if (!img || !target || !workspace || !out_grad || width <= 0 || height <= 0 || !(lambda >= 0.f && lambda <= 1.f))
+    return VG_ERR_INVALID;
+  if (workspace_bytes < vg_loss_workspace_bytes(width, height)) return VG_ERR_CAPACITY;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t plane = (size_t)width * height;
+  const float* maps = static_cast<const float*>(workspace);
+  const dim3 grid((width + LT - 1) / LT, (height + LT - 1) / LT, 3);
+  const double inv = 1.0 / (3.0 * (double)plane);
+  note_launches(1);
+  ssim_backward_kernel<false><<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, make_window(),
+                                                            (float)((1.0 - lambda) * inv), out_grad, scale);
+  return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;
+}
+
 // ----------------------------------------------------------------------------------------------
 // Allocation-free variant of the loss entry point.
 //
@@ -474,21 +495,61 @@ constexpr size_t kNoAllocBytes = kNoAllocMapBytes + kNoAllocMaxBlocks * 2 * size
 
 static __device__ __align__(256) unsigned char g_loss_scratch[kNoAllocBytes];
 
-// Device address of g_loss_scratch on each device, looked up once per device (with that device
-// current) on the first call made there.
+// Device address of g_loss_scratch, looked up (cudaGetSymbolAddress, with the device current) on
+// the first call in each CUDA context and cached per device together with that context's unique
+// id.  A device reset or a new primary context loads the module again, possibly at another
+// address, so a call made in a different context than the cached one looks the address up again.
+// The context id comes from the driver (cuCtxGetCurrent, cuCtxGetId) through the runtime's
+// entry-point query, so the library needs no link-time dependency on the driver library; where
+// that query is unavailable the address is looked up on every call.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  void* ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
+struct ScratchSlot {
+  void* addr = nullptr;
+  unsigned long long ctx_id = 0;
+};
 std::mutex g_scratch_mu;
-void* g_scratch_addr[64] = {nullptr};
+ScratchSlot g_scratch_slot[64];
 
 vg_status loss_scratch(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return VG_ERR_CUDA;
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchSlot& sl = g_scratch_slot[dev];
+  if (!sl.addr || !have_id || sl.ctx_id != id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_loss_scratch) != cudaSuccess || !p) return VG_ERR_CUDA;
-    g_scratch_addr[dev] = p;
+    unsigned long long now = 0;
+    // the lookup may have created the context: key the cache on the context it used
+    sl.addr = current_context_id(&now) ? p : nullptr;
+    sl.ctx_id = now;
+    *out = p;
+    return VG_OK;
   }
-  *out = g_scratch_addr[dev];
+  *out = sl.addr;
   return VG_OK;
 }
 

@@ -280,12 +280,15 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __rest
       }
     }
     touched[i] = cnt;
+    if (cp.key_inputs)
+      cp.key_inputs[i] = P.valid ? make_float4(P.u, P.v, P.r, P.depth) : make_float4(0.f, 0.f, -1.f, 0.f);
   }
   // 2. the block's visible count, published before the heavy per-Gaussian work so that later
   //    blocks rarely wait in their look-back
   unsigned tot;
   const unsigned ex = block_exclusive_scan((unsigned)vis, &tot, s_sm);
-  if (threadIdx.x == 0) st_relaxed(cp.status + blk, (blk == 0 ? kFlagPrefix : kFlagAggregate) | tot);
+  const bool publish = (int)blk != cp.stall_block;
+  if (threadIdx.x == 0 && publish) st_relaxed(cp.status + blk, (blk == 0 ? kFlagPrefix : kFlagAggregate) | tot);
   // 3. the splat record: colour from spherical harmonics along the viewing direction, opacity,
   //    the accurate blending position and the alpha >= alpha_min box
   if (vis) {
@@ -376,12 +379,12 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __rest
         excl += part;
         if (done) break;
         p -= take;
-        if (take == 0 && global_timer_ns() - start > 1000000000ull) {   // a predecessor never published
+        if (take == 0 && global_timer_ns() - start > cp.wait_ns) {   // a predecessor never published
           if (lane == 0) atomicOr(&hdr->status, (unsigned)VG_STATUS_WAIT_TIMEOUT);
           break;
         }
       }
-      if (lane == 0) st_relaxed(cp.status + blk, kFlagPrefix | (excl + tot));
+      if (lane == 0 && publish) st_relaxed(cp.status + blk, kFlagPrefix | (excl + tot));
     }
     if (lane == 0) {
       s_base = excl;
@@ -635,6 +638,7 @@ template <int DEG>
 __global__ void __launch_bounds__(128, 4) preprocess_backward_kernel(
     const DevTables* __restrict__ tab, const uint32_t* __restrict__ vis_ids, const WsHeader* __restrict__ hdr,
     const Splat* __restrict__ splats, const float* __restrict__ g2d, int accumulate) {
+  if (render_dead(hdr)) return;   // the compacted list may hold unwritten slots
   const int nv = (int)hdr->visible;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += gridDim.x * blockDim.x)
     project_adjoint<DEG>(tab, splats, g2d, accumulate, (int)vis_ids[t]);

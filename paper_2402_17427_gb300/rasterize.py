@@ -32,6 +32,7 @@ class RasterSettings:
     guard: float = 1.3
     stop_rule: int = 0
     count_blends: bool = False
+    test_stall: bool = False      # diagnostic: make the compaction's look-back give up (tests only)
 
     def c(self, accumulate: bool = False) -> B.vg_raster_opts:
         o = B.vg_raster_opts()
@@ -40,7 +41,8 @@ class RasterSettings:
         o.dilation, o.alpha_max, o.alpha_min = self.dilation, self.alpha_max, self.alpha_min
         o.t_min, o.guard, o.stop_rule = self.t_min, self.guard, self.stop_rule
         o.flags = (B.VG_FLAG_COUNT_BLENDS if self.count_blends else 0) | \
-                  (B.VG_FLAG_ACCUMULATE_GRADS if accumulate else 0)
+                  (B.VG_FLAG_ACCUMULATE_GRADS if accumulate else 0) | \
+                  (B.VG_FLAG_TEST_STALL_LOOKBACK if self.test_stall else 0)
         return o
 
 
@@ -105,10 +107,17 @@ class Rasterizer:
         self.counters = None
         self._pending = []
 
-    def forward(self, means, log_scales, quats, logits, sh, degree, cam: Camera, events=None):
+    def forward(self, means, log_scales, quats, logits, sh, degree, cam: Camera, events=None, key_inputs=None):
+        """key_inputs: optional float32 CUDA tensor [n, 4] that receives the FP32 (u, v, r, depth)
+        each Gaussian's tile rectangle and sort key were decided from (parity tests)."""
         opts = self.settings.c()
         if events is not None:
             opts.events = ctypes.pointer(events)
+        if key_inputs is not None:
+            if not (key_inputs.is_cuda and key_inputs.dtype == torch.float32 and key_inputs.is_contiguous()
+                    and key_inputs.numel() >= 4 * int(means.shape[0])):
+                raise ValueError("key_inputs must be a contiguous float32 CUDA tensor of n x 4 entries")
+            opts.key_inputs = key_inputs.data_ptr()
         g = gaussians_c(means, log_scales, quats, logits, sh, degree)
         camc = camera_c(cam)
         dev = means.device
@@ -116,7 +125,7 @@ class Rasterizer:
         rgb = torch.empty((3, H, W), dtype=torch.float32, device=dev)
         T = torch.empty((H, W), dtype=torch.float32, device=dev)
         last = torch.empty((H, W), dtype=torch.int32, device=dev)
-        counters = torch.zeros(B.VG_CNT_LEN, dtype=torch.int64, device=dev)
+        counters = torch.empty(B.VG_CNT_LEN, dtype=torch.int64, device=dev)   # every entry written by the call
         for _attempt in range(4):
             buf, nbytes = self.ws.ensure(g.n, W, H, opts)
             B.vg_rasterize_forward(g, camc, opts, buf.data_ptr(), nbytes, self.ws.capacity, rgb.data_ptr(),
@@ -189,12 +198,18 @@ class LossL1DSSIM:
         self.buf = None
         self.loss = None
         self.grad = None
+        self.calls = 0          # forward calls on this workspace (the SSIM maps they leave behind)
 
-    def __call__(self, img: torch.Tensor, target: torch.Tensor, reuse: bool = False):
+    def _workspace(self, img):
         _, H, W = img.shape
         need = B.vg_loss_workspace_bytes(W, H)
         if self.buf is None or self.buf.numel() < need:
             self.buf = torch.empty(need, dtype=torch.uint8, device=img.device)
+        self.calls += 1
+        return W, H
+
+    def __call__(self, img: torch.Tensor, target: torch.Tensor, reuse: bool = False):
+        W, H = self._workspace(img)
         if reuse and self.grad is not None and self.grad.shape == img.shape:
             loss, grad = self.loss, self.grad
         else:
@@ -205,18 +220,42 @@ class LossL1DSSIM:
                            self.buf.data_ptr(), self.buf.numel(), loss.data_ptr(), grad.data_ptr(), _stream())
         return loss, grad
 
+    def value(self, img: torch.Tensor, target: torch.Tensor):
+        """The loss alone; the workspace keeps what grad_scaled needs."""
+        W, H = self._workspace(img)
+        loss = torch.empty((), dtype=torch.float32, device=img.device)
+        B.vg_loss_l1_dssim(img.data_ptr(), target.data_ptr(), W, H, self.lam, self.buf.data_ptr(), self.buf.numel(),
+                           loss.data_ptr(), None, _stream())
+        return loss
+
+    def grad_scaled(self, img: torch.Tensor, target: torch.Tensor, scale: torch.Tensor, buf: torch.Tensor):
+        """scale * dL/dimage from the state the last value() call left in `buf`."""
+        _, H, W = img.shape
+        grad = torch.empty_like(img)
+        B.vg_loss_l1_dssim_grad(img.data_ptr(), target.data_ptr(), W, H, self.lam, buf.data_ptr(), buf.numel(),
+                                scale.data_ptr(), grad.data_ptr(), _stream())
+        return grad
+
 
 class _LossFn(torch.autograd.Function):
+    """Forward computes the loss only; backward runs the gradient pass scaled on the device by the
+    incoming gradient (no separate elementwise product)."""
+
     @staticmethod
     def forward(ctx, img, target, lossobj):
-        loss, grad = lossobj(img, target)
-        ctx.save_for_backward(grad)
+        img, target = img.contiguous(), target.contiguous()
+        loss = lossobj.value(img, target)
+        ctx.save_for_backward(img, target)
+        ctx.lossobj, ctx.buf, ctx.call = lossobj, lossobj.buf, lossobj.calls
         return loss
 
     @staticmethod
     def backward(ctx, g):
-        (grad,) = ctx.saved_tensors
-        return grad * g, None, None
+        img, target = ctx.saved_tensors
+        if ctx.lossobj.buf is ctx.buf and ctx.lossobj.calls != ctx.call:
+            raise RuntimeError("the loss workspace was used by another forward before this backward")
+        scale = g.detach().to(torch.float32).contiguous()
+        return ctx.lossobj.grad_scaled(img, target, scale, ctx.buf), None, None
 
 
 def l1_dssim_loss(img, target, lam: float = 0.2, lossobj: LossL1DSSIM | None = None):

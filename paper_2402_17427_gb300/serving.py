@@ -41,6 +41,7 @@ class ServeStats:
     batches: int
     mean_batch: float
     max_inflight: int
+    max_inflight_bytes: int
     rerenders: int
     mean_cells_per_view: float
 
@@ -48,6 +49,22 @@ class ServeStats:
         d = dataclasses.asdict(self)
         d.pop("latencies_ms")
         return d
+
+
+def admit(queue_bytes, inflight_bytes: int, any_inflight: bool, budget: int, max_batch: int) -> int:
+    """How many requests from the head of the queue (their in-flight device bytes, in arrival order)
+    the next batch takes: as many as fit the memory budget next to what is already in flight, up
+    to max_batch.  A request larger than the whole budget is still served, alone, once nothing else
+    is in flight; otherwise requests that do not fit wait in the queue."""
+    k, est = 0, 0
+    for e in queue_bytes:
+        if k == max_batch:
+            break
+        if inflight_bytes + est + e > budget and (k > 0 or any_inflight):
+            break
+        k += 1
+        est += e
+    return k
 
 
 class _Slot:
@@ -72,18 +89,25 @@ class SceneServer:
         self.slots = [_Slot(self.device) for _ in range(slots)]
         self.max_batch = max_batch
         self.budget = int(mem_budget_gb * (1 << 30))
-        self.ppm = pairs_per_mpix           # running estimate of (Gaussian, tile) pairs per megapixel
+        self.ppm0 = pairs_per_mpix           # prior before the first observation
+        self.ppm = None                      # largest (Gaussian, tile) pairs per megapixel seen
         self.resident_bytes = sum(sum(t.numel() * 4 for t in p) for p in self.params)
 
     # -------------------------------------------------------------------------------- one batch
+    def _ppm(self) -> float:
+        return self.ppm if self.ppm is not None else self.ppm0
+
     def _capacity(self, cams):
-        """Pair-list capacity for a batch: its megapixels times the running pairs-per-megapixel."""
+        """Pair-list capacity for a batch: its megapixels times the largest pairs-per-megapixel any
+        batch has needed so far (never lowered, so a capacity that held once holds again), with a
+        25 % margin."""
         mpix = sum(c.width * c.height for c in cams) / 1e6
-        return max(1 << 16, int(mpix * self.ppm * 1.5))
+        return max(1 << 16, int(mpix * self._ppm() * 1.25))
 
     def _observe(self, cams, counters):
         mpix = sum(c.width * c.height for c in cams) / 1e6
-        self.ppm = max(0.9 * self.ppm, float(counters[B.VG_CNT_PAIRS]) / max(mpix, 1e-6))
+        seen = float(counters[B.VG_CNT_PAIRS]) / max(mpix, 1e-6)
+        self.ppm = seen if self.ppm is None else max(self.ppm, seen)
 
     def _launch(self, slot: _Slot, cams, capacity: int):
         opts = [self.settings.c() for _ in cams]
@@ -97,7 +121,7 @@ class SceneServer:
             outs = [(torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.device),
                      torch.empty((c.height, c.width), dtype=torch.float32, device=self.device),
                      torch.empty((c.height, c.width), dtype=torch.int32, device=self.device)) for c in cams]
-            counters = torch.zeros(B.VG_CNT_LEN, dtype=torch.int64, device=self.device)
+            counters = torch.empty(B.VG_CNT_LEN, dtype=torch.int64, device=self.device)   # all written by the call
             kept = B.vg_render_views(self.gs, self.aabbs, camc, opts, slot.buf.data_ptr(), need, capacity,
                                      [o[0].data_ptr() for o in outs], [o[1].data_ptr() for o in outs],
                                      [o[2].data_ptr() for o in outs], counters.data_ptr(), slot.stream.cuda_stream)
@@ -128,7 +152,7 @@ class SceneServer:
         """Device memory one request holds while in flight: its image buffers and its share of
         the batch workspace (pairs at 64 B, visible Gaussians at about 200 B)."""
         px = cam.width * cam.height
-        return 20 * px + int(64 * 1.5 * self.ppm * px / 1e6) + int(200 * self.n.sum() / 4)
+        return 20 * px + int(64 * 1.25 * self._ppm() * px / 1e6) + int(200 * self.n.sum() / 4)
 
     def serve(self, requests, keep_outputs: bool = False, time_limit_s: float | None = None,
               warmup_s: float = 0.0):
@@ -145,6 +169,7 @@ class SceneServer:
         batch_sizes = []
         rerenders = 0
         max_inflight = 0
+        max_inflight_bytes = 0
         kept_cells = []
         inflight_bytes = 0
         torch.cuda.synchronize(self.device)
@@ -178,14 +203,13 @@ class SceneServer:
                         outputs[r.rid] = o
             # admission: a free slot and room in the memory budget
             free = [s for s in self.slots if not s.busy]
+            k = 0
             if queue and free:
-                batch, est = [], 0
-                while queue and len(batch) < self.max_batch:
-                    e = self._bytes(queue[0].camera)
-                    if batch and inflight_bytes + est + e > self.budget:
-                        break
-                    batch.append(queue.popleft())
-                    est += e
+                head = [self._bytes(queue[i].camera) for i in range(min(len(queue), self.max_batch))]
+                k = admit(head, inflight_bytes, bool(inflight), self.budget, self.max_batch)
+            if k > 0:
+                batch = [queue.popleft() for _ in range(k)]
+                est = sum(head[:k])
                 slot = free[0]
                 cams = [r.camera for r in batch]
                 outs, counters, ev, kept, _ = self._launch(slot, cams, self._capacity(cams))
@@ -196,6 +220,7 @@ class SceneServer:
                 batches += 1
                 batch_sizes.append(len(batch))
                 max_inflight = max(max_inflight, len(inflight))
+                max_inflight_bytes = max(max_inflight_bytes, inflight_bytes)
                 continue
             # nothing to do right now: wait briefly for an arrival or a completion
             if inflight or (nxt < len(reqs)):
@@ -211,6 +236,7 @@ class SceneServer:
                            p50_ms=float(np.percentile(L, 50)), p99_ms=float(np.percentile(L, 99)),
                            mean_ms=float(L.mean()), throughput_rps=len(served) / dur, mpix_per_s=mpix / dur,
                            batches=batches, mean_batch=float(np.mean(batch_sizes)) if batch_sizes else 0.0,
-                           max_inflight=max_inflight, rerenders=rerenders,
+                           max_inflight=max_inflight, max_inflight_bytes=int(max_inflight_bytes),
+                           rerenders=rerenders,
                            mean_cells_per_view=float(np.mean(kept_cells)) if kept_cells else 0.0)
         return (stats, outputs) if keep_outputs else stats

@@ -104,6 +104,45 @@ def reachable_subset(g, cam, tiles, tile_size, guard=1.3, dilation=0.3, margin_p
     return np.nonzero(keep)[0]
 
 
+def conservative_tile_rects(g, cam, tile_size, guard=1.3, dilation=0.3, margin_px=4.0):
+    """For every Gaussian, a tile rectangle that contains every tile its own rectangle can reach
+    (the bound of reachable_subset): returns (ok, tx0, tx1, ty0, ty1), ok false for a Gaussian
+    behind the near plane or whose bound misses the image."""
+    means = np.asarray(g.means, np.float64)
+    R_ = np.asarray(cam.R, np.float64)
+    p = means @ R_.T + np.asarray(cam.t, np.float64)
+    z = p[:, 2]
+    front = z > cam.near * 0.999
+    zs = np.where(front, z, 1.0)
+    limx = guard * 0.5 * cam.width / cam.fx
+    limy = guard * 0.5 * cam.height / cam.fy
+    smax2 = np.exp(2.0 * np.asarray(g.log_scales, np.float64).max(1))
+    tr = ((cam.fx / zs) ** 2 * (1 + limx ** 2) + (cam.fy / zs) ** 2 * (1 + limy ** 2)) * smax2 + 2 * dilation
+    rb = 3.0 * np.sqrt(tr) * 1.001 + margin_px
+    u = cam.fx * p[:, 0] / zs + cam.cx
+    v = cam.fy * p[:, 1] / zs + cam.cy
+    tiles_x = (cam.width + tile_size - 1) // tile_size
+    tiles_y = (cam.height + tile_size - 1) // tile_size
+    x0 = np.floor((u - rb) / tile_size)
+    x1 = np.floor((u + rb) / tile_size)
+    y0 = np.floor((v - rb) / tile_size)
+    y1 = np.floor((v + rb) / tile_size)
+    ok = front & (x1 >= 0) & (x0 <= tiles_x - 1) & (y1 >= 0) & (y0 <= tiles_y - 1)
+    clip = lambda a, hi: np.clip(np.nan_to_num(a, nan=0.0, posinf=hi, neginf=0.0), 0, hi).astype(np.int64)
+    return ok, clip(x0, tiles_x - 1), clip(x1, tiles_x - 1), clip(y0, tiles_y - 1), clip(y1, tiles_y - 1)
+
+
+def subset_reaching(rects, mask, tiles_x, tiles_y):
+    """Indices (ascending) of the Gaussians whose conservative rectangle meets a tile of `mask`
+    (uint8 [tiles]), by a 2D prefix sum over the mask."""
+    ok, x0, x1, y0, y1 = rects
+    m = np.asarray(mask, np.int64).reshape(tiles_y, tiles_x)
+    S = np.zeros((tiles_y + 1, tiles_x + 1), np.int64)
+    S[1:, 1:] = m.cumsum(0).cumsum(1)
+    cnt = S[y1 + 1, x1 + 1] - S[y0, x1 + 1] - S[y1 + 1, x0] + S[y0, x0]
+    return np.nonzero(ok & (cnt > 0))[0]
+
+
 def group_errors(gpu, ref, keep_mask):
     """Per parameter group: relative L2 error over the kept Gaussians, and the worst element
     error normalised by (|ref| + 1e-3 max|ref|)."""

@@ -63,21 +63,25 @@ def test_batch_equals_single_views_mixed_tile_sizes():
 
 @pytest.mark.slow
 def test_aerial_cells_batched_sampled_parity():
-    """Eight uneven cells (0.3M..3.0M Gaussians, 1152x864 nadir views) in one batched call."""
+    """Eight uneven cells (0.3M..3.0M Gaussians, 1152x864 nadir views) in one batched call, each at
+    the tile size and chunk depth the autotuner picked for it (as the benchmark runs them); every
+    cell is checked against the oracle at its own tile size."""
     cells = scenes.aerial_cells(step=3)
-    br = BT.BatchRasterizer()
     params = [R.to_device(c.gaussians) for c in cells]
     cams = [c.camera for c in cells]
+    tuner = BT.AutoTuner()
+    settings = [tuner.choose(p, 3, cam) for p, cam in zip(params, cams)]
+    br = BT.BatchRasterizer(settings)
     outs = br.forward(params, 3, cams)
     rng = np.random.default_rng(1)
     dLs, masks, picks = [], [], []
-    for c in cells:
-        cam = c.camera
-        tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    for c, s in zip(cells, settings):
+        cam, T = c.camera, s.tile_size
+        tx, ty = (cam.width + T - 1) // T, (cam.height + T - 1) // T
         tiles = sorted(set(rng.choice(tx * ty, 3, replace=False).tolist()) | {(ty // 2) * tx + tx // 2})
         m = np.zeros(tx * ty, np.uint8)
         m[tiles] = 1
-        pm = np.repeat(np.repeat(m.reshape(ty, tx).astype(bool), 16, 0), 16, 1)[:cam.height, :cam.width]
+        pm = np.repeat(np.repeat(m.reshape(ty, tx).astype(bool), T, 0), T, 1)[:cam.height, :cam.width]
         w = rng.standard_normal((3, cam.height, cam.width)).astype(np.float32)
         w[:, ~pm] = 0
         dLs.append(w)
@@ -85,18 +89,18 @@ def test_aerial_cells_batched_sampled_parity():
         picks.append((tiles, pm))
     grads = br.backward(params, 3, cams, outs, [torch.from_numpy(d).cuda() for d in dLs])
     torch.cuda.synchronize()
-    for k, c in enumerate(cells):
+    for k, (c, s) in enumerate(zip(cells, settings)):
         g, cam = c.gaussians, c.camera
         tiles, pm = picks[k]
-        sub = reachable_subset(g, cam, tiles, 16)
-        orc = oracle.render(g.subset(sub), cam, oracle.Options(), tile_mask=masks[k])
+        sub = reachable_subset(g, cam, tiles, s.tile_size)
+        orc = oracle.render(g.subset(sub), cam, oracle_opts(s), tile_mask=masks[k])
         amb = orc.amb.astype(bool)
         img = outs[k][0].cpu().numpy()
-        assert np.abs(img - orc.image)[:, pm & ~amb].max() <= 1e-4
+        assert np.abs(img - orc.image)[:, pm & ~amb].max() <= 1e-4, (k, s.tile_size)
         w = dLs[k].copy()
         w[:, amb] = 0
         if amb.any():   # ambiguous pixels were weighted on the GPU: redo that cell's backward alone
-            r, p1, single = run_forward(g, cam)
+            r, p1, single = run_forward(g, cam, s)
             gk = run_backward(r, p1, g, cam, single, w)
         else:
             gk = {n: t.cpu().numpy().astype(np.float64) for n, t in
@@ -106,7 +110,7 @@ def test_aerial_cells_batched_sampled_parity():
         errs = group_errors({n: v[sub] for n, v in gk.items()}, ref, keep)
         for name, (rel, _e, norm) in errs.items():
             if norm > 0:
-                assert rel <= 2e-3, (k, name, errs)
+                assert rel <= 2e-3, (k, s.tile_size, name, errs)
 
 
 def _small_city():

@@ -224,6 +224,67 @@ def test_tile_ranges_follow_from_rectangles(oracle_lib, case):
     assert r.ranges[:, 1].max() == r.num_pairs
 
 
+def _brute_lists(uvrd, W, H, tile):
+    """Per tile, by enumeration of its pixel samples: the Gaussians whose closed box
+    [u - r, u + r] x [v - r, v + r] (edges rounded to FP32 as computed) contains one of the tile's
+    pixels inside the image, ordered by (FP32 depth bits, index)."""
+    tx_n, ty_n = (W + tile - 1) // tile, (H + tile - 1) // tile
+    u, v, r, d = (uvrd[:, k].astype(np.float32) for k in range(4))
+    ok = r >= 0
+    x0, x1 = (u - r).astype(np.float32), (u + r).astype(np.float32)
+    y0, y1 = (v - r).astype(np.float32), (v + r).astype(np.float32)
+    bits = d.view(np.uint32)
+    lists = []
+    for t in range(tx_n * ty_n):
+        ty, tx = divmod(t, tx_n)
+        xs = np.arange(tx * tile, min(W, (tx + 1) * tile), dtype=np.float32)
+        ys = np.arange(ty * tile, min(H, (ty + 1) * tile), dtype=np.float32)
+        hitx = ((xs[None, :] >= x0[:, None]) & (xs[None, :] <= x1[:, None])).any(1)
+        hity = ((ys[None, :] >= y0[:, None]) & (ys[None, :] <= y1[:, None])).any(1)
+        ids = np.nonzero(ok & hitx & hity)[0]
+        lists.append(sorted(ids.tolist(), key=lambda i: (int(bits[i]), i)))
+    return lists
+
+
+@pytest.mark.parametrize("W,H,tile,seed", [(48, 40, 16, 0), (33, 35, 8, 1), (70, 64, 32, 2)])
+def test_pairs_from_fp32_matches_per_pixel_enumeration(oracle_lib, W, H, tile, seed):
+    # given FP32 decision inputs (as another implementation would report them), the oracle's key
+    # generation, stable sort and ranges equal a per-pixel enumeration of each tile; the inputs
+    # include edges on pixel centres, rectangles off every image side, culled entries and exact
+    # depth ties
+    rng = np.random.default_rng(seed)
+    n = 160
+    u = rng.uniform(-20, W + 20, n).astype(np.float32)
+    v = rng.uniform(-20, H + 20, n).astype(np.float32)
+    r = rng.uniform(0.0, 14.0, n).astype(np.float32)
+    u[:20] = np.round(u[:20])                      # u - r, u + r exactly on pixel samples
+    r[:20] = np.round(r[:20])
+    r[20:30] = -1.0                                # culled
+    d = rng.uniform(0.5, 3.0, n).astype(np.float32)
+    d[30:60:2] = d[31:61:2]                        # exact depth ties
+    uvrd = np.stack([u, v, r, d], 1)
+    keys, ids, ranges = oracle_lib.pairs_from_fp32(uvrd, W, H, tile)
+    want = _brute_lists(uvrd, W, H, tile)
+    assert ranges[:, 1].max() == len(ids) == sum(len(x) for x in want)
+    for t, lst in enumerate(want):
+        s, e = ranges[t]
+        assert ids[s:e].tolist() == lst, t
+        if not lst:
+            assert s == e == 0
+    assert np.all(keys[1:] >= keys[:-1])
+
+
+def test_pairs_from_fp32_reproduces_the_forward_lists(oracle_lib):
+    # the forward pass's own FP32 decision inputs give back its own lists
+    g, cam, _ = scenes.small_cell(0)
+    r = oracle_lib.render(g, cam)
+    rec = r.rec
+    uvrd = np.stack([rec["u32"], rec["v32"], np.where(rec["valid"], rec["r32"], -1.0), rec["depth32"]], 1)
+    keys, ids, ranges = oracle_lib.pairs_from_fp32(uvrd, cam.width, cam.height, 16)
+    assert np.array_equal(keys, r.keys) and np.array_equal(ids, r.vals)
+    assert np.array_equal(ranges, r.ranges)
+
+
 # ------------------------------------------------------------------ invariants
 
 def test_transmittance_monotone_and_bounded(oracle_lib):
@@ -307,6 +368,60 @@ def test_adjoint_matches_central_differences(oracle_lib, seed, deg):
     w = np.random.default_rng(seed).standard_normal((3, 32, 32))
     rep = _fd_check(oracle_lib, g, cam, w)
     assert all(v >= 20 for k, v in rep.items() if k != "logits") and rep["logits"] >= 15
+
+
+def _group_dirs(rng, sc, ids, group):
+    """One direction per target over one parameter group (random signs, scaled by max(1, |theta|)),
+    in the raw-parameter layout mean 3, log-scale 3, quaternion 4, logit 1, SH 3K."""
+    F = 11 + 3 * sc.K
+    spans = {"means": (0, 3), "log_scales": (3, 6), "quats": (6, 10), "logits": (10, 11), "sh": (11, F)}
+    a, b = spans[group]
+    dirs = np.zeros((len(ids), F))
+    flat = np.concatenate([sc.means, sc.log_scales, sc.quats, sc.logits[:, None], sc.sh.reshape(sc.n, -1)], 1)
+    dirs[:, a:b] = rng.choice([-1.0, 1.0], (len(ids), b - a)) * np.maximum(1.0, np.abs(flat[ids, a:b]))
+    return dirs
+
+
+def test_tile_local_differences_equal_full_renders_and_the_adjoint(oracle_lib):
+    # re-rendering only the perturbed Gaussian's tiles gives the full loss difference (every other
+    # pixel is unchanged), and the directional derivative equals the adjoint's
+    g, cam, _ = scenes.tiny_scene(n=60, width=64, height=48, degree=2, seed=13)
+    sc = oracle_lib.Scene64.of(g)
+    r0 = oracle_lib.render(sc, cam)
+    w = np.random.default_rng(3).standard_normal((3, 48, 64))
+    grads = r0.backward(w)
+    rng = np.random.default_rng(4)
+    vis = np.nonzero(r0.rec["visible"])[0]
+    ids = rng.choice(vis, min(12, len(vis)), replace=False)
+    eps = 1e-6
+    flat_names = ["means", "log_scales", "quats", "logits", "sh"]
+    used = 0
+    for group in flat_names:
+        dirs = _group_dirs(rng, sc, ids, group)
+        fd, flags = r0.fd_directional(w, ids, dirs, eps)
+        G = np.concatenate([grads["means"], grads["log_scales"], grads["quats"], grads["logits"][:, None],
+                            grads["sh"].reshape(sc.n, -1)], 1)
+        for k, i in enumerate(ids):
+            if flags[k]:
+                continue
+            # the same difference from two full renders of the perturbed scene
+            full = []
+            for e in (eps, -eps):
+                sp = oracle_lib.Scene64(sc.means.copy(), sc.log_scales.copy(), sc.quats.copy(), sc.logits.copy(),
+                                        sc.sh.copy(), sc.sh_degree)
+                d = dirs[k]
+                sp.means[i] += e * d[0:3]
+                sp.log_scales[i] += e * d[3:6]
+                sp.quats[i] += e * d[6:10]
+                sp.logits[i] += e * d[10]
+                sp.sh[i] += e * d[11:].reshape(sc.K, 3)
+                full.append((oracle_lib.render(sp, cam).image * w).sum())
+            fd_full = (full[0] - full[1]) / (2 * eps)
+            assert abs(fd[k] - fd_full) <= 1e-7 * (abs(fd_full) + 1.0), (group, i, fd[k], fd_full)
+            an = float(G[i] @ dirs[k])
+            assert abs(fd[k] - an) <= 1e-6 * (abs(an) + np.abs(G[i] * dirs[k]).sum()) + 1e-9, (group, i, fd[k], an)
+            used += 1
+    assert used >= 40
 
 
 def test_adjoint_guard_band_and_white_background(oracle_lib):

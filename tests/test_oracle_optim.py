@@ -18,6 +18,34 @@ def test_adam_constant_gradient_closed_form():
         assert np.allclose(p, -t * lr * gd / (np.abs(gd) + eps), rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("betas,eps", [((0.9, 0.999), 1e-15), ((0.8, 0.95), 1e-8)])
+def test_adam_matches_torch_optim_adam(betas, eps):
+    # an independent implementation (torch.optim.Adam, FP64 on the CPU) over several steps of
+    # gradients that change sign and magnitude from step to step, with elements small enough that
+    # eps matters next to sqrt(v): swapped betas, eps inside the square root or a missing bias
+    # correction each fail this
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    n = 64
+    p0 = rng.normal(0.0, 1.0, n)
+    scale = np.concatenate([np.full(n // 2, 1e-2), np.full(n // 4, 1e-9), np.full(n - n // 2 - n // 4, 1e-14)])
+    lr = 0.003
+    pt = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([pt], lr=lr, betas=betas, eps=eps)
+    p, m, v = p0.copy(), np.zeros(n), np.zeros(n)
+    for t in range(1, 8):
+        g = (rng.standard_normal(n) * scale * (1.0 + t)).astype(np.float32)
+        opt.zero_grad()
+        pt.grad = torch.tensor(g.astype(np.float64))
+        opt.step()
+        p, m, v = OO.adam_step(p, g, m, v, lr, t, b1=betas[0], b2=betas[1], eps=eps)
+        ref = pt.detach().numpy()
+        assert np.allclose(p, ref, rtol=1e-12, atol=1e-15 * lr), (t, np.abs(p - ref).max())
+        st = opt.state[pt]
+        assert np.allclose(m, st["exp_avg"].numpy(), rtol=1e-12, atol=0)
+        assert np.allclose(v, st["exp_avg_sq"].numpy(), rtol=1e-12, atol=0)
+
+
 def test_accumulate_sums_normalised_norms():
     acc, cnt = OO.accumulate(np.zeros(4), np.zeros(4, np.int64), [1, 3, 1], [3.0, 0.0, -1.0], [0.0, 2.0, 0.0],
                              width=2, height=4)

@@ -65,3 +65,11 @@ def test_noalloc_loss_rejects_images_beyond_its_scratch():
     with pytest.raises(B.VGError) as e:
         _noalloc(x, x, 0.2)
     assert e.value.status == B.VG_ERR_CAPACITY
+
+
+def test_noalloc_loss_rejects_a_side_beyond_16384_as_an_argument_error():
+    # few pixels, but one side over the 16384 every entry point accepts
+    x = torch.zeros((3, 1, 20000), dtype=torch.float32, device="cuda")
+    with pytest.raises(B.VGError) as e:
+        _noalloc(x, x, 0.2)
+    assert e.value.status == B.VG_ERR_INVALID
