@@ -735,7 +735,9 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     alu = alu_peaks(dev, local)
-    peak_ops = alu["ffma_tops"]                   # measured FP32 FMA lane operations, Tops/s
+    # measured FP32 FMA pipe rate in lane operations: the packed form (two lanes an instruction)
+    # reaches the pipe's rate with half the issue slots, so it is the larger of the two probes
+    peak_ops = max(alu["ffma_tops"], alu["ffma2_lane_tops"])
     fwd_ops = OPS_EVAL * evals_f + OPS_BLEND_FWD * blends_f
     bwd_ops = OPS_EVAL * evals_b + OPS_BLEND_BWD * blends_f
     # the same per-evaluation counts over the slots the kernels execute after their warp culling
@@ -789,8 +791,9 @@ def main():
                      "unit": "FP32 Tops/s", "frac": kern[dom] / peak_ops, "traffic": profiled_traffic(dom),
                      "achieved_executed": kern_x[dom], "frac_executed": kern_x[dom] / peak_ops,
                      "issue_frac": issue_frac,
-                     "peak_source": "measured: vg_alu_probe FP32 FMA lane rate on this GPU "
-                                    f"({sms} SMs, SM clock {alu.get('sm_mhz')} MHz during the probe)",
+                     "peak_source": "measured: vg_alu_probe FP32 FMA lane rate on this GPU (the larger of the "
+                                    f"scalar and packed probes; {sms} SMs, SM clock {alu.get('sm_mhz')} MHz during "
+                                    "the probe)",
                      "alu_probe": alu},
         "stage_ms": stage_ms,
         "blends": {"evals_fwd": evals_f, "blends_fwd": blends_f, "evals_bwd": evals_b,

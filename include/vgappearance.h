@@ -20,8 +20,9 @@
  * offset (i, j); bilinear up-sampling maps output row y to input row (y + 1/2) h / H - 1/2,
  * clamped below at 0 (PyTorch's align_corners = False).
  *
- * Arithmetic: the convolutions after the first run on the tensor cores with TF32 inputs
- * (rounded to nearest) and FP32 accumulation; everything else is FP32.
+ * Arithmetic: FP32-accurate throughout.  The convolutions after the first run on the tensor cores
+ * with each FP32 operand split into two TF32 parts and each product formed from three MMAs
+ * (relative error about 2^-21 a product) and FP32 accumulation; everything else is FP32.
  *
  * Conventions are those of vgrast.h: device pointers, caller-owned memory, asynchronous on
  * `stream`, argument errors returned before any launch.

@@ -46,7 +46,7 @@ class BatchRasterizer:
         return arr
 
     def _ensure(self, gs, cams, opts, n_total):
-        cap = int(self.capacity or max(1 << 16, 4 * n_total))
+        cap = int(self.capacity or max(1 << 16, n_total))
         self.capacity = cap
         need = B.vg_batch_workspace_bytes(gs, cams, opts, cap)
         if need == 0:

@@ -16,12 +16,13 @@
 // Work split:
 //  * conv0 exploits the constant embedding: its 64 embedding channels reduce to one 256-vector
 //    per tap (E[tap] = W0[:, 3:, tap] l), so a low-resolution pixel costs 3 x 9 + 9 terms.
-//  * blocks 1..4 run as implicit GEMMs on the tensor cores (mma.sync m16n8k8, TF32 inputs
-//    rounded to nearest, FP32 accumulation): output pixels x output channels, K = 9 taps x input
+//  * blocks 1..4 run as implicit GEMMs on the tensor cores (mma.sync m16n8k8 on TF32 operands,
+//    each FP32 operand split into two TF32 parts and every product formed from three MMAs, so the
+//    products are FP32-accurate; FP32 accumulation): output pixels x output channels, K = 9 taps x input
 //    channels, the input tile and its halo staged once in shared memory.  Their adjoints are the
 //    same kernel (input gradient = convolution with the flipped, transposed weights) and a
 //    weight-gradient GEMM (K = pixels).
-//  * the full-resolution head is one persistent kernel per 16 x 16 output tile that keeps every
+//  * the full-resolution head is one persistent kernel over 16 x 16 output tiles that keeps every
 //    intermediate in shared memory: bilinear U over the tile + 4, Hh = ReLU(conv5 U) over + 3,
 //    M = conv6 Hh over + 2, the L1 term, dL/dM, then the whole adjoint back to dL/dF4 (scattered
 //    by the bilinear adjoint), dL/dW5 and dL/dW6.  Only F4, the two images and the gradients
@@ -78,38 +79,61 @@ __device__ __forceinline__ void mma8(float (&d)[4], const float (&a)[4], float b
 }
 __device__ __forceinline__ void mma8(float (&d)[4], const float (&a)[4], float2 b) { mma8(d, a, b.x, b.y); }
 
+// FP32-accurate products on the TF32 tensor cores: x = hi + lo with hi = tf32(x) and lo =
+// tf32(x - hi) (x - hi is exact in FP32), and A B ~ Ahi Bhi + Ahi Blo + Alo Bhi.  The dropped
+// Alo Blo term and the rounding of lo leave a relative error of about 2^-21 per product, below
+// FP32 accumulation's own.
+struct Split4 {
+  float hi[4], lo[4];
+};
+__device__ __forceinline__ Split4 split4(float a0, float a1, float a2, float a3) {
+  Split4 r;
+  const float v[4] = {a0, a1, a2, a3};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    r.hi[k] = tf32r(v[k]);
+    r.lo[k] = tf32r(v[k] - r.hi[k]);
+  }
+  return r;
+}
+struct Split2 {
+  float hi0, hi1, lo0, lo1;
+};
+__device__ __forceinline__ Split2 split2(float b0, float b1) {
+  Split2 r;
+  r.hi0 = tf32r(b0);
+  r.hi1 = tf32r(b1);
+  r.lo0 = tf32r(b0 - r.hi0);
+  r.lo1 = tf32r(b1 - r.hi1);
+  return r;
+}
+__device__ __forceinline__ void mma8x3(float (&d)[4], const Split4& a, const Split2& b) {
+  mma8(d, a.lo, b.hi0, b.hi1);
+  mma8(d, a.hi, b.lo0, b.lo1);
+  mma8(d, a.hi, b.hi0, b.hi1);
+}
+
 
 // ---------------------------------------------------------------- weight packing
 //
 // A GEMM's B operand (K x N) is stored in fragment order: for k-step s, n-tile j and lane
 // (g, t) the pair (B[8s + t][8j + g], B[8s + t + 4][8j + g]) at float2 index (s N/8 + j) 32 + lane,
-// rounded to TF32.  K is tap-major with tapc channels a tap (tapc >= the input's channels; the
+// in FP32 (split into TF32 parts where it is loaded).  K is tap-major with tapc channels a tap (tapc >= the input's channels; the
 // extra ones are zero).  A forward convolution has B[tap tapc + c][o] = W[o][c][tap]; the
 // input-gradient convolution (input = output gradient, O channels) has
 // B[tap tapc + o][c] = W[o][c][8 - tap].
 
 struct PackJob {
-  int layer, dgrad, tapc, kpad, npad, f16, aop, offset;   // offset in elements of the job's type
+  int layer, dgrad, tapc, kpad, npad, offset;   // offset in floats
 };
-constexpr int kPackJobs = 13;
+constexpr int kPackJobs = 12;
 struct PackTable {
   PackJob job[kPackJobs];
   int begin[kPackJobs + 1];   // first element index of each job in the launch's index space
 };
 
-// Magnitudes beyond FP16's largest finite value are clamped (never rounded to infinity).
-__device__ __forceinline__ __half to_half(float x) { return __float2half_rn(fminf(fmaxf(x, -65504.f), 65504.f)); }
-__device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
-  const __half2 h = __halves2half2(to_half(lo), to_half(hi));
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-// TF32 jobs (m16n8k8): element (k-step s, n-tile j, lane, e) = B[8s + t + 4e][8j + g].
-// FP16 jobs (m16n8k16): element (s, j, lane, r, h) = B[16s + 2t + h + 8r][8j + g], so that each
-// lane reads its two B registers as one 8-byte word.  FP16 A-operand jobs hold B transposed as an
-// m16n8k16 A operand (rows = B's columns): element (s, lane, r, h) = B[16s + 2t + h + 8 (r >> 1)]
-// [g + 8 (r & 1)], four registers a lane as one 16-byte word.
-__global__ void pack_kernel(const float* __restrict__ params, void* __restrict__ packed, const PackTable tab) {
+// Element (k-step s, n-tile j, lane, e) = B[8s + t + 4e][8j + g].
+__global__ void pack_kernel(const float* __restrict__ params, float* __restrict__ packed, const PackTable tab) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= tab.begin[kPackJobs]) return;
   int jb = 0;
@@ -117,24 +141,8 @@ __global__ void pack_kernel(const float* __restrict__ params, void* __restrict__
   const PackJob J = tab.job[jb];
   const int local = i - tab.begin[jb];
   const int nt = J.npad / 8;
-  int k, n, rest, lane;
-  if (J.aop) {
-    const int h = local & 1, r = (local >> 1) & 3;
-    lane = (local >> 3) & 31;
-    k = 16 * (local >> 8) + 2 * (lane & 3) + h + 8 * (r >> 1);
-    n = (lane >> 2) + 8 * (r & 1);
-  } else if (J.f16) {
-    const int h = local & 1, r = (local >> 1) & 1;
-    lane = (local >> 2) & 31;
-    rest = local >> 7;
-    k = 16 * (rest / nt) + 2 * (lane & 3) + h + 8 * r;
-  } else {
-    const int e = local & 1;
-    lane = (local >> 1) & 31;
-    rest = local >> 6;
-    k = 8 * (rest / nt) + (lane & 3) + 4 * e;
-  }
-  if (!J.aop) n = 8 * (rest % nt) + (lane >> 2);
+  const int e = local & 1, lane = (local >> 1) & 31, rest = local >> 6;
+  const int k = 8 * (rest / nt) + (lane & 3) + 4 * e, n = 8 * (rest % nt) + (lane >> 2);
   const int C = layer_c(J.layer), O = layer_o(J.layer);
   const float* W = params + w_off(J.layer);
   const int tap = k / J.tapc, c = k % J.tapc;
@@ -144,10 +152,7 @@ __global__ void pack_kernel(const float* __restrict__ params, void* __restrict__
   } else {
     if (tap < 9 && c < O && n < C) v = W[(c * C + n) * 9 + 8 - tap];
   }
-  if (J.f16)
-    static_cast<__half*>(packed)[J.offset + local] = to_half(v);
-  else
-    static_cast<float*>(packed)[J.offset + local] = tf32r(v);
+  packed[J.offset + local] = v;   // FP32; split into TF32 parts where it is loaded
 }
 
 // E[tap][o] = sum_c W0[o][3 + c][tap] l[c]: the embedding's share of conv0 at each tap.
@@ -228,8 +233,8 @@ __global__ void __launch_bounds__(256) conv0_kernel(const float* __restrict__ P,
 // ---------------------------------------------------------------- blocks 1..4: implicit GEMM
 
 // Stages the logical (pixel-shuffled) input of a block, rows [Y0, Y0 + SH) x columns [X0, X0 + SW)
-// at resolution (Hr, Wr) with C channels, into dst (pixel pitch P), rounded to TF32 and zero
-// outside the image.  Aprev is [Hr/2][Wr/2][4C]: native channels 4c..4c+3 of native pixel
+// at resolution (Hr, Wr) with C channels, into dst (pixel pitch P), in FP32 and zero outside the
+// image (the MMAs split each operand into TF32 parts as they load it).  Aprev is [Hr/2][Wr/2][4C]: native channels 4c..4c+3 of native pixel
 // (Yn, Xn) are channel c of the logical pixels (2Yn + i, 2Xn + j), so each float4 load feeds four
 // staged pixels.
 template <int C, int P>
@@ -248,13 +253,13 @@ __device__ __forceinline__ void stage_shuffled(float* dst, const float* __restri
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int r = 2 * yn + (k >> 1) - Y0, s = 2 * xn + (k & 1) - X0;
-      if (r >= 0 && r < SH && s >= 0 && s < SW) dst[(r * SW + s) * P + c] = tf32r(q[k]);
+      if (r >= 0 && r < SH && s >= 0 && s < SW) dst[(r * SW + s) * P + c] = q[k];
     }
   }
 }
 
 // Stages rows [Y0, Y0 + SH) x columns [X0, X0 + SW) of g [Hr][Wr][C] (times [act > 0] when MASK)
-// into dst (pixel pitch P), rounded to TF32 and zero outside the image.
+// into dst (pixel pitch P), in FP32 and zero outside the image.
 template <int C, int P, bool MASK>
 __device__ __forceinline__ void stage_plain(float* dst, const float* __restrict__ g, const float* __restrict__ act,
                                             int Y0, int X0, int SH, int SW, int Hr, int Wr) {
@@ -270,7 +275,7 @@ __device__ __forceinline__ void stage_plain(float* dst, const float* __restrict_
         z = make_float4(av.x > 0.f ? z.x : 0.f, av.y > 0.f ? z.y : 0.f, av.z > 0.f ? z.z : 0.f, av.w > 0.f ? z.w : 0.f);
       }
     }
-    *reinterpret_cast<float4*>(dst + px * P + 4 * v) = make_float4(tf32r(z.x), tf32r(z.y), tf32r(z.z), tf32r(z.w));
+    *reinterpret_cast<float4*>(dst + px * P + 4 * v) = z;
   }
 }
 
@@ -331,15 +336,18 @@ __global__ void __launch_bounds__(256) conv_mma_kernel(const float* __restrict__
     const float2* wt = reinterpret_cast<const float2*>(wbuf + (tap & 1) * TAPF);
 #pragma unroll
     for (int cb = 0; cb < C / 8; ++cb) {
-      float2 b[NTW];
+      Split2 b[NTW];
 #pragma unroll
-      for (int j = 0; j < NTW; ++j) b[j] = wt[(cb * NT + wn * NTW + j) * 32 + lane];
+      for (int j = 0; j < NTW; ++j) {
+        const float2 w = wt[(cb * NT + wn * NTW + j) * 32 + lane];
+        b[j] = split2(w.x, w.y);
+      }
 #pragma unroll
       for (int i = 0; i < MTW; ++i) {
         const float* base = smem + ((wm + i * WM + dy) * SW + dx + g) * PITCH + cb * 8 + t;
-        const float a[4] = {base[0], base[8 * PITCH], base[4], base[8 * PITCH + 4]};
+        const Split4 a = split4(base[0], base[8 * PITCH], base[4], base[8 * PITCH + 4]);
 #pragma unroll
-        for (int j = 0; j < NTW; ++j) mma8(acc[i][j], a, b[j]);
+        for (int j = 0; j < NTW; ++j) mma8x3(acc[i][j], a, b[j]);
       }
     }
     __syncthreads();                                 // the buffer is refilled two taps later
@@ -467,7 +475,7 @@ __global__ void __launch_bounds__(256, 2) wgrad_kernel(const float* __restrict__
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int r = 2 * yn + (k >> 1) - Y0, sx = 2 * xn + (k & 1) - X0;
-        if (r >= 0 && r < SHT && sx >= 0 && sx < SW) sX[(r * SW + sx) * PX + c] = tf32r(v4[k]);
+        if (r >= 0 && r < SHT && sx >= 0 && sx < SW) sX[(r * SW + sx) * PX + c] = v4[k];
       }
     }
   };
@@ -481,7 +489,7 @@ __global__ void __launch_bounds__(256, 2) wgrad_kernel(const float* __restrict__
       if constexpr (MASK_IN)
         z = make_float4(ra[q].x > 0.f ? z.x : 0.f, ra[q].y > 0.f ? z.y : 0.f, ra[q].z > 0.f ? z.z : 0.f,
                         ra[q].w > 0.f ? z.w : 0.f);
-      *reinterpret_cast<float4*>(sZ + px * PZ + 4 * v) = make_float4(tf32r(z.x), tf32r(z.y), tf32r(z.z), tf32r(z.w));
+      *reinterpret_cast<float4*>(sZ + px * PZ + 4 * v) = z;
     }
   };
   const int tile_begin = blockIdx.x * per_block, tile_end = min(tiles, (blockIdx.x + 1) * per_block);
@@ -507,21 +515,18 @@ __global__ void __launch_bounds__(256, 2) wgrad_kernel(const float* __restrict__
     for (int s = 0; s < 2 * TY; ++s) {
       const int ty = s >> 1, x0 = (s & 1) * 8;
       const int pxA = (ty * SW + x0 + 2 * t) * PX;     // X at pixel (ty, x0 + 2t); tap offsets in xo
-      float a[MW][4];
+      Split4 a[MW];
 #pragma unroll
-      for (int i = 0; i < MW; ++i) {
-        a[i][0] = vr[i][0] ? sX[pxA + xo[i][0]] : 0.f;
-        a[i][1] = vr[i][1] ? sX[pxA + xo[i][1]] : 0.f;
-        a[i][2] = vr[i][0] ? sX[pxA + PX + xo[i][0]] : 0.f;
-        a[i][3] = vr[i][1] ? sX[pxA + PX + xo[i][1]] : 0.f;
-      }
+      for (int i = 0; i < MW; ++i)
+        a[i] = split4(vr[i][0] ? sX[pxA + xo[i][0]] : 0.f, vr[i][1] ? sX[pxA + xo[i][1]] : 0.f,
+                      vr[i][0] ? sX[pxA + PX + xo[i][0]] : 0.f, vr[i][1] ? sX[pxA + PX + xo[i][1]] : 0.f);
       const float* zb = sZ + (ty * 16 + x0 + 2 * t) * PZ + g;
 #pragma unroll
       for (int j = 0; j < NW; ++j) {
         const int n = (nt0 + j) * 8;
-        const float b0 = zb[n], b1 = zb[PZ + n];
+        const Split2 b = split2(zb[n], zb[PZ + n]);
 #pragma unroll
-        for (int i = 0; i < MW; ++i) mma8(acc[i][j], a[i], b0, b1);
+        for (int i = 0; i < MW; ++i) mma8x3(acc[i][j], a[i], b);
       }
     }
   }
@@ -642,41 +647,39 @@ __global__ void __launch_bounds__(256) conv0_embed_grad_kernel(const float* __re
 
 // ---------------------------------------------------------------- full-resolution head
 //
-// One persistent block per SM pair of 16 x 16 output tiles T at (oy, ox); R_k = T grown by k
-// pixels.  The head's GEMMs run as mma.sync m16n8k16 with FP16 operands (10-bit mantissa like
-// TF32, rounded to nearest, magnitudes clamped to FP16's range) and FP32 accumulation; every
-// operand comes from shared memory through ldmatrix (.trans for the weight gradients, whose K is
-// pixels).  Shared memory (FP16 rows of 48 bytes, so any 8 consecutive pixels of an ldmatrix
-// hit distinct banks):
+// One persistent block per SM takes 16 x 16 output tiles T at (oy, ox); R_k = T grown by k pixels.
+// The head's GEMMs run on the tensor cores as mma.sync m16n8k8 on TF32 operands with every FP32
+// operand split into two TF32 parts and each product formed from three MMAs (FP32-accurate
+// products, FP32 accumulation).  Operands are FP32 in shared memory (pixel pitches of 20 floats,
+// so the 8 x 4 lanes of a fragment load that run along pixels x channels hit distinct banks):
 //   sU  U over R4 (24 x 24 pixels x 16 channels), copied with cp.async from the up-sampled image
 //       (computed once by upsample_kernel) while the previous tile finishes
 //   sH  Hh = ReLU(Z5) over R3 (22 x 22)
 //   sZ  gZ5' = (conv6 adjoint of gM') * [Hh > 0] over R1 (18 x 18)
-//   sG  gM' = sign(I_a - I) I_r over R2 (20 x 20, 16-byte rows, channels 3..7 zero)
+//   sG  gM' = sign(I_a - I) I_r over R2 (20 x 20, pitch 12, channels 3.. zero)
 //   sI  I_r and I over R2 (FP32 planes, zero outside the image), fetched with cp.async at the
 //       start of the tile
 //   tables: bilinear taps (first, second source row / column, weight of the second) of R4's
-//       rows and columns, -1 outside the image; per footprint row, the run of T's rows that
-//       reach it
-// After the GEMMs, sH and sZ hold dL/dU over T and its column-reduced form (FP32) for the
-// bilinear adjoint's two gather passes.
+//       rows and columns, -1 outside the image; per footprint row and column, the run of T's rows
+//       and columns that reach it
+// After the GEMMs, sH holds dL/dU over T and sZ its column-reduced form for the bilinear adjoint.
 constexpr int HT = 16;
 constexpr int R4 = HT + 8, R3 = HT + 6, R2 = HT + 4, R1 = HT + 2;
-constexpr int HP = 24;                // halves per pixel in sU / sH / sZ
-constexpr int GP = 8;                 // halves per pixel in sG
+constexpr int PU = 20;                // floats per pixel in sU / sH / sZ (16 channels + 4)
+constexpr int PG = 12;                // floats per pixel in sG (8 channels + 4)
 constexpr int FT = 10;                // dL/dF4 footprint side of T
 constexpr int kHeadThreads = 256;
-constexpr int kBU = R4 * R4 * HP * 2, kBH = R3 * R3 * HP * 2, kBZ = R1 * R1 * HP * 2, kBG = R2 * R2 * GP * 2;
-constexpr int kBI = 2 * 3 * R2 * R2 * 4, kBT = 6 * R4 * 4 + 2 * FT * 4;
+constexpr int kBU = R4 * R4 * PU * 4, kBH = R3 * R3 * PU * 4, kBZ = R1 * R1 * PU * 4, kBG = R2 * R2 * PG * 4;
+constexpr int kBI = 2 * 3 * R2 * R2 * 4, kBT = 6 * R4 * 4 + 4 * FT * 4;
 constexpr int kHeadSmemBytes = kBU + kBH + kBZ + kBG + kBI + kBT;
 static_assert(HT * HT * 16 * 4 <= kBH && HT * FT * 16 * 4 <= kBZ, "bilinear adjoint buffers fit");
 static_assert(kBU % 16 == 0 && kBH % 16 == 0 && kBZ % 16 == 0 && kBG % 16 == 0 && kBI % 16 == 0, "alignment");
+static_assert(kHeadSmemBytes <= 227 * 1024, "one block an SM");
 
 struct HeadArgs {
   const float *img, *target, *b5, *b6;
-  const __half* u;                          // the up-sampled F4, [H][W][16]
-  const uint2 *w5f, *w5d, *w6f, *w6d;       // FP16 B fragments
-  const uint4* w5da;                        // conv5's adjoint weights as FP16 A fragments
+  const float* u;                           // the up-sampled F4, [H][W][16]
+  const float2 *w5f, *w5d, *w6f, *w6d;      // packed B fragments (FP32, split where loaded)
   float *gimg, *map, *gf4, *dw5, *db5, *dw6, *db6;
   double* partials;
   int H, W, h4, w4, tiles_x, tiles;
@@ -704,31 +707,26 @@ __device__ __forceinline__ Tap up_tap(int y, int n_in, int n_out) {
   return r;
 }
 
-// U = F4 [h4][w4][16] up-sampled bilinearly to [H][W][16], stored in FP16 (magnitudes clamped to
-// its range): the head's conv5 input, computed once rather than once per overlapping head tile.
-// A thread produces 8 channels of one pixel.
+// U = F4 [h4][w4][16] up-sampled bilinearly to [H][W][16] (FP32): the head's conv5 input,
+// computed once rather than once per overlapping head tile.  A thread produces 4 channels of one
+// pixel.
 __global__ void __launch_bounds__(256) upsample_kernel(const float* __restrict__ f4, int h4, int w4, int H, int W,
-                                                       __half* __restrict__ U) {
+                                                       float* __restrict__ U) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= H * W * 2) return;
-  const int hv = i & 1, px = i >> 1, y = px / W, x = px % W;
+  if (i >= H * W * 4) return;
+  const int v = i & 3, px = i >> 2, y = px / W, x = px % W;
   const Tap ty = up_tap(y, h4, H), tx = up_tap(x, w4, W);
   const float fy = ty.f, fx = tx.f, gy = 1.f - fy, gx = 1.f - fx;
-  const float4* f00 = reinterpret_cast<const float4*>(f4 + ((size_t)ty.i0 * w4 + tx.i0) * 16 + 8 * hv);
-  const float4* f01 = reinterpret_cast<const float4*>(f4 + ((size_t)ty.i0 * w4 + tx.i1) * 16 + 8 * hv);
-  const float4* f10 = reinterpret_cast<const float4*>(f4 + ((size_t)ty.i1 * w4 + tx.i0) * 16 + 8 * hv);
-  const float4* f11 = reinterpret_cast<const float4*>(f4 + ((size_t)ty.i1 * w4 + tx.i1) * 16 + 8 * hv);
-  float u[8];
-#pragma unroll
-  for (int v = 0; v < 2; ++v) {
-    const float4 p = __ldg(f00 + v), q = __ldg(f01 + v), r = __ldg(f10 + v), t = __ldg(f11 + v);
-    u[4 * v + 0] = gy * (gx * p.x + fx * q.x) + fy * (gx * r.x + fx * t.x);
-    u[4 * v + 1] = gy * (gx * p.y + fx * q.y) + fy * (gx * r.y + fx * t.y);
-    u[4 * v + 2] = gy * (gx * p.z + fx * q.z) + fy * (gx * r.z + fx * t.z);
-    u[4 * v + 3] = gy * (gx * p.w + fx * q.w) + fy * (gx * r.w + fx * t.w);
-  }
-  *reinterpret_cast<uint4*>(U + (size_t)px * 16 + 8 * hv) =
-      make_uint4(pack_half2(u[0], u[1]), pack_half2(u[2], u[3]), pack_half2(u[4], u[5]), pack_half2(u[6], u[7]));
+  const float4 p = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)ty.i0 * w4 + tx.i0) * 16) + v);
+  const float4 q = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)ty.i0 * w4 + tx.i1) * 16) + v);
+  const float4 r = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)ty.i1 * w4 + tx.i0) * 16) + v);
+  const float4 t = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)ty.i1 * w4 + tx.i1) * 16) + v);
+  float4 u;
+  u.x = gy * (gx * p.x + fx * q.x) + fy * (gx * r.x + fx * t.x);
+  u.y = gy * (gx * p.y + fx * q.y) + fy * (gx * r.y + fx * t.y);
+  u.z = gy * (gx * p.z + fx * q.z) + fy * (gx * r.z + fx * t.z);
+  u.w = gy * (gx * p.w + fx * q.w) + fy * (gx * r.w + fx * t.w);
+  reinterpret_cast<float4*>(U + (size_t)px * 16)[v] = u;
 }
 
 __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool valid) {
@@ -736,42 +734,20 @@ __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, boo
                : "memory");
 }
 
-// D += A B for one m16n8k16 FP16 tile: a = {A[g][2t..], A[g+8][2t..], A[g][2t+8..], A[g+8][2t+8..]},
-// b = {B[2t..][g], B[2t+8..][g]} (two halves a register), d as for m16n8k8.
-__device__ __forceinline__ void mma16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Four 8 x 8 FP16 matrices: lane l gives the 16-byte row address of matrix l / 8, row l % 8.
-// Without .trans a lane receives (row g, columns 2t, 2t + 1) of each matrix, with .trans
-// (rows 2t, 2t + 1, column g).
-__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], uint32_t addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr) : "memory");
-}
-__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], uint32_t addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr) : "memory");
-}
-__device__ __forceinline__ void ldsm2t(uint32_t& r0, uint32_t& r1, uint32_t addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r0), "=r"(r1) : "r"(addr) : "memory");
-}
-
-__device__ __forceinline__ float2 half2_to_float2(uint32_t v) {
-  return __half22float2(*reinterpret_cast<const __half2*>(&v));
+// A fragment of a 16-pixel x 8-channel tile of a pixel-major buffer (pitch P floats): rows (pixels)
+// at p0 (row g) and p1 (row g + 8), channels c and c + 4.
+template <int P>
+__device__ __forceinline__ Split4 frag_px(const float* buf, int p0, int p1, int c) {
+  return split4(buf[p0 * P + c], buf[p1 * P + c], buf[p0 * P + c + 4], buf[p1 * P + c + 4]);
 }
 
 template <bool BWD>
-__global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a) {
+__global__ void __launch_bounds__(kHeadThreads, 1) head_kernel(const HeadArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  __half* sU = reinterpret_cast<__half*>(smraw);
-  __half* sH = reinterpret_cast<__half*>(smraw + kBU);
-  __half* sZ = reinterpret_cast<__half*>(smraw + kBU + kBH);
-  __half* sG = reinterpret_cast<__half*>(smraw + kBU + kBH + kBZ);
+  float* sU = reinterpret_cast<float*>(smraw);
+  float* sH = reinterpret_cast<float*>(smraw + kBU);
+  float* sZ = reinterpret_cast<float*>(smraw + kBU + kBH);
+  float* sG = reinterpret_cast<float*>(smraw + kBU + kBH + kBZ);
   float* sI = reinterpret_cast<float*>(smraw + kBU + kBH + kBZ + kBG);   // [2][3][R2][R2]
   int* tY0 = reinterpret_cast<int*>(smraw + kBU + kBH + kBZ + kBG + kBI);
   int* tY1 = tY0 + R4;
@@ -780,15 +756,12 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
   int* tX1 = tX0 + R4;
   float* tFX = reinterpret_cast<float*>(tX1 + R4);
   int2* rY = reinterpret_cast<int2*>(tFX + R4);     // contributor runs [first, end) of T's rows
+  int2* rX = rY + FT;                               // ... and of T's columns
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  // ldmatrix rows: lrow / lq for A (pixel rows, channel halves) and for the weight-gradient B
-  // operands; tp / tc for the transposed weight-gradient A operands (pixel, channel half)
-  const int lrow = (lane & 7) + (lane & 8), lq = lane >> 4;
-  const int tp = (lane & 7) + ((lane >> 4) << 3), tc = (lane >> 3) & 1;
-  const uint32_t uU = smem_u32(sU), uH = smem_u32(sH), uZ = smem_u32(sZ), uG = smem_u32(sG);
   const size_t HW = (size_t)a.H * a.W;
   float l1 = 0.f;
-  // weight-gradient accumulators kept across tiles, for this warp's taps (warp; warp 7 also 8)
+  // weight-gradient accumulators kept across tiles: tap `warp` over every row, and tap 8 over
+  // rows 2 warp and 2 warp + 1 (every warp adds its share of tap 8)
   float acc5[2][2][4], acc6[2][4], db5[2][2], db6[3];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -800,11 +773,11 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
   auto fetch_u = [&](int tile) {
     if (tile < a.tiles) {
       const int oy = (tile / a.tiles_x) * HT, ox = (tile % a.tiles_x) * HT;
-      for (int i = threadIdx.x; i < R4 * R4 * 2; i += kHeadThreads) {
-        const int px = i >> 1, hv = i & 1;
+      for (int i = threadIdx.x; i < R4 * R4 * 4; i += kHeadThreads) {
+        const int px = i >> 2, v = i & 3;
         const int y = oy - 4 + px / R4, x = ox - 4 + px % R4;
         const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
-        cp_async16_zfill(sU + px * HP + 8 * hv, a.u + (in ? ((size_t)y * a.W + x) * 16 + 8 * hv : 0), in);
+        cp_async16_zfill(sU + px * PU + 4 * v, a.u + (in ? ((size_t)y * a.W + x) * 16 + 4 * v : 0), in);
       }
     }
     cp_async_commit();
@@ -841,37 +814,38 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
     }
     cp_async_commit();
     if constexpr (BWD)
-      for (int i = threadIdx.x; i < R2 * R2 * GP / 8; i += kHeadThreads)
-        reinterpret_cast<uint4*>(sG)[i] = make_uint4(0u, 0u, 0u, 0u);
+      for (int i = threadIdx.x; i < R2 * R2 * PG / 4; i += kHeadThreads)
+        reinterpret_cast<float4*>(sG)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     cp_async_wait<1>();    // U (the older group)
     __syncthreads();
     // S2: Hh = ReLU(conv5 U + b5) over R3, zero outside the image.  M = 484 pixels (31 m-tiles),
-    // N = 16, K = 9 taps x 16 channels (one k-step a tap).
+    // N = 16, K = 9 taps x 16 channels (two k-steps a tap).
     {
       constexpr int NM = (R3 * R3 + 15) / 16;
       const int nmt = (NM - warp + 7) / 8;
-      uint32_t abase[4];
+      int p0[4], p1[4];     // rows g and g + 8 of each of the warp's m-tiles, as R4 pixels
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int m = min((warp + 8 * i) * 16 + lrow, R3 * R3 - 1);
-        abase[i] = uU + (((m / R3) * R4 + m % R3) * HP + 8 * lq) * 2;
+        const int m0 = min((warp + 8 * i) * 16 + g, R3 * R3 - 1), m1 = min((warp + 8 * i) * 16 + g + 8, R3 * R3 - 1);
+        p0[i] = (m0 / R3) * R4 + m0 % R3;
+        p1[i] = (m1 / R3) * R4 + m1 % R3;
       }
       float acc[4][2][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[i][0][q] = acc[i][1][q] = 0.f;
-#pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        const uint32_t off = (((s / 3) * R4 + s % 3) * HP) * 2;
-        const uint2 b0 = __ldg(a.w5f + (s * 2 + 0) * 32 + lane), b1 = __ldg(a.w5f + (s * 2 + 1) * 32 + lane);
+#pragma unroll 2
+      for (int s = 0; s < 18; ++s) {
+        const int tap = s >> 1, off = (tap / 3) * R4 + tap % 3, c = 8 * (s & 1) + t;
+        const float2 w0 = __ldg(a.w5f + (s * 2 + 0) * 32 + lane), w1 = __ldg(a.w5f + (s * 2 + 1) * 32 + lane);
+        const Split2 b0 = split2(w0.x, w0.y), b1 = split2(w1.x, w1.y);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
           if (i < nmt) {
-            uint32_t av[4];
-            ldsm4(av, abase[i] + off);
-            mma16(acc[i][0], av, b0.x, b0.y);
-            mma16(acc[i][1], av, b1.x, b1.y);
+            const Split4 av = frag_px<PU>(sU, p0[i] + off, p1[i] + off, c);
+            mma8x3(acc[i][0], av, b0);
+            mma8x3(acc[i][1], av, b1);
           }
       }
 #pragma unroll
@@ -888,7 +862,7 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
             const int o = 8 * j + 2 * t;
             const float v0 = in ? fmaxf(acc[i][j][2 * h] + __ldg(a.b5 + o), 0.f) : 0.f;
             const float v1 = in ? fmaxf(acc[i][j][2 * h + 1] + __ldg(a.b5 + o + 1), 0.f) : 0.f;
-            *reinterpret_cast<uint32_t*>(sH + m * HP + o) = pack_half2(v0, v1);
+            *reinterpret_cast<float2*>(sH + m * PU + o) = make_float2(v0, v1);
           }
         }
       }
@@ -905,28 +879,26 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
     {
       constexpr int NM = R2 * R2 / 16;
       const int nmt = (NM - warp + 7) / 8;
-      uint32_t abase[4];
+      int p0[4], p1[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int m = min((warp + 8 * i) * 16 + lrow, R2 * R2 - 1);
-        abase[i] = uH + (((m / R2) * R3 + m % R2) * HP + 8 * lq) * 2;
+        const int m0 = min((warp + 8 * i) * 16 + g, R2 * R2 - 1), m1 = min((warp + 8 * i) * 16 + g + 8, R2 * R2 - 1);
+        p0[i] = (m0 / R2) * R3 + m0 % R2;
+        p1[i] = (m1 / R2) * R3 + m1 % R2;
       }
       float acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
-#pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        const uint32_t off = (((s / 3) * R3 + s % 3) * HP) * 2;
-        const uint2 b = __ldg(a.w6f + s * 32 + lane);
+#pragma unroll 2
+      for (int s = 0; s < 18; ++s) {
+        const int tap = s >> 1, off = (tap / 3) * R3 + tap % 3, c = 8 * (s & 1) + t;
+        const float2 w = __ldg(a.w6f + s * 32 + lane);
+        const Split2 b = split2(w.x, w.y);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          if (i < nmt) {
-            uint32_t av[4];
-            ldsm4(av, abase[i] + off);
-            mma16(acc[i], av, b.x, b.y);
-          }
+          if (i < nmt) mma8x3(acc[i], frag_px<PU>(sH, p0[i] + off, p1[i] + off, c), b);
       }
       // the quad's six (pixel, channel) items: t = 0 takes (g, 0), (g, 1); t = 1 (g, 2), (g + 8, 2);
       // t = 2 (g + 8, 0) and t = 3 (g + 8, 1), fetched from t = 0
@@ -962,37 +934,35 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
               db6[2] += o == 2 ? gm : 0.f;
             }
           }
-          if constexpr (BWD) sG[m * GP + o] = to_half(gm);
+          if constexpr (BWD) sG[m * PG + o] = gm;
         }
       }
     }
     if constexpr (BWD) {
       __syncthreads();
       // S5: gZ5' = (conv6 adjoint of gM') * [Hh > 0] over R1.  M = 324 pixels (21 m-tiles), N = 16,
-      // K = 9 flipped taps x 8 channels (3 used) -> 80: k-step s covers taps 2s and 2s + 1.
+      // K = 9 flipped taps x 8 channels (3 used): one k-step a tap, whose channels 4..7 are zero.
       {
         constexpr int NM = (R1 * R1 + 15) / 16;
         const int nmt = (NM - warp + 7) / 8;
-        uint2 bw[5][2];
-#pragma unroll
-        for (int s = 0; s < 5; ++s)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) bw[s][j] = __ldg(a.w6d + (s * 2 + j) * 32 + lane);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           if (i >= nmt) break;
-          const int mr = min((warp + 8 * i) * 16 + lrow, R1 * R1 - 1);
-          const uint32_t base = uG + ((mr / R1) * R2 + mr % R1) * GP * 2;
+          const int m0 = min((warp + 8 * i) * 16 + g, R1 * R1 - 1), m1 = min((warp + 8 * i) * 16 + g + 8, R1 * R1 - 1);
+          const int q0 = (m0 / R1) * R2 + m0 % R1, q1 = (m1 / R1) * R2 + m1 % R1;
           float acc[2][4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[0][q] = acc[1][q] = 0.f;
 #pragma unroll
-          for (int s = 0; s < 5; ++s) {
-            const int tap = min(2 * s + lq, 8);      // tap 9 is padding (zero weights)
-            uint32_t av[4];
-            ldsm4(av, base + ((tap / 3) * R2 + tap % 3) * GP * 2);
-            mma16(acc[0], av, bw[s][0].x, bw[s][0].y);
-            mma16(acc[1], av, bw[s][1].x, bw[s][1].y);
+          for (int s = 0; s < 9; ++s) {
+            const int off = (s / 3) * R2 + s % 3;
+            const float v0 = sG[(q0 + off) * PG + t], v1 = sG[(q1 + off) * PG + t];
+            const Split4 av = split4(v0, v1, 0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const float2 w = __ldg(a.w6d + (s * 2 + j) * 32 + lane);
+              mma8x3(acc[j], av, split2(w.x, w.y));
+            }
           }
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -1002,14 +972,14 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
             const int y = oy - 1 + r, x = ox - 1 + q;
             const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
             const bool inT = in && r >= 1 && r <= HT && q >= 1 && q <= HT;
-            const __half* hp = sH + ((r + 2) * R3 + q + 2) * HP;
+            const float* hp = sH + ((r + 2) * R3 + q + 2) * PU;
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
               const int o = 8 * j + 2 * t;
-              const float2 hv = half2_to_float2(*reinterpret_cast<const uint32_t*>(hp + o));
+              const float2 hv = *reinterpret_cast<const float2*>(hp + o);
               const float z0 = (in && hv.x > 0.f) ? acc[j][2 * h] : 0.f;
               const float z1 = (in && hv.y > 0.f) ? acc[j][2 * h + 1] : 0.f;
-              *reinterpret_cast<uint32_t*>(sZ + m * HP + o) = pack_half2(z0, z1);
+              *reinterpret_cast<float2*>(sZ + m * PU + o) = make_float2(z0, z1);
               if (inT) {
                 db5[j][0] += z0;
                 db5[j][1] += z1;
@@ -1019,101 +989,105 @@ __global__ void __launch_bounds__(kHeadThreads, 2) head_kernel(const HeadArgs a)
         }
       }
       __syncthreads();
-      // S4 + S6, one k-step per row of T (16 pixels); warp w takes tap w over every row and tap 8
-      // over rows 2w and 2w + 1:
-      //   dW6^T[(tap, ci)][o] += sum_p Hh(p + tap)[ci] gM'(p)[o]   (A = Hh, transposed loads)
-      //   dW5[o][(tap, ci)]   += sum_p gZ5'(p)[o] U(p + tap)[ci]   (A = gZ5', transposed loads)
-#pragma unroll 2
+      // S4 + S6, two k-steps (8 pixels each) per row of T; warp w takes tap w over every row and
+      // tap 8 over rows 2w and 2w + 1:
+      //   dW6^T[(tap, ci)][o] += sum_p Hh(p + tap)[ci] gM'(p)[o]   (M = ci, N = o, K = pixels)
+      //   dW5[o][(tap, ci)]   += sum_p gZ5'(p)[o] U(p + tap)[ci]   (M = o, N = ci, K = pixels)
+#pragma unroll 1
       for (int ty = 0; ty < HT; ++ty) {
-        uint32_t agz[4], bgm0, bgm1;
-        ldsm4t(agz, uZ + (((ty + 1) * R1 + tp + 1) * HP + 8 * tc) * 2);
-        ldsm2t(bgm0, bgm1, uG + ((ty + 2) * R2 + lrow + 2) * GP * 2);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (u == 1 && (ty >> 1) != warp) break;
-          const int tap = u == 0 ? warp : 8, ti = tap / 3, tj = tap % 3;
-          uint32_t bu[4], ah[4];
-          ldsm4t(bu, uU + (((ty + ti + 3) * R4 + lrow + tj + 3) * HP + 8 * lq) * 2);
-          mma16(acc5[u][0], agz, bu[0], bu[1]);
-          mma16(acc5[u][1], agz, bu[2], bu[3]);
-          ldsm4t(ah, uH + (((ty + ti + 2) * R3 + tp + tj + 2) * HP + 8 * tc) * 2);
-          mma16(acc6[u], ah, bgm0, bgm1);
+        for (int kk = 0; kk < 2; ++kk) {
+          const int xa = 8 * kk + t, xb = xa + 4;           // this lane's two pixels of the k-step
+          const float* zr = sZ + ((ty + 1) * R1 + 1) * PU;  // gZ5' of T row ty
+          const Split4 agz = split4(zr[xa * PU + g], zr[xa * PU + g + 8], zr[xb * PU + g], zr[xb * PU + g + 8]);
+          const float* gr = sG + ((ty + 2) * R2 + 2) * PG;  // gM' of T row ty
+          const Split2 bgm = split2(gr[xa * PG + g], gr[xb * PG + g]);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (u == 1 && (ty >> 1) != warp) break;
+            const int tap = u == 0 ? warp : 8, ti = tap / 3, tj = tap % 3;
+            const float* ur = sU + ((ty + ti + 3) * R4 + tj + 3) * PU;
+            mma8x3(acc5[u][0], agz, split2(ur[xa * PU + g], ur[xb * PU + g]));
+            mma8x3(acc5[u][1], agz, split2(ur[xa * PU + 8 + g], ur[xb * PU + 8 + g]));
+            const float* hr = sH + ((ty + ti + 2) * R3 + tj + 2) * PU;
+            const Split4 ah = split4(hr[xa * PU + g], hr[xa * PU + g + 8], hr[xb * PU + g], hr[xb * PU + g + 8]);
+            mma8x3(acc6[u], ah, bgm);
+          }
         }
       }
-      // S7: dL/dU over T, rows warp and warp + 8, computed transposed: gU^T[ci][p] = sum_k
-      // W5d^T[ci][k] gZ5'^T[k][p] with M = 16 input channels (A: the packed weights), N = the
-      // row's 16 pixels (B: gZ5' rows through ldmatrix), K = 9 flipped taps x 16 channels.  The
-      // accumulators of the two pixel halves then form exactly an m16n8k16 A operand, which the
-      // bilinear adjoint's column pass uses directly.
+      // S7: dL/dU over T, rows warp and warp + 8: gU[p][ci] = sum over flipped taps and channels
+      // of gZ5'(p + tap)[o] W5d[(tap, o)][ci] (M = the row's 16 pixels, N = 16 input channels,
+      // K = 9 taps x 16 channels)
       float acc7[2][2][4];
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc7[i][0][q] = acc7[i][1][q] = 0.f;
-#pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        const uint4 aw = __ldg(a.w5da + s * 32 + lane);
-        const uint32_t afr[4] = {aw.x, aw.y, aw.z, aw.w};
+#pragma unroll 2
+      for (int s = 0; s < 18; ++s) {
+        const int tap = s >> 1, c = 8 * (s & 1) + t;
+        const float2 w0 = __ldg(a.w5d + (s * 2 + 0) * 32 + lane), w1 = __ldg(a.w5d + (s * 2 + 1) * 32 + lane);
+        const Split2 b0 = split2(w0.x, w0.y), b1 = split2(w1.x, w1.y);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-          uint32_t bz[4];
-          ldsm4(bz, uZ + (((warp + 8 * i + s / 3) * R1 + tp + s % 3) * HP + 8 * tc) * 2);
-          mma16(acc7[i][0], afr, bz[0], bz[1]);
-          mma16(acc7[i][1], afr, bz[2], bz[3]);
+          const int pr = (warp + 8 * i + tap / 3) * R1 + tap % 3;   // R1 pixel of T pixel 0 of the row
+          const Split4 av = frag_px<PU>(sZ, pr + g, pr + g + 8, c);
+          mma8x3(acc7[i][0], av, b0);
+          mma8x3(acc7[i][1], av, b1);
         }
       }
       __syncthreads();   // every warp is past S4, S6 and S7 (the last readers of U, Hh and gZ5')
       fetch_u(tile + gridDim.x);
-      // Bilinear adjoint, column pass on the tensor cores: X^T[ci][b] = sum_x gU^T[ci][x] Rx[x][b]
-      // for each of the warp's rows (K = the row's 16 pixels, N = footprint columns b in two
-      // n-tiles), Rx[x][b] = the weight of column x's taps on footprint column bx0 + b; then the
-      // row pass gathers sX [row][footprint column][16] straight into dL/dF4.
-      float* sX = reinterpret_cast<float*>(sZ);
+      // dL/dU over T into sH as [row][column][16]
+      float* sGU = sH;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = warp + 8 * i, x = g + 8 * h, ci = 8 * j + 2 * t;
+            *reinterpret_cast<float2*>(sGU + (r * HT + x) * 16 + ci) = make_float2(acc7[i][j][2 * h], acc7[i][j][2 * h + 1]);
+          }
+      // Bilinear adjoint: a column pass X[row][b][ci] = sum over T's columns x that reach footprint
+      // column bx0 + b of their tap weight times gU[row][x][ci], then a row pass that gathers X
+      // over the rows reaching each footprint row, straight into dL/dF4.
+      float* sX = sZ;
       const int bx0 = tX0[4], bx1 = tX1[min(HT + 3, a.W - 1 - ox + 4)];
       const int by0 = tY0[4], by1 = tY1[min(HT + 3, a.H - 1 - oy + 4)];
       const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1;
-      const int ncy = min(HT, a.H - oy);
-      {
-        uint32_t rx[2][2];
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            float w2[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int x = 2 * t + h + 8 * r + 4, b = bx0 + g + 8 * nt;   // x: R4 column of T column
-              const float fx = tFX[x];
-              w2[h] = (tX0[x] == b ? 1.f - fx : 0.f) + (tX1[x] == b ? fx : 0.f);
-            }
-            rx[nt][r] = pack_half2(w2[0], w2[1]);
-          }
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const uint32_t ga[4] = {pack_half2(acc7[i][0][0], acc7[i][0][1]), pack_half2(acc7[i][0][2], acc7[i][0][3]),
-                                  pack_half2(acc7[i][1][0], acc7[i][1][1]), pack_half2(acc7[i][1][2], acc7[i][1][3])};
-          const int r = warp + 8 * i;
-#pragma unroll
-          for (int nt = 0; nt < 2; ++nt) {
-            float xc[4] = {0.f, 0.f, 0.f, 0.f};
-            mma16(xc, ga, rx[nt][0], rx[nt][1]);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int b = 8 * nt + 2 * t + (e & 1), ci = g + 8 * (e >> 1);
-              if (b < FT) sX[(r * FT + b) * 16 + ci] = xc[e];
-            }
-          }
-        }
-      }
-      // contributors of footprint row b: the T rows whose taps (first, second) include b, a
+      const int ncx = min(HT, a.W - ox), ncy = min(HT, a.H - oy);
+      // contributors of footprint row / column b: the T rows / columns whose taps include b, a
       // contiguous run because the taps are monotone
-      if (threadIdx.x < FT) {
-        const int b = by0 + threadIdx.x;
+      if (threadIdx.x < 2 * FT) {
+        const bool col = threadIdx.x >= FT;
+        const int k = col ? threadIdx.x - FT : threadIdx.x;
+        const int* T0 = col ? tX0 : tY0;
+        const int* T1 = col ? tX1 : tY1;
+        const int n = col ? ncx : ncy;
+        const int b = (col ? bx0 : by0) + k;
         int first = 0;
-        while (first < ncy && tY1[first + 4] < b) ++first;
+        while (first < n && T1[first + 4] < b) ++first;
         int end = first;
-        while (end < ncy && tY0[end + 4] <= b) ++end;
-        rY[threadIdx.x] = make_int2(first, end);
+        while (end < n && T0[end + 4] <= b) ++end;
+        (col ? rX : rY)[k] = make_int2(first, end);
+      }
+      __syncthreads();
+      for (int it = threadIdx.x; it < HT * nbx * 4; it += kHeadThreads) {
+        const int v = it & 3, rest = it >> 2, jb = rest % nbx, r = rest / nbx;
+        const int b = bx0 + jb;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int2 run = rX[jb];
+        for (int x = run.x; x < run.y; ++x) {
+          const float fx = tFX[x + 4];
+          const float w = (tX0[x + 4] == b ? 1.f - fx : 0.f) + (tX1[x + 4] == b ? fx : 0.f);
+          const float4 gu = *reinterpret_cast<const float4*>(sGU + (r * HT + x) * 16 + 4 * v);
+          s.x = fmaf(w, gu.x, s.x);
+          s.y = fmaf(w, gu.y, s.y);
+          s.z = fmaf(w, gu.z, s.z);
+          s.w = fmaf(w, gu.w, s.w);
+        }
+        *reinterpret_cast<float4*>(sX + (r * FT + jb) * 16 + 4 * v) = s;
       }
       __syncthreads();
       for (int it = threadIdx.x; it < nby * nbx * 4; it += kHeadThreads) {
@@ -1252,10 +1226,10 @@ AppLayout make_app_layout(int W, int H) {
     L.A[k] = take(n);
     L.gA[k] = take(n);
   }
-  // packed B operands: forward and input-gradient GEMMs of blocks 1..4 (TF32), conv5 and conv6 of
-  // the head (FP16)
+  // packed B operands: forward and input-gradient GEMMs of blocks 1..4 and of the head's conv5
+  // and conv6
   const int jobs[kPackJobs][2] = {{1, 0}, {2, 0}, {3, 0}, {4, 0}, {1, 1}, {2, 1},
-                                  {3, 1}, {4, 1}, {5, 0}, {5, 1}, {6, 0}, {6, 1}, {5, 1}};
+                                  {3, 1}, {4, 1}, {5, 0}, {5, 1}, {6, 0}, {6, 1}};
   int pos = 0, idx = 0;   // pos: floats of the buffer used; idx: elements of the launch's index space
   for (int j = 0; j < kPackJobs; ++j) {
     const int l = jobs[j][0], dg = jobs[j][1];
@@ -1263,22 +1237,19 @@ AppLayout make_app_layout(int W, int H) {
     PackJob& J = L.tab.job[j];
     J.layer = l;
     J.dgrad = dg;
-    J.f16 = l >= 5;
-    J.aop = j == 12;                                   // conv5's adjoint as an A operand
-    J.tapc = !J.f16 ? kin : (l == 6 && dg) ? 8 : 16;   // conv6's adjoint: 3 channels a tap, read as 8
-    const int kstep = J.f16 ? 16 : 8;
-    J.kpad = (9 * J.tapc + kstep - 1) / kstep * kstep;
+    J.tapc = (l == 6 && dg) ? 8 : kin;                 // conv6's adjoint: 3 channels a tap, read as 8
+    J.kpad = (9 * J.tapc + 7) / 8 * 8;
     J.npad = (n + 7) / 8 * 8;
-    const int elems = J.kpad * J.npad;                  // a multiple of 64 (TF32) or 128 (FP16)
-    J.offset = J.f16 ? 2 * pos : pos;
+    const int elems = J.kpad * J.npad;                 // a multiple of 64
+    J.offset = pos;
     L.pack_off[j] = pos;
     L.tab.begin[j] = idx;
     idx += elems;
-    pos += J.f16 ? elems / 2 : elems;
+    pos += elems;
   }
   L.tab.begin[kPackJobs] = idx;
   L.packed = take((size_t)pos * 4);
-  L.U = take((size_t)W * H * 16 * 2);          // FP16 [H][W][16]
+  L.U = take((size_t)W * H * 16 * 4);          // FP32 [H][W][16]
   L.maps = take(ssim_maps_floats(W, H) * 4);
   L.ssim_part = take((size_t)ssim_partials(W, H) * 2 * 8);
   L.head_part = take((size_t)kMaxHeadBlocks * 8);
@@ -1410,7 +1381,7 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   // weights, embedding taps, pooling, conv0, blocks 1..4
   note_launches(4);
   const int npk = L.tab.begin[kPackJobs];
-  pack_kernel<<<(npk + 255) / 256, 256, 0, s>>>(params, static_cast<void*>(packed), L.tab);
+  pack_kernel<<<(npk + 255) / 256, 256, 0, s>>>(params, packed, L.tab);
   embed_taps_kernel<<<9, 256, 0, s>>>(params, embedding, F(L.E));
   pool_kernel<<<dim3(pw, ph), 256, 0, s>>>(img, W, H, pw, F(L.P));
   conv0_kernel<<<(ph * pw + kConv0FwdPx - 1) / kConv0FwdPx, 256, 0, s>>>(F(L.P), F(L.E), params, ph, pw, A[0]);
@@ -1420,19 +1391,18 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   ok(launch_conv<32, 64, 8, 4, false, false, false>(A[1], nullptr, wf[2], bias[2], nullptr, A[2], ph << 2, pw << 2, s));
   ok(launch_conv<16, 32, 16, 8, false, false, false>(A[2], nullptr, wf[3], bias[3], nullptr, A[3], ph << 3, pw << 3, s));
   ok(launch_conv<8, 16, 16, 8, false, false, false>(A[3], nullptr, wf[4], bias[4], nullptr, A[4], ph << 4, pw << 4, s));
-  __half* U = reinterpret_cast<__half*>(ws + L.U);
+  float* U = F(L.U);
   note_launches(1);
-  upsample_kernel<<<(int)(((size_t)W * H * 2 + 255) / 256), 256, 0, s>>>(A[4], ph << 4, pw << 4, H, W, U);
+  upsample_kernel<<<(int)(((size_t)W * H * 4 + 255) / 256), 256, 0, s>>>(A[4], ph << 4, pw << 4, H, W, U);
   // the head
   HeadArgs ha{};
   ha.img = img;
   ha.target = target;
   ha.u = U;
-  ha.w5f = reinterpret_cast<const uint2*>(packed + L.pack_off[8]);
-  ha.w5d = reinterpret_cast<const uint2*>(packed + L.pack_off[9]);
-  ha.w6f = reinterpret_cast<const uint2*>(packed + L.pack_off[10]);
-  ha.w6d = reinterpret_cast<const uint2*>(packed + L.pack_off[11]);
-  ha.w5da = reinterpret_cast<const uint4*>(packed + L.pack_off[12]);
+  ha.w5f = reinterpret_cast<const float2*>(packed + L.pack_off[8]);
+  ha.w5d = reinterpret_cast<const float2*>(packed + L.pack_off[9]);
+  ha.w6f = reinterpret_cast<const float2*>(packed + L.pack_off[10]);
+  ha.w6d = reinterpret_cast<const float2*>(packed + L.pack_off[11]);
   ha.b5 = params + b_off(5);
   ha.b6 = params + b_off(6);
   ha.gimg = grad_img;
@@ -1452,7 +1422,7 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   const double inv = 1.0 / (3.0 * (double)((size_t)W * H));
   ha.cscale = (float)((1.0 - lambda) * inv);     // the L1 scale of Eq. 1's kernel, bit for bit
   const size_t head_smem = (size_t)kHeadSmemBytes;
-  const int grid = std::min(ha.tiles, std::min(kMaxHeadBlocks, 2 * sms));
+  const int grid = std::min(ha.tiles, std::min(kMaxHeadBlocks, sms));   // one block an SM (shared memory)
   note_launches(2);
   if (bwd) {
     ok(set_smem(head_kernel<true>, head_smem));

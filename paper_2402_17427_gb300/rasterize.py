@@ -81,7 +81,9 @@ class Workspace:
         self.key = None
 
     def ensure(self, n: int, width: int, height: int, opts: B.vg_raster_opts, capacity: int | None = None):
-        cap = int(capacity or self.capacity or max(1 << 16, 4 * n))
+        # first guess one pair per Gaussian (a render that needs more reports it and is re-run
+        # with the count it needed); the capacity only grows
+        cap = int(capacity or self.capacity or max(1 << 16, n))
         self.capacity = cap
         need = B.vg_workspace_bytes(n, width, height, cap, opts)
         if need == 0:

@@ -1,17 +1,15 @@
 """GPU parity of the decoupled appearance model (paper Sec. 4.2, Eq. 3, and the CNN of the
 supplementary material) against the FP64 appearance oracle, through the C ABI.
 
-Tolerances follow from the arithmetic.  The convolutions after the first run on TF32 inputs (10
-explicit mantissa bits, unit roundoff u = 2^-11, rounded to nearest) with FP32 accumulation: the
-GPU computes the exact network of slightly perturbed operands.  The map M is held to 2e-3 of its
-range (about 4 u).  A weight gradient is a sum over every pixel whose terms can cancel (with 1 x 2
-pooled cells the first layers' gradients are differences of near-equal terms), so its bound comes
-from the oracle itself: the relative change of that gradient when the tensor-core layers' weights
-are rounded to TF32 (one of the perturbations the GPU applies, the activations' roundings being of
-the same size) is its sensitivity s, and the GPU must agree within max(3e-3, 4 s).  The L1 term's
-sign is a decision taken in floating point: where |I_r M - I| is within the map's error bound the
-two sides may legitimately differ, so dL/dI_r must agree element-wise (within 2e-3 of its scale)
-everywhere except at such pixels.
+Tolerances are those of FP32 arithmetic, which is what the method runs in.  The tensor-core
+convolutions split every FP32 operand into two TF32 parts and form each product from three MMAs,
+so products carry a relative error of about 2^-21 and accumulate in FP32; the other layers are
+plain FP32.  The map M is held to 1e-4 of its range, the loss to 1e-5 relative, and every gradient
+group (the embedding, each layer's weights and biases) to a relative L2 error of 2e-3 against the
+FP64 oracle, with no allowance for reduced-precision operands.  The L1 term's sign is a decision
+taken in floating point: where |I_r M - I| is within twice the map's bound the two sides may
+legitimately differ, so dL/dI_r must agree element-wise (within 2e-3 of its scale) everywhere
+except at such pixels.
 """
 import numpy as np
 import pytest
@@ -65,41 +63,32 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-def _tf32(x):
-    """Round to the TF32 format (10 explicit mantissa bits, to nearest, ties away from zero)."""
-    a = np.asarray(x, np.float32).copy()
-    bits = a.view(np.uint32)
-    bits[:] = (bits + np.uint32(0x1000)) & np.uint32(0xFFFFE000)
-    return a.astype(np.float64)
-
-
 def _compare(W, H, seed, lam=0.2):
     img, target, emb, weights = _case(W, H, seed)
     g = _gpu(img, target, emb, weights, lam)
     w64 = [(w.astype(np.float64), b.astype(np.float64)) for w, b in weights]
     e64 = emb.astype(np.float64)
     L, M, gi, ge, gw = OA.loss_and_grads(img, target, e64, w64, lam)
-    # sensitivity of every gradient to TF32 rounding of the tensor-core layers' weights
-    wt = [w64[0]] + [(_tf32(w), b) for w, b in w64[1:]]
-    _, _, _, ge_t, gw_t = OA.loss_and_grads(img, target, e64, wt, lam)
-    tol = lambda ref, pert: max(3e-3, 4 * _rel(pert, ref))
     # the map and the loss
     span = M.max() - M.min()
-    assert np.abs(g["map"] - M).max() <= 2e-3 * span, np.abs(g["map"] - M).max() / span
-    assert g["loss"][0] == pytest.approx(L, rel=1e-4)
+    assert np.abs(g["map"] - M).max() <= 1e-4 * span, np.abs(g["map"] - M).max() / span
+    assert g["loss"][0] == pytest.approx(L, rel=1e-5)
     # the gradient of the image, element-wise where the L1 sign is settled
     d = img.astype(np.float64) * M - target
-    settled = np.abs(d) > 4e-3 * span
+    settled = np.abs(d) > 2e-4 * span
     scale = np.abs(gi).max()
     off = np.abs(g["grad_img"] - gi) > 2e-3 * scale
     assert not (off & settled).any()           # any disagreement is at a pixel whose sign is unsettled
     assert off.mean() <= (~settled).mean()
     # the embedding and every layer's weight and bias gradients
-    assert _rel(g["grad_embedding"], ge) <= tol(ge, ge_t)
+    errs = {"embedding": _rel(g["grad_embedding"], ge)}
     views = AP.layer_views(torch.from_numpy(g["grad_params"]))
-    for k, ((gw_gpu, gb_gpu), (dw, db), (dw_t, db_t)) in enumerate(zip(views, gw, gw_t)):
-        assert _rel(gw_gpu.numpy(), dw) <= tol(dw, dw_t), k
-        assert _rel(gb_gpu.numpy(), db) <= tol(db, db_t), k
+    for k, ((gw_gpu, gb_gpu), (dw, db)) in enumerate(zip(views, gw)):
+        if np.linalg.norm(dw) > 0:
+            errs[f"w{k}"] = _rel(gw_gpu.numpy(), dw)
+        if np.linalg.norm(db) > 0:
+            errs[f"b{k}"] = _rel(gb_gpu.numpy(), db)
+    assert max(errs.values()) <= 2e-3, errs
     return g
 
 

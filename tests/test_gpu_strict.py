@@ -64,7 +64,10 @@ def _check_key_path(uvrd, orc):
         assert np.array_equal(uvrd[both, k].view(np.uint32), orc.rec[name][both].view(np.uint32)), name
     assert np.array_equal(uvrd[both, 3].view(np.uint32), orc.rec["depth32"][both].view(np.uint32))
     r_gpu, r_orc = uvrd[both, 2].astype(np.float64), orc.rec["radius"][both]
-    assert np.abs(r_gpu - r_orc).max() <= 1e-5 * r_orc.max()
+    rel = np.abs(r_gpu - r_orc) / r_orc
+    # FP32 through exp, the covariance products and two square roots: a few units in 1e-6, up to
+    # about 1.2e-5 for Gaussians thousands of pixels wide (the oracle's rectangle band covers it)
+    assert rel.max() <= 2e-5, (rel.max(), np.percentile(rel, 99))
     return int(both.sum())
 
 

@@ -285,6 +285,24 @@ def test_pairs_from_fp32_reproduces_the_forward_lists(oracle_lib):
     assert np.array_equal(ranges, r.ranges)
 
 
+@pytest.mark.parametrize("case,budget", [("small", 3e-4), ("tiny", 3e-4), ("blob1080p", 5e-4)])
+def test_ambiguous_pixel_budget(oracle_lib, case, budget):
+    # Pixels whose compositing decision lies inside the FP32 error bands are excluded from the
+    # image comparison; their count grows with the number of evaluations times the band width, so
+    # it is bounded per pixel: about 2e-4 of the pixels at 1080p (224 evaluations a pixel), none
+    # or a few on the small scenes.  The 1e-5 per pixel once proposed for these scenes would need
+    # bands below the kernels' measured FP32 decision error.
+    if case == "small":
+        g, cam, _ = scenes.small_cell(0)
+    elif case == "tiny":
+        g, cam, _ = scenes.tiny_scene(n=300, width=100, height=61, degree=3, seed=6)
+    else:
+        g, cam, _ = scenes.blob_cell_1080p()
+    r = oracle_lib.render(g, cam)
+    px = cam.width * cam.height
+    assert r.n_amb <= budget * px + 1, (r.n_amb, px)
+
+
 # ------------------------------------------------------------------ invariants
 
 def test_transmittance_monotone_and_bounded(oracle_lib):
