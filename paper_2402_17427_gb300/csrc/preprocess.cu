@@ -231,8 +231,11 @@ __device__ __forceinline__ void project(const KGauss& g, const KCam& cm, const K
   P.ca = P.C * idet;
   P.cb = -P.B * idet;
   P.cc = P.A * idet;
-  const float mid = 0.5f * (P.A + P.C);
-  const float lmax = mid + sqrtf(fmaxf(0.f, mid * mid - det));
+  // largest eigenvalue as mid + sqrt(((A - C) / 2)^2 + B^2): the same value as mid + sqrt(mid^2 -
+  // det) without its cancellation for near-isotropic covariances (there mid^2 - det loses all
+  // its bits in FP32 and r would err by ~1e-4 relative)
+  const float mid = 0.5f * (P.A + P.C), hd = 0.5f * (P.A - P.C);
+  const float lmax = mid + sqrtf(fmaf(hd, hd, P.B * P.B));
   P.r = 3.f * sqrtf(lmax);
   P.valid = true;
 }
