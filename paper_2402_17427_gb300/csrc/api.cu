@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256) init_header(WsHeader* hdr, SortCtl* ctl) 
   hdr->tile_bits = 0;
   hdr->evals_run_bwd = 0;
   hdr->scatter = 0;
+  hdr->sort_next = 0;
   for (int k = 0; k < kTileClasses; ++k) hdr->work_fwd[k] = hdr->work_bwd[k] = 0;
 }
 
@@ -150,7 +151,7 @@ int tile_class(int ts) { return ts == 8 ? 0 : (ts == 16 ? 1 : 2); }
 struct Call {
   std::vector<unsigned char> table;
   HostPlan plan{};
-  int n_views = 0, n_segs = 0, total_n = 0, total_tiles = 0, total_rows = 0, degree = 0;
+  int n_views = 0, n_segs = 0, total_n = 0, total_tiles = 0, degree = 0;
   int64_t total_n64 = 0, total_tiles64 = 0;
   KView* views() { return reinterpret_cast<KView*>(table.data() + sizeof(TableHeader)); }
   KSeg* segs() { return reinterpret_cast<KSeg*>(table.data() + sizeof(TableHeader) + n_views * sizeof(KView)); }
@@ -180,7 +181,6 @@ vg_status make_call(Call& c, const vg_gaussians* segs, int n_segs, const int* se
     kv.tile_base = (int)tiles;
     kv.tile_class = tile_class(ts);
     tiles += (int64_t)kv.tiles_x * kv.tiles_y;
-    c.total_rows += kv.tiles_y;
     c.plan.class_tiles[kv.tile_class] += kv.tiles_x * kv.tiles_y;
   }
   if (tiles > 0x7FFFFFFFll) return VG_ERR_INVALID;
@@ -289,7 +289,7 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
   if (e != cudaSuccess) return VG_ERR_CUDA;
   stage_event(ev, VG_STAGE_PROJECT, false, s);
   stage_event(ev, VG_STAGE_SORT, true, s);
-  e = launch_binning(tab, c.total_n, c.total_tiles, c.total_rows, pair_capacity, L, ws, s);
+  e = launch_binning(tab, c.total_n, c.total_tiles, pair_capacity, L, ws, s);
   if (e != cudaSuccess) return VG_ERR_CUDA;
   stage_event(ev, VG_STAGE_SORT, false, s);
   stage_event(ev, VG_STAGE_BLEND, true, s);

@@ -301,10 +301,10 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
     s_rank[threadIdx.x] = s;
     if (threadIdx.x == 0) s_off[256] = (unsigned)tot;
     __syncthreads();
-    // pair k of the batch: its owner (the last g with s_off[g] <= k; owners have cnt > 0), tile
-    // and depth rank
-    auto pair_at = [&](unsigned k, uint32_t& tile, uint32_t& rank) {
-      int lo = 0, hi = 255;
+    for (unsigned k = threadIdx.x; k < (unsigned)tot; k += 256) {
+      const unsigned long long j = run + k;
+      if (j >= cap) break;
+      int lo = 0, hi = 255;              // last g with s_off[g] <= k (owners have cnt > 0)
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
@@ -312,35 +312,13 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
       const int within = (int)(k - s_off[lo]);
       const int w = s_w[lo];
       const int ty = s_ty0[lo] + within / w, tx = s_tx0[lo] + within % w;
-      tile = (uint32_t)(s_base[lo] + ty * s_tilesx[lo] + tx);
-      rank = s_rank[lo];
-    };
-    if (scatter) {
-      // four pairs a thread at a time, so that four cursor atomics are in flight together
-      constexpr int U = 4;
-      for (unsigned k0 = threadIdx.x; k0 < (unsigned)tot; k0 += U * 256) {
-        uint32_t tile[U], rank[U];
-        unsigned pos[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const unsigned k = k0 + u * 256;
-          tile[u] = 0xFFFFFFFFu;
-          if (k < (unsigned)tot && run + k < cap) pair_at(k, tile[u], rank[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) pos[u] = tile[u] != 0xFFFFFFFFu ? atomicAdd(cursor + tile[u], 1u) : 0xFFFFFFFFu;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (pos[u] < cap) lists[pos[u]] = rank[u];
-      }
-    } else {
-      for (unsigned k = threadIdx.x; k < (unsigned)tot; k += 256) {
-        const unsigned long long j = run + k;
-        if (j >= cap) break;
-        uint32_t tile, rank;
-        pair_at(k, tile, rank);
+      const uint32_t tile = (uint32_t)(s_base[lo] + ty * s_tilesx[lo] + tx);
+      if (scatter) {
+        const unsigned pos = atomicAdd(cursor + tile, 1u);
+        if (pos < cap) lists[pos] = s_rank[lo];
+      } else {
         pkeys[j] = tile;
-        pvals[j] = rank;
+        pvals[j] = s_rank[lo];
       }
     }
     run += tot;
@@ -492,36 +470,6 @@ __global__ void __launch_bounds__(256) tile_count(const DevTables* __restrict__ 
   }
 }
 
-// Per-tile pair counts from tile_count's differences: a warp per tile row of a view sums the
-// replicas of the row's differences and scans them along the row, writing the counts over replica
-// 0 (each warp owns its row, so nothing else reads those words meanwhile).
-__global__ void __launch_bounds__(256) tile_rows(const DevTables* __restrict__ tab, int tiles, unsigned* __restrict__ tdiff) {
-  const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  int v = 0, r = row;
-  while (v < tab->h.n_views && r >= tview(tab, v).tiles_y) r -= tview(tab, v++).tiles_y;
-  if (v >= tab->h.n_views) return;
-  const KView& vw = tview(tab, v);
-  unsigned* out = tdiff + vw.tile_base + r * vw.tiles_x;
-  unsigned carry = 0;
-  for (int x0 = 0; x0 < vw.tiles_x; x0 += 32) {
-    const int x = x0 + lane;
-    unsigned c = 0;
-    if (x < vw.tiles_x) {
-#pragma unroll
-      for (int k = 0; k < kCountCopies; ++k) c += out[(size_t)k * tiles + x];
-    }
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, c, o);
-      if (lane >= o) c += y;
-    }
-    c += carry;
-    carry = __shfl_sync(0xffffffffu, c, 31);
-    if (x < vw.tiles_x) out[x] = c;
-  }
-}
-
 // Tile ranges, the digit histograms of the tile-sort passes and the largest-first tile order,
 // all from the per-tile pair counts, which are known before the pairs are emitted.  One block,
 // with the counts in shared memory: a scan along every tile row turns tile_count's differences
@@ -531,7 +479,7 @@ __global__ void __launch_bounds__(256) tile_rows(const DevTables* __restrict__ t
 // With nothing to sort (no pairs, or more than cap) every range is empty, as the sort leaves it.
 constexpr int kPrepThreads = 256;
 constexpr int kPrepTiles = 16384;        // tiles of a render that takes this path (two words each)
-constexpr int kSortMaxList = 8192;       // longest list the scatter path sorts (sort_long_lists' shared memory)
+constexpr int kSortMaxList = 2048;       // longest list sort_lists takes (64 registers a lane)
 
 __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __restrict__ tab, int tiles, unsigned cap,
                                                           int tpasses, const unsigned* __restrict__ tdiff,
@@ -543,39 +491,63 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
   __shared__ unsigned s_h[kMaxPasses][kRadix];
   __shared__ unsigned s_cnt[kBuckets + 1];   // bucket counts, then the longest list
   __shared__ unsigned long long sm[8];
-  // the per-tile counts (tile_rows), each thread a run of consecutive tiles
-  const int per = (tiles + kPrepThreads - 1) / kPrepThreads;
-  const int t_lo = min(tiles, (int)threadIdx.x * per), t_hi = min(tiles, t_lo + per);
-  unsigned long long own = 0;
-  unsigned longest = 0;
-  for (int t = t_lo; t < t_hi; ++t) {
-    const unsigned c = tdiff[t];
-    s_c[t] = c;
-    own += c;
-    longest = max(longest, c);
+  // the replicas of tile_count's differences, summed; eight loads in flight per thread
+  for (int t0 = 0; t0 < tiles; t0 += 8 * kPrepThreads) {
+    unsigned v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = 0u;
+#pragma unroll
+    for (int r = 0; r < kCountCopies; ++r)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * kPrepThreads + (int)threadIdx.x;
+        if (t < tiles) v[u] += tdiff[(size_t)r * tiles + t];
+      }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * kPrepThreads + (int)threadIdx.x;
+      if (t < tiles) s_c[t] = v[u];
+    }
   }
   for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) s_h[k / kRadix][k % kRadix] = 0;
   for (int k = threadIdx.x; k <= kBuckets; k += blockDim.x) s_cnt[k] = 0;
-  const int lane = threadIdx.x & 31;
-  // 2. exclusive offsets over the tile ids: one block scan of the threads' run totals
-  unsigned long long run;
-  {
-    const unsigned long long ex = block_exclusive_scan(own, &run, sm);
-    unsigned long long at = ex;
-    for (int t = t_lo; t < t_hi; ++t) {
-      s_x[t] = (unsigned)at;
-      at += s_c[t];
+  __syncthreads();
+  // 1. counts: an inclusive scan along every tile row of every view, a warp per row
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int v = 0; v < tab->h.n_views; ++v) {
+    const KView& vw = tview(tab, v);
+    const int txn = vw.tiles_x;
+    for (int ty = warp; ty < vw.tiles_y; ty += nwarps) {
+      unsigned* row = s_c + vw.tile_base + ty * txn;
+      unsigned carry = 0;
+      for (int x0 = 0; x0 < txn; x0 += 32) {
+        const int x = x0 + lane;
+        unsigned c = x < txn ? row[x] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, c, o);
+          if (lane >= o) c += y;
+        }
+        c += carry;
+        carry = __shfl_sync(0xffffffffu, c, 31);
+        if (x < txn) row[x] = c;
+      }
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) longest = max(longest, __shfl_xor_sync(0xffffffffu, longest, o));
-  if (lane == 0) atomicMax(&s_cnt[kBuckets], longest);
   __syncthreads();
-  // the list-building mode: scatter + per-list sort when every list fits sort_lists / sort_long_lists
-  const bool scatter = s_cnt[kBuckets] <= (unsigned)kSortMaxList;
-  if (threadIdx.x == 0) hdr->scatter = scatter ? 1u : 0u;
+  // 2. exclusive offsets over the tile ids, a block-wide scan per 256 tiles
+  unsigned long long run = 0;
+  for (int t0 = 0; t0 < tiles; t0 += kPrepThreads) {
+    const int t = t0 + threadIdx.x;
+    const unsigned c = t < tiles ? s_c[t] : 0u;
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan((unsigned long long)c, &tot, sm);
+    if (t < tiles) s_x[t] = (unsigned)(run + ex);
+    run += tot;
+  }
   const bool any = run > 0 && run <= cap;
   const uint32_t lt = lanemask_lt();
+  unsigned longest = 0;
   // 3. ranges, digit histograms, order buckets (view by view: the bucket needs the tile class);
   //    lanes adding to the same shared counter are merged first
   for (int v = 0; v < tab->h.n_views; ++v) {
@@ -589,7 +561,8 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
         ranges[t] = c ? make_uint2(s_x[t], s_x[t] + c) : make_uint2(0u, 0u);
         cursor[t] = s_x[t];
       }
-      for (int p = 0; p < (scatter ? 0 : tpasses); ++p) {
+      longest = max(longest, c);
+      for (int p = 0; p < tpasses; ++p) {
         // consecutive lanes hold consecutive tiles, so equal digits sit in runs of lanes: a
         // segmented scan leaves each run's sum in its last lane, which adds it
         const unsigned d = in ? ((unsigned)t >> (p * kRadixBits)) & (kRadix - 1) : 0xFFFFFFFFu;   // nondecreasing
@@ -610,7 +583,12 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
       if (in && (peers & lt) == 0) atomicAdd(&s_cnt[bk], (unsigned)__popc(peers));
     }
   }
+  // the list-building mode: scatter + per-list sort when every list fits one warp's registers
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) longest = max(longest, __shfl_xor_sync(0xffffffffu, longest, o));
+  if (lane == 0) atomicMax(&s_cnt[kBuckets], longest);
   __syncthreads();
+  if (threadIdx.x == 0) hdr->scatter = s_cnt[kBuckets] <= (unsigned)kSortMaxList ? 1u : 0u;
   for (int k = threadIdx.x; k < tpasses * kRadix; k += blockDim.x) hist[k] = s_h[k / kRadix][k % kRadix];
   if (threadIdx.x == 0) {
     unsigned acc = 0;
@@ -634,7 +612,7 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
 }
 
 // ---- 5. per-list sort of the scattered tile lists ---------------------------------------------
-// One warp per tile (warps take the largest lists first) sorts the depth ranks of its list
+// One warp per tile (largest lists first, pulled from a counter) sorts the depth ranks of its list
 // ascending in place.  The list sits in registers, R a lane (entry i * 32 + lane in register i,
 // padded with the largest value), and a bitonic network orders it: partners closer than 32
 // entries are exchanged by shuffles, wider ones are the same lane's registers.  The ranks of a
@@ -683,8 +661,11 @@ __global__ void __launch_bounds__(256) sort_lists(const uint2* __restrict__ rang
                                                   int tiles, uint32_t* __restrict__ lists, WsHeader* hdr) {
   if (!hdr->scatter || hdr->pair_n == 0 || render_dead(hdr)) return;
   const int lane = threadIdx.x & 31;
-  const int warps = gridDim.x * (blockDim.x >> 5);
-  for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < tiles; item += warps) {
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&hdr->sort_next, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= (unsigned)tiles) break;
     const uint2 rg = ranges[order[item]];
     const int n = (int)(rg.y - rg.x);
     uint32_t* L = lists + rg.x;
@@ -699,37 +680,17 @@ __global__ void __launch_bounds__(256) sort_lists(const uint2* __restrict__ rang
   }
 }
 
-// Lists of 1025 .. kSortMaxList entries (few, if any): a block per list, the list padded to a
-// power of two in shared memory and sorted by the same bitonic network with a barrier per stage.
-constexpr int kLongSortThreads = 512;
-__global__ void __launch_bounds__(kLongSortThreads) sort_long_lists(const uint2* __restrict__ ranges, int tiles,
-                                                                    uint32_t* __restrict__ lists,
-                                                                    const WsHeader* hdr) {
+// Lists of 1025 .. kSortMaxList entries (few, if any), one warp each; kept out of sort_lists so
+// that the 64-register form does not set the register budget of the common one.
+__global__ void __launch_bounds__(256) sort_long_lists(const uint2* __restrict__ ranges, int tiles,
+                                                       uint32_t* __restrict__ lists, const WsHeader* hdr) {
   if (!hdr->scatter || hdr->pair_n == 0 || render_dead(hdr)) return;
-  __shared__ uint32_t sv[kSortMaxList];
-  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles; t += warps) {
     const uint2 rg = ranges[t];
     const int n = (int)(rg.y - rg.x);
-    if (n <= 1024 || n > kSortMaxList) continue;      // uniform over the block
-    int N = 2048;
-    while (N < n) N <<= 1;
-    uint32_t* L = lists + rg.x;
-    for (int e = threadIdx.x; e < N; e += kLongSortThreads) sv[e] = e < n ? L[e] : 0xFFFFFFFFu;
-    __syncthreads();
-    for (int k = 2; k <= N; k <<= 1) {
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int q = threadIdx.x; q < N / 2; q += kLongSortThreads) {
-          const int i = (q / j) * 2 * j + (q % j), p = i + j;   // the pair (i, i + j), i's bit j clear
-          const uint32_t a = sv[i], b = sv[p];
-          const bool asc = (i & k) == 0;
-          sv[i] = asc ? min(a, b) : max(a, b);
-          sv[p] = asc ? max(a, b) : min(a, b);
-        }
-        __syncthreads();
-      }
-    }
-    for (int e = threadIdx.x; e < n; e += kLongSortThreads) L[e] = sv[e];
-    __syncthreads();
+    if (n > 1024) warp_bitonic<64>(lists + rg.x, n, lane);   // n <= kSortMaxList in scatter mode
   }
 }
 
@@ -818,7 +779,7 @@ int onesweep_blocks() {
   return cached;
 }
 
-cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int rows, int64_t capacity, const Layout& L, char* ws,
+cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capacity, const Layout& L, char* ws,
                            cudaStream_t s) {
   const int B = sort_blocks();
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
@@ -864,7 +825,6 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int rows, int
     cudaMemsetAsync(tdiff, 0, (size_t)kCountCopies * tiles * sizeof(unsigned), side);
     tile_count<<<2 * std::max(1, sort_blocks()), 256, 0, side>>>(tab, U(L.vis_ids), U(L.touched), rects, hdr, tdiff,
                                                                 tiles);
-    tile_rows<<<(rows + 7) / 8, 256, 0, side>>>(tab, tiles, tdiff);
     tile_prep<<<1, kPrepThreads, smem, side>>>(tab, tiles, cap, tpasses, tdiff, ranges, ctl->hist[1][0], U(L.order),
                                                U(L.cursor), hdr);
     if (join) cudaEventRecord(join, side);
@@ -903,8 +863,8 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int rows, int
     // scatter mode: each list ordered by depth rank (the radix passes above returned at once);
     // radix mode: this returns at once
     sort_lists<<<4 * B, 256, 0, s>>>(ranges, U(L.order), tiles, U(L.pvals[0]), hdr);
-    sort_long_lists<<<std::max(1, std::min(B, tiles)), kLongSortThreads, 0, s>>>(ranges, tiles, U(L.pvals[0]), hdr);
-    note_launches(kMaxPasses + 3 + tpasses + 5);
+    sort_long_lists<<<std::max(1, std::min(B, (tiles + 7) / 8)), 256, 0, s>>>(ranges, tiles, U(L.pvals[0]), hdr);
+    note_launches(kMaxPasses + 3 + tpasses + 4);
     return cudaGetLastError();
   }
   note_launches(kMaxPasses + 4 + tpasses + 1);

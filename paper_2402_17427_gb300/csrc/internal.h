@@ -117,6 +117,7 @@ struct WsHeader {
   unsigned int pad[3];
   unsigned long long evals_run_bwd;  // pixel slots the backward pass evaluated (optional count)
   unsigned int scatter;         // tile lists built by scatter + per-list sort (else radix passes)
+  unsigned int sort_next;       // work counter of the per-list sort
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
@@ -226,8 +227,8 @@ cudaError_t launch_zero_culled(const DevTables* tab, int total_n, int degree, co
 
 // Depth order of the visible Gaussians, pair generation (with the depth-ordered splat records),
 // tile sort, ranges and the largest-first order of the tiles.
-cudaError_t launch_binning(const DevTables* tab, int total_n, int total_tiles, int total_rows, int64_t capacity,
-                           const Layout& L, char* ws, cudaStream_t s);
+cudaError_t launch_binning(const DevTables* tab, int total_n, int total_tiles, int64_t capacity, const Layout& L,
+                           char* ws, cudaStream_t s);
 
 cudaError_t launch_blend_forward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool count,
                                  cudaStream_t s);

@@ -110,11 +110,11 @@ def test_strict_lists_blob_cell_1080p_full_frame():
     assert _check_key_path(uvrd, orc) > 100_000
 
 
-@pytest.mark.parametrize("n,longest", [(1600, (1025, 8192)), (12000, (8193, 10 ** 9))])
+@pytest.mark.parametrize("n,longest", [(1600, (1025, 2048)), (3000, (2049, 10 ** 9))])
 def test_strict_lists_long_lists_both_list_builders(n, longest):
-    """Dense clusters whose longest tile list is 1025..8192 entries (scattered into place and the
-    long lists sorted by a block in shared memory) or longer than 8192 (the radix passes instead):
-    both give exactly the oracle's lists."""
+    """Dense clusters whose longest tile list is 1025..2048 entries (scattered into place and
+    sorted by the 64-register warp sort) or longer than 2048 (the radix passes instead): both
+    give exactly the oracle's lists."""
     g, cam, _ = scenes.tiny_scene(n=n, width=96, height=64, degree=1, seed=8, box=0.25, log_scale=(-3.0, 0.3))
     s = R.RasterSettings()
     r, uvrd, cnt = _render_recording(g, cam, s)
