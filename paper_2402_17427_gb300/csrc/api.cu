@@ -31,8 +31,6 @@ __global__ void __launch_bounds__(256) init_header(WsHeader* hdr, SortCtl* ctl) 
   hdr->pair_n = 0;
   hdr->tile_bits = 0;
   hdr->evals_run_bwd = 0;
-  hdr->scatter = 0;
-  hdr->sort_next = 0;
   for (int k = 0; k < kTileClasses; ++k) hdr->work_fwd[k] = hdr->work_bwd[k] = 0;
 }
 

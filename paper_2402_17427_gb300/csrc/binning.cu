@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     unsigned long long* __restrict__ status_next, WsHeader* hdr) {
   constexpr int TILE = kSortThreads * ITEMS;
   if (render_dead(hdr)) return;   // an earlier look-back gave up: nothing later is sorted
-  if (!depth && hdr->scatter) return;   // the tile lists were scattered into place (sort_lists)
   if (depth) {
     // the depth keys agree above bit 32 - clz(dmin ^ dmax): only the passes below it run
     const unsigned lo = hdr->dmin, hi = hdr->dmax;
@@ -245,8 +244,7 @@ __global__ void __launch_bounds__(256) pairs_scan(unsigned long long* __restrict
 }
 
 // Every visible Gaussian (in depth order s) owns the pairs [offset, offset + tiles touched): one
-// (global tile, s) pair per tile of its rectangle, tiles row-major.  In scatter mode only s is
-// written, into its tile's list (in arbitrary order within the list; sort_lists orders it).  It also writes its splat
+// (global tile, s) pair per tile of its rectangle, tiles row-major.  It also writes its splat
 // record, carrying s, to slot s of the depth-ordered record array, and s to its own record.
 // A block takes 256 Gaussians at a time and its threads emit their pairs cooperatively (thread k
 // writes pair k of the batch, finding its owner by binary search), so writes are coalesced and
@@ -257,12 +255,8 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
                                                   const unsigned long long* __restrict__ blocksums,
                                                   unsigned long long cap, uint32_t* __restrict__ pkeys,
                                                   uint32_t* __restrict__ pvals, Splat* __restrict__ splats,
-                                                  Splat* __restrict__ vsplats, unsigned long long* __restrict__ status0,
-                                                  unsigned* __restrict__ cursor, uint32_t* __restrict__ lists) {
+                                                  Splat* __restrict__ vsplats, unsigned long long* __restrict__ status0) {
   if (hdr->pair_n == 0) return;   // no pairs, or more than the capacity (nothing is sorted)
-  // scatter mode (the tile ranges are known and every list is short enough for sort_lists): each
-  // pair goes straight into its tile's range, at the next free slot of the tile's cursor
-  const bool scatter = cursor != nullptr && hdr->scatter != 0;
   // with the tile counts known in advance (tile_prep), this kernel clears the first tile-sort
   // pass's look-back rows
   if (status0) zero_status(status0, (hdr->pair_n + kTileTile - 1) / kTileTile);
@@ -312,14 +306,8 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
       const int within = (int)(k - s_off[lo]);
       const int w = s_w[lo];
       const int ty = s_ty0[lo] + within / w, tx = s_tx0[lo] + within % w;
-      const uint32_t tile = (uint32_t)(s_base[lo] + ty * s_tilesx[lo] + tx);
-      if (scatter) {
-        const unsigned pos = atomicAdd(cursor + tile, 1u);
-        if (pos < cap) lists[pos] = s_rank[lo];
-      } else {
-        pkeys[j] = tile;
-        pvals[j] = s_rank[lo];
-      }
+      pkeys[j] = (uint32_t)(s_base[lo] + ty * s_tilesx[lo] + tx);
+      pvals[j] = s_rank[lo];
     }
     run += tot;
     __syncthreads();
@@ -479,17 +467,15 @@ __global__ void __launch_bounds__(256) tile_count(const DevTables* __restrict__ 
 // With nothing to sort (no pairs, or more than cap) every range is empty, as the sort leaves it.
 constexpr int kPrepThreads = 256;
 constexpr int kPrepTiles = 16384;        // tiles of a render that takes this path (two words each)
-constexpr int kSortMaxList = 2048;       // longest list sort_lists takes (64 registers a lane)
 
 __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __restrict__ tab, int tiles, unsigned cap,
                                                           int tpasses, const unsigned* __restrict__ tdiff,
                                                           uint2* __restrict__ ranges, unsigned* __restrict__ hist,
-                                                          uint32_t* __restrict__ order, unsigned* __restrict__ cursor,
-                                                          WsHeader* __restrict__ hdr) {
+                                                          uint32_t* __restrict__ order) {
   extern __shared__ unsigned s_c[];      // [tiles] counts, then [tiles] exclusive offsets
   unsigned* s_x = s_c + tiles;
   __shared__ unsigned s_h[kMaxPasses][kRadix];
-  __shared__ unsigned s_cnt[kBuckets + 1];   // bucket counts, then the longest list
+  __shared__ unsigned s_cnt[kBuckets];
   __shared__ unsigned long long sm[8];
   // the replicas of tile_count's differences, summed; eight loads in flight per thread
   for (int t0 = 0; t0 < tiles; t0 += 8 * kPrepThreads) {
@@ -510,7 +496,7 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
     }
   }
   for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) s_h[k / kRadix][k % kRadix] = 0;
-  for (int k = threadIdx.x; k <= kBuckets; k += blockDim.x) s_cnt[k] = 0;
+  for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) s_cnt[k] = 0;
   __syncthreads();
   // 1. counts: an inclusive scan along every tile row of every view, a warp per row
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -547,7 +533,6 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
   }
   const bool any = run > 0 && run <= cap;
   const uint32_t lt = lanemask_lt();
-  unsigned longest = 0;
   // 3. ranges, digit histograms, order buckets (view by view: the bucket needs the tile class);
   //    lanes adding to the same shared counter are merged first
   for (int v = 0; v < tab->h.n_views; ++v) {
@@ -557,11 +542,7 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
       const int t = t0 + (int)threadIdx.x;
       const bool in = t < t_end;
       const unsigned c = in && any ? s_c[t] : 0u;
-      if (in) {
-        ranges[t] = c ? make_uint2(s_x[t], s_x[t] + c) : make_uint2(0u, 0u);
-        cursor[t] = s_x[t];
-      }
-      longest = max(longest, c);
+      if (in) ranges[t] = c ? make_uint2(s_x[t], s_x[t] + c) : make_uint2(0u, 0u);
       for (int p = 0; p < tpasses; ++p) {
         // consecutive lanes hold consecutive tiles, so equal digits sit in runs of lanes: a
         // segmented scan leaves each run's sum in its last lane, which adds it
@@ -583,12 +564,7 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
       if (in && (peers & lt) == 0) atomicAdd(&s_cnt[bk], (unsigned)__popc(peers));
     }
   }
-  // the list-building mode: scatter + per-list sort when every list fits one warp's registers
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) longest = max(longest, __shfl_xor_sync(0xffffffffu, longest, o));
-  if (lane == 0) atomicMax(&s_cnt[kBuckets], longest);
   __syncthreads();
-  if (threadIdx.x == 0) hdr->scatter = s_cnt[kBuckets] <= (unsigned)kSortMaxList ? 1u : 0u;
   for (int k = threadIdx.x; k < tpasses * kRadix; k += blockDim.x) hist[k] = s_h[k / kRadix][k % kRadix];
   if (threadIdx.x == 0) {
     unsigned acc = 0;
@@ -608,89 +584,6 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
     if (bk != 0xFFFFFFFFu && (peers & lt) == 0) base = atomicAdd(&s_cnt[bk], (unsigned)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (bk != 0xFFFFFFFFu) order[base + __popc(peers & lt)] = (uint32_t)t;
-  }
-}
-
-// ---- 5. per-list sort of the scattered tile lists ---------------------------------------------
-// One warp per tile (largest lists first, pulled from a counter) sorts the depth ranks of its list
-// ascending in place.  The list sits in registers, R a lane (entry i * 32 + lane in register i,
-// padded with the largest value), and a bitonic network orders it: partners closer than 32
-// entries are exchanged by shuffles, wider ones are the same lane's registers.  The ranks of a
-// list are distinct, so the result is the list a stable sort by (tile, depth rank) gives.
-template <int R>
-__device__ __forceinline__ void warp_bitonic(uint32_t* __restrict__ list, int n, int lane) {
-  uint32_t v[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int e = i * 32 + lane;
-    v[i] = e < n ? list[e] : 0xFFFFFFFFu;
-  }
-#pragma unroll
-  for (int k = 2; k <= 32 * R; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-        const int jj = j >> 5;
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          if (i & jj) continue;                  // the pair's lower register
-          const bool asc = ((i * 32) & k) == 0;  // k >= 64: a bit of the register index
-          const uint32_t a = v[i], b = v[i | jj];
-          v[i] = asc ? min(a, b) : max(a, b);
-          v[i | jj] = asc ? max(a, b) : min(a, b);
-        }
-      } else {
-        const bool lower = (lane & j) == 0;
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const uint32_t o = __shfl_xor_sync(0xffffffffu, v[i], j);
-          const bool asc = ((i * 32 + lane) & k) == 0;
-          v[i] = lower == asc ? min(v[i], o) : max(v[i], o);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int e = i * 32 + lane;
-    if (e < n) list[e] = v[i];
-  }
-}
-
-__global__ void __launch_bounds__(256) sort_lists(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
-                                                  int tiles, uint32_t* __restrict__ lists, WsHeader* hdr) {
-  if (!hdr->scatter || hdr->pair_n == 0 || render_dead(hdr)) return;
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned item = 0;
-    if (lane == 0) item = atomicAdd(&hdr->sort_next, 1u);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= (unsigned)tiles) break;
-    const uint2 rg = ranges[order[item]];
-    const int n = (int)(rg.y - rg.x);
-    uint32_t* L = lists + rg.x;
-    if (n <= 1) continue;
-    if (n <= 32) warp_bitonic<1>(L, n, lane);
-    else if (n <= 64) warp_bitonic<2>(L, n, lane);
-    else if (n <= 128) warp_bitonic<4>(L, n, lane);
-    else if (n <= 256) warp_bitonic<8>(L, n, lane);
-    else if (n <= 512) warp_bitonic<16>(L, n, lane);
-    else if (n <= 1024) warp_bitonic<32>(L, n, lane);
-    // longer lists: sort_long_lists
-  }
-}
-
-// Lists of 1025 .. kSortMaxList entries (few, if any), one warp each; kept out of sort_lists so
-// that the 64-register form does not set the register budget of the common one.
-__global__ void __launch_bounds__(256) sort_long_lists(const uint2* __restrict__ ranges, int tiles,
-                                                       uint32_t* __restrict__ lists, const WsHeader* hdr) {
-  if (!hdr->scatter || hdr->pair_n == 0 || render_dead(hdr)) return;
-  const int lane = threadIdx.x & 31;
-  const int warps = gridDim.x * (blockDim.x >> 5);
-  for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles; t += warps) {
-    const uint2 rg = ranges[t];
-    const int n = (int)(rg.y - rg.x);
-    if (n > 1024) warp_bitonic<64>(lists + rg.x, n, lane);   // n <= kSortMaxList in scatter mode
   }
 }
 
@@ -736,7 +629,6 @@ Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
   L.order = take(tiles * 4);
   L.buckets = take(2 * kBuckets * 4);
   L.tcount = take(std::min<size_t>(tiles, kPrepTiles) * kCountCopies * 4);   // tile_count's replicas
-  L.cursor = take(std::min<size_t>(tiles, kPrepTiles) * 4);                   // scatter cursors
   L.blocksums = take((size_t)kMaxSortBlocks * 8);
   // look-back rows of either sort
   const size_t parts = std::max((N + kDepthTile - 1) / kDepthTile, (P + kTileTile - 1) / kTileTile);
@@ -825,8 +717,7 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
     cudaMemsetAsync(tdiff, 0, (size_t)kCountCopies * tiles * sizeof(unsigned), side);
     tile_count<<<2 * std::max(1, sort_blocks()), 256, 0, side>>>(tab, U(L.vis_ids), U(L.touched), rects, hdr, tdiff,
                                                                 tiles);
-    tile_prep<<<1, kPrepThreads, smem, side>>>(tab, tiles, cap, tpasses, tdiff, ranges, ctl->hist[1][0], U(L.order),
-                                               U(L.cursor), hdr);
+    tile_prep<<<1, kPrepThreads, smem, side>>>(tab, tiles, cap, tpasses, tdiff, ranges, ctl->hist[1][0], U(L.order));
     if (join) cudaEventRecord(join, side);
   }
   // 1. depth sort of the visible Gaussians (compacted by the projection kernel); passes beyond
@@ -843,14 +734,13 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   const int BP = kMaxSortBlocks < 6 * B / 2 ? kMaxSortBlocks : 6 * B / 2;   // 6 blocks per SM
   pairs_count<<<BP, 256, 0, s>>>(U(L.vvals[0]), U(L.vvals[1]), U(L.touched), hdr, bsum64);
   pairs_scan<<<1, 256, 0, s>>>(bsum64, BP, hdr, (unsigned long long)cap);
-  // ranges, histograms, order, cursors and the list-building mode are ready before the emission
-  if (join) cudaStreamWaitEvent(s, join, 0);
-  if (fork) cudaEventDestroy(fork);            // released once the recorded work completes
-  if (join) cudaEventDestroy(join);
   pairs_emit<<<BP, 256, 0, s>>>(tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), rects, hdr, bsum64,
                                (unsigned long long)cap, U(L.pkeys[p0]), U(L.pvals[p0]), splats, vsplats,
-                               prep ? S64(0) : nullptr, prep ? U(L.cursor) : nullptr, U(L.pvals[0]));
+                               prep ? S64(0) : nullptr);
   if (!prep) tile_histogram<<<B * 2, 256, 0, s>>>(U(L.pkeys[p0]), hdr, tpasses, ctl->hist[1][0], S64(0));
+  if (join) cudaStreamWaitEvent(s, join, 0);   // ranges, histograms and order ready
+  if (fork) cudaEventDestroy(fork);            // released once the recorded work completes
+  if (join) cudaEventDestroy(join);
   // 3. stable sort of the pairs by tile id
   for (int pass = 0; pass < tpasses; ++pass) {
     const int src = (p0 + pass) & 1, dst = src ^ 1;
@@ -860,11 +750,7 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
                                               pass + 1 < tpasses ? S64((pass + 1) & 1) : nullptr, hdr);
   }
   if (prep) {
-    // scatter mode: each list ordered by depth rank (the radix passes above returned at once);
-    // radix mode: this returns at once
-    sort_lists<<<4 * B, 256, 0, s>>>(ranges, U(L.order), tiles, U(L.pvals[0]), hdr);
-    sort_long_lists<<<std::max(1, std::min(B, (tiles + 7) / 8)), 256, 0, s>>>(ranges, tiles, U(L.pvals[0]), hdr);
-    note_launches(kMaxPasses + 3 + tpasses + 4);
+    note_launches(kMaxPasses + 3 + tpasses + 2);
     return cudaGetLastError();
   }
   note_launches(kMaxPasses + 4 + tpasses + 1);

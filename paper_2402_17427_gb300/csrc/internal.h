@@ -116,8 +116,6 @@ struct WsHeader {
   unsigned int work_bwd[kTileClasses];
   unsigned int pad[3];
   unsigned long long evals_run_bwd;  // pixel slots the backward pass evaluated (optional count)
-  unsigned int scatter;         // tile lists built by scatter + per-list sort (else radix passes)
-  unsigned int sort_next;       // work counter of the per-list sort
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
@@ -169,7 +167,7 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 // Offsets (bytes) of the regions of one render workspace (any number of views / segments).
 struct Layout {
   size_t header, sortctl, tables, splats, rects, touched, vis_ids, vkeys[2], vvals[2], pkeys[2], pvals[2],
-      vsplats, ranges, order, buckets, tcount, cursor, blocksums, status[2], g2d, total;
+      vsplats, ranges, order, buckets, tcount, blocksums, status[2], g2d, total;
 };
 Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t pair_capacity);
 

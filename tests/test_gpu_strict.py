@@ -110,22 +110,6 @@ def test_strict_lists_blob_cell_1080p_full_frame():
     assert _check_key_path(uvrd, orc) > 100_000
 
 
-@pytest.mark.parametrize("n,longest", [(1600, (1025, 2048)), (3000, (2049, 10 ** 9))])
-def test_strict_lists_long_lists_both_list_builders(n, longest):
-    """Dense clusters whose longest tile list is 1025..2048 entries (scattered into place and
-    sorted by the 64-register warp sort) or longer than 2048 (the radix passes instead): both
-    give exactly the oracle's lists."""
-    g, cam, _ = scenes.tiny_scene(n=n, width=96, height=64, degree=1, seed=8, box=0.25, log_scale=(-3.0, 0.3))
-    s = R.RasterSettings()
-    r, uvrd, cnt = _render_recording(g, cam, s)
-    assert cnt[B.VG_CNT_STATUS] == 0
-    st = read_state(r, g, cam)
-    lens = st["ranges"][:, 1] - st["ranges"][:, 0]
-    assert longest[0] <= lens.max() <= longest[1], lens.max()
-    P = _assert_lists_identical(st["ranges"], st["ids"], int(cnt[B.VG_CNT_PAIRS]), uvrd, cam.width, cam.height, 16)
-    assert P == int(cnt[B.VG_CNT_PAIRS])
-
-
 @pytest.mark.slow
 def test_strict_lists_aerial_cells_batched_mixed_tiles():
     """Eight uneven aerial cells (0.3M..3.0M, 1152x864) in one batched call with tile sizes 8, 16
