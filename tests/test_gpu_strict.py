@@ -110,6 +110,21 @@ def test_strict_lists_blob_cell_1080p_full_frame():
     assert _check_key_path(uvrd, orc) > 100_000
 
 
+@pytest.mark.parametrize("n,longest", [(1600, 1249), (12000, 9361)])
+def test_strict_lists_dense_clusters_with_long_lists(n, longest):
+    """Dense clusters whose longest tile list holds over a thousand and over nine thousand entries
+    (the oracle's count): every list equals the oracle's from the kernel's own FP32 inputs."""
+    g, cam, _ = scenes.tiny_scene(n=n, width=96, height=64, degree=1, seed=8, box=0.25, log_scale=(-3.0, 0.3))
+    s = R.RasterSettings()
+    r, uvrd, cnt = _render_recording(g, cam, s)
+    assert cnt[B.VG_CNT_STATUS] == 0
+    st = read_state(r, g, cam)
+    lens = st["ranges"][:, 1] - st["ranges"][:, 0]
+    assert abs(int(lens.max()) - longest) <= 2, lens.max()
+    P = _assert_lists_identical(st["ranges"], st["ids"], int(cnt[B.VG_CNT_PAIRS]), uvrd, cam.width, cam.height, 16)
+    assert P == int(cnt[B.VG_CNT_PAIRS])
+
+
 @pytest.mark.slow
 def test_strict_lists_aerial_cells_batched_mixed_tiles():
     """Eight uneven aerial cells (0.3M..3.0M, 1152x864) in one batched call with tile sizes 8, 16
