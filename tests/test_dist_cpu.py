@@ -75,7 +75,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     sys.path.insert(0, ROOT)
     import bench
     calls = []
-    monkeypatch.setattr(bench, "oracle_step_time", lambda *a, **k: calls.append(a) or (1.0, 1, "x"))
+    monkeypatch.setattr(bench, "oracle_sampled_step", lambda *a, **k: calls.append(a) or (1.0, 2.0, 1, "x"))
     # a rank other than 0 returns before reading its arguments, the scene or the oracle
     assert bench.run_reference(None, 2, 1) is None
     assert calls == []
