@@ -298,37 +298,108 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
   return cuda_status(cudaGetLastError());
 }
 
-// One non-blocking helper stream per device for work forked off the caller's stream.
+}  // namespace
+
+// The unique id of the current context, from the driver (cuCtxGetCurrent, cuCtxGetId) through the
+// runtime's entry-point query, so that the library needs no link-time dependency on the driver
+// library.  Objects cached per device (side streams, events, module addresses) are keyed on it: a
+// device reset destroys them with their context, and the next call in the new context makes new
+// ones instead of using dead handles.
+bool current_context_id(unsigned long long* id) {
+  typedef int (*CtxGetCurrentFn)(void**);
+  typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  void* ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
+namespace {
+
+// The current device and context id; false if either is unknown (then nothing is cached).
+bool device_context(int* dev, unsigned long long* ctx) {
+  if (cudaGetDevice(dev) != cudaSuccess || *dev < 0 || *dev >= 64) return false;
+  if (current_context_id(ctx)) return true;
+  cudaFree(nullptr);                   // makes the device's primary context current if none is
+  return current_context_id(ctx);
+}
+
+struct SideStreams {
+  unsigned long long ctx = 0;
+  cudaStream_t fixed[kSideStreams] = {};
+  cudaStream_t keys[kSideCallers] = {}, sides[kSideCallers] = {};
+  int used = 0;
+};
+std::mutex g_side_mu;
+SideStreams g_side[64];
+
+// The device's side-stream set for the current context (emptied when the context changed).
+SideStreams* side_set(int* dev) {
+  unsigned long long ctx = 0;
+  if (!device_context(dev, &ctx)) return nullptr;
+  SideStreams& S = g_side[*dev];
+  if (S.ctx != ctx) S = SideStreams{ctx};
+  return &S;
+}
+
+struct CallEvents {
+  unsigned long long ctx = 0;
+  cudaEvent_t ev[kCallEvents] = {};
+};
+thread_local CallEvents t_events[64];
+
 }  // namespace
 
 cudaStream_t side_stream(int k) {
-  static std::mutex mu;
-  static cudaStream_t streams[64][kSideStreams] = {};
+  if (k < 0 || k >= kSideStreams) return nullptr;
+  std::lock_guard<std::mutex> lock(g_side_mu);
   int dev = 0;
-  if (k < 0 || k >= kSideStreams || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!streams[dev][k] && cudaStreamCreateWithFlags(&streams[dev][k], cudaStreamNonBlocking) != cudaSuccess)
-    streams[dev][k] = nullptr;
-  return streams[dev][k];
+  SideStreams* S = side_set(&dev);
+  if (!S) return nullptr;
+  if (!S->fixed[k] && cudaStreamCreateWithFlags(&S->fixed[k], cudaStreamNonBlocking) != cudaSuccess)
+    S->fixed[k] = nullptr;
+  return S->fixed[k];
 }
 
 cudaStream_t side_stream_for(cudaStream_t caller) {
-  constexpr int kCallers = 32;
-  static std::mutex mu;
-  static cudaStream_t keys[64][kCallers] = {}, sides[64][kCallers] = {};
-  static int used[64] = {};
+  std::lock_guard<std::mutex> lock(g_side_mu);
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  for (int i = 0; i < used[dev]; ++i)
-    if (keys[dev][i] == caller) return sides[dev][i];
-  if (used[dev] == kCallers) return nullptr;
+  SideStreams* S = side_set(&dev);
+  if (!S) return nullptr;
+  for (int i = 0; i < S->used; ++i)
+    if (S->keys[i] == caller) return S->sides[i];
+  if (S->used == kSideCallers) return nullptr;
   cudaStream_t side = nullptr;
   if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-  keys[dev][used[dev]] = caller;
-  sides[dev][used[dev]] = side;
-  ++used[dev];
+  S->keys[S->used] = caller;
+  S->sides[S->used] = side;
+  ++S->used;
   return side;
+}
+
+cudaEvent_t call_event(int slot) {
+  if (slot < 0 || slot >= kCallEvents) return nullptr;
+  int dev = 0;
+  unsigned long long ctx = 0;
+  if (!device_context(&dev, &ctx)) return nullptr;
+  CallEvents& E = t_events[dev];
+  if (E.ctx != ctx) E = CallEvents{ctx};
+  if (!E.ev[slot] && cudaEventCreateWithFlags(&E.ev[slot], cudaEventDisableTiming) != cudaSuccess)
+    E.ev[slot] = nullptr;
+  return E.ev[slot];
 }
 
 namespace {
@@ -357,9 +428,7 @@ vg_status run_backward(Call& c, const vg_raster_opts* opts0, void* workspace, si
   cudaEvent_t fork = nullptr, join = nullptr;
   if (!accumulate && c.total_n > 0) {
     cudaStream_t side = side_stream();
-    if (!side || cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)
-      return VG_ERR_CUDA;
+    if (!side || !(fork = call_event(kEvBackwardFork)) || !(join = call_event(kEvBackwardJoin))) return VG_ERR_CUDA;
     cudaEventRecord(fork, s);
     cudaStreamWaitEvent(side, fork, 0);
     e = launch_zero_culled(tab, c.total_n, c.degree, reinterpret_cast<const uint32_t*>(ws + L.touched), side);
@@ -370,11 +439,7 @@ vg_status run_backward(Call& c, const vg_raster_opts* opts0, void* workspace, si
                                    reinterpret_cast<const uint32_t*>(ws + L.vis_ids),
                                    reinterpret_cast<const WsHeader*>(ws + L.header),
                                    reinterpret_cast<const float*>(ws + L.g2d), accumulate, s);
-  if (join) {
-    cudaStreamWaitEvent(s, join, 0);   // always joined, so no work of the call outlives it on s
-    cudaEventDestroy(fork);            // released once the recorded work completes
-    cudaEventDestroy(join);
-  }
+  if (join) cudaStreamWaitEvent(s, join, 0);   // always joined, so no work of the call outlives it on s
   stage_event(ev, VG_STAGE_PROJECT_BACKWARD, false, s);
   return cuda_status(e);
 }

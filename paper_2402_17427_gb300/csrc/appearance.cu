@@ -1293,18 +1293,11 @@ cudaError_t launch_wgrad(const float* Aprev, const float* gA, const float* A, fl
   return cudaGetLastError();
 }
 
-// Events of one call's fork / join with the side stream, released at the end of the call (the
-// recorded work keeps them alive until it completes).
+// Events of one call's fork / join with the side streams: the call's own slots of the reused
+// per-thread events.
 struct Events {
-  cudaEvent_t ev[16] = {};
   int n = 0;
-  cudaEvent_t make() {
-    if (n == 16 || cudaEventCreateWithFlags(&ev[n], cudaEventDisableTiming) != cudaSuccess) return nullptr;
-    return ev[n++];
-  }
-  ~Events() {
-    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
-  }
+  cudaEvent_t make() { return n == kCallEvents - kEvAppearance ? nullptr : call_event(kEvAppearance + n++); }
 };
 
 // Makes `to` wait for the work enqueued so far on `from`.

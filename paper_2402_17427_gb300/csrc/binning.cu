@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "internal.h"
 #include "vg_common.cuh"
@@ -595,16 +596,19 @@ int ceil_log2(unsigned x) {
 
 }  // namespace
 
+// Per-device grid sizes, computed on first use; concurrent first calls compute the same value.
 int sort_blocks() {
-  static int cached = 0;
-  if (cached == 0) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cached = sms > 0 ? sms * 2 : 256;
-    if (cached > kMaxSortBlocks) cached = kMaxSortBlocks;
+    v = std::min(sms > 0 ? sms * 2 : 256, kMaxSortBlocks);
+    cached[dev].store(v, std::memory_order_relaxed);
   }
-  return cached;
+  return v;
 }
 
 Layout make_layout(int64_t total_n, int64_t total_tiles, int64_t cap) {
@@ -660,15 +664,18 @@ Compact make_compact(const Layout& L, char* ws, int total_n, const vg_raster_opt
 // Resident blocks of a look-back pass on this device (persistent grid).
 template <int ITEMS>
 int onesweep_blocks() {
-  static int cached = 0;
-  if (cached == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
+    int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_pass<ITEMS>, kSortThreads, 0);
-    cached = std::max(1, sms) * std::max(1, per_sm);
+    v = std::max(1, sms) * std::max(1, per_sm);
+    cached[dev].store(v, std::memory_order_relaxed);
   }
-  return cached;
+  return v;
 }
 
 cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capacity, const Layout& L, char* ws,
@@ -698,21 +705,24 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   cudaEvent_t fork = nullptr, join = nullptr;
   if (prep) {
     cudaStream_t side = side_stream_for(s);
-    if (side && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
-        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess) {
+    if (side && (fork = call_event(kEvBinningFork)) && (join = call_event(kEvBinningJoin))) {
       cudaEventRecord(fork, s);
       cudaStreamWaitEvent(side, fork, 0);
     } else {
       side = s;
+      join = nullptr;
     }
     unsigned* tdiff = U(L.tcount);
     const size_t smem = (size_t)2 * tiles * sizeof(unsigned);
-    static bool opted[64] = {};      // the shared-memory opt-in, once per device
+    // the shared-memory opt-in, once per device and context (function attributes live in the
+    // context); the flag is per host thread, so concurrent callers each make it once
+    thread_local unsigned long long opted_ctx[64] = {};
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !opted[dev]) {
+    unsigned long long ctx = 0;
+    const bool known = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && current_context_id(&ctx);
+    if (!known || opted_ctx[dev] != ctx) {
       cudaFuncSetAttribute(tile_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * kPrepTiles * sizeof(unsigned)));
-      if (dev >= 0 && dev < 64) opted[dev] = true;
+      if (known) opted_ctx[dev] = ctx;
     }
     cudaMemsetAsync(tdiff, 0, (size_t)kCountCopies * tiles * sizeof(unsigned), side);
     tile_count<<<2 * std::max(1, sort_blocks()), 256, 0, side>>>(tab, U(L.vis_ids), U(L.touched), rects, hdr, tdiff,
@@ -739,8 +749,6 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
                                prep ? S64(0) : nullptr);
   if (!prep) tile_histogram<<<B * 2, 256, 0, s>>>(U(L.pkeys[p0]), hdr, tpasses, ctl->hist[1][0], S64(0));
   if (join) cudaStreamWaitEvent(s, join, 0);   // ranges, histograms and order ready
-  if (fork) cudaEventDestroy(fork);            // released once the recorded work completes
-  if (join) cudaEventDestroy(join);
   // 3. stable sort of the pairs by tile id
   for (int pass = 0; pass < tpasses; ++pass) {
     const int src = (p0 + pass) & 1, dst = src ^ 1;

@@ -233,14 +233,28 @@ cudaError_t launch_blend_forward(const DevTables* tab, const HostPlan& plan, con
 cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, const Layout& L, char* ws, bool abs,
                                   bool count, cudaStream_t s);
 
-// Non-blocking streams per device (created on first use) for work that overlaps the caller's
-// stream; callers fork to them and join back with events within the same call.
+// Unique id of the current CUDA context (false if none is current or the driver cannot say).
+bool current_context_id(unsigned long long* id);
+
+// Non-blocking streams per device and context (created on first use) for work that overlaps the
+// caller's stream; callers fork to them and join back with events within the same call.
 constexpr int kSideStreams = 4;
+constexpr int kSideCallers = 32;
 cudaStream_t side_stream(int k = 0);
 // A side stream of the current device dedicated to work forked from `caller`, so that forks from
 // calls running concurrently on different streams do not queue behind one another (created on
 // first use; nullptr once 32 callers of this device have one, or if creation fails).
 cudaStream_t side_stream_for(cudaStream_t caller);
+
+// Fork / join events, created once per host thread, device and context and reused by every call:
+// each call site owns its slots.  Recording an event again while earlier waits on it are pending
+// is legal, since each cudaStreamWaitEvent takes the record that precedes it in host order, and
+// one thread's calls are issued one after another.  nullptr if creation fails.
+enum CallEventSlot {
+  kEvBackwardFork, kEvBackwardJoin, kEvBinningFork, kEvBinningJoin, kEvLossFork, kEvLossJoin,
+  kEvAppearance, kCallEvents = kEvAppearance + 16
+};
+cudaEvent_t call_event(int slot);
 
 // SSIM half of the loss (loss.cu), for the appearance loss of Eq. 3: the moment pass (maps
 // [9][H][W], partials [ssim_partials][2] = (sum S, sum |x - y|) per block) and the gradient pass

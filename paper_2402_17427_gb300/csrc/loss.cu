@@ -386,8 +386,8 @@ Win make_window() {
 cudaError_t finalize_beside(const double* partials, int nb, double inv, float lambda, float* out_loss, bool beside,
                             cudaStream_t s, cudaEvent_t* fork, cudaEvent_t* join) {
   cudaStream_t side = beside ? side_stream(1) : nullptr;
-  if (!side || cudaEventCreateWithFlags(fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(join, cudaEventDisableTiming) != cudaSuccess) {
+  if (!side || !(*fork = call_event(kEvLossFork)) || !(*join = call_event(kEvLossJoin))) {
+    *join = nullptr;
     loss_finalize<<<1, 1024, 0, s>>>(partials, nb, inv, lambda, out_loss);
     return cudaGetLastError();
   }
@@ -450,8 +450,6 @@ extern "C" vg_status vg_loss_l1_dssim(const float* img, const float* target, int
   if (out_grad)
     ssim_backward_kernel<false><<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
   if (join) cudaStreamWaitEvent(s, join, 0);   // nothing of the call outlives it on s
-  if (fork) cudaEventDestroy(fork);
-  if (join) cudaEventDestroy(join);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? VG_OK : VG_ERR_CUDA;
 }
@@ -499,32 +497,8 @@ static __device__ __align__(256) unsigned char g_loss_scratch[kNoAllocBytes];
 // the first call in each CUDA context and cached per device together with that context's unique
 // id.  A device reset or a new primary context loads the module again, possibly at another
 // address, so a call made in a different context than the cached one looks the address up again.
-// The context id comes from the driver (cuCtxGetCurrent, cuCtxGetId) through the runtime's
-// entry-point query, so the library needs no link-time dependency on the driver library; where
-// that query is unavailable the address is looked up on every call.
-typedef int (*CtxGetCurrentFn)(void**);
-typedef int (*CtxGetIdFn)(void*, unsigned long long*);
-
-bool current_context_id(unsigned long long* id) {
-  static CtxGetCurrentFn get_current = nullptr;
-  static CtxGetIdFn get_id = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
-    f = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      get_id = reinterpret_cast<CtxGetIdFn>(f);
-  });
-  void* ctx = nullptr;
-  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
-  return get_id(ctx, id) == 0;
-}
-
+// Where the context id is unavailable (current_context_id, api.cu) the address is looked up on
+// every call.
 struct ScratchSlot {
   void* addr = nullptr;
   unsigned long long ctx_id = 0;
