@@ -22,7 +22,9 @@
  *
  * Arithmetic: FP32-accurate throughout.  The convolutions after the first run on the tensor cores
  * with each FP32 operand split into two TF32 parts and each product formed from three MMAs
- * (relative error about 2^-21 a product) and FP32 accumulation; everything else is FP32.
+ * (relative error about 2^-21 a product) and FP32 accumulation: the four up-sampling blocks on
+ * warp-level MMAs, the two full-resolution convolutions and their adjoints on the fifth-generation
+ * tensor cores (tcgen05, accumulators in tensor memory).  Everything else is FP32.
  *
  * Conventions are those of vgrast.h: device pointers, caller-owned memory, asynchronous on
  * `stream`, argument errors returned before any launch.
@@ -62,6 +64,8 @@ size_t vg_appearance_workspace_bytes(int32_t width, int32_t height);
  *                    when grad_img is NULL
  * Gradients of the sums of many terms use atomic additions, so they are not bit-reproducible
  * from run to run (the loss and the map are).
+ * Every wait of the tensor-core passes on their MMAs is bounded (1 s); one that gives up makes
+ * *out_loss NaN (the other outputs are then undefined) and leaves the context usable.
  * Errors: VG_ERR_INVALID (NULL where a pointer is required, sizes, lambda, gradient pointers
  * partly NULL), VG_ERR_CAPACITY (workspace too small), VG_ERR_CUDA (launch failure). */
 vg_status vg_appearance_loss(const float* img, const float* target, int32_t width, int32_t height,

@@ -22,11 +22,11 @@
 //    channels, the input tile and its halo staged once in shared memory.  Their adjoints are the
 //    same kernel (input gradient = convolution with the flipped, transposed weights) and a
 //    weight-gradient GEMM (K = pixels).
-//  * the full-resolution head is one persistent kernel over 16 x 16 output tiles that keeps every
-//    intermediate in shared memory: bilinear U over the tile + 4, Hh = ReLU(conv5 U) over + 3,
-//    M = conv6 Hh over + 2, the L1 term, dL/dM, then the whole adjoint back to dL/dF4 (scattered
-//    by the bilinear adjoint), dL/dW5 and dL/dW6.  Only F4, the two images and the gradients
-//    touch HBM; the 16-channel full-resolution maps never do.
+//  * the full-resolution head: bilinear up-sampling of F4 to U, then conv5, conv6 (with the L1
+//    term), conv6's adjoint and conv5's adjoint as four passes of one implicit-GEMM kernel on the
+//    fifth-generation tensor cores (tcgen05.mma kind::tf32 with the accumulator in tensor memory,
+//    the same three-product split for FP32-accurate products), the up-sampling's adjoint as two
+//    gathers, and the head's weight gradients in FP32 on the CUDA cores.
 //  * the SSIM half and the block-mean gradient reuse the loss kernels of Eq. 1.
 // The backward pass works in units of c = (1 - lambda) / (3 H W) (dL/dI_a = c sign(I_a - I)),
 // multiplying by c where results leave the head.
@@ -37,6 +37,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "tcgen05.cuh"
 #include "vg_common.cuh"
 #include "vgappearance.h"
 
@@ -77,7 +78,6 @@ __device__ __forceinline__ void mma8(float (&d)[4], const float (&a)[4], float b
       : "r"(__float_as_uint(a[0])), "r"(__float_as_uint(a[1])), "r"(__float_as_uint(a[2])),
         "r"(__float_as_uint(a[3])), "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)));
 }
-__device__ __forceinline__ void mma8(float (&d)[4], const float (&a)[4], float2 b) { mma8(d, a, b.x, b.y); }
 
 // FP32-accurate products on the TF32 tensor cores: x = hi + lo with hi = tf32(x) and lo =
 // tf32(x - hi) (x - hi is exact in FP32), and A B ~ Ahi Bhi + Ahi Blo + Alo Bhi.  The dropped
@@ -126,7 +126,7 @@ __device__ __forceinline__ void mma8x3(float (&d)[4], const Split4& a, const Spl
 struct PackJob {
   int layer, dgrad, tapc, kpad, npad, offset;   // offset in floats
 };
-constexpr int kPackJobs = 12;
+constexpr int kPackJobs = 8;
 struct PackTable {
   PackJob job[kPackJobs];
   int begin[kPackJobs + 1];   // first element index of each job in the launch's index space
@@ -647,44 +647,284 @@ __global__ void __launch_bounds__(256) conv0_embed_grad_kernel(const float* __re
 
 // ---------------------------------------------------------------- full-resolution head
 //
-// One persistent block per SM takes 16 x 16 output tiles T at (oy, ox); R_k = T grown by k pixels.
-// The head's GEMMs run on the tensor cores as mma.sync m16n8k8 on TF32 operands with every FP32
-// operand split into two TF32 parts and each product formed from three MMAs (FP32-accurate
-// products, FP32 accumulation).  Operands are FP32 in shared memory (pixel pitches of 20 floats,
-// so the 8 x 4 lanes of a fragment load that run along pixels x channels hit distinct banks):
-//   sU  U over R4 (24 x 24 pixels x 16 channels), copied with cp.async from the up-sampled image
-//       (computed once by upsample_kernel) while the previous tile finishes
-//   sH  Hh = ReLU(Z5) over R3 (22 x 22)
-//   sZ  gZ5' = (conv6 adjoint of gM') * [Hh > 0] over R1 (18 x 18)
-//   sG  gM' = sign(I_a - I) I_r over R2 (20 x 20, pitch 12, channels 3.. zero)
-//   sI  I_r and I over R2 (FP32 planes, zero outside the image), fetched with cp.async at the
-//       start of the tile
-//   tables: bilinear taps (first, second source row / column, weight of the second) of R4's
-//       rows and columns, -1 outside the image; per footprint row and column, the run of T's rows
-//       and columns that reach it
-// After the GEMMs, sH holds dL/dU over T and sZ its column-reduced form for the bilinear adjoint.
-constexpr int HT = 16;
-constexpr int R4 = HT + 8, R3 = HT + 6, R2 = HT + 4, R1 = HT + 2;
-constexpr int PU = 20;                // floats per pixel in sU / sH / sZ (16 channels + 4)
-constexpr int PG = 12;                // floats per pixel in sG (8 channels + 4)
-constexpr int FT = 10;                // dL/dF4 footprint side of T
-constexpr int kHeadThreads = 256;
-constexpr int kBU = R4 * R4 * PU * 4, kBH = R3 * R3 * PU * 4, kBZ = R1 * R1 * PU * 4, kBG = R2 * R2 * PG * 4;
-constexpr int kBI = 2 * 3 * R2 * R2 * 4, kBT = 6 * R4 * 4 + 4 * FT * 4;
-constexpr int kHeadSmemBytes = kBU + kBH + kBZ + kBG + kBI + kBT;
-static_assert(HT * HT * 16 * 4 <= kBH && HT * FT * 16 * 4 <= kBZ, "bilinear adjoint buffers fit");
-static_assert(kBU % 16 == 0 && kBH % 16 == 0 && kBZ % 16 == 0 && kBG % 16 == 0 && kBI % 16 == 0, "alignment");
-static_assert(kHeadSmemBytes <= 227 * 1024, "one block an SM");
+// At the image's resolution the head's 16-channel maps do not fit on chip, so each of its four 3 x 3
+// convolutions is one pass over the image with its input and output in HBM (channels-last FP32):
+//   conv5       Hh = ReLU(conv5 U + b5)                                        [H][W][16]
+//   conv6       M = conv6 Hh + b6, the L1 term, dL/dI_r's L1 part and
+//               gM' = sign(I_a - I) I_r                                         [H][W][8] (3 used)
+//   conv6 adj.  gZ5' = (conv6^T gM') * [Hh > 0]                                 [H][W][16]
+//   conv5 adj.  gU = conv5^T gZ5'                                               [H][W][16]
+// then the bilinear adjoint gU -> dL/dF4 and the weight gradients.  Gradients are formed in units
+// of c = (1 - lambda) / (3 H W) (dL/dI_a = c sign(I_a - I)) and multiplied by c where they leave
+// the head.
+//
+// The convolutions are implicit GEMMs on the fifth-generation tensor cores (tcgen05.mma,
+// kind::tf32): M = 128 output pixels (an M-tile of 16 rows x 8 columns), N = 16 output channels
+// (conv6's 3 padded with zero weights), K = 9 taps x the input's channels, accumulated in tensor
+// memory.  Every operand is split into two TF32 parts, x = hi + lo with hi = tf32(x) and
+// lo = tf32(x - hi), and each product is formed as lo.hi + hi.lo + hi.hi, so the products are
+// FP32-accurate (relative error about 2^-21; the dropped lo.lo term is below FP32 rounding).
+//
+// Shared-memory operands use the no-swizzle K-major layout: a core matrix is 8 rows of 16 bytes
+// (4 channels), rows 16 bytes apart.  The input patch of an M-tile (18 x 10 pixels with its halo)
+// is stored as [part][channel group][18][10][4 floats], so the 8 pixels of one output row segment
+// are one core matrix, the next output row is 160 bytes further (the stride between core matrices
+// along M) and the next channel group one plane further (the stride along K); a tap (dy, dx) only
+// moves the start address by (10 dy + dx) x 16 bytes.  Weights are [part][tap][group][16][4].
 
-struct HeadArgs {
-  const float *img, *target, *b5, *b6;
-  const float* u;                           // the up-sampled F4, [H][W][16]
-  const float2 *w5f, *w5d, *w6f, *w6d;      // packed B fragments (FP32, split where loaded)
-  float *gimg, *map, *gf4, *dw5, *db5, *dw6, *db6;
-  double* partials;
-  int H, W, h4, w4, tiles_x, tiles;
+constexpr int kTcThreads = 128;                      // four warps: staging, epilogue; one thread issues
+constexpr int kTcRows = 16, kTcCols = 8;             // output pixels of an M-tile
+constexpr int kPatchH = kTcRows + 2, kPatchW = kTcCols + 2, kPatchPx = kPatchH * kPatchW;
+constexpr uint32_t kPatchPlane = kPatchPx * 16;      // bytes of one channel group of a patch part
+constexpr uint64_t kTcWaitNs = 1000000000ull;        // bounded wait for the MMAs of one tile (1 s)
+enum : int { kEpiRelu = 0, kEpiL1 = 1, kEpiMask = 2, kEpiStore = 3 };
+
+template <int C>
+struct TcShape {
+  static constexpr int CG = C / 4;                           // channel groups (K = 8 per MMA: 2 groups)
+  static constexpr uint32_t PartA = CG * kPatchPlane;
+  static constexpr uint32_t BufA = 2 * PartA;                // hi and lo parts of one patch
+  static constexpr uint32_t PartB = 9 * CG * 16 * 16;        // one part of the weights
+  static constexpr uint32_t Smem = 2 * BufA + 2 * PartB;     // two patch buffers + weights
+};
+
+struct TcArgs {
+  const float* in;                 // [H][W][C]
+  const float* w;                  // the layer's OIHW weights
+  const float* bias;               // conv5 / conv6 forward
+  const float *img, *target;       // kEpiL1: I_r and I (CHW)
+  const float* act;                // kEpiMask: Hh
+  float* out;                      // Hh, gM', gZ5' or gU (null: not written)
+  float *map, *gimg;               // kEpiL1 (null: not written)
+  float* dbias;                    // kEpiL1: db6, kEpiMask: db5 (null: not formed)
+  double* partials;                // kEpiL1: the L1 sum of each CTA
+  unsigned* status;                // bit 0: a bounded wait gave up
+  int H, W, tiles_x, tiles, wo, wc;     // wo x wc: the layer's output x input channels
+  bool adjoint;                    // B from the flipped, transposed weights
   float cscale;
 };
+
+__device__ __forceinline__ float4 split_hi(float4 v) { return make_float4(tf32r(v.x), tf32r(v.y), tf32r(v.z), tf32r(v.w)); }
+__device__ __forceinline__ float4 split_lo(float4 v, float4 h) {
+  return make_float4(tf32r(v.x - h.x), tf32r(v.y - h.y), tf32r(v.z - h.z), tf32r(v.w - h.w));
+}
+
+// B[n][tap][k]: forward W[n][k][tap]; adjoint W[k][n][8 - tap] (n = the layer's input channel).
+// Entries past the layer's channels are zero.
+template <int C>
+__device__ void tc_stage_weights(unsigned char* sB, const TcArgs& a) {
+  using S = TcShape<C>;
+  for (int i = threadIdx.x; i < 9 * S::CG * 16; i += kTcThreads) {
+    const int n = i & 15, cg = (i >> 4) % S::CG, tap = i / (16 * S::CG);
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * cg + j;
+      if (!a.adjoint) v[j] = (n < a.wo && k < a.wc) ? __ldg(a.w + ((size_t)n * a.wc + k) * 9 + tap) : 0.f;
+      else v[j] = (k < a.wo && n < a.wc) ? __ldg(a.w + ((size_t)k * a.wc + n) * 9 + (8 - tap)) : 0.f;
+    }
+    const float4 x = make_float4(v[0], v[1], v[2], v[3]), h = split_hi(x);
+    const uint32_t off = (uint32_t)(((tap * S::CG + cg) * 16 + n) * 16);
+    *reinterpret_cast<float4*>(sB + off) = h;
+    *reinterpret_cast<float4*>(sB + S::PartB + off) = split_lo(x, h);
+  }
+}
+
+// The M-tile's input patch, rows Y0 - 1 .. Y0 + 16 and columns X0 - 1 .. X0 + 8, zero outside the
+// image, split into its two TF32 parts.  All loads are issued before the first store.
+template <int C>
+__device__ __forceinline__ void tc_stage_patch(unsigned char* sA, const float* __restrict__ in, int Y0, int X0, int H,
+                                               int W) {
+  using S = TcShape<C>;
+  constexpr int N = kPatchPx * S::CG, IT = (N + kTcThreads - 1) / kTcThreads;
+  float4 v[IT];
+#pragma unroll
+  for (int q = 0; q < IT; ++q) {
+    const int i = threadIdx.x + kTcThreads * q;
+    const int px = i / S::CG, cg = i % S::CG;
+    const int Y = Y0 - 1 + px / kPatchW, X = X0 - 1 + px % kPatchW;
+    v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < N && Y >= 0 && Y < H && X >= 0 && X < W)
+      v[q] = __ldg(reinterpret_cast<const float4*>(in + ((size_t)Y * W + X) * C) + cg);
+  }
+#pragma unroll
+  for (int q = 0; q < IT; ++q) {
+    const int i = threadIdx.x + kTcThreads * q;
+    if (i >= N) continue;
+    const int px = i / S::CG, cg = i % S::CG;
+    const uint32_t off = (uint32_t)cg * kPatchPlane + (uint32_t)px * 16;
+    const float4 h = split_hi(v[q]);
+    *reinterpret_cast<float4*>(sA + off) = h;
+    *reinterpret_cast<float4*>(sA + S::PartA + off) = split_lo(v[q], h);
+  }
+}
+
+// The MMAs of one M-tile: 9 taps x C / 8 k-steps x 3 part products into the accumulator d.
+template <int C>
+__device__ __forceinline__ void tc_issue(uint32_t a_buf, uint32_t b_buf, uint32_t d) {
+  using S = TcShape<C>;
+  constexpr uint32_t idesc = tc::idesc_tf32(128, 16);
+  bool acc = false;
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+    for (int ks = 0; ks < C / 8; ++ks) {
+      const uint32_t ao = 2 * ks * kPatchPlane + (uint32_t)(dy * kPatchW + dx) * 16;
+      const uint32_t bo = (uint32_t)((tap * S::CG + 2 * ks) * 256);
+#pragma unroll
+      for (int pr = 0; pr < 3; ++pr) {           // lo.hi, hi.lo, hi.hi
+        const uint32_t pa = pr == 0 ? S::PartA : 0u, pb = pr == 1 ? S::PartB : 0u;
+        tc::mma_tf32(d, tc::desc(a_buf + pa + ao, kPatchPlane, kPatchW * 16), tc::desc(b_buf + pb + bo, 256, 128),
+                     idesc, acc);
+        acc = true;
+      }
+    }
+  }
+}
+
+// Per-thread sums the epilogues carry across tiles.
+struct TcSums {
+  float l1 = 0.f;
+  float db[16] = {};
+};
+
+// Epilogue of one M-tile: waits for its MMAs, reads the thread's pixel (row m = 32 warp + lane of
+// the accumulator) and applies the layer's output step.  Returns false if the wait gave up.
+template <int EPI>
+__device__ __forceinline__ bool tc_epilogue(const TcArgs& a, int tile, uint32_t tm, uint64_t* mbar, uint32_t parity,
+                                            TcSums& sums) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool ok = tc::mbar_wait(mbar, parity, kTcWaitNs);
+  __syncwarp();
+  tc::fence_after_sync();
+  float v[16];
+  tc::ld16(tm + ((uint32_t)(32 * warp) << 16), v);
+  const int m = 32 * warp + lane;
+  const int Y = (tile / a.tiles_x) * kTcRows + (m >> 3), X = (tile % a.tiles_x) * kTcCols + (m & 7);
+  if (!ok || Y >= a.H || X >= a.W) return ok;
+  const size_t pix = (size_t)Y * a.W + X;
+  if constexpr (EPI == kEpiRelu) {
+    float4* o = reinterpret_cast<float4*>(a.out + pix * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      o[q] = make_float4(fmaxf(v[4 * q] + __ldg(a.bias + 4 * q), 0.f), fmaxf(v[4 * q + 1] + __ldg(a.bias + 4 * q + 1), 0.f),
+                         fmaxf(v[4 * q + 2] + __ldg(a.bias + 4 * q + 2), 0.f),
+                         fmaxf(v[4 * q + 3] + __ldg(a.bias + 4 * q + 3), 0.f));
+  } else if constexpr (EPI == kEpiStore) {
+    float4* o = reinterpret_cast<float4*>(a.out + pix * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else if constexpr (EPI == kEpiMask) {
+    const float4* h = reinterpret_cast<const float4*>(a.act + pix * 16);
+    float4* o = reinterpret_cast<float4*>(a.out + pix * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 hv = __ldg(h + q);
+      const float4 z = make_float4(hv.x > 0.f ? v[4 * q] : 0.f, hv.y > 0.f ? v[4 * q + 1] : 0.f,
+                                   hv.z > 0.f ? v[4 * q + 2] : 0.f, hv.w > 0.f ? v[4 * q + 3] : 0.f);
+      o[q] = z;
+      sums.db[4 * q] += z.x;
+      sums.db[4 * q + 1] += z.y;
+      sums.db[4 * q + 2] += z.z;
+      sums.db[4 * q + 3] += z.w;
+    }
+  } else {   // kEpiL1: M, the L1 term and its gradients
+    const size_t HW = (size_t)a.H * a.W;
+    float gm[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      const float Mv = v[o] + __ldg(a.bias + o);
+      const float iv = __ldg(a.img + o * HW + pix), tv = __ldg(a.target + o * HW + pix);
+      const float d = iv * Mv - tv;
+      const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+      gm[o] = sgn * iv;
+      sums.l1 += fabsf(d);
+      if (a.map) a.map[o * HW + pix] = Mv;
+      if (a.gimg) a.gimg[o * HW + pix] = a.cscale * sgn * Mv;
+      sums.db[o] += gm[o];
+    }
+    if (a.out) {
+      float4* o = reinterpret_cast<float4*>(a.out + pix * 8);
+      o[0] = make_float4(gm[0], gm[1], gm[2], 0.f);
+      o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  return true;
+}
+
+template <int C, int EPI>
+__global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(const TcArgs a) {
+  using S = TcShape<C>;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* sA = tc_smem;                 // two patch buffers
+  unsigned char* sB = tc_smem + 2 * S::BufA;   // the weights
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tslot;
+  __shared__ double red[kTcThreads / 32];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) tc::alloc(&tslot, 32);        // two 16-column accumulators
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::mbar_init_fence();
+  }
+  tc_stage_weights<C>(sB, a);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot, a0 = smem_u32(sA), b0 = smem_u32(sB);
+  TcSums sums;
+  bool ok = true;
+  int k = 0, prev = -1;
+  // tile k is staged into buffer k & 1 and accumulated in columns 16 (k & 1); its epilogue runs
+  // while the MMAs of tile k + 1 execute
+  for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, ++k) {
+    const int b = k & 1;
+    tc_stage_patch<C>(sA + b * S::BufA, a.in, (tile / a.tiles_x) * kTcRows, (tile % a.tiles_x) * kTcCols, a.H, a.W);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      tc_issue<C>(a0 + b * S::BufA, b0, tmem + 16u * b);
+      tc::commit(&mbar[b]);
+    }
+    if (prev >= 0) ok &= tc_epilogue<EPI>(a, prev, tmem + 16u * (b ^ 1), &mbar[b ^ 1], ((k - 1) >> 1) & 1, sums);
+    prev = tile;
+  }
+  if (prev >= 0) ok &= tc_epilogue<EPI>(a, prev, tmem + 16u * ((k - 1) & 1), &mbar[(k - 1) & 1], ((k - 1) >> 1) & 1, sums);
+  if (!ok) {
+    atomicOr(a.status, 1u);
+    // the last commit of each buffer, waited for again (bounded) before the memory is freed
+    for (int j = 1; j <= 2 && k - j >= 0; ++j) tc::mbar_wait(&mbar[(k - j) & 1], ((k - j) >> 1) & 1, kTcWaitNs);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, 32);
+  // the per-CTA sums of the epilogue
+  const int lane = tid & 31;
+  if constexpr (EPI == kEpiL1) {
+    const float l = warp_sum(sums.l1);
+    if (lane == 0) red[warp] = (double)l;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0;
+      for (int w = 0; w < kTcThreads / 32; ++w) s += red[w];
+      a.partials[blockIdx.x] = s;
+    }
+  }
+  if constexpr (EPI == kEpiL1 || EPI == kEpiMask) {
+    if (a.dbias) {
+      constexpr int NB = EPI == kEpiL1 ? 3 : 16;
+#pragma unroll
+      for (int o = 0; o < NB; ++o) {
+        const float s = warp_sum(sums.db[o]);
+        if (lane == 0) atomicAdd(a.dbias + o, a.cscale * s);
+      }
+    }
+  }
+}
 
 // Bilinear up-sampling from n_in to n_out samples: output y reads rows i0 and i1 with weight f
 // on i1, where (y + 1/2) n_in / n_out - 1/2 = ((2y + 1) n_in - n_out) / (2 n_out), clamped below at
@@ -707,9 +947,14 @@ __device__ __forceinline__ Tap up_tap(int y, int n_in, int n_out) {
   return r;
 }
 
-// U = F4 [h4][w4][16] up-sampled bilinearly to [H][W][16] (FP32): the head's conv5 input,
-// computed once rather than once per overlapping head tile.  A thread produces 4 channels of one
-// pixel.
+// Weight of output sample y on input sample i under up_tap.
+__device__ __forceinline__ float up_weight(int y, int i, int n_in, int n_out) {
+  const Tap t = up_tap(y, n_in, n_out);
+  return (t.i0 == i ? 1.f - t.f : 0.f) + (t.i1 == i ? t.f : 0.f);
+}
+
+// U = F4 [h4][w4][16] up-sampled bilinearly to [H][W][16] (FP32): conv5's input.  A thread produces
+// 4 channels of one pixel.
 __global__ void __launch_bounds__(256) upsample_kernel(const float* __restrict__ f4, int h4, int w4, int H, int W,
                                                        float* __restrict__ U) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -729,431 +974,93 @@ __global__ void __launch_bounds__(256) upsample_kernel(const float* __restrict__
   reinterpret_cast<float4*>(U + (size_t)px * 16)[v] = u;
 }
 
-__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
-               : "memory");
-}
-
-// A fragment of a 16-pixel x 8-channel tile of a pixel-major buffer (pitch P floats): rows (pixels)
-// at p0 (row g) and p1 (row g + 8), channels c and c + 4.
-template <int P>
-__device__ __forceinline__ Split4 frag_px(const float* buf, int p0, int p1, int c) {
-  return split4(buf[p0 * P + c], buf[p1 * P + c], buf[p0 * P + c + 4], buf[p1 * P + c + 4]);
-}
-
-template <bool BWD>
-__global__ void __launch_bounds__(kHeadThreads, 1) head_kernel(const HeadArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float* sU = reinterpret_cast<float*>(smraw);
-  float* sH = reinterpret_cast<float*>(smraw + kBU);
-  float* sZ = reinterpret_cast<float*>(smraw + kBU + kBH);
-  float* sG = reinterpret_cast<float*>(smraw + kBU + kBH + kBZ);
-  float* sI = reinterpret_cast<float*>(smraw + kBU + kBH + kBZ + kBG);   // [2][3][R2][R2]
-  int* tY0 = reinterpret_cast<int*>(smraw + kBU + kBH + kBZ + kBG + kBI);
-  int* tY1 = tY0 + R4;
-  float* tFY = reinterpret_cast<float*>(tY1 + R4);
-  int* tX0 = reinterpret_cast<int*>(tFY + R4);
-  int* tX1 = tX0 + R4;
-  float* tFX = reinterpret_cast<float*>(tX1 + R4);
-  int2* rY = reinterpret_cast<int2*>(tFX + R4);     // contributor runs [first, end) of T's rows
-  int2* rX = rY + FT;                               // ... and of T's columns
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  const size_t HW = (size_t)a.H * a.W;
-  float l1 = 0.f;
-  // weight-gradient accumulators kept across tiles: tap `warp` over every row, and tap 8 over
-  // rows 2 warp and 2 warp + 1 (every warp adds its share of tap 8)
-  float acc5[2][2][4], acc6[2][4], db5[2][2], db6[3];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    acc5[0][0][q] = acc5[0][1][q] = acc5[1][0][q] = acc5[1][1][q] = 0.f;
-    acc6[0][q] = acc6[1][q] = 0.f;
+// The adjoint of the up-sampling, as two gathers (no atomics): the column pass
+//   X[y][a][c] = sum_x wx(x, a) gU[y][x][c]   ([H][w4][16])
+// and the row pass dL/dF4[b][a][c] = scale sum_y wy(y, b) X[y][a][c].  Along one line of samples,
+// input sample a receives from the outputs x with (a - 1/2) n_out / n_in - 1/2 <= x <
+// (a + 3/2) n_out / n_in - 1/2, all inside the window scanned below.  A thread produces 4 channels
+// of one output; consecutive threads take consecutive inputs a (column pass) or consecutive lines
+// (row pass), so that both read and write contiguous memory.
+template <bool LINES_FAST>
+__global__ void __launch_bounds__(256) upsample_adjoint_kernel(const float* __restrict__ g, int n_lines, int n_out,
+                                                               int n_in, size_t line_stride, size_t sample_stride,
+                                                               size_t out_line_stride, size_t out_sample_stride,
+                                                               float scale, float* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)n_lines * n_in * 4) return;
+  const int v = (int)(i & 3);
+  const size_t r = i >> 2;
+  const int a = LINES_FAST ? (int)(r / n_lines) : (int)(r % n_in);
+  const int line = LINES_FAST ? (int)(r % n_lines) : (int)(r / n_in);
+  const int lo = max(0, (int)floorf((float)(a - 1) * n_out / n_in) - 2);
+  const int hi = min(n_out - 1, (int)ceilf((float)(a + 2) * n_out / n_in) + 2);
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int x = lo; x <= hi; ++x) {
+    const float w = up_weight(x, a, n_in, n_out);
+    if (w == 0.f) continue;
+    const float4 gv = __ldg(reinterpret_cast<const float4*>(g + line * line_stride + x * sample_stride) + v);
+    s.x = fmaf(w, gv.x, s.x);
+    s.y = fmaf(w, gv.y, s.y);
+    s.z = fmaf(w, gv.z, s.z);
+    s.w = fmaf(w, gv.w, s.w);
   }
-  db5[0][0] = db5[0][1] = db5[1][0] = db5[1][1] = db6[0] = db6[1] = db6[2] = 0.f;
-  // U over R4 around a tile, zero outside the image
-  auto fetch_u = [&](int tile) {
-    if (tile < a.tiles) {
-      const int oy = (tile / a.tiles_x) * HT, ox = (tile % a.tiles_x) * HT;
-      for (int i = threadIdx.x; i < R4 * R4 * 4; i += kHeadThreads) {
-        const int px = i >> 2, v = i & 3;
-        const int y = oy - 4 + px / R4, x = ox - 4 + px % R4;
-        const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
-        cp_async16_zfill(sU + px * PU + 4 * v, a.u + (in ? ((size_t)y * a.W + x) * 16 + 4 * v : 0), in);
-      }
-    }
-    cp_async_commit();
-  };
-  fetch_u(blockIdx.x);
+  reinterpret_cast<float4*>(out + line * out_line_stride + a * out_sample_stride)[v] =
+      make_float4(scale * s.x, scale * s.y, scale * s.z, scale * s.w);
+}
 
-  for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
-    const int oy = (tile / a.tiles_x) * HT, ox = (tile % a.tiles_x) * HT;
+// Weight gradient of a head convolution on the CUDA cores (FP32):
+//   dW[o][ci][tap] += scale sum_p Z(p)[o] X(p + tap - (1, 1))[ci]   (X zero outside the image)
+// with X [H][W][16] and Z [H][W][ZC] (channels past NO zero).  A thread owns 4 output x 4 input
+// channels of one tap (16 sums) and a phase of the pixels; a block takes tiles of 8 x 32 pixels,
+// staged in shared memory with X's one-pixel halo.
+constexpr int kWgThreads = 144, kWgRows = 8, kWgCols = 32;
+template <int ZC, int NO>
+__global__ void __launch_bounds__(kWgThreads) head_wgrad_kernel(const float* __restrict__ X, const float* __restrict__ Z,
+                                                                int H, int W, int tiles_x, int tiles, float scale,
+                                                                float* __restrict__ dW) {
+  constexpr int NOG = (NO + 3) / 4, GROUPS = NOG * 4 * 9, PHASES = kWgThreads / GROUPS;
+  constexpr int XH = kWgRows + 2, XW = kWgCols + 2, NPX = kWgRows * kWgCols;
+  static_assert(kWgThreads % GROUPS == 0 && NPX % PHASES == 0, "thread layout");
+  __shared__ __align__(16) float sX[XH * XW * 16];
+  __shared__ __align__(16) float sZ[NPX * 4 * NOG];
+  const int grp = threadIdx.x % GROUPS, phase = threadIdx.x / GROUPS;
+  const int og = grp % NOG, cg = (grp / NOG) % 4, tap = grp / (4 * NOG);
+  const int dy = tap / 3, dx = tap % 3;
+  float acc[4][4] = {};
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int Y0 = (tile / tiles_x) * kWgRows, X0 = (tile % tiles_x) * kWgCols;
     __syncthreads();
-    // S0: tap tables (for the bilinear adjoint); gM' cleared; I_r and I over R2 in flight; U
-    // fetched during the last tile
-    if (threadIdx.x < 2 * R4) {
-      const bool col = threadIdx.x >= R4;
-      const int k = col ? threadIdx.x - R4 : threadIdx.x;
-      const int v = (col ? ox : oy) - 4 + k, n = col ? a.W : a.H, nin = col ? a.w4 : a.h4;
-      int i0 = -1, i1 = -1;
-      float f = 0.f;
-      if (v >= 0 && v < n) {
-        const Tap tq = up_tap(v, nin, n);
-        i0 = tq.i0;
-        i1 = tq.i1;
-        f = tq.f;
-      }
-      (col ? tX0 : tY0)[k] = i0;
-      (col ? tX1 : tY1)[k] = i1;
-      (col ? tFX : tFY)[k] = f;
+    for (int i = threadIdx.x; i < XH * XW * 4; i += kWgThreads) {
+      const int px = i >> 2, q = i & 3, Y = Y0 - 1 + px / XW, Xc = X0 - 1 + px % XW;
+      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (Y >= 0 && Y < H && Xc >= 0 && Xc < W) xv = __ldg(reinterpret_cast<const float4*>(X + ((size_t)Y * W + Xc) * 16) + q);
+      reinterpret_cast<float4*>(sX)[i] = xv;
     }
-    for (int i = threadIdx.x; i < 2 * 3 * R2 * R2; i += kHeadThreads) {
-      const int px = i % (R2 * R2), plane = i / (R2 * R2), c = plane % 3;
-      const int y = oy - 2 + px / R2, x = ox - 2 + px % R2;
-      const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
-      const float* src = (plane < 3 ? a.img : a.target) + (in ? (size_t)c * HW + (size_t)y * a.W + x : 0);
-      cp_async4_zfill(sI + i, src, in);
+    for (int i = threadIdx.x; i < NPX * NOG; i += kWgThreads) {
+      const int px = i / NOG, q = i % NOG, Y = Y0 + px / kWgCols, Xc = X0 + px % kWgCols;
+      float4 zv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (Y < H && Xc < W) zv = __ldg(reinterpret_cast<const float4*>(Z + ((size_t)Y * W + Xc) * ZC) + q);
+      reinterpret_cast<float4*>(sZ)[i] = zv;
     }
-    cp_async_commit();
-    if constexpr (BWD)
-      for (int i = threadIdx.x; i < R2 * R2 * PG / 4; i += kHeadThreads)
-        reinterpret_cast<float4*>(sG)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    cp_async_wait<1>();    // U (the older group)
     __syncthreads();
-    // S2: Hh = ReLU(conv5 U + b5) over R3, zero outside the image.  M = 484 pixels (31 m-tiles),
-    // N = 16, K = 9 taps x 16 channels (two k-steps a tap).
-    {
-      constexpr int NM = (R3 * R3 + 15) / 16;
-      const int nmt = (NM - warp + 7) / 8;
-      int p0[4], p1[4];     // rows g and g + 8 of each of the warp's m-tiles, as R4 pixels
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int m0 = min((warp + 8 * i) * 16 + g, R3 * R3 - 1), m1 = min((warp + 8 * i) * 16 + g + 8, R3 * R3 - 1);
-        p0[i] = (m0 / R3) * R4 + m0 % R3;
-        p1[i] = (m1 / R3) * R4 + m1 % R3;
-      }
-      float acc[4][2][4];
+#pragma unroll 4
+    for (int p = phase; p < NPX; p += PHASES) {
+      const int r = p / kWgCols, c = p % kWgCols;
+      const float4 z = reinterpret_cast<const float4*>(sZ)[p * NOG + og];
+      const float4 x = reinterpret_cast<const float4*>(sX)[((r + dy) * XW + c + dx) * 4 + cg];
+      const float zz[4] = {z.x, z.y, z.z, z.w}, xx[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][0][q] = acc[i][1][q] = 0.f;
-#pragma unroll 2
-      for (int s = 0; s < 18; ++s) {
-        const int tap = s >> 1, off = (tap / 3) * R4 + tap % 3, c = 8 * (s & 1) + t;
-        const float2 w0 = __ldg(a.w5f + (s * 2 + 0) * 32 + lane), w1 = __ldg(a.w5f + (s * 2 + 1) * 32 + lane);
-        const Split2 b0 = split2(w0.x, w0.y), b1 = split2(w1.x, w1.y);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (i < nmt) {
-            const Split4 av = frag_px<PU>(sU, p0[i] + off, p1[i] + off, c);
-            mma8x3(acc[i][0], av, b0);
-            mma8x3(acc[i][1], av, b1);
-          }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (i >= nmt) break;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int m = (warp + 8 * i) * 16 + g + 8 * h;
-          if (m >= R3 * R3) continue;
-          const int y = oy - 3 + m / R3, x = ox - 3 + m % R3;
-          const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const int o = 8 * j + 2 * t;
-            const float v0 = in ? fmaxf(acc[i][j][2 * h] + __ldg(a.b5 + o), 0.f) : 0.f;
-            const float v1 = in ? fmaxf(acc[i][j][2 * h + 1] + __ldg(a.b5 + o + 1), 0.f) : 0.f;
-            *reinterpret_cast<float2*>(sH + m * PU + o) = make_float2(v0, v1);
-          }
-        }
-      }
-    }
-    if constexpr (BWD) {
-      cp_async_wait<0>();    // I_r and I
-    } else {
-      __syncthreads();       // every warp is past S2, the last reader of U
-      fetch_u(tile + gridDim.x);
-      cp_async_wait<1>();    // I_r and I (older than the next U)
-    }
-    __syncthreads();
-    // S3: M = conv6 Hh + b6 over R2 (N = 8, channels 0..2 used); the L1 term and gM' over R2.
-    {
-      constexpr int NM = R2 * R2 / 16;
-      const int nmt = (NM - warp + 7) / 8;
-      int p0[4], p1[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int m0 = min((warp + 8 * i) * 16 + g, R2 * R2 - 1), m1 = min((warp + 8 * i) * 16 + g + 8, R2 * R2 - 1);
-        p0[i] = (m0 / R2) * R3 + m0 % R2;
-        p1[i] = (m1 / R2) * R3 + m1 % R2;
-      }
-      float acc[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
-#pragma unroll 2
-      for (int s = 0; s < 18; ++s) {
-        const int tap = s >> 1, off = (tap / 3) * R3 + tap % 3, c = 8 * (s & 1) + t;
-        const float2 w = __ldg(a.w6f + s * 32 + lane);
-        const Split2 b = split2(w.x, w.y);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (i < nmt) mma8x3(acc[i], frag_px<PU>(sH, p0[i] + off, p1[i] + off, c), b);
-      }
-      // the quad's six (pixel, channel) items: t = 0 takes (g, 0), (g, 1); t = 1 (g, 2), (g + 8, 2);
-      // t = 2 (g + 8, 0) and t = 3 (g + 8, 1), fetched from t = 0
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (i >= nmt) break;
-        const float v2 = __shfl_sync(0xffffffffu, acc[i][2], lane & ~3);
-        const float v3 = __shfl_sync(0xffffffffu, acc[i][3], lane & ~3);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          if (k == 1 && t >= 2) break;
-          const int h = t == 0 ? 0 : (t == 1 ? k : 1);
-          const int o = t == 0 ? k : (t == 1 ? 2 : t - 2);
-          const float av = t == 0 ? acc[i][k] : (t == 1 ? acc[i][2 * k] : (t == 2 ? v2 : v3));
-          const int m = (warp + 8 * i) * 16 + g + 8 * h;
-          const int r = m / R2, q = m % R2;
-          const int y = oy - 2 + r, x = ox - 2 + q;
-          if (y < 0 || y >= a.H || x < 0 || x >= a.W) continue;
-          const bool inT = r >= 2 && r < 2 + HT && q >= 2 && q < 2 + HT;
-          const size_t pix = (size_t)o * HW + (size_t)y * a.W + x;
-          const float Mv = av + __ldg(a.b6 + o);
-          const float iv = sI[o * R2 * R2 + m], tv = sI[(3 + o) * R2 * R2 + m];
-          const float d = iv * Mv - tv;
-          const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-          const float gm = sgn * iv;
-          if (inT) {
-            l1 += fabsf(d);
-            if (a.map) a.map[pix] = Mv;
-            if constexpr (BWD) {
-              a.gimg[pix] = a.cscale * sgn * Mv;
-              db6[0] += o == 0 ? gm : 0.f;
-              db6[1] += o == 1 ? gm : 0.f;
-              db6[2] += o == 2 ? gm : 0.f;
-            }
-          }
-          if constexpr (BWD) sG[m * PG + o] = gm;
-        }
-      }
-    }
-    if constexpr (BWD) {
-      __syncthreads();
-      // S5: gZ5' = (conv6 adjoint of gM') * [Hh > 0] over R1.  M = 324 pixels (21 m-tiles), N = 16,
-      // K = 9 flipped taps x 8 channels (3 used): one k-step a tap, whose channels 4..7 are zero.
-      {
-        constexpr int NM = (R1 * R1 + 15) / 16;
-        const int nmt = (NM - warp + 7) / 8;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          if (i >= nmt) break;
-          const int m0 = min((warp + 8 * i) * 16 + g, R1 * R1 - 1), m1 = min((warp + 8 * i) * 16 + g + 8, R1 * R1 - 1);
-          const int q0 = (m0 / R1) * R2 + m0 % R1, q1 = (m1 / R1) * R2 + m1 % R1;
-          float acc[2][4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[0][q] = acc[1][q] = 0.f;
-#pragma unroll
-          for (int s = 0; s < 9; ++s) {
-            const int off = (s / 3) * R2 + s % 3;
-            const float v0 = sG[(q0 + off) * PG + t], v1 = sG[(q1 + off) * PG + t];
-            const Split4 av = split4(v0, v1, 0.f, 0.f);
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              const float2 w = __ldg(a.w6d + (s * 2 + j) * 32 + lane);
-              mma8x3(acc[j], av, split2(w.x, w.y));
-            }
-          }
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int m = (warp + 8 * i) * 16 + g + 8 * h;
-            if (m >= R1 * R1) continue;
-            const int r = m / R1, q = m % R1;
-            const int y = oy - 1 + r, x = ox - 1 + q;
-            const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
-            const bool inT = in && r >= 1 && r <= HT && q >= 1 && q <= HT;
-            const float* hp = sH + ((r + 2) * R3 + q + 2) * PU;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              const int o = 8 * j + 2 * t;
-              const float2 hv = *reinterpret_cast<const float2*>(hp + o);
-              const float z0 = (in && hv.x > 0.f) ? acc[j][2 * h] : 0.f;
-              const float z1 = (in && hv.y > 0.f) ? acc[j][2 * h + 1] : 0.f;
-              *reinterpret_cast<float2*>(sZ + m * PU + o) = make_float2(z0, z1);
-              if (inT) {
-                db5[j][0] += z0;
-                db5[j][1] += z1;
-              }
-            }
-          }
-        }
-      }
-      __syncthreads();
-      // S4 + S6, two k-steps (8 pixels each) per row of T; warp w takes tap w over every row and
-      // tap 8 over rows 2w and 2w + 1:
-      //   dW6^T[(tap, ci)][o] += sum_p Hh(p + tap)[ci] gM'(p)[o]   (M = ci, N = o, K = pixels)
-      //   dW5[o][(tap, ci)]   += sum_p gZ5'(p)[o] U(p + tap)[ci]   (M = o, N = ci, K = pixels)
-#pragma unroll 1
-      for (int ty = 0; ty < HT; ++ty) {
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const int xa = 8 * kk + t, xb = xa + 4;           // this lane's two pixels of the k-step
-          const float* zr = sZ + ((ty + 1) * R1 + 1) * PU;  // gZ5' of T row ty
-          const Split4 agz = split4(zr[xa * PU + g], zr[xa * PU + g + 8], zr[xb * PU + g], zr[xb * PU + g + 8]);
-          const float* gr = sG + ((ty + 2) * R2 + 2) * PG;  // gM' of T row ty
-          const Split2 bgm = split2(gr[xa * PG + g], gr[xb * PG + g]);
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            if (u == 1 && (ty >> 1) != warp) break;
-            const int tap = u == 0 ? warp : 8, ti = tap / 3, tj = tap % 3;
-            const float* ur = sU + ((ty + ti + 3) * R4 + tj + 3) * PU;
-            mma8x3(acc5[u][0], agz, split2(ur[xa * PU + g], ur[xb * PU + g]));
-            mma8x3(acc5[u][1], agz, split2(ur[xa * PU + 8 + g], ur[xb * PU + 8 + g]));
-            const float* hr = sH + ((ty + ti + 2) * R3 + tj + 2) * PU;
-            const Split4 ah = split4(hr[xa * PU + g], hr[xa * PU + g + 8], hr[xb * PU + g], hr[xb * PU + g + 8]);
-            mma8x3(acc6[u], ah, bgm);
-          }
-        }
-      }
-      // S7: dL/dU over T, rows warp and warp + 8: gU[p][ci] = sum over flipped taps and channels
-      // of gZ5'(p + tap)[o] W5d[(tap, o)][ci] (M = the row's 16 pixels, N = 16 input channels,
-      // K = 9 taps x 16 channels)
-      float acc7[2][2][4];
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc7[i][0][q] = acc7[i][1][q] = 0.f;
-#pragma unroll 2
-      for (int s = 0; s < 18; ++s) {
-        const int tap = s >> 1, c = 8 * (s & 1) + t;
-        const float2 w0 = __ldg(a.w5d + (s * 2 + 0) * 32 + lane), w1 = __ldg(a.w5d + (s * 2 + 1) * 32 + lane);
-        const Split2 b0 = split2(w0.x, w0.y), b1 = split2(w1.x, w1.y);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int pr = (warp + 8 * i + tap / 3) * R1 + tap % 3;   // R1 pixel of T pixel 0 of the row
-          const Split4 av = frag_px<PU>(sZ, pr + g, pr + g + 8, c);
-          mma8x3(acc7[i][0], av, b0);
-          mma8x3(acc7[i][1], av, b1);
-        }
-      }
-      __syncthreads();   // every warp is past S4, S6 and S7 (the last readers of U, Hh and gZ5')
-      fetch_u(tile + gridDim.x);
-      // dL/dU over T into sH as [row][column][16]
-      float* sGU = sH;
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int r = warp + 8 * i, x = g + 8 * h, ci = 8 * j + 2 * t;
-            *reinterpret_cast<float2*>(sGU + (r * HT + x) * 16 + ci) = make_float2(acc7[i][j][2 * h], acc7[i][j][2 * h + 1]);
-          }
-      // Bilinear adjoint: a column pass X[row][b][ci] = sum over T's columns x that reach footprint
-      // column bx0 + b of their tap weight times gU[row][x][ci], then a row pass that gathers X
-      // over the rows reaching each footprint row, straight into dL/dF4.
-      float* sX = sZ;
-      const int bx0 = tX0[4], bx1 = tX1[min(HT + 3, a.W - 1 - ox + 4)];
-      const int by0 = tY0[4], by1 = tY1[min(HT + 3, a.H - 1 - oy + 4)];
-      const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1;
-      const int ncx = min(HT, a.W - ox), ncy = min(HT, a.H - oy);
-      // contributors of footprint row / column b: the T rows / columns whose taps include b, a
-      // contiguous run because the taps are monotone
-      if (threadIdx.x < 2 * FT) {
-        const bool col = threadIdx.x >= FT;
-        const int k = col ? threadIdx.x - FT : threadIdx.x;
-        const int* T0 = col ? tX0 : tY0;
-        const int* T1 = col ? tX1 : tY1;
-        const int n = col ? ncx : ncy;
-        const int b = (col ? bx0 : by0) + k;
-        int first = 0;
-        while (first < n && T1[first + 4] < b) ++first;
-        int end = first;
-        while (end < n && T0[end + 4] <= b) ++end;
-        (col ? rX : rY)[k] = make_int2(first, end);
-      }
-      __syncthreads();
-      for (int it = threadIdx.x; it < HT * nbx * 4; it += kHeadThreads) {
-        const int v = it & 3, rest = it >> 2, jb = rest % nbx, r = rest / nbx;
-        const int b = bx0 + jb;
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int2 run = rX[jb];
-        for (int x = run.x; x < run.y; ++x) {
-          const float fx = tFX[x + 4];
-          const float w = (tX0[x + 4] == b ? 1.f - fx : 0.f) + (tX1[x + 4] == b ? fx : 0.f);
-          const float4 gu = *reinterpret_cast<const float4*>(sGU + (r * HT + x) * 16 + 4 * v);
-          s.x = fmaf(w, gu.x, s.x);
-          s.y = fmaf(w, gu.y, s.y);
-          s.z = fmaf(w, gu.z, s.z);
-          s.w = fmaf(w, gu.w, s.w);
-        }
-        *reinterpret_cast<float4*>(sX + (r * FT + jb) * 16 + 4 * v) = s;
-      }
-      __syncthreads();
-      for (int it = threadIdx.x; it < nby * nbx * 4; it += kHeadThreads) {
-        const int v = it & 3, rest = it >> 2, jb = rest % nbx, ja = rest / nbx;
-        const int b = by0 + ja;
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int2 run = rY[ja];
-        for (int r = run.x; r < run.y; ++r) {
-          const float fy = tFY[r + 4];
-          const float w = (tY0[r + 4] == b ? 1.f - fy : 0.f) + (tY1[r + 4] == b ? fy : 0.f);
-          const float4 gx = *reinterpret_cast<const float4*>(sX + (r * FT + jb) * 16 + 4 * v);
-          s.x = fmaf(w, gx.x, s.x);
-          s.y = fmaf(w, gx.y, s.y);
-          s.z = fmaf(w, gx.z, s.z);
-          s.w = fmaf(w, gx.w, s.w);
-        }
-        atomicAdd(reinterpret_cast<float4*>(a.gf4 + ((size_t)b * a.w4 + bx0 + jb) * 16 + 4 * v),
-                  make_float4(a.cscale * s.x, a.cscale * s.y, a.cscale * s.z, a.cscale * s.w));
-      }
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(zz[i], xx[j], acc[i][j]);
     }
   }
-  cp_async_wait<0>();      // the (empty) last prefetch group
-  if constexpr (BWD) {
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int tap = u == 0 ? warp : 8;
+  for (int i = 0; i < 4; ++i) {
+    const int o = 4 * og + i;
+    if (o >= NO) continue;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        // dW6^T: rows ci = g (+ 8), columns o = 2t (+ 1)
-        const int ci = g + 8 * (e >> 1), o = 2 * t + (e & 1);
-        if (o < 3) atomicAdd(a.dw6 + (o * 16 + ci) * 9 + tap, a.cscale * acc6[u][e]);
-      }
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          // dW5: rows o = g (+ 8), columns ci = 8j + 2t (+ 1)
-          const int o = g + 8 * (e >> 1), ci = 8 * j + 2 * t + (e & 1);
-          atomicAdd(a.dw5 + (o * 16 + ci) * 9 + tap, a.cscale * acc5[u][j][e]);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        float v = db5[j][e];
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        if (g == 0) atomicAdd(a.db5 + 8 * j + 2 * t + e, a.cscale * v);
-      }
-#pragma unroll
-    for (int o = 0; o < 3; ++o) {
-      const float v = warp_sum(db6[o]);
-      if (lane == 0) atomicAdd(a.db6 + o, a.cscale * v);
-    }
-  }
-  // the block's L1 sum (FP32 per warp, FP64 across warps)
-  __shared__ double red[kHeadThreads / 32];
-  l1 = warp_sum(l1);
-  if (lane == 0) red[warp] = (double)l1;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0;
-    for (int k = 0; k < kHeadThreads / 32; ++k) s += red[k];
-    a.partials[blockIdx.x] = s;
+    for (int j = 0; j < 4; ++j) atomicAdd(dW + ((size_t)o * 16 + 4 * cg + j) * 9 + tap, scale * acc[i][j]);
   }
 }
 
@@ -1168,10 +1075,12 @@ __global__ void __launch_bounds__(256) pool_grad_add_kernel(const float* __restr
   grad[(size_t)c * W * H + (size_t)y * W + x] += gP[((y >> 5) * pw + (x >> 5)) * 3 + c] * (1.f / 1024.f);
 }
 
-// L = (1 - lambda) sum|I_a - I| / n + lambda (1 - sum S / n), n = 3 H W.
+// L = (1 - lambda) sum|I_a - I| / n + lambda (1 - sum S / n), n = 3 H W; NaN if a bounded wait of
+// the head gave up (status bit 0).
 __global__ void __launch_bounds__(256) appearance_finalize(const double* __restrict__ ssim_part, int ns,
                                                            const double* __restrict__ head_part, int nh, double inv,
-                                                           float lambda, float* __restrict__ out_loss) {
+                                                           float lambda, const unsigned* __restrict__ status,
+                                                           float* __restrict__ out_loss) {
   __shared__ double red[2][8];
   double s = 0, l = 0;
   for (int b = threadIdx.x; b < ns; b += blockDim.x) s += ssim_part[2 * b];
@@ -1192,7 +1101,7 @@ __global__ void __launch_bounds__(256) appearance_finalize(const double* __restr
       ts += red[0][k];
       tl += red[1][k];
     }
-    *out_loss = (float)((1.0 - lambda) * tl * inv + lambda * (1.0 - ts * inv));
+    *out_loss = *status ? __int_as_float(0x7fc00000) : (float)((1.0 - lambda) * tl * inv + lambda * (1.0 - ts * inv));
   }
 }
 
@@ -1200,7 +1109,7 @@ __global__ void __launch_bounds__(256) appearance_finalize(const double* __restr
 
 // Workspace regions (floats unless noted), for an H x W image with (h, w) = (H / 32, W / 32).
 struct AppLayout {
-  size_t E, G, P, gP, A[5], gA[5], U, packed, maps, ssim_part, head_part, total;
+  size_t E, G, P, gP, A[5], gA[5], U, Hh, gM, gZ, gU, gX, packed, maps, ssim_part, head_part, status, total;
   int pack_off[kPackJobs];
   PackTable tab;
 };
@@ -1226,10 +1135,8 @@ AppLayout make_app_layout(int W, int H) {
     L.A[k] = take(n);
     L.gA[k] = take(n);
   }
-  // packed B operands: forward and input-gradient GEMMs of blocks 1..4 and of the head's conv5
-  // and conv6
-  const int jobs[kPackJobs][2] = {{1, 0}, {2, 0}, {3, 0}, {4, 0}, {1, 1}, {2, 1},
-                                  {3, 1}, {4, 1}, {5, 0}, {5, 1}, {6, 0}, {6, 1}};
+  // packed B operands: forward and input-gradient GEMMs of blocks 1..4
+  const int jobs[kPackJobs][2] = {{1, 0}, {2, 0}, {3, 0}, {4, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}};
   int pos = 0, idx = 0;   // pos: floats of the buffer used; idx: elements of the launch's index space
   for (int j = 0; j < kPackJobs; ++j) {
     const int l = jobs[j][0], dg = jobs[j][1];
@@ -1237,7 +1144,7 @@ AppLayout make_app_layout(int W, int H) {
     PackJob& J = L.tab.job[j];
     J.layer = l;
     J.dgrad = dg;
-    J.tapc = (l == 6 && dg) ? 8 : kin;                 // conv6's adjoint: 3 channels a tap, read as 8
+    J.tapc = kin;
     J.kpad = (9 * J.tapc + 7) / 8 * 8;
     J.npad = (n + 7) / 8 * 8;
     const int elems = J.kpad * J.npad;                 // a multiple of 64
@@ -1249,10 +1156,17 @@ AppLayout make_app_layout(int W, int H) {
   }
   L.tab.begin[kPackJobs] = idx;
   L.packed = take((size_t)pos * 4);
-  L.U = take((size_t)W * H * 16 * 4);          // FP32 [H][W][16]
+  const size_t HW = (size_t)W * H;
+  L.U = take(HW * 16 * 4);                     // the head's maps, FP32 channels-last: U, Hh, gZ5', gU
+  L.Hh = take(HW * 16 * 4);                    //   [H][W][16]
+  L.gM = take(HW * 8 * 4);                     //   gM' [H][W][8]
+  L.gZ = take(HW * 16 * 4);
+  L.gU = take(HW * 16 * 4);
+  L.gX = take((size_t)H * (w << 4) * 16 * 4);  //   the up-sampling adjoint's column pass [H][w4][16]
   L.maps = take(ssim_maps_floats(W, H) * 4);
   L.ssim_part = take((size_t)ssim_partials(W, H) * 2 * 8);
   L.head_part = take((size_t)kMaxHeadBlocks * 8);
+  L.status = take(16);
   L.total = off;
   return L;
 }
@@ -1290,6 +1204,34 @@ cudaError_t launch_wgrad(const float* Aprev, const float* gA, const float* A, fl
   const dim3 grid((tiles + per - 1) / per, gy);
   note_launches(1);
   k<<<grid, 256, smem, s>>>(Aprev, gA, A, dW, db, Hr, Wr, tiles_x, tiles, per);
+  return cudaGetLastError();
+}
+
+// One persistent pass of a head convolution: as many CTAs as fit on the GPU (shared memory, four
+// warps each), at most one per M-tile.
+template <int C, int EPI>
+cudaError_t launch_tc_conv(const TcArgs& a, int sms, cudaStream_t s, int* grid_out = nullptr) {
+  using S = TcShape<C>;
+  auto k = tc_conv_kernel<C, EPI>;
+  cudaError_t e = set_smem(k, S::Smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTcThreads, S::Smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min({a.tiles, std::max(1, per_sm) * sms, kMaxHeadBlocks}));
+  if (grid_out) *grid_out = grid;
+  note_launches(1);
+  k<<<grid, kTcThreads, S::Smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int ZC, int NO>
+cudaError_t launch_head_wgrad(const float* X, const float* Z, int H, int W, float scale, float* dW, int sms,
+                              cudaStream_t s) {
+  const int tiles_x = (W + kWgCols - 1) / kWgCols, tiles = tiles_x * ((H + kWgRows - 1) / kWgRows);
+  const int grid = std::max(1, std::min(tiles, 6 * sms));
+  note_launches(1);
+  head_wgrad_kernel<ZC, NO><<<grid, kWgThreads, 0, s>>>(X, Z, H, W, tiles_x, tiles, scale, dW);
   return cudaGetLastError();
 }
 
@@ -1368,7 +1310,6 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   ok(launch_ssim_moments(img, target, W, H, lambda, F(L.maps), ssim_part, side));
   if (bwd) {
     ok(cudaMemsetAsync(grad_params, 0, (size_t)kParams * sizeof(float), s));
-    ok(cudaMemsetAsync(gA[4], 0, (size_t)(ph << 4) * (pw << 4) * 16 * sizeof(float), s));
     ok(cudaMemsetAsync(F(L.G), 0, 9 * 256 * sizeof(float), s));
   }
   // weights, embedding taps, pooling, conv0, blocks 1..4
@@ -1384,52 +1325,81 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   ok(launch_conv<32, 64, 8, 4, false, false, false>(A[1], nullptr, wf[2], bias[2], nullptr, A[2], ph << 2, pw << 2, s));
   ok(launch_conv<16, 32, 16, 8, false, false, false>(A[2], nullptr, wf[3], bias[3], nullptr, A[3], ph << 3, pw << 3, s));
   ok(launch_conv<8, 16, 16, 8, false, false, false>(A[3], nullptr, wf[4], bias[4], nullptr, A[4], ph << 4, pw << 4, s));
+  // the head: up-sampling, conv5, conv6 with the L1 term (and, for the backward, gM')
   float* U = F(L.U);
+  float* Hh = F(L.Hh);
+  unsigned* status = reinterpret_cast<unsigned*>(ws + L.status);
+  ok(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
+  const int h4 = ph << 4, w4 = pw << 4;
   note_launches(1);
-  upsample_kernel<<<(int)(((size_t)W * H * 4 + 255) / 256), 256, 0, s>>>(A[4], ph << 4, pw << 4, H, W, U);
-  // the head
-  HeadArgs ha{};
-  ha.img = img;
-  ha.target = target;
-  ha.u = U;
-  ha.w5f = reinterpret_cast<const float2*>(packed + L.pack_off[8]);
-  ha.w5d = reinterpret_cast<const float2*>(packed + L.pack_off[9]);
-  ha.w6f = reinterpret_cast<const float2*>(packed + L.pack_off[10]);
-  ha.w6d = reinterpret_cast<const float2*>(packed + L.pack_off[11]);
-  ha.b5 = params + b_off(5);
-  ha.b6 = params + b_off(6);
-  ha.gimg = grad_img;
-  ha.map = out_map;
-  ha.gf4 = gA[4];
-  ha.dw5 = grad_params ? grad_params + w_off(5) : nullptr;
-  ha.db5 = grad_params ? grad_params + b_off(5) : nullptr;
-  ha.dw6 = grad_params ? grad_params + w_off(6) : nullptr;
-  ha.db6 = grad_params ? grad_params + b_off(6) : nullptr;
-  ha.partials = head_part;
-  ha.H = H;
-  ha.W = W;
-  ha.h4 = ph << 4;
-  ha.w4 = pw << 4;
-  ha.tiles_x = (W + HT - 1) / HT;
-  ha.tiles = ha.tiles_x * ((H + HT - 1) / HT);
+  upsample_kernel<<<(int)(((size_t)W * H * 4 + 255) / 256), 256, 0, s>>>(A[4], h4, w4, H, W, U);
   const double inv = 1.0 / (3.0 * (double)((size_t)W * H));
-  ha.cscale = (float)((1.0 - lambda) * inv);     // the L1 scale of Eq. 1's kernel, bit for bit
-  const size_t head_smem = (size_t)kHeadSmemBytes;
-  const int grid = std::min(ha.tiles, std::min(kMaxHeadBlocks, sms));   // one block an SM (shared memory)
-  note_launches(2);
-  if (bwd) {
-    ok(set_smem(head_kernel<true>, head_smem));
-    head_kernel<true><<<grid, kHeadThreads, head_smem, s>>>(ha);
-  } else {
-    ok(set_smem(head_kernel<false>, head_smem));
-    head_kernel<false><<<grid, kHeadThreads, head_smem, s>>>(ha);
+  TcArgs ta{};
+  ta.H = H;
+  ta.W = W;
+  ta.tiles_x = (W + kTcCols - 1) / kTcCols;
+  ta.tiles = ta.tiles_x * ((H + kTcRows - 1) / kTcRows);
+  ta.status = status;
+  ta.cscale = (float)((1.0 - lambda) * inv);     // the L1 scale of Eq. 1's kernel, bit for bit
+  ta.wc = 16;
+  int nhead = 0;                                 // CTAs of the conv6 pass (its L1 partial sums)
+  {
+    TcArgs c5 = ta;
+    c5.in = U;
+    c5.w = params + w_off(5);
+    c5.bias = params + b_off(5);
+    c5.out = Hh;
+    c5.wo = 16;
+    ok(launch_tc_conv<16, kEpiRelu>(c5, sms, s));
+    TcArgs c6 = ta;
+    c6.in = Hh;
+    c6.w = params + w_off(6);
+    c6.bias = params + b_off(6);
+    c6.img = img;
+    c6.target = target;
+    c6.map = out_map;
+    c6.gimg = grad_img;
+    c6.out = bwd ? F(L.gM) : nullptr;
+    c6.dbias = bwd ? grad_params + b_off(6) : nullptr;
+    c6.partials = head_part;
+    c6.wo = 3;
+    ok(launch_tc_conv<16, kEpiL1>(c6, sms, s, &nhead));
   }
   ok(link(E, side, s));      // the SSIM partials and maps
-  appearance_finalize<<<1, 256, 0, s>>>(ssim_part, ssim_partials(W, H), head_part, grid, inv, lambda, out_loss);
+  appearance_finalize<<<1, 256, 0, s>>>(ssim_part, ssim_partials(W, H), head_part, nhead, inv, lambda, status, out_loss);
   ok(cudaGetLastError());
   if (!bwd) return e == cudaSuccess ? VG_OK : VG_ERR_CUDA;
-  // dL/dI_r's SSIM and L1 terms (the block-mean term is added at the end)
   float* gp = grad_params;
+  // the head's adjoint: gZ5' (and db5), gU, dL/dF4 = gA[4]; the weight gradients beside it
+  {
+    TcArgs a6 = ta;
+    a6.in = F(L.gM);
+    a6.w = params + w_off(6);
+    a6.act = Hh;
+    a6.out = F(L.gZ);
+    a6.dbias = gp + b_off(5);
+    a6.wo = 3;
+    a6.adjoint = true;
+    ok(launch_tc_conv<8, kEpiMask>(a6, sms, s));
+    ok(link(E, s, sd[1]));
+    ok(launch_head_wgrad<16, 16>(U, F(L.gZ), H, W, ta.cscale, gp + w_off(5), sms, sd[1]));
+    ok(launch_head_wgrad<8, 3>(Hh, F(L.gM), H, W, ta.cscale, gp + w_off(6), sms, sd[1]));
+    TcArgs a5 = ta;
+    a5.in = F(L.gZ);
+    a5.w = params + w_off(5);
+    a5.out = F(L.gU);
+    a5.wo = 16;
+    a5.adjoint = true;
+    ok(launch_tc_conv<16, kEpiStore>(a5, sms, s));
+    note_launches(2);
+    const size_t n1 = (size_t)H * w4 * 4, n2 = (size_t)w4 * h4 * 4;
+    upsample_adjoint_kernel<false><<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(
+        F(L.gU), H, W, w4, (size_t)W * 16, 16, (size_t)w4 * 16, 16, 1.f, F(L.gX));
+    upsample_adjoint_kernel<true><<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(
+        F(L.gX), w4, H, h4, 16, (size_t)w4 * 16, 16, (size_t)w4 * 16, ta.cscale, gA[4]);
+    ok(cudaGetLastError());
+  }
+  // dL/dI_r's SSIM and L1 terms (the block-mean term is added at the end)
   ok(link(E, s, sd[0]));
   ok(launch_ssim_grad_appearance(img, target, F(L.maps), W, H, nullptr, 0, 0, grad_img, sd[0]));
   // blocks 4..1: the input-gradient chain on s (each launch writes the next block's masked output
