@@ -670,7 +670,11 @@ __global__ void __launch_bounds__(256) conv0_embed_grad_kernel(const float* __re
 // is stored as [part][channel group][18][10][4 floats], so the 8 pixels of one output row segment
 // are one core matrix, the next output row is 160 bytes further (the stride between core matrices
 // along M) and the next channel group one plane further (the stride along K); a tap (dy, dx) only
-// moves the start address by (10 dy + dx) x 16 bytes.  Weights are [part][tap][group][16][4].
+// moves the start address by (10 dy + dx) x 16 bytes.  Weights are [tap][group][part][16][4]: for
+// one tap and channel group the hi rows are followed by the lo rows, so that one N = 32 operand
+// holds [W_hi | W_lo] and a k-step takes two MMAs, A_hi [W_hi | W_lo] into accumulator columns
+// 0..31 and A_lo W_hi into columns 16..31 (the products hi.hi | hi.lo + lo.hi), reading each part
+// of the activations from shared memory once; the epilogue adds the two halves.
 
 constexpr int kTcThreads = 128;                      // four warps: staging, epilogue; one thread issues
 constexpr int kTcRows = 16, kTcCols = 8;             // output pixels of an M-tile
@@ -684,8 +688,8 @@ struct TcShape {
   static constexpr int CG = C / 4;                           // channel groups (K = 8 per MMA: 2 groups)
   static constexpr uint32_t PartA = CG * kPatchPlane;
   static constexpr uint32_t BufA = 2 * PartA;                // hi and lo parts of one patch
-  static constexpr uint32_t PartB = 9 * CG * 16 * 16;        // one part of the weights
-  static constexpr uint32_t Smem = 2 * BufA + 2 * PartB;     // two patch buffers + weights
+  static constexpr uint32_t SizeB = 9 * CG * 2 * 16 * 16;    // the weights, both parts
+  static constexpr uint32_t Smem = 2 * BufA + SizeB;         // two patch buffers + weights
 };
 
 struct TcArgs {
@@ -724,61 +728,65 @@ __device__ void tc_stage_weights(unsigned char* sB, const TcArgs& a) {
       else v[j] = (k < a.wo && n < a.wc) ? __ldg(a.w + ((size_t)k * a.wc + n) * 9 + (8 - tap)) : 0.f;
     }
     const float4 x = make_float4(v[0], v[1], v[2], v[3]), h = split_hi(x);
-    const uint32_t off = (uint32_t)(((tap * S::CG + cg) * 16 + n) * 16);
+    const uint32_t off = (uint32_t)(((tap * S::CG + cg) * 32 + n) * 16);
     *reinterpret_cast<float4*>(sB + off) = h;
-    *reinterpret_cast<float4*>(sB + S::PartB + off) = split_lo(x, h);
+    *reinterpret_cast<float4*>(sB + off + 256) = split_lo(x, h);
   }
 }
 
 // The M-tile's input patch, rows Y0 - 1 .. Y0 + 16 and columns X0 - 1 .. X0 + 8, zero outside the
-// image, split into its two TF32 parts.  All loads are issued before the first store.
+// image: loaded into registers (tc_load_patch, issued a tile ahead so that the loads are in flight
+// while the previous tile's epilogue runs), then split into its two TF32 parts in shared memory.
 template <int C>
-__device__ __forceinline__ void tc_stage_patch(unsigned char* sA, const float* __restrict__ in, int Y0, int X0, int H,
-                                               int W) {
-  using S = TcShape<C>;
-  constexpr int N = kPatchPx * S::CG, IT = (N + kTcThreads - 1) / kTcThreads;
+struct TcPatch {
+  static constexpr int N = kPatchPx * (C / 4), IT = (N + kTcThreads - 1) / kTcThreads;
   float4 v[IT];
+};
+template <int C>
+__device__ __forceinline__ void tc_load_patch(TcPatch<C>& r, const float* __restrict__ in, int Y0, int X0, int H,
+                                              int W) {
+  constexpr int CG = C / 4;
 #pragma unroll
-  for (int q = 0; q < IT; ++q) {
+  for (int q = 0; q < TcPatch<C>::IT; ++q) {
     const int i = threadIdx.x + kTcThreads * q;
-    const int px = i / S::CG, cg = i % S::CG;
+    const int px = i / CG, cg = i % CG;
     const int Y = Y0 - 1 + px / kPatchW, X = X0 - 1 + px % kPatchW;
-    v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < N && Y >= 0 && Y < H && X >= 0 && X < W)
-      v[q] = __ldg(reinterpret_cast<const float4*>(in + ((size_t)Y * W + X) * C) + cg);
+    r.v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < TcPatch<C>::N && Y >= 0 && Y < H && X >= 0 && X < W)
+      r.v[q] = __ldg(reinterpret_cast<const float4*>(in + ((size_t)Y * W + X) * C) + cg);
   }
+}
+template <int C>
+__device__ __forceinline__ void tc_store_patch(unsigned char* sA, const TcPatch<C>& r) {
+  using S = TcShape<C>;
 #pragma unroll
-  for (int q = 0; q < IT; ++q) {
+  for (int q = 0; q < TcPatch<C>::IT; ++q) {
     const int i = threadIdx.x + kTcThreads * q;
-    if (i >= N) continue;
+    if (i >= TcPatch<C>::N) continue;
     const int px = i / S::CG, cg = i % S::CG;
     const uint32_t off = (uint32_t)cg * kPatchPlane + (uint32_t)px * 16;
-    const float4 h = split_hi(v[q]);
+    const float4 h = split_hi(r.v[q]);
     *reinterpret_cast<float4*>(sA + off) = h;
-    *reinterpret_cast<float4*>(sA + S::PartA + off) = split_lo(v[q], h);
+    *reinterpret_cast<float4*>(sA + S::PartA + off) = split_lo(r.v[q], h);
   }
 }
 
-// The MMAs of one M-tile: 9 taps x C / 8 k-steps x 3 part products into the accumulator d.
+// The MMAs of one M-tile: 9 taps x C / 8 k-steps x 2 into the 32-column accumulator d.  The
+// descriptors of the patch buffer's and the weights' first core matrices are formed once; an
+// operand's offset only adds to the start-address field (16-byte units, no carry: shared
+// addresses stay below 2^18).
 template <int C>
-__device__ __forceinline__ void tc_issue(uint32_t a_buf, uint32_t b_buf, uint32_t d) {
+__device__ __forceinline__ void tc_issue(uint64_t a_hi, uint64_t b_desc, uint32_t d) {
   using S = TcShape<C>;
-  constexpr uint32_t idesc = tc::idesc_tf32(128, 16);
-  bool acc = false;
-#pragma unroll 1
+  constexpr uint32_t idesc32 = tc::idesc_tf32(128, 32), idesc16 = tc::idesc_tf32(128, 16);
+#pragma unroll
   for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
     for (int ks = 0; ks < C / 8; ++ks) {
-      const uint32_t ao = 2 * ks * kPatchPlane + (uint32_t)(dy * kPatchW + dx) * 16;
-      const uint32_t bo = (uint32_t)((tap * S::CG + 2 * ks) * 256);
-#pragma unroll
-      for (int pr = 0; pr < 3; ++pr) {           // lo.hi, hi.lo, hi.hi
-        const uint32_t pa = pr == 0 ? S::PartA : 0u, pb = pr == 1 ? S::PartB : 0u;
-        tc::mma_tf32(d, tc::desc(a_buf + pa + ao, kPatchPlane, kPatchW * 16), tc::desc(b_buf + pb + bo, 256, 128),
-                     idesc, acc);
-        acc = true;
-      }
+      const uint64_t ao = (2 * ks * kPatchPlane + (uint32_t)((tap / 3) * kPatchW + tap % 3) * 16) >> 4;
+      const uint64_t bo = (uint64_t)((tap * S::CG + 2 * ks) * 512) >> 4;
+      tc::mma_tf32(d, a_hi + ao, b_desc + bo, idesc32, tap + ks > 0);                    // A_hi [W_hi | W_lo]
+      tc::mma_tf32(d + 16, a_hi + ao + (S::PartA >> 4), b_desc + bo, idesc16, true);     // A_lo W_hi
     }
   }
 }
@@ -789,20 +797,50 @@ struct TcSums {
   float db[16] = {};
 };
 
-// Epilogue of one M-tile: waits for its MMAs, reads the thread's pixel (row m = 32 warp + lane of
-// the accumulator) and applies the layer's output step.  Returns false if the wait gave up.
+// The epilogue's other inputs at the thread's pixel, loaded a tile ahead: Hh (kEpiMask) or I_r
+// and I (kEpiL1).
+struct TcEpiIn {
+  float4 x[4];
+};
+
+__device__ __forceinline__ bool tc_pixel(const TcArgs& a, int tile, int& Y, int& X) {
+  const int m = threadIdx.x;      // accumulator row = lane of tensor memory = this thread
+  Y = (tile / a.tiles_x) * kTcRows + (m >> 3);
+  X = (tile % a.tiles_x) * kTcCols + (m & 7);
+  return Y < a.H && X < a.W;
+}
+
+template <int EPI>
+__device__ __forceinline__ void tc_load_epi(const TcArgs& a, int tile, TcEpiIn& e) {
+  int Y, X;
+  if (!tc_pixel(a, tile, Y, X)) return;
+  const size_t pix = (size_t)Y * a.W + X;
+  if constexpr (EPI == kEpiMask) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e.x[q] = __ldg(reinterpret_cast<const float4*>(a.act + pix * 16) + q);
+  } else if constexpr (EPI == kEpiL1) {
+    const size_t HW = (size_t)a.H * a.W;
+    e.x[0] = make_float4(__ldg(a.img + pix), __ldg(a.img + HW + pix), __ldg(a.img + 2 * HW + pix), 0.f);
+    e.x[1] = make_float4(__ldg(a.target + pix), __ldg(a.target + HW + pix), __ldg(a.target + 2 * HW + pix), 0.f);
+  }
+}
+
+// Epilogue of one M-tile: waits for its MMAs, reads the thread's accumulator row (row m = 32 warp +
+// lane = the thread index) and applies the layer's output step.  Returns false if the wait gave up.
 template <int EPI>
 __device__ __forceinline__ bool tc_epilogue(const TcArgs& a, int tile, uint32_t tm, uint64_t* mbar, uint32_t parity,
-                                            TcSums& sums) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                                            const TcEpiIn& e, TcSums& sums) {
+  const int warp = threadIdx.x >> 5;
   const bool ok = tc::mbar_wait(mbar, parity, kTcWaitNs);
   __syncwarp();
   tc::fence_after_sync();
-  float v[16];
+  float v[16], w[16];
   tc::ld16(tm + ((uint32_t)(32 * warp) << 16), v);
-  const int m = 32 * warp + lane;
-  const int Y = (tile / a.tiles_x) * kTcRows + (m >> 3), X = (tile % a.tiles_x) * kTcCols + (m & 7);
-  if (!ok || Y >= a.H || X >= a.W) return ok;
+  tc::ld16(tm + ((uint32_t)(32 * warp) << 16) + 16u, w);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] += w[j];      // hi.hi + (hi.lo + lo.hi)
+  int Y, X;
+  if (!tc_pixel(a, tile, Y, X) || !ok) return ok;
   const size_t pix = (size_t)Y * a.W + X;
   if constexpr (EPI == kEpiRelu) {
     float4* o = reinterpret_cast<float4*>(a.out + pix * 16);
@@ -816,11 +854,10 @@ __device__ __forceinline__ bool tc_epilogue(const TcArgs& a, int tile, uint32_t 
 #pragma unroll
     for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   } else if constexpr (EPI == kEpiMask) {
-    const float4* h = reinterpret_cast<const float4*>(a.act + pix * 16);
     float4* o = reinterpret_cast<float4*>(a.out + pix * 16);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float4 hv = __ldg(h + q);
+      const float4 hv = e.x[q];
       const float4 z = make_float4(hv.x > 0.f ? v[4 * q] : 0.f, hv.y > 0.f ? v[4 * q + 1] : 0.f,
                                    hv.z > 0.f ? v[4 * q + 2] : 0.f, hv.w > 0.f ? v[4 * q + 3] : 0.f);
       o[q] = z;
@@ -831,14 +868,14 @@ __device__ __forceinline__ bool tc_epilogue(const TcArgs& a, int tile, uint32_t 
     }
   } else {   // kEpiL1: M, the L1 term and its gradients
     const size_t HW = (size_t)a.H * a.W;
+    const float ir[3] = {e.x[0].x, e.x[0].y, e.x[0].z}, it[3] = {e.x[1].x, e.x[1].y, e.x[1].z};
     float gm[3];
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
       const float Mv = v[o] + __ldg(a.bias + o);
-      const float iv = __ldg(a.img + o * HW + pix), tv = __ldg(a.target + o * HW + pix);
-      const float d = iv * Mv - tv;
+      const float d = ir[o] * Mv - it[o];
       const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-      gm[o] = sgn * iv;
+      gm[o] = sgn * ir[o];
       sums.l1 += fabsf(d);
       if (a.map) a.map[o * HW + pix] = Mv;
       if (a.gimg) a.gimg[o * HW + pix] = a.cscale * sgn * Mv;
@@ -863,37 +900,48 @@ __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(const TcArgs a) {
   __shared__ uint32_t tslot;
   __shared__ double red[kTcThreads / 32];
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (warp == 0) tc::alloc(&tslot, 32);        // two 16-column accumulators
+  if (warp == 0) tc::alloc(&tslot, 64);        // two 32-column accumulators
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
     tc::mbar_init_fence();
   }
+  TcPatch<C> pre;
+  TcEpiIn epi_next, epi_prev;
+  int tile = blockIdx.x;
+  if (tile < a.tiles) tc_load_patch<C>(pre, a.in, (tile / a.tiles_x) * kTcRows, (tile % a.tiles_x) * kTcCols, a.H, a.W);
   tc_stage_weights<C>(sB, a);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = tslot, a0 = smem_u32(sA), b0 = smem_u32(sB);
+  const uint32_t tmem = tslot;
+  const uint64_t a_desc = tc::desc(smem_u32(sA), kPatchPlane, kPatchW * 16);
+  const uint64_t b_desc = tc::desc(smem_u32(sB), 512, 128);
   TcSums sums;
   bool ok = true;
   int k = 0, prev = -1;
-  // tile k is staged into buffer k & 1 and accumulated in columns 16 (k & 1); its epilogue runs
-  // while the MMAs of tile k + 1 execute
-  for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, ++k) {
+  // tile k is staged into buffer k & 1 and accumulated in columns 32 (k & 1); its epilogue runs
+  // in iteration k + 1, while the MMAs of tile k + 1 execute and the patch of tile k + 2 loads
+  for (; tile < a.tiles; tile += gridDim.x, ++k) {
     const int b = k & 1;
-    tc_stage_patch<C>(sA + b * S::BufA, a.in, (tile / a.tiles_x) * kTcRows, (tile % a.tiles_x) * kTcCols, a.H, a.W);
+    tc_store_patch<C>(sA + b * S::BufA, pre);
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      tc_issue<C>(a0 + b * S::BufA, b0, tmem + 16u * b);
+      tc_issue<C>(a_desc + ((b * S::BufA) >> 4), b_desc, tmem + 32u * b);
       tc::commit(&mbar[b]);
     }
-    if (prev >= 0) ok &= tc_epilogue<EPI>(a, prev, tmem + 16u * (b ^ 1), &mbar[b ^ 1], ((k - 1) >> 1) & 1, sums);
+    const int next = tile + gridDim.x;
+    if (next < a.tiles) tc_load_patch<C>(pre, a.in, (next / a.tiles_x) * kTcRows, (next % a.tiles_x) * kTcCols, a.H, a.W);
+    tc_load_epi<EPI>(a, tile, epi_next);
+    if (prev >= 0) ok &= tc_epilogue<EPI>(a, prev, tmem + 32u * (b ^ 1), &mbar[b ^ 1], ((k - 1) >> 1) & 1, epi_prev, sums);
+    epi_prev = epi_next;
     prev = tile;
   }
-  if (prev >= 0) ok &= tc_epilogue<EPI>(a, prev, tmem + 16u * ((k - 1) & 1), &mbar[(k - 1) & 1], ((k - 1) >> 1) & 1, sums);
+  if (prev >= 0)
+    ok &= tc_epilogue<EPI>(a, prev, tmem + 32u * ((k - 1) & 1), &mbar[(k - 1) & 1], ((k - 1) >> 1) & 1, epi_prev, sums);
   if (!ok) {
     atomicOr(a.status, 1u);
     // the last commit of each buffer, waited for again (bounded) before the memory is freed
@@ -901,7 +949,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(const TcArgs a) {
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::dealloc(tmem, 32);
+  if (warp == 0) tc::dealloc(tmem, 64);
   // the per-CTA sums of the epilogue
   const int lane = tid & 31;
   if constexpr (EPI == kEpiL1) {
@@ -947,25 +995,36 @@ __device__ __forceinline__ Tap up_tap(int y, int n_in, int n_out) {
   return r;
 }
 
-// Weight of output sample y on input sample i under up_tap.
-__device__ __forceinline__ float up_weight(int y, int i, int n_in, int n_out) {
-  const Tap t = up_tap(y, n_in, n_out);
-  return (t.i0 == i ? 1.f - t.f : 0.f) + (t.i1 == i ? t.f : 0.f);
+// Tap tables of the up-sampling: taps[y] = (i0, f) of output row y (entries [0, H)) and of output
+// column x (entries [H, H + W)), so that the up-sampling and its adjoint divide nothing per sample.
+__global__ void __launch_bounds__(256) tap_table_kernel(int h4, int w4, int H, int W, int2* __restrict__ taps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= H + W) return;
+  const Tap t = i < H ? up_tap(i, h4, H) : up_tap(i - H, w4, W);
+  taps[i] = make_int2(t.i0, __float_as_int(t.f));
+}
+
+// Weight of output sample y (tap (i0, f) from the table) on input sample i.
+__device__ __forceinline__ float up_weight(int2 t, int i, int n_in) {
+  const float f = __int_as_float(t.y);
+  const int i1 = min(t.x + 1, n_in - 1);
+  return (t.x == i ? 1.f - f : 0.f) + (i1 == i ? f : 0.f);
 }
 
 // U = F4 [h4][w4][16] up-sampled bilinearly to [H][W][16] (FP32): conv5's input.  A thread produces
 // 4 channels of one pixel.
 __global__ void __launch_bounds__(256) upsample_kernel(const float* __restrict__ f4, int h4, int w4, int H, int W,
-                                                       float* __restrict__ U) {
+                                                       const int2* __restrict__ taps, float* __restrict__ U) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= H * W * 4) return;
   const int v = i & 3, px = i >> 2, y = px / W, x = px % W;
-  const Tap ty = up_tap(y, h4, H), tx = up_tap(x, w4, W);
-  const float fy = ty.f, fx = tx.f, gy = 1.f - fy, gx = 1.f - fx;
-  const float4 p = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)ty.i0 * w4 + tx.i0) * 16) + v);
-  const float4 q = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)ty.i0 * w4 + tx.i1) * 16) + v);
-  const float4 r = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)ty.i1 * w4 + tx.i0) * 16) + v);
-  const float4 t = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)ty.i1 * w4 + tx.i1) * 16) + v);
+  const int2 ty = __ldg(taps + y), tx = __ldg(taps + H + x);
+  const int y0 = ty.x, y1 = min(ty.x + 1, h4 - 1), x0 = tx.x, x1 = min(tx.x + 1, w4 - 1);
+  const float fy = __int_as_float(ty.y), fx = __int_as_float(tx.y), gy = 1.f - fy, gx = 1.f - fx;
+  const float4 p = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)y0 * w4 + x0) * 16) + v);
+  const float4 q = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)y0 * w4 + x1) * 16) + v);
+  const float4 r = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)y1 * w4 + x0) * 16) + v);
+  const float4 t = __ldg(reinterpret_cast<const float4*>(f4 + ((size_t)y1 * w4 + x1) * 16) + v);
   float4 u;
   u.x = gy * (gx * p.x + fx * q.x) + fy * (gx * r.x + fx * t.x);
   u.y = gy * (gx * p.y + fx * q.y) + fy * (gx * r.y + fx * t.y);
@@ -985,7 +1044,8 @@ template <bool LINES_FAST>
 __global__ void __launch_bounds__(256) upsample_adjoint_kernel(const float* __restrict__ g, int n_lines, int n_out,
                                                                int n_in, size_t line_stride, size_t sample_stride,
                                                                size_t out_line_stride, size_t out_sample_stride,
-                                                               float scale, float* __restrict__ out) {
+                                                               const int2* __restrict__ taps, float scale,
+                                                               float* __restrict__ out) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)n_lines * n_in * 4) return;
   const int v = (int)(i & 3);
@@ -996,7 +1056,7 @@ __global__ void __launch_bounds__(256) upsample_adjoint_kernel(const float* __re
   const int hi = min(n_out - 1, (int)ceilf((float)(a + 2) * n_out / n_in) + 2);
   float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int x = lo; x <= hi; ++x) {
-    const float w = up_weight(x, a, n_in, n_out);
+    const float w = up_weight(__ldg(taps + x), a, n_in);
     if (w == 0.f) continue;
     const float4 gv = __ldg(reinterpret_cast<const float4*>(g + line * line_stride + x * sample_stride) + v);
     s.x = fmaf(w, gv.x, s.x);
@@ -1008,59 +1068,115 @@ __global__ void __launch_bounds__(256) upsample_adjoint_kernel(const float* __re
       make_float4(scale * s.x, scale * s.y, scale * s.z, scale * s.w);
 }
 
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
 // Weight gradient of a head convolution on the CUDA cores (FP32):
 //   dW[o][ci][tap] += scale sum_p Z(p)[o] X(p + tap - (1, 1))[ci]   (X zero outside the image)
-// with X [H][W][16] and Z [H][W][ZC] (channels past NO zero).  A thread owns 4 output x 4 input
-// channels of one tap (16 sums) and a phase of the pixels; a block takes tiles of 8 x 32 pixels,
-// staged in shared memory with X's one-pixel halo.
-constexpr int kWgThreads = 144, kWgRows = 8, kWgCols = 32;
-template <int ZC, int NO>
-__global__ void __launch_bounds__(kWgThreads) head_wgrad_kernel(const float* __restrict__ X, const float* __restrict__ Z,
+// with X [H][W][16] and Z [H][W][ZC] (channels past NO zero).  A block takes tiles of ROWS x 32
+// pixels, staged in shared memory with X's one-pixel halo by cp.async, double-buffered (the next
+// tile's copies are in flight while this one computes).  X's pixels are 80 bytes apart in shared
+// memory (16 channels + 4 of padding), so that 8 consecutive pixels fall on 8 different bank
+// quads.  The sums are updated by packed FP32 FMAs.
+//  * NO = 16: a thread owns 4 output x 8 input channels of one tap (32 sums) and a phase of the
+//    pixels; within a warp the output-channel groups vary fastest, so the Z loads are broadcasts.
+//  * NO = 3: warp w owns tap w, lane l the pixels of column l; a thread keeps 4 (3 used) x 16
+//    sums, and the warp adds its lanes' sums before the atomic additions.
+constexpr int kWgThreads = 288, kWgCols = 32, kWgPitch = 5;      // pitch: float4s per staged X pixel
+template <int NOG, int ROWS>
+struct WgShape {
+  static constexpr int XH = ROWS + 2, XW = kWgCols + 2, NPX = ROWS * kWgCols;
+  static constexpr int XF4 = XH * XW * kWgPitch, ZF4 = NPX * NOG;   // float4s of one buffer's X and Z
+  static constexpr size_t Smem = 2 * (size_t)(XF4 + ZF4) * 16;
+};
+template <int ZC, int NO, int ROWS>
+__global__ void __launch_bounds__(kWgThreads, NO > 4 ? 3 : 2) head_wgrad_kernel(const float* __restrict__ X, const float* __restrict__ Z,
                                                                 int H, int W, int tiles_x, int tiles, float scale,
                                                                 float* __restrict__ dW) {
-  constexpr int NOG = (NO + 3) / 4, GROUPS = NOG * 4 * 9, PHASES = kWgThreads / GROUPS;
-  constexpr int XH = kWgRows + 2, XW = kWgCols + 2, NPX = kWgRows * kWgCols;
-  static_assert(kWgThreads % GROUPS == 0 && NPX % PHASES == 0, "thread layout");
-  __shared__ __align__(16) float sX[XH * XW * 16];
-  __shared__ __align__(16) float sZ[NPX * 4 * NOG];
-  const int grp = threadIdx.x % GROUPS, phase = threadIdx.x / GROUPS;
-  const int og = grp % NOG, cg = (grp / NOG) % 4, tap = grp / (4 * NOG);
-  const int dy = tap / 3, dx = tap % 3;
-  float acc[4][4] = {};
-  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int Y0 = (tile / tiles_x) * kWgRows, X0 = (tile % tiles_x) * kWgCols;
-    __syncthreads();
-    for (int i = threadIdx.x; i < XH * XW * 4; i += kWgThreads) {
-      const int px = i >> 2, q = i & 3, Y = Y0 - 1 + px / XW, Xc = X0 - 1 + px % XW;
-      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (Y >= 0 && Y < H && Xc >= 0 && Xc < W) xv = __ldg(reinterpret_cast<const float4*>(X + ((size_t)Y * W + Xc) * 16) + q);
-      reinterpret_cast<float4*>(sX)[i] = xv;
+  constexpr int NOG = (NO + 3) / 4;
+  using S = WgShape<NOG, ROWS>;
+  extern __shared__ __align__(16) float4 wg_smem[];   // [2][X patch | Z tile]
+  auto stage = [&](int buf, int tile) {
+    float4* sX = wg_smem + buf * (S::XF4 + S::ZF4);
+    float4* sZ = sX + S::XF4;
+    const int Y0 = (tile / tiles_x) * ROWS, X0 = (tile % tiles_x) * kWgCols;
+    for (int i = threadIdx.x; i < S::XH * S::XW * 4; i += kWgThreads) {
+      const int px = i >> 2, q = i & 3, Y = Y0 - 1 + px / S::XW, Xc = X0 - 1 + px % S::XW;
+      const bool in = Y >= 0 && Y < H && Xc >= 0 && Xc < W;
+      cp_async16_zfill(sX + px * kWgPitch + q, X + (in ? ((size_t)Y * W + Xc) * 16 + 4 * q : 0), in);
     }
-    for (int i = threadIdx.x; i < NPX * NOG; i += kWgThreads) {
+    for (int i = threadIdx.x; i < S::ZF4; i += kWgThreads) {
       const int px = i / NOG, q = i % NOG, Y = Y0 + px / kWgCols, Xc = X0 + px % kWgCols;
-      float4 zv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (Y < H && Xc < W) zv = __ldg(reinterpret_cast<const float4*>(Z + ((size_t)Y * W + Xc) * ZC) + q);
-      reinterpret_cast<float4*>(sZ)[i] = zv;
+      const bool in = Y < H && Xc < W;
+      cp_async16_zfill(sZ + i, Z + (in ? ((size_t)Y * W + Xc) * ZC + 4 * q : 0), in);
     }
-    __syncthreads();
+  };
+  constexpr bool WIDE = NO > 4;                       // the two thread layouts above
+  constexpr int GROUPS = WIDE ? NOG * 2 * 9 : 9, PHASES = kWgThreads / GROUPS;
+  static_assert(kWgThreads % GROUPS == 0 && S::NPX % PHASES == 0 && (WIDE || kWgThreads == 9 * 32), "thread layout");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = WIDE ? threadIdx.x % GROUPS : warp, phase = WIDE ? threadIdx.x / GROUPS : lane;
+  const int og = WIDE ? grp % NOG : 0, ch = WIDE ? (grp / NOG) % 2 : 0, tap = WIDE ? grp / (2 * NOG) : warp;
+  constexpr int NJ = WIDE ? 4 : 8;                    // float2 pairs of input channels a thread owns
+  const int dy = tap / 3, dx = tap % 3;
+  float2 acc[4][NJ];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  if (blockIdx.x < tiles) stage(0, blockIdx.x);
+  cp_async_commit();
+  int k = 0;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++k) {
+    const int next = tile + gridDim.x;
+    if (next < tiles) stage((k + 1) & 1, next);     // that buffer's last readers passed the barrier below
+    cp_async_commit();
+    cp_async_wait<1>();                              // this thread's copies of this tile
+    __syncthreads();                                 // ... and everyone's
+    const float4* sX = wg_smem + (k & 1) * (S::XF4 + S::ZF4);
+    const float4* sZ = sX + S::XF4;
 #pragma unroll 4
-    for (int p = phase; p < NPX; p += PHASES) {
+    for (int p = phase; p < S::NPX; p += PHASES) {
       const int r = p / kWgCols, c = p % kWgCols;
-      const float4 z = reinterpret_cast<const float4*>(sZ)[p * NOG + og];
-      const float4 x = reinterpret_cast<const float4*>(sX)[((r + dy) * XW + c + dx) * 4 + cg];
-      const float zz[4] = {z.x, z.y, z.z, z.w}, xx[4] = {x.x, x.y, x.z, x.w};
+      const float4 z = sZ[p * NOG + og];
+      const float4* xp = sX + ((r + dy) * S::XW + c + dx) * kWgPitch + 2 * ch;
+      float2 xx[NJ];
+#pragma unroll
+      for (int q = 0; q < NJ / 2; ++q) {
+        const float4 xv = xp[q];
+        xx[2 * q] = make_float2(xv.x, xv.y);
+        xx[2 * q + 1] = make_float2(xv.z, xv.w);
+      }
+      const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(zz[i], xx[j], acc[i][j]);
+        for (int j = 0; j < NJ; ++j) acc[i][j] = __ffma2_rn(make_float2(zz[i], zz[i]), xx[j], acc[i][j]);
     }
+    __syncthreads();                                 // the buffer is free for the copies two tiles on
   }
+  cp_async_wait<0>();
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int o = 4 * og + i;
     if (o >= NO) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) atomicAdd(dW + ((size_t)o * 16 + 4 * cg + j) * 9 + tap, scale * acc[i][j]);
+    for (int j = 0; j < NJ; ++j) {
+      const int ci = 8 * ch + 2 * j;
+      float2 v = acc[i][j];
+      if constexpr (!WIDE) {      // every lane of the warp holds sums of the same (o, ci, tap)
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+          v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
+          v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
+        }
+        if (lane != 0) continue;
+      }
+      atomicAdd(dW + ((size_t)o * 16 + ci) * 9 + tap, scale * v.x);
+      atomicAdd(dW + ((size_t)o * 16 + ci + 1) * 9 + tap, scale * v.y);
+    }
   }
 }
 
@@ -1109,7 +1225,7 @@ __global__ void __launch_bounds__(256) appearance_finalize(const double* __restr
 
 // Workspace regions (floats unless noted), for an H x W image with (h, w) = (H / 32, W / 32).
 struct AppLayout {
-  size_t E, G, P, gP, A[5], gA[5], U, Hh, gM, gZ, gU, gX, packed, maps, ssim_part, head_part, status, total;
+  size_t E, G, P, gP, A[5], gA[5], U, Hh, gM, gZ, gU, gX, taps, packed, maps, ssim_part, head_part, status, total;
   int pack_off[kPackJobs];
   PackTable tab;
 };
@@ -1163,6 +1279,7 @@ AppLayout make_app_layout(int W, int H) {
   L.gZ = take(HW * 16 * 4);
   L.gU = take(HW * 16 * 4);
   L.gX = take((size_t)H * (w << 4) * 16 * 4);  //   the up-sampling adjoint's column pass [H][w4][16]
+  L.taps = take((size_t)(H + W) * 8);           //   the up-sampling's taps of rows and columns
   L.maps = take(ssim_maps_floats(W, H) * 4);
   L.ssim_part = take((size_t)ssim_partials(W, H) * 2 * 8);
   L.head_part = take((size_t)kMaxHeadBlocks * 8);
@@ -1174,6 +1291,16 @@ AppLayout make_app_layout(int W, int H) {
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// CTAs of `kernel` an SM holds by its registers and shared memory (dynamic + static), at most cap.
+template <typename K>
+int resident_per_sm(K kernel, int threads, size_t dyn_smem, int cap) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 1;
+  const int by_regs = 65536 / std::max(1, ((fa.numRegs * threads + 255) / 256) * 256);
+  const int by_smem = (int)((227u * 1024u) / (dyn_smem + fa.sharedSizeBytes + 1024u));
+  return std::max(1, std::min({cap, by_regs, by_smem}));
 }
 
 template <int C, int O, int MT, int WM, bool DGRAD, bool MASK_IN, bool MASK_OUT>
@@ -1207,31 +1334,35 @@ cudaError_t launch_wgrad(const float* Aprev, const float* gA, const float* A, fl
   return cudaGetLastError();
 }
 
-// One persistent pass of a head convolution: as many CTAs as fit on the GPU (shared memory, four
-// warps each), at most one per M-tile.
+// One persistent pass of a head convolution: as many CTAs as the shared memory and the registers
+// of an SM hold (at most 6; their tensor memory, 64 columns each, stays within the 512 of an SM), at most one
+// per M-tile.
 template <int C, int EPI>
 cudaError_t launch_tc_conv(const TcArgs& a, int sms, cudaStream_t s, int* grid_out = nullptr) {
   using S = TcShape<C>;
   auto k = tc_conv_kernel<C, EPI>;
   cudaError_t e = set_smem(k, S::Smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTcThreads, S::Smem);
-  if (e != cudaSuccess) return e;
-  const int grid = std::max(1, std::min({a.tiles, std::max(1, per_sm) * sms, kMaxHeadBlocks}));
+  const int per_sm = resident_per_sm(k, kTcThreads, S::Smem, 6);
+  const int grid = std::max(1, std::min({a.tiles, per_sm * sms, kMaxHeadBlocks}));
   if (grid_out) *grid_out = grid;
   note_launches(1);
   k<<<grid, kTcThreads, S::Smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int ZC, int NO>
+template <int ZC, int NO, int ROWS>
 cudaError_t launch_head_wgrad(const float* X, const float* Z, int H, int W, float scale, float* dW, int sms,
                               cudaStream_t s) {
-  const int tiles_x = (W + kWgCols - 1) / kWgCols, tiles = tiles_x * ((H + kWgRows - 1) / kWgRows);
-  const int grid = std::max(1, std::min(tiles, 6 * sms));
+  using S = WgShape<(NO + 3) / 4, ROWS>;
+  auto k = head_wgrad_kernel<ZC, NO, ROWS>;
+  cudaError_t e = set_smem(k, S::Smem);
+  if (e != cudaSuccess) return e;
+  const int tiles_x = (W + kWgCols - 1) / kWgCols, tiles = tiles_x * ((H + ROWS - 1) / ROWS);
+  const int grid = std::max(1, std::min(tiles, resident_per_sm(k, kWgThreads, S::Smem, 8) * sms));
   note_launches(1);
-  head_wgrad_kernel<ZC, NO><<<grid, kWgThreads, 0, s>>>(X, Z, H, W, tiles_x, tiles, scale, dW);
+  k<<<grid, kWgThreads, S::Smem, s>>>(X, Z, H, W, tiles_x, tiles, scale, dW);
   return cudaGetLastError();
 }
 
@@ -1331,8 +1462,10 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
   unsigned* status = reinterpret_cast<unsigned*>(ws + L.status);
   ok(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
   const int h4 = ph << 4, w4 = pw << 4;
-  note_launches(1);
-  upsample_kernel<<<(int)(((size_t)W * H * 4 + 255) / 256), 256, 0, s>>>(A[4], h4, w4, H, W, U);
+  int2* taps = reinterpret_cast<int2*>(ws + L.taps);
+  note_launches(2);
+  tap_table_kernel<<<(H + W + 255) / 256, 256, 0, s>>>(h4, w4, H, W, taps);
+  upsample_kernel<<<(int)(((size_t)W * H * 4 + 255) / 256), 256, 0, s>>>(A[4], h4, w4, H, W, taps, U);
   const double inv = 1.0 / (3.0 * (double)((size_t)W * H));
   TcArgs ta{};
   ta.H = H;
@@ -1382,8 +1515,8 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
     a6.adjoint = true;
     ok(launch_tc_conv<8, kEpiMask>(a6, sms, s));
     ok(link(E, s, sd[1]));
-    ok(launch_head_wgrad<16, 16>(U, F(L.gZ), H, W, ta.cscale, gp + w_off(5), sms, sd[1]));
-    ok(launch_head_wgrad<8, 3>(Hh, F(L.gM), H, W, ta.cscale, gp + w_off(6), sms, sd[1]));
+    ok(launch_head_wgrad<16, 16, 4>(U, F(L.gZ), H, W, ta.cscale, gp + w_off(5), sms, sd[1]));
+    ok(launch_head_wgrad<8, 3, 8>(Hh, F(L.gM), H, W, ta.cscale, gp + w_off(6), sms, sd[1]));
     TcArgs a5 = ta;
     a5.in = F(L.gZ);
     a5.w = params + w_off(5);
@@ -1394,9 +1527,9 @@ extern "C" vg_status vg_appearance_loss(const float* img, const float* target, i
     note_launches(2);
     const size_t n1 = (size_t)H * w4 * 4, n2 = (size_t)w4 * h4 * 4;
     upsample_adjoint_kernel<false><<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(
-        F(L.gU), H, W, w4, (size_t)W * 16, 16, (size_t)w4 * 16, 16, 1.f, F(L.gX));
+        F(L.gU), H, W, w4, (size_t)W * 16, 16, (size_t)w4 * 16, 16, taps + H, 1.f, F(L.gX));
     upsample_adjoint_kernel<true><<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(
-        F(L.gX), w4, H, h4, 16, (size_t)w4 * 16, 16, (size_t)w4 * 16, ta.cscale, gA[4]);
+        F(L.gX), w4, H, h4, 16, (size_t)w4 * 16, 16, (size_t)w4 * 16, taps, ta.cscale, gA[4]);
     ok(cudaGetLastError());
   }
   // dL/dI_r's SSIM and L1 terms (the block-mean term is added at the end)
