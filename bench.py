@@ -45,14 +45,14 @@ OPS_EVAL, OPS_BLEND_FWD, OPS_BLEND_BWD = 11, 7, 37
 TRAFFIC_SOURCES = ("paper_2402_17427_gb300/csrc/blend.cu", "paper_2402_17427_gb300/csrc/vg_common.cuh",
                    "paper_2402_17427_gb300/csrc/internal.h")
 PROFILED_TRAFFIC = {
-    "sources_sha256": "8e64db79c7c93cf315b96deb786bad9147f4e6a8ec644f0762fb8dafdb827f4c",
-    "blend": 18659584 + 1308160,
-    "blend_backward": 67466240 + 1256960,
+    "sources_sha256": "86d9390a7898dc691a3cd9957edbb6c9ffe8fb227439085229039c4fabf2df84",
+    "blend": 18658304 + 1180672,
+    "blend_backward": 67462400 + 1327104,
 }
 # Warp instructions issued per launch (smsp__inst_executed.sum) of the compositing kernels on this
 # workload, from the same captures; held to the same source hash.
 PROFILED_INSTRUCTIONS = {
-    "sources_sha256": "8e64db79c7c93cf315b96deb786bad9147f4e6a8ec644f0762fb8dafdb827f4c",
+    "sources_sha256": "86d9390a7898dc691a3cd9957edbb6c9ffe8fb227439085229039c4fabf2df84",
     "blend": 257451654,
     "blend_backward": 406137345,
 }

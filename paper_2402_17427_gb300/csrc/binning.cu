@@ -55,7 +55,8 @@ __device__ __forceinline__ void zero_status(unsigned long long* status, unsigned
 // atomic counter, so every partition a block waits on has already been taken by a running block.
 // A partition holds 256 * ITEMS keys; warp w owns keys [w*32*ITEMS, (w+1)*32*ITEMS) in
 // warp-striped order (item k of lane l is key w*32*ITEMS + k*32 + l), so ranks taken item by
-// item with match.any follow the input order.
+// item follow the input order.  The lanes holding the same digit are found by one ballot per
+// digit bit (measured faster here than match.any: sort stage 187 vs 196 us at 1080p).
 // The keys are reordered by digit in shared memory and written out in runs, so the global
 // stores of a digit are contiguous.
 template <int ITEMS>
