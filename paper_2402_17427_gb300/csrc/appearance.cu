@@ -1158,6 +1158,28 @@ __global__ void __launch_bounds__(kWgThreads, NO > 4 ? 3 : 2) head_wgrad_kernel(
     __syncthreads();                                 // the buffer is free for the copies two tiles on
   }
   cp_async_wait<0>();
+  if constexpr (WIDE) {
+    // the phases of one group add their sums in shared memory (the staging buffers are free), so
+    // that one thread a group makes the atomic additions
+    static_assert((size_t)kWgThreads * 32 * 4 <= S::Smem, "the reduction fits the staging buffers");
+    float2* red = reinterpret_cast<float2*>(wg_smem);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) red[(i * NJ + j) * kWgThreads + threadIdx.x] = acc[i][j];
+    __syncthreads();
+    if (phase != 0) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j)
+        for (int q = 1; q < PHASES; ++q) {
+          const float2 v = red[(i * NJ + j) * kWgThreads + threadIdx.x + q * GROUPS];
+          acc[i][j].x += v.x;
+          acc[i][j].y += v.y;
+        }
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int o = 4 * og + i;
