@@ -32,7 +32,7 @@ constexpr float kNegTwoLn2 = -1.3862943611198906f;   // true conic = scaled coni
 template <int TS, bool BWD>
 struct TileShape {
   static constexpr int kPix = TS * TS;
-  static constexpr int kPPT = TS == 8 ? (BWD ? 2 : 1) : TS == 16 ? (BWD ? 8 : 2) : (BWD ? 8 : 4);
+  static constexpr int kPPT = TS == 8 ? (BWD ? 2 : 1) : TS == 16 ? (BWD ? 4 : 2) : (BWD ? 8 : 4);
   static constexpr int kThreads = kPix / kPPT;
   static constexpr int kClass = TS == 8 ? 0 : (TS == 16 ? 1 : 2);
   static constexpr int kWarpRows = 32 * kPPT / TS;      // a warp covers TS columns x kWarpRows rows
