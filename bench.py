@@ -125,6 +125,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for the CPU baseline")
+    ap.add_argument("--cpu-single-thread", action="store_true",
+                    help="also time the CPU baseline on one host thread (adds about a minute)")
     ap.add_argument("--no-patterns", action="store_true", help="skip the batched-cells and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--only-pattern", choices=["appearance", "evaluation", "optimiser", "partition", "memory_scale",
@@ -212,15 +214,16 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------------ CPU oracle
 
-def oracle_step_time(g, cam, target, budget_s: float, seed: int = 0):
-    """Seconds one full step takes on the FP64 oracle, from a bounded sample.
+def oracle_step_time(g, cam, target, budget_s: float, seed: int = 0, threads: int | None = None):
+    """Seconds one full step takes on the FP64 oracle, from a bounded sample (on all host cores
+    unless `threads` is given).
 
     The projection, pair generation and sort of all N Gaussians run in full (an empty tile mask);
     compositing + adjoint run on a random sample of tiles and are scaled by total/sampled tiles;
     the loss runs on a 270x480 crop and is scaled by the pixel ratio.
     """
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     opts = oracle.Options(n_threads=threads)
     sc = oracle.Scene64.of(g)
     tiles_x, tiles_y = (cam.width + 15) // 16, (cam.height + 15) // 16
@@ -265,7 +268,7 @@ def oracle_sampled_step(g, cam, target, frac: float, seed: int):
     and adjoint of a random `frac` of the tiles, the loss on a 480x270 crop.  Returns (seconds this
     took, the full-step seconds it stands for, threads, sample description)."""
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     opts = oracle.Options(n_threads=threads)
     sc = oracle.Scene64.of(g)
     tiles_x, tiles_y = (cam.width + 15) // 16, (cam.height + 15) // 16
@@ -650,11 +653,11 @@ def main():
     ras = R.Rasterizer(R.RasterSettings(), device=dev, check="sync")
     lossf = R.LossL1DSSIM(0.2)
 
-    def step(evf=None, evb=None, prm=None, tgt=None):
+    def step(evf=None, evb=None, prm=None, tgt=None, lf=None):
         prm = params if prm is None else prm
         tgt = target_t if tgt is None else tgt
         rgb, T, last = ras.forward(*prm, g.sh_degree, cam, events=evf)
-        L, dL = lossf(rgb, tgt, reuse=True)
+        L, dL = (lf or lossf)(rgb, tgt, reuse=True)
         grads = ras.backward(*prm, g.sh_degree, cam, T, last, dL, grads=step.grads, events=evb)
         return L, T, last
 
@@ -702,12 +705,15 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     launches0 = B.vg_kernel_launches()
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(K)]   # each step's start, for the spread
     start.record()
     for k in range(K):
+        marks[k].record()
         step(stage_ev[k][0], stage_ev[k][0])
     end.record()
     torch.cuda.synchronize()
     launches = B.vg_kernel_launches() - launches0
+    per_step = [marks[k].elapsed_time(marks[k + 1] if k + 1 < K else end) for k in range(K)]
     clk = clocks.stop()
     if pg:
         pg.barrier()
@@ -728,9 +734,11 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in host) + host_target.numel() * 4
         dsets = [params, [torch.empty_like(t) for t in params]]
         dtg = [target_t, torch.empty_like(target_t)]
-        comp, cs = torch.cuda.current_stream(), torch.cuda.Stream()
+        comp, cs, ds = torch.cuda.current_stream(), torch.cuda.Stream(), torch.cuda.Stream()
         ready = [torch.cuda.Event(), torch.cuda.Event()]
         free = [torch.cuda.Event(), torch.cuda.Event()]
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        lossfs = [R.LossL1DSSIM(0.2), R.LossL1DSSIM(0.2)]   # step k writes its loss into set k % 2
 
         def upload(b):
             with torch.cuda.stream(cs):
@@ -743,15 +751,23 @@ def main():
         def run(n, out):
             free[0].record(comp)
             free[1].record(comp)
+            copied[0].record(comp)
+            copied[1].record(comp)
             upload(0)
             for i in range(n):
                 b = i & 1
                 if i + 1 < n:
                     upload(1 - b)
                 comp.wait_event(ready[b])
-                L = step(prm=dsets[b], tgt=dtg[b])[0]
+                comp.wait_event(copied[b])    # step i - 2's loss, in the same set, has reached the host
+                L = step(prm=dsets[b], tgt=dtg[b], lf=lossfs[b])[0]
                 free[b].record(comp)
-                out[i].copy_(L.view(-1)[:1], non_blocking=True)   # the step's loss, device to host
+                # the step's loss, device to host, on a third stream so that the next step's kernels
+                # do not queue behind the copy
+                with torch.cuda.stream(ds):
+                    ds.wait_event(free[b])
+                    out[i].copy_(L.view(-1)[:1], non_blocking=True)
+                    copied[b].record(ds)
 
         ke = max(3, K // 2)
         losses = torch.empty((ke, 1), dtype=torch.float32).pin_memory()
@@ -760,6 +776,7 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         run(ke, losses)
+        comp.wait_stream(ds)       # the timed region ends after the last loss has reached the host
         e1.record()
         torch.cuda.synchronize()
         assert bool(torch.isfinite(losses).all())       # every step's loss, read on the host
@@ -807,6 +824,9 @@ def main():
         try:
             t, threads, sample = oracle_step_time(g, cam, target, args.cpu_budget)
             cpu = {"value": 1.0 / t, "unit": "steps/s", "cores": threads, "kind": "oracle", "sample": sample}
+            if args.cpu_single_thread:
+                t1, _, sample1 = oracle_step_time(g, cam, target, args.cpu_budget, seed=1, threads=1)
+                cpu["single_thread"] = {"value": 1.0 / t1, "unit": "steps/s", "cores": 1, "sample": sample1}
         except Exception as e:  # the oracle is test infrastructure; report, never fail the GPU number
             cpu = {"value": None, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {e}"}
@@ -823,6 +843,8 @@ def main():
     line = {
         "metric": METRIC, "value": job_rate(ws, ms), "unit": "steps/s", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "step_ms": {"median": float(np.median(per_step)), "p90": float(np.percentile(per_step, 90)),
+                    "min": float(np.min(per_step)), "max": float(np.max(per_step))},
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": N, "width": cam.width, "height": cam.height,
                    "sh_degree": g.sh_degree, "tile": 16, "visible": V, "pairs": P,
