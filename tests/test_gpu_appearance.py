@@ -92,10 +92,12 @@ def _compare(W, H, seed, lam=0.2):
     return g
 
 
-@pytest.mark.parametrize("W,H,seed", [(100, 70, 0), (330, 200, 1), (64, 32, 2)])
+@pytest.mark.parametrize("W,H,seed", [(100, 70, 0), (330, 200, 1), (64, 32, 2), (47, 33, 6), (257, 129, 7)])
 def test_appearance_matches_oracle(W, H, seed):
-    # (100, 70): 3 x 2 pooled cells, 6 rows and 4 columns outside them, ragged 16 x 16 head tiles;
-    # (330, 200): 10 x 6 cells, 21 x 13 head tiles; (64, 32): the smallest shapes (1 x 2 cells)
+    # (100, 70): 3 x 2 pooled cells, 6 rows and 4 columns outside them, ragged head M-tiles
+    # (16 x 8 pixels); (330, 200): 10 x 6 cells; (64, 32): the smallest shapes (1 x 2 cells);
+    # (47, 33): one cell, up-sampling 16 -> 33 rows and 16 -> 47 columns (factors 2.06 and 2.94),
+    # partial M-tiles on both edges; (257, 129): odd sizes, a last M-tile column of one pixel
     _compare(W, H, seed)
 
 
