@@ -75,3 +75,47 @@ def test_threads_on_own_streams_match_serial_runs():
         for a, b in zip(out[2:], ref[j][2:]):
             tol = 1e-5 * float(b.abs().max()) + 1e-30
             assert float((a - b).abs().max()) <= tol, (k, it, j)
+
+
+def test_appearance_calls_on_concurrent_streams_match_serial_runs():
+    """Two host threads evaluate the appearance loss (Eq. 3) with every gradient on streams of their
+    own at once: their tensor-core passes allocate tensor memory side by side on the same SMs.  The
+    loss and the map must equal the serial runs bit for bit, the gradients to FP32 rounding."""
+    from paper_2402_17427_gb300 import appearance as AP
+    rng = np.random.default_rng(11)
+    cases = []
+    for k, (W, H) in enumerate([(640, 360), (512, 384)]):
+        img = torch.from_numpy(rng.random((3, H, W), dtype=np.float32)).cuda()
+        tgt = torch.from_numpy(rng.random((3, H, W), dtype=np.float32)).cuda()
+        cases.append((img, tgt))
+    models = [AP.AppearanceModel(2, seed=3), AP.AppearanceModel(2, seed=3)]
+    ref = []
+    for (img, tgt), m in zip(cases, models):
+        out = m.loss(img, tgt, 1, 0.2, want_map=True)
+        torch.cuda.synchronize()
+        ref.append({k: v.clone() for k, v in out.items()})
+    errors, results = [], {}
+
+    def worker(k):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for it in range(5):
+                    out = models[k].loss(cases[k][0], cases[k][1], 1, 0.2, want_map=True)
+                    s.synchronize()
+                    results[(k, it)] = {n: v.clone() for n, v in out.items()}
+        except Exception as e:      # reported to the main thread
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert len(results) == 10
+    for (k, it), out in results.items():
+        assert torch.equal(out["loss"], ref[k]["loss"]) and torch.equal(out["map"], ref[k]["map"]), (k, it)
+        for n in ("grad_img", "grad_embedding", "grad_params"):
+            tol = 1e-5 * float(ref[k][n].abs().max()) + 1e-30
+            assert float((out[n] - ref[k][n]).abs().max()) <= tol, (k, it, n)
