@@ -66,15 +66,19 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     const unsigned* __restrict__ hist, unsigned* next_part, unsigned long long* status_cur,
     unsigned long long* __restrict__ status_next, WsHeader* hdr) {
   constexpr int TILE = kSortThreads * ITEMS;
-  if (render_dead(hdr)) return;   // an earlier look-back gave up: nothing later is sorted
+  // the prologue's loads are issued together, then tested
+  const bool dead = render_dead(hdr);   // an earlier look-back gave up: nothing later is sorted
+  const unsigned n_all = *n_ptr;
+  const unsigned lo = depth ? hdr->dmin : 0u, hi = depth ? hdr->dmax : 0u;
+  const unsigned hist_d = hist[threadIdx.x];
+  if (dead) return;
   if (depth) {
     // the depth keys agree above bit 32 - clz(dmin ^ dmax): only the passes below it run
-    const unsigned lo = hdr->dmin, hi = hdr->dmax;
-    const unsigned bits = (*n_ptr > 1 && hi > lo) ? 32u - __clz(lo ^ hi) : 0u;
+    const unsigned bits = (n_all > 1 && hi > lo) ? 32u - __clz(lo ^ hi) : 0u;
     if (shift == 0 && blockIdx.x == 0 && threadIdx.x == 0) hdr->depth_bits = bits;   // for depth_order()
     if ((unsigned)shift >= bits) return;
   }
-  const unsigned n = min(*n_ptr, cap);
+  const unsigned n = min(n_all, cap);
   const unsigned nparts = (n + TILE - 1) / TILE;
   constexpr int WARPS = kSortThreads / 32;
   __shared__ unsigned s_gstart[kRadix];          // first output slot of each digit (whole pass)
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d = threadIdx.x;
   {
     unsigned tot;
-    s_gstart[d] = block_exclusive_scan(hist[d], &tot, sm);
+    s_gstart[d] = block_exclusive_scan(hist_d, &tot, sm);
   }
   const uint32_t lt = lanemask_lt();
   for (;;) {
@@ -204,10 +208,13 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
 __global__ void __launch_bounds__(256) pairs_count(const uint32_t* order0, const uint32_t* order1,
                                                    const uint32_t* __restrict__ touched, const WsHeader* __restrict__ hdr,
                                                    unsigned long long* __restrict__ blocksums) {
-  if (render_dead(hdr)) return;   // pairs_scan then records no pairs
+  // the prologue's loads are issued together, then tested
+  const bool dead = render_dead(hdr);   // pairs_scan then records no pairs
+  const unsigned nvis = hdr->visible;
   const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
+  if (dead) return;
   unsigned begin, end;
-  segment(hdr->visible, begin, end, 256);
+  segment(nvis, begin, end, 256);
   unsigned long long c = 0;
   for (unsigned s = begin + threadIdx.x; s < end; s += blockDim.x) c += touched[order[s]];
 #pragma unroll
@@ -258,17 +265,19 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
                                                   unsigned long long cap, uint32_t* __restrict__ pkeys,
                                                   uint32_t* __restrict__ pvals, Splat* __restrict__ splats,
                                                   Splat* __restrict__ vsplats, unsigned long long* __restrict__ status0) {
-  if (hdr->pair_n == 0) return;   // no pairs, or more than the capacity (nothing is sorted)
+  // the prologue's loads are issued together, then tested
+  const unsigned pair_n = hdr->pair_n, nvis = hdr->visible;
+  const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
+  if (pair_n == 0) return;   // no pairs, or more than the capacity (nothing is sorted)
   // with the tile counts known in advance (tile_prep), this kernel clears the first tile-sort
   // pass's look-back rows
-  if (status0) zero_status(status0, (hdr->pair_n + kTileTile - 1) / kTileTile);
-  const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
+  if (status0) zero_status(status0, (pair_n + kTileTile - 1) / kTileTile);
   __shared__ unsigned long long sm[8];
   __shared__ unsigned s_off[257];
   __shared__ uint32_t s_rank[256];
   __shared__ int s_base[256], s_tilesx[256], s_tx0[256], s_ty0[256], s_w[256];
   unsigned begin, end;
-  segment(hdr->visible, begin, end, 256);
+  segment(nvis, begin, end, 256);
   unsigned long long run = blocksums[blockIdx.x];
   for (unsigned t0 = begin; t0 < end; t0 += 256) {
     const unsigned s = t0 + threadIdx.x;
@@ -428,8 +437,9 @@ __global__ void __launch_bounds__(256) tile_count(const DevTables* __restrict__ 
                                                   const uint32_t* __restrict__ touched, const uint2* __restrict__ rects,
                                                   const WsHeader* __restrict__ hdr, unsigned* __restrict__ tdiff,
                                                   int tiles) {
-  if (render_dead(hdr)) return;   // every count stays 0: every tile list is empty
+  const bool dead = render_dead(hdr);   // every count stays 0: every tile list is empty
   const unsigned nv = hdr->visible;
+  if (dead) return;
   tdiff += (size_t)(blockIdx.x % kCountCopies) * tiles;
   const uint32_t lt = lanemask_lt();
   const unsigned stride = gridDim.x * blockDim.x;

@@ -205,9 +205,11 @@ struct Compact {
   unsigned long long wait_ns;      // limit of each look-back wait
 };
 // Every kernel after the first look-back of a render checks this once: after a wait gave up the
-// compacted and sorted arrays may hold unwritten slots, so no stage may index with them.
+// compacted and sorted arrays may hold unwritten slots, so no stage may index with them.  The flag
+// is set by an earlier kernel of the stream, so a plain load sees it (kernels of one stream see
+// each other's writes); the L1 cache then merges the loads of a block's warps.
 __device__ __forceinline__ bool render_dead(const WsHeader* hdr) {
-  return (*(volatile const unsigned*)&hdr->status & VG_STATUS_WAIT_TIMEOUT) != 0u;
+  return (hdr->status & VG_STATUS_WAIT_TIMEOUT) != 0u;
 }
 cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Splat* splats, uint2* rects,
                               uint32_t* touched, const Compact& cp, WsHeader* hdr, cudaStream_t s);

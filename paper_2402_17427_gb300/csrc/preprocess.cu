@@ -641,8 +641,9 @@ template <int DEG>
 __global__ void __launch_bounds__(128, 4) preprocess_backward_kernel(
     const DevTables* __restrict__ tab, const uint32_t* __restrict__ vis_ids, const WsHeader* __restrict__ hdr,
     const Splat* __restrict__ splats, const float* __restrict__ g2d, int accumulate) {
-  if (render_dead(hdr)) return;   // the compacted list may hold unwritten slots
+  const bool dead = render_dead(hdr);   // the compacted list may hold unwritten slots
   const int nv = (int)hdr->visible;
+  if (dead) return;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += gridDim.x * blockDim.x)
     project_adjoint<DEG>(tab, splats, g2d, accumulate, (int)vis_ids[t]);
 }
