@@ -16,6 +16,7 @@ namespace vg {
 namespace {
 
 __global__ void __launch_bounds__(256) init_header(WsHeader* hdr, SortCtl* ctl) {
+  pdl_enter();
   unsigned* c = reinterpret_cast<unsigned*>(ctl);
   for (unsigned i = threadIdx.x; i < sizeof(SortCtl) / sizeof(unsigned); i += blockDim.x) c[i] = 0;
   if (threadIdx.x != 0) return;
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(256) init_header(WsHeader* hdr, SortCtl* ctl) 
 }
 
 __global__ void publish_counters(const WsHeader* hdr, int64_t* c) {
+  pdl_enter();
   c[VG_CNT_PAIRS] = (int64_t)hdr->pairs;
   c[VG_CNT_VISIBLE] = (int64_t)hdr->visible;
   c[VG_CNT_STATUS] = (int64_t)hdr->status;
@@ -278,7 +280,7 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
   const vg_stage_events* ev = opts0->events;
   if (cudaMemcpyAsync(ws + L.tables, c.table.data(), c.table.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return VG_ERR_CUDA;
-  init_header<<<1, 256, 0, s>>>(hdr, reinterpret_cast<SortCtl*>(ws + L.sortctl));
+  launch_pdl(init_header, 1, 256, 0, s, hdr, reinterpret_cast<SortCtl*>(ws + L.sortctl));
   note_launches(2);   // init_header + publish_counters
   stage_event(ev, VG_STAGE_PROJECT, true, s);
   cudaError_t e = launch_preprocess(tab, c.total_n, c.degree, reinterpret_cast<Splat*>(ws + L.splats),
@@ -294,7 +296,7 @@ vg_status run_forward(Call& c, const vg_raster_opts* opts0, void* workspace, siz
   e = launch_blend_forward(tab, c.plan, L, ws, (opts0->flags & VG_FLAG_COUNT_BLENDS) != 0, s);
   if (e != cudaSuccess) return VG_ERR_CUDA;
   stage_event(ev, VG_STAGE_BLEND, false, s);
-  publish_counters<<<1, 1, 0, s>>>(hdr, counters);
+  launch_pdl(publish_counters, 1, 1, 0, s, hdr, counters);
   return cuda_status(cudaGetLastError());
 }
 
@@ -677,7 +679,7 @@ extern "C" vg_status vg_read_counters(const void* workspace, size_t workspace_by
                                       vg_stream stream) {
   if (!workspace || !counters || !aligned(workspace, 256) || workspace_bytes < 256) return VG_ERR_INVALID;
   note_launches(1);
-  publish_counters<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(static_cast<const WsHeader*>(workspace),
+  launch_pdl(publish_counters, 1, 1, 0, reinterpret_cast<cudaStream_t>(stream), static_cast<const WsHeader*>(workspace),
                                                                         counters);
   return cuda_status(cudaGetLastError());
 }

@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     uint32_t* __restrict__ vout, const unsigned* n_ptr, unsigned cap, bool depth, int shift,
     const unsigned* __restrict__ hist, unsigned* next_part, unsigned long long* status_cur,
     unsigned long long* __restrict__ status_next, WsHeader* hdr) {
+  pdl_enter();
   constexpr int TILE = kSortThreads * ITEMS;
   // the prologue's loads are issued together, then tested
   const bool dead = render_dead(hdr);   // an earlier look-back gave up: nothing later is sorted
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
 __global__ void __launch_bounds__(256) pairs_count(const uint32_t* order0, const uint32_t* order1,
                                                    const uint32_t* __restrict__ touched, const WsHeader* __restrict__ hdr,
                                                    unsigned long long* __restrict__ blocksums) {
+  pdl_enter();
   // the prologue's loads are issued together, then tested
   const bool dead = render_dead(hdr);   // pairs_scan then records no pairs
   const unsigned nvis = hdr->visible;
@@ -231,6 +233,7 @@ __global__ void __launch_bounds__(256) pairs_count(const uint32_t* order0, const
 
 __global__ void __launch_bounds__(256) pairs_scan(unsigned long long* __restrict__ blocksums, int B, WsHeader* hdr,
                                                   unsigned long long cap) {
+  pdl_enter();
   if (render_dead(hdr)) {          // the depth order may hold unwritten slots: emit nothing
     if (threadIdx.x == 0) { hdr->pairs = 0; hdr->pair_n = 0; }
     return;
@@ -265,6 +268,7 @@ __global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ 
                                                   unsigned long long cap, uint32_t* __restrict__ pkeys,
                                                   uint32_t* __restrict__ pvals, Splat* __restrict__ splats,
                                                   Splat* __restrict__ vsplats, unsigned long long* __restrict__ status0) {
+  pdl_enter();
   // the prologue's loads are issued together, then tested
   const unsigned pair_n = hdr->pair_n, nvis = hdr->visible;
   const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
@@ -332,6 +336,7 @@ __global__ void __launch_bounds__(256) tile_histogram(const uint32_t* __restrict
                                                       const WsHeader* __restrict__ hdr, int tpasses,
                                                       unsigned* __restrict__ hist,
                                                       unsigned long long* __restrict__ status0) {
+  pdl_enter();
   __shared__ unsigned h[kMaxPasses][kRadix];
 #pragma unroll
   for (int p = 0; p < kMaxPasses; ++p) h[p][threadIdx.x] = 0;
@@ -378,6 +383,7 @@ __global__ void __launch_bounds__(256) tile_histogram(const uint32_t* __restrict
 
 __global__ void __launch_bounds__(256) tile_ranges(const uint32_t* __restrict__ keys, const WsHeader* __restrict__ hdr,
                                                    unsigned tiles, uint2* __restrict__ ranges) {
+  pdl_enter();
   const unsigned n = hdr->pair_n;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t t = keys[i];
@@ -402,11 +408,13 @@ __device__ __forceinline__ int tile_bucket(const DevTables* tab, const uint2* ra
 
 __global__ void __launch_bounds__(256) order_count(const DevTables* __restrict__ tab, const uint2* __restrict__ ranges,
                                                    int tiles, unsigned* __restrict__ buckets) {
+  pdl_enter();
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x)
     atomicAdd(&buckets[tile_bucket(tab, ranges, t)], 1u);
 }
 
 __global__ void order_scan(unsigned* __restrict__ buckets) {
+  pdl_enter();
   if (threadIdx.x == 0) {
     unsigned run = 0;
     for (int k = 0; k < kBuckets; ++k) {
@@ -420,6 +428,7 @@ __global__ void order_scan(unsigned* __restrict__ buckets) {
 __global__ void __launch_bounds__(256) order_scatter(const DevTables* __restrict__ tab, const uint2* __restrict__ ranges,
                                                      int tiles, unsigned* __restrict__ buckets,
                                                      uint32_t* __restrict__ order) {
+  pdl_enter();
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
     const unsigned pos = atomicAdd(&buckets[kBuckets + tile_bucket(tab, ranges, t)], 1u);
     order[pos] = (uint32_t)t;
@@ -437,6 +446,7 @@ __global__ void __launch_bounds__(256) tile_count(const DevTables* __restrict__ 
                                                   const uint32_t* __restrict__ touched, const uint2* __restrict__ rects,
                                                   const WsHeader* __restrict__ hdr, unsigned* __restrict__ tdiff,
                                                   int tiles) {
+  pdl_enter();
   const bool dead = render_dead(hdr);   // every count stays 0: every tile list is empty
   const unsigned nv = hdr->visible;
   if (dead) return;
@@ -484,6 +494,7 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
                                                           int tpasses, const unsigned* __restrict__ tdiff,
                                                           uint2* __restrict__ ranges, unsigned* __restrict__ hist,
                                                           uint32_t* __restrict__ order) {
+  pdl_enter();
   extern __shared__ unsigned s_c[];      // [tiles] counts, then [tiles] exclusive offsets
   unsigned* s_x = s_c + tiles;
   __shared__ unsigned s_h[kMaxPasses][kRadix];
@@ -746,27 +757,34 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   //    depth_order() names
   for (int pass = 0; pass < kMaxPasses; ++pass) {
     const int src = pass & 1, dst = src ^ 1;
-    onesweep_pass<kDepthItems><<<OBD, kSortThreads, 0, s>>>(U(L.vkeys[src]), U(L.vvals[src]), U(L.vkeys[dst]), U(L.vvals[dst]),
+    launch_pdl(onesweep_pass<kDepthItems>, OBD, kSortThreads, 0, s, U(L.vkeys[src]), U(L.vvals[src]), U(L.vkeys[dst]), U(L.vvals[dst]),
                                               &hdr->visible, 0xFFFFFFFFu, true, pass * kRadixBits,
                                               ctl->hist[0][pass], &ctl->next_part[0][pass], S64(src), S64(dst), hdr);
   }
   // 2. pairs in depth order, written where the tile sort's passes leave the result in buffer 0
   const int p0 = tpasses & 1;
   const int BP = kMaxSortBlocks < 6 * B / 2 ? kMaxSortBlocks : 6 * B / 2;   // 6 blocks per SM
-  pairs_count<<<BP, 256, 0, s>>>(U(L.vvals[0]), U(L.vvals[1]), U(L.touched), hdr, bsum64);
-  pairs_scan<<<1, 256, 0, s>>>(bsum64, BP, hdr, (unsigned long long)cap);
-  pairs_emit<<<BP, 256, 0, s>>>(tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), rects, hdr, bsum64,
+  launch_pdl(pairs_count, BP, 256, 0, s, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), hdr, bsum64);
+  launch_pdl(pairs_scan, 1, 256, 0, s, bsum64, BP, hdr, (unsigned long long)cap);
+  launch_pdl(pairs_emit, BP, 256, 0, s, tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), rects, hdr, bsum64,
                                (unsigned long long)cap, U(L.pkeys[p0]), U(L.pvals[p0]), splats, vsplats,
                                prep ? S64(0) : nullptr);
-  if (!prep) tile_histogram<<<B * 2, 256, 0, s>>>(U(L.pkeys[p0]), hdr, tpasses, ctl->hist[1][0], S64(0));
+  if (!prep) launch_pdl(tile_histogram, B * 2, 256, 0, s, U(L.pkeys[p0]), hdr, tpasses, ctl->hist[1][0], S64(0));
   if (join) cudaStreamWaitEvent(s, join, 0);   // ranges, histograms and order ready
-  // 3. stable sort of the pairs by tile id
+  // 3. stable sort of the pairs by tile id (the first pass after the join with the side stream is
+  //    launched plainly: programmatic serialization relaxes only the edge to the previous kernel)
   for (int pass = 0; pass < tpasses; ++pass) {
     const int src = (p0 + pass) & 1, dst = src ^ 1;
-    onesweep_pass<kTileItems><<<OBT, kSortThreads, 0, s>>>(U(L.pkeys[src]), U(L.pvals[src]), U(L.pkeys[dst]), U(L.pvals[dst]),
-                                              &hdr->pair_n, cap, false, pass * kRadixBits, ctl->hist[1][pass],
-                                              &ctl->next_part[1][pass], S64(pass & 1),
-                                              pass + 1 < tpasses ? S64((pass + 1) & 1) : nullptr, hdr);
+    auto k = onesweep_pass<kTileItems>;
+    unsigned long long* nxt = pass + 1 < tpasses ? S64((pass + 1) & 1) : nullptr;
+    if (pass == 0 && join)
+      k<<<OBT, kSortThreads, 0, s>>>(U(L.pkeys[src]), U(L.pvals[src]), U(L.pkeys[dst]), U(L.pvals[dst]), &hdr->pair_n, cap,
+                                     false, pass * kRadixBits, ctl->hist[1][pass], &ctl->next_part[1][pass],
+                                     S64(pass & 1), nxt, hdr);
+    else
+      launch_pdl(k, OBT, kSortThreads, 0, s, U(L.pkeys[src]), U(L.pvals[src]), U(L.pkeys[dst]), U(L.pvals[dst]),
+                 &hdr->pair_n, cap, false, pass * kRadixBits, ctl->hist[1][pass], &ctl->next_part[1][pass],
+                 S64(pass & 1), nxt, hdr);
   }
   if (prep) {
     note_launches(kMaxPasses + 3 + tpasses + 2);
@@ -774,15 +792,15 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   }
   note_launches(kMaxPasses + 4 + tpasses + 1);
   cudaMemsetAsync(ranges, 0, (size_t)tiles * sizeof(uint2), s);
-  tile_ranges<<<B * 4, 256, 0, s>>>(U(L.pkeys[0]), hdr, (unsigned)tiles, ranges);
+  launch_pdl(tile_ranges, B * 4, 256, 0, s, U(L.pkeys[0]), hdr, (unsigned)tiles, ranges);
   // 4. largest-first tile order
   {
     unsigned* buckets = U(L.buckets);
     cudaMemsetAsync(buckets, 0, kBuckets * sizeof(unsigned), s);
     const int tgrid = (tiles + 255) / 256;
-    order_count<<<tgrid, 256, 0, s>>>(tab, ranges, tiles, buckets);
-    order_scan<<<1, 32, 0, s>>>(buckets);
-    order_scatter<<<tgrid, 256, 0, s>>>(tab, ranges, tiles, buckets, U(L.order));
+    launch_pdl(order_count, tgrid, 256, 0, s, tab, ranges, tiles, buckets);
+    launch_pdl(order_scan, 1, 32, 0, s, buckets);
+    launch_pdl(order_scatter, tgrid, 256, 0, s, tab, ranges, tiles, buckets, U(L.order));
     note_launches(3);
   }
   return cudaGetLastError();

@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(TileShape<TS, false>::kThreads)
 blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ vsplats,
                      const uint32_t* __restrict__ lists, const uint2* __restrict__ ranges,
                      const uint32_t* __restrict__ order, int item_begin, int item_count, WsHeader* __restrict__ hdr) {
+  pdl_enter();
   using S = TileShape<TS, false>;
   __shared__ __align__(128) Splat buf[2][kCh];
   __shared__ int s_item;
@@ -399,6 +400,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
                       const uint32_t* __restrict__ lists, const uint2* __restrict__ ranges,
                       const uint32_t* __restrict__ order, int item_begin, int item_count, float* __restrict__ g2d,
                       const uint32_t* dorder0, const uint32_t* dorder1, WsHeader* __restrict__ hdr) {
+  pdl_enter();
   using S = TileShape<TS, true>;
   const uint32_t* __restrict__ dorder = depth_order(hdr, dorder0, dorder1);
   const bool dead = render_dead(hdr);   // a look-back gave up: every list counts as empty
@@ -647,11 +649,13 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
 }
 
 __global__ void zero_g2d(float* __restrict__ g2d, const WsHeader* __restrict__ hdr) {
+  pdl_enter();
   const size_t n = (size_t)hdr->visible * 9;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) g2d[i] = 0.f;
 }
 
 __global__ void reset_bwd_queues(WsHeader* hdr) {
+  pdl_enter();
   if (threadIdx.x < kTileClasses) hdr->work_bwd[threadIdx.x] = 0;
   if (threadIdx.x == 0) hdr->evals_run_bwd = 0;
 }
@@ -677,10 +681,10 @@ cudaError_t fwd_class(const DevTables* tab, const HostPlan& plan, const Splat* v
   const int begin = plan.class_begin[S::kClass];
   if (count) {
     auto k = blend_forward_kernel<TS, true>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, hdr);
+    launch_pdl(k, resident_grid(k, S::kThreads, items), S::kThreads, 0, s, tab, vsplats, lists, ranges, order, begin, items, hdr);
   } else {
     auto k = blend_forward_kernel<TS, false>;
-    k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, hdr);
+    launch_pdl(k, resident_grid(k, S::kThreads, items), S::kThreads, 0, s, tab, vsplats, lists, ranges, order, begin, items, hdr);
   }
   return cudaGetLastError();
 }
@@ -691,7 +695,7 @@ void bwd_launch(const DevTables* tab, const Splat* vsplats, const uint32_t* list
                 WsHeader* hdr, cudaStream_t s) {
   using S = TileShape<TS, true>;
   auto k = blend_backward_kernel<TS, ABS, COUNT>;
-  k<<<resident_grid(k, S::kThreads, items), S::kThreads, 0, s>>>(tab, vsplats, lists, ranges, order, begin, items, g2d,
+  launch_pdl(k, resident_grid(k, S::kThreads, items), S::kThreads, 0, s, tab, vsplats, lists, ranges, order, begin, items, g2d,
                                                                  d0, d1, hdr);
 }
 
@@ -734,8 +738,8 @@ cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, co
   const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + L.order);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
   float* g2d = reinterpret_cast<float*>(ws + L.g2d);
-  reset_bwd_queues<<<1, 32, 0, s>>>(hdr);
-  zero_g2d<<<sort_blocks() * 2, 256, 0, s>>>(g2d, hdr);
+  launch_pdl(reset_bwd_queues, 1, 32, 0, s, hdr);
+  launch_pdl(zero_g2d, sort_blocks() * 2, 256, 0, s, g2d, hdr);
   note_launches(2);
   const uint32_t* d0 = reinterpret_cast<const uint32_t*>(ws + L.vvals[0]);
   const uint32_t* d1 = reinterpret_cast<const uint32_t*>(ws + L.vvals[1]);

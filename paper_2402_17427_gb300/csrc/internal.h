@@ -208,6 +208,16 @@ struct Compact {
 // compacted and sorted arrays may hold unwritten slots, so no stage may index with them.  The flag
 // is set by an earlier kernel of the stream, so a plain load sees it (kernels of one stream see
 // each other's writes); the L1 cache then merges the loads of a block's warps.
+// Programmatic dependent launch: the kernels of a call may be launched so that their blocks are
+// scheduled while the previous kernel of the stream is still finishing.  Every such kernel starts
+// with pdl_enter(): it waits until the previous kernel has completed and its writes are visible
+// (nothing is read or written before), and lets the next kernel be scheduled likewise.  Launched
+// without the attribute, both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ bool render_dead(const WsHeader* hdr) {
   return (hdr->status & VG_STATUS_WAIT_TIMEOUT) != 0u;
 }
@@ -257,6 +267,23 @@ enum CallEventSlot {
   kEvAppearance, kCallEvents = kEvAppearance + 16
 };
 cudaEvent_t call_event(int slot);
+
+// Launches `kernel` with programmatic stream serialization (see pdl_enter()).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // SSIM half of the loss (loss.cu), for the appearance loss of Eq. 3: the moment pass (maps
 // [9][H][W], partials [ssim_partials][2] = (sum S, sum |x - y|) per block) and the gradient pass

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(kLossThreads) ssim_forward_kernel(const float*
                                                                     const float* __restrict__ y, int W, int H,
                                                                     Win win, float dLdS, float* __restrict__ maps,
                                                                     double* __restrict__ partials) {
+  pdl_enter();
   __shared__ __align__(16) float4 s4[NRP][QP];   // (x row 2p, x row 2p + 1, y row 2p, y row 2p + 1)
   __shared__ __align__(16) float hs[5][LTH * LT];
   __shared__ double red[kLossThreads / 32];
@@ -238,6 +239,7 @@ __global__ void __launch_bounds__(kLossThreads) ssim_forward_kernel(const float*
 
 __global__ void __launch_bounds__(1024) loss_finalize(const double* __restrict__ partials, int nb, double inv,
                                                       float lambda, float* __restrict__ out_loss) {
+  pdl_enter();
   __shared__ double sm[2][32];
   double s = 0, l = 0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {   // independent loads, fixed order
@@ -353,6 +355,7 @@ __global__ void __launch_bounds__(kLossThreads) ssim_backward_kernel(const float
                                                                      Win win, float l1_scale,
                                                                      float* __restrict__ grad,
                                                                      const float* __restrict__ scale = nullptr) {
+  pdl_enter();
   ssim_backward_body<kAppear>(x, y, maps, W, H, win, l1_scale, grad, nullptr, 0, 0, scale);
 }
 
@@ -444,11 +447,13 @@ extern "C" vg_status vg_loss_l1_dssim(const float* img, const float* target, int
   const double inv = 1.0 / (3.0 * (double)plane);
   const Win win = make_window();
   note_launches(out_grad ? 3 : 2);
+  // the call's first kernel follows whatever the caller queued on s: a plain launch
   ssim_forward_kernel<<<grid, kLossThreads, 0, s>>>(img, target, width, height, win, (float)(-lambda * inv), maps, partials);
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaError_t e = finalize_beside(partials, nb, inv, lambda, out_loss, out_grad != nullptr, s, &fork, &join);
   if (out_grad)
-    ssim_backward_kernel<false><<<grid, kLossThreads, 0, s>>>(img, target, maps, width, height, win, (float)((1.0 - lambda) * inv), out_grad);
+    launch_pdl(ssim_backward_kernel<false>, grid, kLossThreads, 0, s, img, target, maps, width, height, win,
+               (float)((1.0 - lambda) * inv), out_grad, static_cast<const float*>(nullptr));
   if (join) cudaStreamWaitEvent(s, join, 0);   // nothing of the call outlives it on s
   if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? VG_OK : VG_ERR_CUDA;

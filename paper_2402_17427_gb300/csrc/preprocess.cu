@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __rest
                                                          Splat* __restrict__ splats, uint2* __restrict__ rects,
                                                          uint32_t* __restrict__ touched, const Compact cp,
                                                          WsHeader* __restrict__ hdr) {
+  pdl_enter();
   // blocks take their Gaussians in ticket order, so the look-back below only ever waits on
   // blocks that are already running
   __shared__ unsigned s_blk, s_base;
@@ -415,6 +416,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const DevTables* __rest
 template <int DEG>
 __global__ void __launch_bounds__(256) zero_culled_grads(const DevTables* __restrict__ tab, int total_n,
                                                          const uint32_t* __restrict__ touched) {
+  pdl_enter();
   constexpr int F = 3 * (DEG + 1) * (DEG + 1);
   const int lane = threadIdx.x & 31;
   const int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31;
@@ -641,6 +643,7 @@ template <int DEG>
 __global__ void __launch_bounds__(128, 4) preprocess_backward_kernel(
     const DevTables* __restrict__ tab, const uint32_t* __restrict__ vis_ids, const WsHeader* __restrict__ hdr,
     const Splat* __restrict__ splats, const float* __restrict__ g2d, int accumulate) {
+  pdl_enter();
   const bool dead = render_dead(hdr);   // the compacted list may hold unwritten slots
   const int nv = (int)hdr->visible;
   if (dead) return;
@@ -659,10 +662,10 @@ cudaError_t launch_preprocess(const DevTables* tab, int total_n, int degree, Spl
   if (cudaMemsetAsync(cp.status, 0, (size_t)blocks * sizeof(unsigned long long), s) != cudaSuccess)
     return cudaGetLastError();
   switch (degree) {
-    case 0: preprocess_kernel<0><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, cp, hdr); break;
-    case 1: preprocess_kernel<1><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, cp, hdr); break;
-    case 2: preprocess_kernel<2><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, cp, hdr); break;
-    default: preprocess_kernel<3><<<blocks, 256, 0, s>>>(tab, total_n, splats, rects, touched, cp, hdr); break;
+    case 0: launch_pdl(preprocess_kernel<0>, blocks, 256, 0, s, tab, total_n, splats, rects, touched, cp, hdr); break;
+    case 1: launch_pdl(preprocess_kernel<1>, blocks, 256, 0, s, tab, total_n, splats, rects, touched, cp, hdr); break;
+    case 2: launch_pdl(preprocess_kernel<2>, blocks, 256, 0, s, tab, total_n, splats, rects, touched, cp, hdr); break;
+    default: launch_pdl(preprocess_kernel<3>, blocks, 256, 0, s, tab, total_n, splats, rects, touched, cp, hdr); break;
   }
   return cudaGetLastError();
 }
@@ -697,10 +700,10 @@ cudaError_t launch_preprocess_backward(const DevTables* tab, int total_n, int de
   const int blocks = std::max(1, std::min((total_n + 127) / 128, per_sm * std::max(sms, 1)));
   note_launches(1);
   switch (degree) {
-    case 0: preprocess_backward_kernel<0><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc); break;
-    case 1: preprocess_backward_kernel<1><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc); break;
-    case 2: preprocess_backward_kernel<2><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc); break;
-    default: preprocess_backward_kernel<3><<<blocks, 128, 0, s>>>(tab, vis_ids, hdr, splats, g2d, acc); break;
+    case 0: launch_pdl(preprocess_backward_kernel<0>, blocks, 128, 0, s, tab, vis_ids, hdr, splats, g2d, acc); break;
+    case 1: launch_pdl(preprocess_backward_kernel<1>, blocks, 128, 0, s, tab, vis_ids, hdr, splats, g2d, acc); break;
+    case 2: launch_pdl(preprocess_backward_kernel<2>, blocks, 128, 0, s, tab, vis_ids, hdr, splats, g2d, acc); break;
+    default: launch_pdl(preprocess_backward_kernel<3>, blocks, 128, 0, s, tab, vis_ids, hdr, splats, g2d, acc); break;
   }
   return cudaGetLastError();
 }
