@@ -648,16 +648,16 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
   }
 }
 
-__global__ void zero_g2d(float* __restrict__ g2d, const WsHeader* __restrict__ hdr) {
+// Before the adjoint: the 2D-gradient accumulators of the visible Gaussians zeroed, the adjoint's
+// work queues and its evaluation counter reset (block 0).
+__global__ void prepare_backward(float* __restrict__ g2d, WsHeader* __restrict__ hdr) {
   pdl_enter();
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < kTileClasses) hdr->work_bwd[threadIdx.x] = 0;
+    if (threadIdx.x == 0) hdr->evals_run_bwd = 0;
+  }
   const size_t n = (size_t)hdr->visible * 9;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) g2d[i] = 0.f;
-}
-
-__global__ void reset_bwd_queues(WsHeader* hdr) {
-  pdl_enter();
-  if (threadIdx.x < kTileClasses) hdr->work_bwd[threadIdx.x] = 0;
-  if (threadIdx.x == 0) hdr->evals_run_bwd = 0;
 }
 
 template <typename K>
@@ -738,9 +738,8 @@ cudaError_t launch_blend_backward(const DevTables* tab, const HostPlan& plan, co
   const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + L.order);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
   float* g2d = reinterpret_cast<float*>(ws + L.g2d);
-  launch_pdl(reset_bwd_queues, 1, 32, 0, s, hdr);
-  launch_pdl(zero_g2d, sort_blocks() * 2, 256, 0, s, g2d, hdr);
-  note_launches(2);
+  launch_pdl(prepare_backward, sort_blocks() * 2, 256, 0, s, g2d, hdr);
+  note_launches(1);
   const uint32_t* d0 = reinterpret_cast<const uint32_t*>(ws + L.vvals[0]);
   const uint32_t* d1 = reinterpret_cast<const uint32_t*>(ws + L.vvals[1]);
   cudaError_t e = bwd_class<8>(tab, plan, vsplats, lists, ranges, order, g2d, d0, d1, hdr, abs, count, s);
