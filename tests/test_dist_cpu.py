@@ -79,3 +79,20 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     # a rank other than 0 returns before reading its arguments, the scene or the oracle
     assert bench.run_reference(None, 2, 1) is None
     assert calls == []
+
+
+def test_cpu_baseline_samplers_run_on_a_tiny_scene():
+    """The two oracle timings bench.py reports (the CPU baseline of the main line, on all host
+    threads and on one, and the reference arm's sampled step) run for real on a small scene."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2402_17427_gb300 import scenes
+    oracle.build()
+    g, cam, target = scenes.tiny_scene(n=200, width=64, height=48, degree=2, seed=3)
+    t, threads, sample = bench.oracle_step_time(g, cam, target, 0.5)
+    assert t > 0 and threads >= 1 and "tiles" in sample
+    t1, threads1, _ = bench.oracle_step_time(g, cam, target, 0.5, seed=1, threads=1)
+    assert t1 > 0 and threads1 == 1
+    took, full, threads2, sample2 = bench.oracle_sampled_step(g, cam, target, 0.5, seed=0)
+    assert 0 < took and 0 < full and threads2 >= 1 and "tiles" in sample2
