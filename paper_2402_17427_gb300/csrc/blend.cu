@@ -565,8 +565,10 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
               const float2 Bn = __ffma2_rn(cg, aT, Bp);
               B[p] = Bn.x;
               B[p + 1] = Bn.y;
-              T[p] = ok0 ? Tb.x : T[p];
-              T[p + 1] = ok1 ? Tb.y : T[p + 1];
+              // a pixel the Gaussian does not reach has a = 0, so 1 - a = 1, whose approximate
+              // reciprocal is exactly 1: Tb = T there, and T needs no select
+              T[p] = Tb.x;
+              T[p + 1] = Tb.y;
               // where alpha is clamped to alpha_max it does not depend on the power (a pixel
               // this Gaussian does not reach has a = 0, hence dal * a = 0)
               float2 dpow = __fmul2_rn(dal, a);
@@ -602,7 +604,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
             const float cg = f1.z * G[p][0] + f1.w * G[p][1] + f2.x * G[p][2];
             const float dal = Tb * cg - B[p] * rom;
             B[p] = fmaf(cg, aT, B[p]);
-            T[p] = ok ? Tb : T[p];
+            T[p] = Tb;                                // = T[p] where a = 0 (see above)
             // where alpha is clamped to alpha_max it does not depend on the power (a pixel
             // this Gaussian does not reach has a = 0, hence dal * a = 0)
             const float dpow = araw < amax ? dal * a : 0.f;
