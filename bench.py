@@ -45,16 +45,16 @@ OPS_EVAL, OPS_BLEND_FWD, OPS_BLEND_BWD = 11, 7, 37
 TRAFFIC_SOURCES = ("paper_2402_17427_gb300/csrc/blend.cu", "paper_2402_17427_gb300/csrc/vg_common.cuh",
                    "paper_2402_17427_gb300/csrc/internal.h")
 PROFILED_TRAFFIC = {
-    "sources_sha256": "61830f41a040a4235a3556c65714ba7479b886fe2ca43412bc7b93fdb2f5136f",
-    "blend": 18663424 + 1178368,
-    "blend_backward": 67471104 + 1157888,
+    "sources_sha256": "00a000ce294a1f82d732c6b7645856d07fe83c499b260a154c6b7b7d778eb59c",
+    "blend": 18666752 + 1185024,
+    "blend_backward": 67482624 + 1193984,
 }
 # Warp instructions issued per launch (smsp__inst_executed.sum) of the compositing kernels on this
 # workload, from the same captures; held to the same source hash.
 PROFILED_INSTRUCTIONS = {
-    "sources_sha256": "61830f41a040a4235a3556c65714ba7479b886fe2ca43412bc7b93fdb2f5136f",
+    "sources_sha256": "00a000ce294a1f82d732c6b7645856d07fe83c499b260a154c6b7b7d778eb59c",
     "blend": 257461382,
-    "blend_backward": 406145857,
+    "blend_backward": 397828373,
 }
 
 
@@ -781,8 +781,22 @@ def main():
         torch.cuda.synchronize()
         assert bool(torch.isfinite(losses).all())       # every step's loss, read on the host
         ems = slowest_ms(pg, e0.elapsed_time(e1) / ke, dev)
+        # the copies alone (same tensors, same copy stream, nothing computing): the host-to-device
+        # link's rate, and the step rate it alone would allow
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            upload(0)
+        torch.cuda.synchronize()
+        c0.record(cs)
+        for _ in range(5):
+            upload(0)
+        c1.record(cs)
+        torch.cuda.synchronize()
+        copy_ms = c0.elapsed_time(c1) / 5
         e2e = {"value": job_rate(ws, ems), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": 4, "pipelined": "inputs of step k+1 copied during step k"}
+               "d2h_bytes_per_step": 4, "pipelined": "inputs of step k+1 copied during step k",
+               "h2d_copy_ms": copy_ms, "h2d_gbs": h2d / copy_ms / 1e6,
+               "copy_bound_steps_per_s": job_rate(ws, copy_ms)}
         ras.verify()
 
     if rank != 0:

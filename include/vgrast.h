@@ -225,6 +225,14 @@ vg_status vg_read_counters(const void* workspace, size_t workspace_bytes, int64_
  * launch with CUDA events. */
 vg_status vg_alu_probe(int32_t kind, int32_t blocks, int32_t iters, float* scratch, vg_stream stream);
 
+/* The compositing kernels' approximate operations applied elementwise, out[i] = op(in[i]) for
+ * i < n (diagnostic; no part of a render): kind 0 the approximate reciprocal (rcp.approx.ftz),
+ * kind 1 the approximate base-2 exponential (ex2.approx.ftz).  in, out: device float [n], caller
+ * owned.  The adjoint of the compositing (Sec. 3, the alpha blending taken back to front)
+ * relies on kind 0 mapping 1 to exactly 1.  VG_ERR_INVALID for an unknown kind, n < 0 or a null
+ * pointer with n > 0; n = 0 launches nothing. */
+vg_status vg_approx_probe(int32_t kind, const float* in, float* out, int32_t n, vg_stream stream);
+
 /* ------------------------------------------------------------------------------------------
  * Loss, Eq. 1:  L = (1 - lambda) mean|I - I_gt| + lambda (1 - mean SSIM(I, I_gt))
  * SSIM: 11x11 Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2, mean over

@@ -26,7 +26,7 @@ EXPORTED = ("vg_default_opts", "vg_status_string", "vg_kernel_launches", "vg_wor
             "vg_rasterize_backward", "vg_read_render_state", "vg_loss_workspace_bytes", "vg_loss_l1_dssim",
             "vg_batch_workspace_bytes", "vg_render_batch", "vg_render_batch_backward",
             "vg_views_workspace_bytes", "vg_render_views", "vg_loss_l1_dssim_noalloc", "vg_read_batch_state",
-            "vg_loss_l1_dssim_grad", "vg_read_counters", "vg_alu_probe",
+            "vg_loss_l1_dssim_grad", "vg_read_counters", "vg_alu_probe", "vg_approx_probe",
             "vg_airspace_boxes", "vg_visibility_workspace_bytes", "vg_camera_visibility", "vg_merge_workspace_bytes",
             "vg_merge_cells", "vg_eval_workspace_bytes", "vg_eval_color_corrected", "vg_adam_step",
             "vg_densify_accumulate", "vg_densify_workspace_bytes", "vg_densify", "vg_appearance_param_count",
@@ -129,6 +129,8 @@ def lib():
     L.vg_read_counters.restype = ctypes.c_int
     L.vg_alu_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]
     L.vg_alu_probe.restype = ctypes.c_int
+    L.vg_approx_probe.argtypes = [ctypes.c_int32, _P, _P, ctypes.c_int32, _P]
+    L.vg_approx_probe.restype = ctypes.c_int
     if hasattr(L, "vg_render_batch"):
         L.vg_batch_workspace_bytes.argtypes = [ctypes.POINTER(vg_gaussians), ctypes.c_int32,
                                                ctypes.POINTER(vg_camera), ctypes.POINTER(vg_raster_opts),
@@ -263,6 +265,10 @@ def vg_read_counters(workspace: int, workspace_bytes: int, counters: int, stream
 
 def vg_alu_probe(kind: int, blocks: int, iters: int, scratch: int, stream: int) -> None:
     _check(lib().vg_alu_probe(kind, blocks, iters, scratch, stream), "vg_alu_probe")
+
+
+def vg_approx_probe(kind: int, inp: int, out: int, n: int, stream: int) -> None:
+    _check(lib().vg_approx_probe(kind, inp, out, n, stream), "vg_approx_probe")
 
 
 def vg_loss_l1_dssim_grad(img: int, target: int, width: int, height: int, lam: float, workspace: int,

@@ -44,12 +44,6 @@ static_assert(TileShape<8, true>::kPPT % TileShape<8, false>::kPPT == 0 &&
                   TileShape<32, true>::kPPT % TileShape<32, false>::kPPT == 0,
               "backward row groups must be unions of forward row groups");
 
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 __device__ __forceinline__ float half_lo(float bits) {
   return __half2float(__ushort_as_half((unsigned short)(__float_as_uint(bits) & 0xFFFFu)));
 }

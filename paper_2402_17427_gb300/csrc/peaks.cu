@@ -61,10 +61,25 @@ __global__ void __launch_bounds__(256) probe_ex2(float* __restrict__ out, int it
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The approximate operations of the compositing kernels, applied elementwise (see vg_approx_probe).
+__global__ void __launch_bounds__(256) probe_approx(int kind, const float* __restrict__ in, float* __restrict__ out,
+                                                    int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = kind == 0 ? rcp_approx(in[i]) : ex2_approx(in[i]);
+}
+
 }  // namespace
 }  // namespace vg
 
 using namespace vg;
+
+extern "C" vg_status vg_approx_probe(int32_t kind, const float* in, float* out, int32_t n, vg_stream stream) {
+  if (kind < 0 || kind > 1 || n < 0 || (n > 0 && (!in || !out))) return VG_ERR_INVALID;
+  if (n == 0) return VG_OK;
+  note_launches(1);
+  probe_approx<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(kind, in, out, n);
+  return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;
+}
 
 extern "C" vg_status vg_alu_probe(int32_t kind, int32_t blocks, int32_t iters, float* scratch, vg_stream stream) {
   if (kind < 0 || kind > 2 || blocks < 1 || blocks > (1 << 20) || iters < 1 || !scratch) return VG_ERR_INVALID;

@@ -53,6 +53,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Approximate reciprocal (special-function unit).  The adjoint compositing relies on it mapping
+// 1 to exactly 1 (a pixel a splat does not reach keeps its transmittance); vg_approx_probe lets
+// a test check that on the GPU at hand.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Exponent (log2 units) of one Gaussian at one pixel, split so that the terms that depend only
 // on the pixel column are shared by the pixels of a thread:
 //   e0 = ca dx dx, e1 = cb dx;  power2 = dy (cc dy + e1) + e0.

@@ -98,6 +98,9 @@ def test_invalid_arguments_rejected_before_any_launch(vg):
                                 256, 256, None)
     assert st == vg.VG_ERR_INVALID
     assert L.vg_loss_l1_dssim(None, None, 10, 10, 0.2, None, 0, None, None, None) == vg.VG_ERR_INVALID
+    assert L.vg_approx_probe(2, 256, 256, 4, None) == vg.VG_ERR_INVALID
+    assert L.vg_approx_probe(0, None, None, 4, None) == vg.VG_ERR_INVALID
+    assert L.vg_approx_probe(0, None, None, 0, None) == vg.VG_OK
     assert vg.status_string(vg.VG_ERR_CAPACITY) == "workspace too small"
 
 
