@@ -206,29 +206,57 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
 
 // ---- 2. pair offsets in depth order and pair generation -----------------------------------------
 
-__global__ void __launch_bounds__(256) pairs_count(const uint32_t* order0, const uint32_t* order1,
-                                                   const uint32_t* __restrict__ touched, const WsHeader* __restrict__ hdr,
-                                                   unsigned long long* __restrict__ blocksums) {
+// The pair generation is split by what it balances over.  pairs_count takes the visible
+// Gaussians in depth order, a contiguous segment of them per block, 256 at a time: it moves each
+// record to slot s of the depth-ordered record array (carrying s, and s into the Gaussian's own
+// record), and writes per Gaussian its first tile key, the packed (rectangle width, tiles a row
+// of its view) and its pair offset within the block's segment; the block's pair total goes to
+// blocksums.  pairs_scan turns the totals into segment offsets.  pairs_emit then splits the pairs
+// themselves evenly over its blocks, so that the nearest (largest) Gaussians, which the depth
+// order puts together, do not serialise one block.
+__global__ void __launch_bounds__(256) pairs_count(const DevTables* __restrict__ tab, const uint32_t* order0,
+                                                   const uint32_t* order1, const uint32_t* __restrict__ touched,
+                                                   const uint2* __restrict__ rects, const WsHeader* __restrict__ hdr,
+                                                   unsigned long long* __restrict__ blocksums,
+                                                   Splat* __restrict__ splats, Splat* __restrict__ vsplats,
+                                                   uint32_t* __restrict__ first_key, uint32_t* __restrict__ shape) {
   pdl_enter();
   // the prologue's loads are issued together, then tested
   const bool dead = render_dead(hdr);   // pairs_scan then records no pairs
   const unsigned nvis = hdr->visible;
   const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
   if (dead) return;
+  // the offsets go to the depth sort's other value buffer, free once the sort is done
+  uint32_t* __restrict__ seg_off = const_cast<uint32_t*>(order == order0 ? order1 : order0);
+  __shared__ unsigned long long sm[8];
   unsigned begin, end;
   segment(nvis, begin, end, 256);
-  unsigned long long c = 0;
-  for (unsigned s = begin + threadIdx.x; s < end; s += blockDim.x) c += touched[order[s]];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  __shared__ unsigned long long sm[8];
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long t = 0;
-    for (int k = 0; k < 8; ++k) t += sm[k];
-    blocksums[blockIdx.x] = t;
+  unsigned long long run = 0;
+  for (unsigned t0 = begin; t0 < end; t0 += 256) {
+    const unsigned s = t0 + threadIdx.x;
+    uint32_t cnt = 0;
+    if (s < end) {
+      const uint32_t id = order[s];
+      cnt = touched[id];
+      // the record in depth order (what the blend kernels gather), carrying its rank
+      const float4* src = reinterpret_cast<const float4*>(splats + id);
+      float4 r0 = src[0], r1 = src[1], r2 = src[2];
+      r2.y = __uint_as_float(s);
+      float4* dst = reinterpret_cast<float4*>(vsplats + s);
+      dst[0] = r0; dst[1] = r1; dst[2] = r2;
+      splats[id].rank = s;
+      const KView& vw = tview(tab, tseg(tab, find_seg(tab, (int)id)).view);
+      const uint2 rc = rects[id];
+      const unsigned tx0 = rc.x & 0xFFFFu, ty0 = rc.y & 0xFFFFu, w = (rc.x >> 16) - tx0 + 1u;
+      first_key[s] = (uint32_t)vw.tile_base + ty0 * (uint32_t)vw.tiles_x + tx0;
+      shape[s] = w | ((uint32_t)vw.tiles_x << 16);   // both below 2^16 (width <= 16384 pixels)
+    }
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan((unsigned long long)cnt, &tot, sm);
+    if (s < end) seg_off[s] = (uint32_t)(run + ex);
+    run += tot;
   }
+  if (threadIdx.x == 0) blocksums[blockIdx.x] = run;
 }
 
 __global__ void __launch_bounds__(256) pairs_scan(unsigned long long* __restrict__ blocksums, int B, WsHeader* hdr,
@@ -255,76 +283,90 @@ __global__ void __launch_bounds__(256) pairs_scan(unsigned long long* __restrict
   }
 }
 
+constexpr int kEmitRun = 16;   // consecutive pairs a thread of pairs_emit produces per round
+
 // Every visible Gaussian (in depth order s) owns the pairs [offset, offset + tiles touched): one
-// (global tile, s) pair per tile of its rectangle, tiles row-major.  It also writes its splat
-// record, carrying s, to slot s of the depth-ordered record array, and s to its own record.
-// A block takes 256 Gaussians at a time and its threads emit their pairs cooperatively (thread k
-// writes pair k of the batch, finding its owner by binary search), so writes are coalesced and
-// large Gaussians do not serialise one thread.
-__global__ void __launch_bounds__(256) pairs_emit(const DevTables* __restrict__ tab, const uint32_t* order0,
-                                                  const uint32_t* order1, const uint32_t* __restrict__ touched,
-                                                  const uint2* __restrict__ rects, const WsHeader* __restrict__ hdr,
-                                                  const unsigned long long* __restrict__ blocksums,
-                                                  unsigned long long cap, uint32_t* __restrict__ pkeys,
-                                                  uint32_t* __restrict__ pvals, Splat* __restrict__ splats,
-                                                  Splat* __restrict__ vsplats, unsigned long long* __restrict__ status0) {
+// (global tile, s) pair per tile of its rectangle, tiles row-major.  A block takes rounds of
+// 256 x kEmitRun consecutive pairs; a thread finds the owner of the first of its kEmitRun pairs
+// by binary search (over the segment offsets in shared memory, then within the segment), steps
+// through the rectangles' tiles from there into shared memory, and the block writes the round out
+// coalesced.
+__global__ void __launch_bounds__(256) pairs_emit(const uint32_t* order0, const uint32_t* order1,
+                                                  const WsHeader* __restrict__ hdr,
+                                                  const unsigned long long* __restrict__ blocksums, int count_blocks,
+                                                  const uint32_t* __restrict__ first_key,
+                                                  const uint32_t* __restrict__ shape, uint32_t* __restrict__ pkeys,
+                                                  uint32_t* __restrict__ pvals, unsigned long long* __restrict__ status0) {
   pdl_enter();
   // the prologue's loads are issued together, then tested
-  const unsigned pair_n = hdr->pair_n, nvis = hdr->visible;
+  const unsigned total = hdr->pair_n, nvis = hdr->visible;
   const uint32_t* __restrict__ order = depth_order(hdr, order0, order1);
-  if (pair_n == 0) return;   // no pairs, or more than the capacity (nothing is sorted)
+  if (total == 0) return;   // no pairs, or more than the capacity (nothing is sorted)
+  const uint32_t* __restrict__ seg_off = order == order0 ? order1 : order0;
   // with the tile counts known in advance (tile_prep), this kernel clears the first tile-sort
   // pass's look-back rows
-  if (status0) zero_status(status0, (pair_n + kTileTile - 1) / kTileTile);
-  __shared__ unsigned long long sm[8];
-  __shared__ unsigned s_off[257];
-  __shared__ uint32_t s_rank[256];
-  __shared__ int s_base[256], s_tilesx[256], s_tx0[256], s_ty0[256], s_w[256];
-  unsigned begin, end;
-  segment(nvis, begin, end, 256);
-  unsigned long long run = blocksums[blockIdx.x];
-  for (unsigned t0 = begin; t0 < end; t0 += 256) {
-    const unsigned s = t0 + threadIdx.x;
-    uint32_t id = 0, cnt = 0;
-    if (s < end) {
-      id = order[s];
-      cnt = touched[id];
-      // the record in depth order (what the blend kernels gather), carrying its rank
-      const float4* src = reinterpret_cast<const float4*>(splats + id);
-      float4 r0 = src[0], r1 = src[1], r2 = src[2];
-      r2.y = __uint_as_float(s);
-      float4* dst = reinterpret_cast<float4*>(vsplats + s);
-      dst[0] = r0; dst[1] = r1; dst[2] = r2;
-      splats[id].rank = s;
-      const KView& vw = tview(tab, tseg(tab, find_seg(tab, (int)id)).view);
-      const uint2 rc = rects[id];
-      s_base[threadIdx.x] = vw.tile_base;
-      s_tilesx[threadIdx.x] = vw.tiles_x;
-      s_tx0[threadIdx.x] = (int)(rc.x & 0xFFFF);
-      s_ty0[threadIdx.x] = (int)(rc.y & 0xFFFF);
-      s_w[threadIdx.x] = (int)(rc.x >> 16) - (int)(rc.x & 0xFFFF) + 1;
-    }
-    unsigned long long tot;
-    const unsigned long long ex = block_exclusive_scan((unsigned long long)cnt, &tot, sm);
-    s_off[threadIdx.x] = (unsigned)ex;
-    s_rank[threadIdx.x] = s;
-    if (threadIdx.x == 0) s_off[256] = (unsigned)tot;
-    __syncthreads();
-    for (unsigned k = threadIdx.x; k < (unsigned)tot; k += 256) {
-      const unsigned long long j = run + k;
-      if (j >= cap) break;
-      int lo = 0, hi = 255;              // last g with s_off[g] <= k (owners have cnt > 0)
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
+  if (status0) zero_status(status0, (total + kTileTile - 1) / kTileTile);
+  __shared__ unsigned long long s_bs[kMaxSortBlocks];
+  __shared__ uint32_t s_pk[256 * (kEmitRun + 1)], s_pv[256 * (kEmitRun + 1)];
+  // pairs_count's segments (segment() over count_blocks blocks, granularity 256); every segment
+  // below nseg holds Gaussians, each with at least one pair, so the offsets increase strictly
+  unsigned seg = (nvis + (unsigned)count_blocks - 1) / (unsigned)count_blocks;
+  seg = (seg + 255u) / 256u * 256u;
+  const int nseg = (int)((nvis + seg - 1) / seg);
+  for (int b = threadIdx.x; b < nseg; b += 256) s_bs[b] = blocksums[b];
+  __syncthreads();
+  // first pair of Gaussian s (s < nvis), and the end of the last
+  auto offset_of = [&](unsigned s) -> unsigned {
+    return s < nvis ? (unsigned)s_bs[s / seg] + seg_off[s] : total;
+  };
+  for (unsigned k0 = blockIdx.x * 256u * kEmitRun; k0 < total; k0 += gridDim.x * 256u * kEmitRun) {
+    const unsigned kb = k0 + threadIdx.x * kEmitRun;
+    if (kb < total) {
+      int b = 0, bh = nseg - 1;            // last segment whose offset is <= kb
+      while (b < bh) {
+        const int mid = (b + bh + 1) >> 1;
+        if (s_bs[mid] <= kb) b = mid; else bh = mid - 1;
       }
-      const int within = (int)(k - s_off[lo]);
-      const int w = s_w[lo];
-      const int ty = s_ty0[lo] + within / w, tx = s_tx0[lo] + within % w;
-      pkeys[j] = (uint32_t)(s_base[lo] + ty * s_tilesx[lo] + tx);
-      pvals[j] = s_rank[lo];
+      const unsigned rem = kb - (unsigned)s_bs[b];
+      unsigned s = (unsigned)b * seg, sh = min(nvis, s + seg) - 1;   // last s of the segment with offset <= rem
+      while (s < sh) {
+        const unsigned mid = (s + sh + 1) >> 1;
+        if (seg_off[mid] <= rem) s = mid; else sh = mid - 1;
+      }
+      unsigned next = offset_of(s + 1);
+      uint32_t sp = shape[s];
+      unsigned w = sp & 0xFFFFu, txn = sp >> 16;
+      const unsigned within = rem - seg_off[s];   // pairs of Gaussian s before kb
+      const unsigned ty = within / w;
+      unsigned tx = within - ty * w;
+      unsigned row = first_key[s] + ty * txn;
+      const int nk = (int)min((unsigned)kEmitRun, total - kb);
+      uint32_t* pk = s_pk + threadIdx.x * (kEmitRun + 1);
+      uint32_t* pv = s_pv + threadIdx.x * (kEmitRun + 1);
+#pragma unroll
+      for (int r = 0; r < kEmitRun; ++r) {
+        if (r < nk) {
+          if (kb + r >= next) {            // the next Gaussian (each has at least one pair)
+            do { ++s; next = offset_of(s + 1); } while (kb + r >= next);
+            sp = shape[s];
+            w = sp & 0xFFFFu;
+            txn = sp >> 16;
+            tx = 0;
+            row = first_key[s];
+          }
+          pk[r] = row + tx;
+          pv[r] = s;
+          if (++tx == w) { tx = 0; row += txn; }
+        }
+      }
     }
-    run += tot;
+    __syncthreads();
+    const unsigned n = min((unsigned)(256 * kEmitRun), total - k0);
+    for (unsigned e = threadIdx.x; e < n; e += 256) {
+      const unsigned at = (e / kEmitRun) * (kEmitRun + 1) + e % kEmitRun;
+      pkeys[k0 + e] = s_pk[at];
+      pvals[k0 + e] = s_pv[at];
+    }
     __syncthreads();
   }
 }
@@ -487,7 +529,7 @@ __global__ void __launch_bounds__(256) tile_count(const DevTables* __restrict__ 
 // gives the ranges, [first, last + 1) for a tile with pairs and (0, 0) for one without; the
 // histograms and the order buckets (tile class, then list length as in tile_bucket) follow.
 // With nothing to sort (no pairs, or more than cap) every range is empty, as the sort leaves it.
-constexpr int kPrepThreads = 256;
+constexpr int kPrepThreads = 1024;
 constexpr int kPrepTiles = 16384;        // tiles of a render that takes this path (two words each)
 
 __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __restrict__ tab, int tiles, unsigned cap,
@@ -499,7 +541,7 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
   unsigned* s_x = s_c + tiles;
   __shared__ unsigned s_h[kMaxPasses][kRadix];
   __shared__ unsigned s_cnt[kBuckets];
-  __shared__ unsigned long long sm[8];
+  __shared__ unsigned long long s_wt[kPrepThreads / 32], s_total;
   // the replicas of tile_count's differences, summed; eight loads in flight per thread
   for (int t0 = 0; t0 < tiles; t0 += 8 * kPrepThreads) {
     unsigned v[8];
@@ -544,16 +586,44 @@ __global__ void __launch_bounds__(kPrepThreads) tile_prep(const DevTables* __res
     }
   }
   __syncthreads();
-  // 2. exclusive offsets over the tile ids, a block-wide scan per 256 tiles
-  unsigned long long run = 0;
-  for (int t0 = 0; t0 < tiles; t0 += kPrepThreads) {
-    const int t = t0 + threadIdx.x;
-    const unsigned c = t < tiles ? s_c[t] : 0u;
-    unsigned long long tot;
-    const unsigned long long ex = block_exclusive_scan((unsigned long long)c, &tot, sm);
-    if (t < tiles) s_x[t] = (unsigned)(run + ex);
-    run += tot;
+  // 2. exclusive offsets over the tile ids: warp w scans its own range of the tiles, 32 at a time
+  //    with a carry; warp 0 scans the warps' totals; each warp then adds its base (offsets are
+  //    used only when the total fits the capacity, so 32 bits hold them)
+  const int per_warp = ((tiles + nwarps - 1) / nwarps + 31) & ~31;
+  const int wb = min(tiles, warp * per_warp), we = min(tiles, wb + per_warp);
+  unsigned long long carry = 0;
+  for (int x0 = wb; x0 < we; x0 += 32) {
+    const int t = x0 + lane;
+    const unsigned c = t < we ? s_c[t] : 0u;
+    unsigned long long incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (t < we) s_x[t] = (unsigned)(carry + incl - c);
+    carry += __shfl_sync(0xffffffffu, incl, 31);
   }
+  if (lane == 0) s_wt[warp] = carry;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long v = lane < nwarps ? s_wt[lane] : 0ull;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane < nwarps) s_wt[lane] = incl - v;
+    if (lane == 31) s_total = incl;
+  }
+  __syncthreads();
+  {
+    const unsigned wbase = (unsigned)s_wt[warp];
+    for (int t = wb + lane; t < we; t += 32) s_x[t] += wbase;
+  }
+  const unsigned long long run = s_total;
+  __syncthreads();
   const bool any = run > 0 && run <= cap;
   const uint32_t lt = lanemask_lt();
   // 3. ranges, digit histograms, order buckets (view by view: the bucket needs the tile class);
@@ -764,11 +834,13 @@ cudaError_t launch_binning(const DevTables* tab, int n, int tiles, int64_t capac
   // 2. pairs in depth order, written where the tile sort's passes leave the result in buffer 0
   const int p0 = tpasses & 1;
   const int BP = kMaxSortBlocks < 6 * B / 2 ? kMaxSortBlocks : 6 * B / 2;   // 6 blocks per SM
-  launch_pdl(pairs_count, BP, 256, 0, s, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), hdr, bsum64);
+  // per Gaussian in depth order: first tile key and rectangle shape in the depth keys' buffers,
+  // free once the depth sort is done
+  launch_pdl(pairs_count, BP, 256, 0, s, tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), rects, hdr, bsum64,
+             splats, vsplats, U(L.vkeys[0]), U(L.vkeys[1]));
   launch_pdl(pairs_scan, 1, 256, 0, s, bsum64, BP, hdr, (unsigned long long)cap);
-  launch_pdl(pairs_emit, BP, 256, 0, s, tab, U(L.vvals[0]), U(L.vvals[1]), U(L.touched), rects, hdr, bsum64,
-                               (unsigned long long)cap, U(L.pkeys[p0]), U(L.pvals[p0]), splats, vsplats,
-                               prep ? S64(0) : nullptr);
+  launch_pdl(pairs_emit, 2 * B, 256, 0, s, U(L.vvals[0]), U(L.vvals[1]), hdr, bsum64, BP, U(L.vkeys[0]),
+             U(L.vkeys[1]), U(L.pkeys[p0]), U(L.pvals[p0]), prep ? S64(0) : nullptr);
   if (!prep) launch_pdl(tile_histogram, B * 2, 256, 0, s, U(L.pkeys[p0]), hdr, tpasses, ctl->hist[1][0], S64(0));
   if (join) cudaStreamWaitEvent(s, join, 0);   // ranges, histograms and order ready
   // 3. stable sort of the pairs by tile id (the first pass after the join with the side stream is
