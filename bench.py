@@ -653,11 +653,15 @@ def main():
     ras = R.Rasterizer(R.RasterSettings(), device=dev, check="sync")
     lossf = R.LossL1DSSIM(0.2)
 
-    def step(evf=None, evb=None, prm=None, tgt=None, lf=None):
+    def step(evf=None, evb=None, prm=None, tgt=None, lf=None, lev=None):
         prm = params if prm is None else prm
         tgt = target_t if tgt is None else tgt
         rgb, T, last = ras.forward(*prm, g.sh_degree, cam, events=evf)
+        if lev:
+            lev[0].record()
         L, dL = (lf or lossf)(rgb, tgt, reuse=True)
+        if lev:
+            lev[1].record()
         grads = ras.backward(*prm, g.sh_degree, cam, T, last, dL, grads=step.grads, events=evb)
         return L, T, last
 
@@ -723,6 +727,17 @@ def main():
     names = ["project", "sort", "blend", "blend_backward", "project_backward"]
     for s, nm in enumerate(names):
         stage_ms[nm] = float(np.mean([stage_ev[k][1][2 * s].elapsed_time(stage_ev[k][1][2 * s + 1]) for k in range(K)]))
+    # the loss call (Eq. 1, both SSIM passes and the reduction), timed in further steps after the
+    # timed region (its two events inside it would add to the step), and what no stage covers:
+    # launch gaps between the calls and the small kernels outside the stages
+    KL = min(K, 50)
+    lev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(KL)]
+    for k in range(KL):
+        step(lev=lev[k])
+    torch.cuda.synchronize()
+    ras.verify()
+    stage_ms["loss"] = float(np.mean([a.elapsed_time(b) for a, b in lev]))
+    stage_ms["unstaged"] = float(ms - sum(stage_ms.values()))
 
     # e2e: the same step from pinned host buffers, every step's inputs copied in and its loss copied
     # out inside the timed region.  Two device input sets: step k computes on one while step k+1's

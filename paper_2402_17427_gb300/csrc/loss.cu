@@ -202,31 +202,55 @@ __global__ void __launch_bounds__(kLossThreads) ssim_forward_kernel(const float*
 #pragma unroll
     for (int f = 0; f < 5; ++f) v[f] = hs[f][hs_at(r0 + i, q)];
   }, m);
+  // the per-pixel SSIM and its three partial derivatives for two rows at once (packed FP32; the
+  // reciprocals approximate, within 1 ulp)
   const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+  const float2 c1 = make_float2(C1, C1), c2 = make_float2(C2, C2), two = make_float2(2.f, 2.f);
+  const float2 dl = make_float2(dLdS, dLdS);
+  auto neg = [](float2 v) { return make_float2(-v.x, -v.y); };
   float ssum = 0.f, l1sum = 0.f;
   const float* sf = reinterpret_cast<const float*>(&s4[0][0]);
   const int gx = ox + q;
 #pragma unroll
-  for (int j = 0; j < GV; ++j) {
-    const int gy = oy + r0 + j, sr = r0 + j + HALO;
-    if (gx >= W || gy >= H) continue;
-    const float* cell = sf + ((sr >> 1) * QP + qcol(q + HALO)) * 4;
-    l1sum += fabsf(cell[sr & 1] - cell[2 + (sr & 1)]);
-    const float mx = m[0][j], my = m[1][j], exx = m[2][j], eyy = m[3][j], exy = m[4][j];
-    const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-    const float N1 = 2.f * mx * my + C1, N2 = 2.f * sxy + C2;
-    const float D1 = mx * mx + my * my + C1, D2 = sxx + syy + C2;
-    const float iD1 = __frcp_rn(D1), iD2 = __frcp_rn(D2);
-    const float iD = iD1 * iD2;
-    const float S = N1 * N2 * iD;
-    const float dS_dmx = 2.f * my * (N2 - N1) * iD - 2.f * mx * S * (iD1 - iD2);
-    const float dS_dexx = -S * iD2;
-    const float dS_dexy = 2.f * N1 * iD;
+  for (int j = 0; j < GV; j += 2) {
+    const int gy = oy + r0 + j;
+    if (gx >= W || gy >= H) continue;      // rows ascend: the pair's second row is outside too
+    const bool in1 = gy + 1 < H;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !in1) break;
+      const int sr = r0 + j + h + HALO;
+      const float* cell = sf + ((sr >> 1) * QP + qcol(q + HALO)) * 4;
+      l1sum += fabsf(cell[sr & 1] - cell[2 + (sr & 1)]);
+    }
+    const float2 mx = make_float2(m[0][j], m[0][j + 1]), my = make_float2(m[1][j], m[1][j + 1]);
+    const float2 exx = make_float2(m[2][j], m[2][j + 1]), eyy = make_float2(m[3][j], m[3][j + 1]);
+    const float2 exy = make_float2(m[4][j], m[4][j + 1]);
+    const float2 mxx = __fmul2_rn(mx, mx), myy = __fmul2_rn(my, my), mxy = __fmul2_rn(mx, my);
+    const float2 sxx = __fadd2_rn(exx, neg(mxx)), syy = __fadd2_rn(eyy, neg(myy)), sxy = __fadd2_rn(exy, neg(mxy));
+    const float2 N1 = __ffma2_rn(two, mxy, c1), N2 = __ffma2_rn(two, sxy, c2);
+    const float2 D1 = __fadd2_rn(__fadd2_rn(mxx, myy), c1), D2 = __fadd2_rn(__fadd2_rn(sxx, syy), c2);
+    const float2 iD1 = make_float2(rcp_approx(D1.x), rcp_approx(D1.y));
+    const float2 iD2 = make_float2(rcp_approx(D2.x), rcp_approx(D2.y));
+    const float2 iD = __fmul2_rn(iD1, iD2);
+    const float2 S = __fmul2_rn(__fmul2_rn(N1, N2), iD);
+    // dS/dmx = 2 my (N2 - N1) iD - 2 mx S (iD1 - iD2), dS/dexx = -S iD2, dS/dexy = 2 N1 iD
+    const float2 t1 = __fmul2_rn(__fmul2_rn(__fmul2_rn(two, my), __fadd2_rn(N2, neg(N1))), iD);
+    const float2 t2 = __fmul2_rn(__fmul2_rn(__fmul2_rn(two, mx), S), __fadd2_rn(iD1, neg(iD2)));
+    const float2 g0 = __fmul2_rn(dl, __fadd2_rn(t1, neg(t2)));
+    const float2 g1 = __fmul2_rn(dl, __fmul2_rn(neg(S), iD2));
+    const float2 g2 = __fmul2_rn(dl, __fmul2_rn(__fmul2_rn(two, N1), iD));
     const size_t pix = (size_t)gy * W + gx;
-    maps[(0 * 3 + c) * plane + pix] = dLdS * dS_dmx;
-    maps[(1 * 3 + c) * plane + pix] = dLdS * dS_dexx;
-    maps[(2 * 3 + c) * plane + pix] = dLdS * dS_dexy;
-    ssum += S;
+    maps[(0 * 3 + c) * plane + pix] = g0.x;
+    maps[(1 * 3 + c) * plane + pix] = g1.x;
+    maps[(2 * 3 + c) * plane + pix] = g2.x;
+    ssum += S.x;
+    if (in1) {
+      maps[(0 * 3 + c) * plane + pix + W] = g0.y;
+      maps[(1 * 3 + c) * plane + pix + W] = g1.y;
+      maps[(2 * 3 + c) * plane + pix + W] = g2.y;
+      ssum += S.y;
+    }
   }
   const double ts = block_sum(ssum, red);
   const double tl = block_sum(l1sum, red);
