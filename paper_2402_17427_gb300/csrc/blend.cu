@@ -15,6 +15,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "vg_common.cuh"
 
@@ -73,6 +75,11 @@ __device__ __forceinline__ bool may_reach(const Splat& sp, float lamin, float cx
   const float best = fmaxf(fmaxf(pw(x0, d0), pw(x1, d1)), fmaxf(pw(e0, y0), pw(e1, y1)));
   return best >= lamin - sp.lo - 0.0625f;
 }
+
+// Log opacity (log2 units) from which a splat may yield alpha >= alpha_max.  Every alpha a splat
+// yields is ex2.approx(power2 + lo) with power2 <= 0, hence at most 2^lo (1 + 2^-21); below this
+// threshold 2^lo < alpha_max 2^-(2^-10), so the alpha_max clamp cannot act.
+__device__ __forceinline__ float clamp_threshold(float amax) { return log2f(amax) - 0.0009765625f; }
 
 // Pixel block of the calling warp inside tile (tx, ty): centre and half extents.
 template <int TS, bool BWD>
@@ -303,7 +310,8 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
               const bool ok1 = !done[p + 1] && !(p2.y > 0.f || q.y < lamin);
               const float2 a = make_float2(fminf(amax, ex2_approx(q.x)), fminf(amax, ex2_approx(q.y)));
               const float2 Tp = make_float2(T[p], T[p + 1]);
-              const float2 Tn = __fmul2_rn(Tp, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a.x, -a.y)));
+              // 1 - a as fma(a, -1, 1): the same rounding, one packed instruction
+              const float2 Tn = __fmul2_rn(Tp, __ffma2_rn(a, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
               const bool stop0 = ok0 && Tn.x < tmin, stop1 = ok1 && Tn.y < tmin;
               const bool blend0 = ok0 && !(stop0 && rule0), blend1 = ok1 && !(stop1 && rule0);
               float2 w = __fmul2_rn(a, Tp);
@@ -413,6 +421,7 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
     const int W = vw.cam.W, H = vw.cam.H;
     const float amax = vw.op.alpha_max;
     const float lamin = log2f(vw.op.alpha_min);
+    const float lclamp = clamp_threshold(amax);
     float wcx, wcy, whw, whh;
     warp_block<TS, true>(tx, ty, wcx, wcy, whw, whh);
     const uint2 rg = dead ? make_uint2(0u, 0u) : ranges[tile];
@@ -530,6 +539,11 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
           // the forward pass (round-to-nearest in both lanes), the sums pairwise.
           if constexpr (S::kPPT % 2 == 0 && !ABS) {
             float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, w6 = s0, w7 = s0, w8 = s0;
+            // CL: the splat's opacity may reach alpha_max, so alpha may be clamped; otherwise every
+            // alpha it yields is below alpha_max and the clamp and its zero gradient are skipped
+            // (the same values: the clamp would not act)
+            auto pixels = [&](auto clamp) {
+            constexpr bool CL = decltype(clamp)::value;
 #pragma unroll
             for (int p = 0; p < S::kPPT; p += 2) {
               const float2 dy = __fadd2_rn(make_float2(dyb[p / FP], dyb[(p + 1) / FP]),
@@ -540,9 +554,10 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
               const bool ok0 = pos < lastp[p] && !(p2.x > 0.f || q.x < lamin);
               const bool ok1 = pos < lastp[p + 1] && !(p2.y > 0.f || q.y < lamin);
               const float2 araw = make_float2(ex2_approx(q.x), ex2_approx(q.y));
-              const float2 a = make_float2(ok0 ? fminf(amax, araw.x) : 0.f, ok1 ? fminf(amax, araw.y) : 0.f);
+              const float2 a = CL ? make_float2(ok0 ? fminf(amax, araw.x) : 0.f, ok1 ? fminf(amax, araw.y) : 0.f)
+                                  : make_float2(ok0 ? araw.x : 0.f, ok1 ? araw.y : 0.f);
               any = any || ok0 || ok1;
-              const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a.x, -a.y));
+              const float2 om = __ffma2_rn(a, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));   // 1 - a
               const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
               const float2 Tp = make_float2(T[p], T[p + 1]), Bp = make_float2(B[p], B[p + 1]);
               const float2 Tb = __fmul2_rn(Tp, rom);
@@ -566,13 +581,17 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
               // where alpha is clamped to alpha_max it does not depend on the power (a pixel
               // this Gaussian does not reach has a = 0, hence dal * a = 0)
               float2 dpow = __fmul2_rn(dal, a);
-              dpow.x = araw.x < amax ? dpow.x : 0.f;
-              dpow.y = araw.y < amax ? dpow.y : 0.f;
+              if constexpr (CL) {
+                dpow.x = araw.x < amax ? dpow.x : 0.f;
+                dpow.y = araw.y < amax ? dpow.y : 0.f;
+              }
               const float2 dpy = __fmul2_rn(dpow, dy);
               s0 = __fadd2_rn(s0, dpow);
               s1 = __fadd2_rn(s1, dpy);
               s2 = __ffma2_rn(dpy, dy, s2);
             }
+            };
+            if (f1.y >= lclamp) pixels(std::true_type()); else pixels(std::false_type());
             S0 = s0.x + s0.y;
             S1 = s1.x + s1.y;
             S2 = s2.x + s2.y;
@@ -614,14 +633,16 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
           }
           }
           if (__any_sync(0xffffffffu, any)) {
-            // fields: du, dv, d conic (a, b, c), d opacity, d rgb; with alpha = o G unclamped,
-            // dL/do = sum dL/dalpha G = S0 / o
-            v[0] = kNegTwoLn2 * (f0.z * dx * S0 + 0.5f * f0.w * S1);
-            v[1] = kNegTwoLn2 * (0.5f * f0.w * dx * S0 + f1.x * S1);
-            v[2] = -0.5f * dx * dx * S0;
-            v[3] = -dx * S1;
-            v[4] = -0.5f * S2;
-            v[5] = S0 * ex2_approx(-f1.y);   // 1 / opacity
+            // fields: the moments of dpow = alpha dL/dalpha over the warp's pixels (sum dx dpow,
+            // sum dy dpow, sum dx^2 dpow, sum dx dy dpow, sum dy^2 dpow, sum dpow), then d rgb;
+            // the projection adjoint maps the moments' totals to du, dv, d conic and d opacity
+            // (grad2d_from_moments: linear, with coefficients constant per splat)
+            v[0] = dx * S0;
+            v[1] = S1;
+            v[2] = dx * v[0];
+            v[3] = dx * S1;
+            v[4] = S2;
+            v[5] = S0;
             const float tot = reduce10(v, lane);
             const int field = reduce10_field(lane);
             const uint32_t rank = __float_as_uint(f2.y);

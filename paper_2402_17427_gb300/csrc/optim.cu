@@ -79,14 +79,21 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a) {
 
 // ---------------------------------------------------------------- statistics
 
-__global__ void __launch_bounds__(256) accumulate_kernel(const float* __restrict__ g2d, const WsHeader* __restrict__ hdr,
+__global__ void __launch_bounds__(256) accumulate_kernel(const float* __restrict__ g2d, const Splat* __restrict__ vsplats,
+                                                         const WsHeader* __restrict__ hdr,
                                                          const uint32_t* d0, const uint32_t* d1, float hw, float hh,
                                                          float* __restrict__ accum, int* __restrict__ count) {
   const uint32_t* __restrict__ dorder = depth_order(hdr, d0, d1);
   const unsigned V = hdr->visible;
   for (unsigned s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
     const unsigned id = dorder[s];
-    const float du = g2d[(size_t)s * 9] * hw, dv = g2d[(size_t)s * 9 + 1] * hh;
+    // the 2D gradient from the compositing adjoint's power moments (slots 0-5), by depth rank
+    float mom[6], d2[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) mom[f] = g2d[(size_t)s * 9 + f];
+    const Splat& rec = vsplats[s];
+    grad2d_from_moments(mom, rec.ca, rec.cb, rec.cc, rec.lo, d2);
+    const float du = d2[0] * hw, dv = d2[1] * hh;
     accum[id] += sqrtf(du * du + dv * dv);     // each Gaussian appears once per view: no race
     count[id] += 1;
   }
@@ -315,8 +322,8 @@ extern "C" vg_status vg_densify_accumulate(const void* workspace, size_t workspa
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const char* ws = static_cast<const char*>(workspace);
   accumulate_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(
-      reinterpret_cast<const float*>(ws + L.g2d), reinterpret_cast<const WsHeader*>(ws + L.header),
-      reinterpret_cast<const uint32_t*>(ws + L.vvals[0]), reinterpret_cast<const uint32_t*>(ws + L.vvals[1]),
+      reinterpret_cast<const float*>(ws + L.g2d), reinterpret_cast<const Splat*>(ws + L.vsplats),
+      reinterpret_cast<const WsHeader*>(ws + L.header), reinterpret_cast<const uint32_t*>(ws + L.vvals[0]), reinterpret_cast<const uint32_t*>(ws + L.vvals[1]),
       0.5f * (float)width, 0.5f * (float)height, accum, reinterpret_cast<int*>(count));
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? VG_OK : VG_ERR_CUDA;

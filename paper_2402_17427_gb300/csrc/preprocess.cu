@@ -501,10 +501,18 @@ __device__ __forceinline__ void project_adjoint(const DevTables* __restrict__ ta
   const KCam cm = tview(tab, sg.view).cam;
   const KOpts op = tview(tab, sg.view).op;
   const int li = (int)l;
-  const uint32_t rank = splats[i].rank;
+  const Splat& rec = splats[i];
+  const uint32_t rank = rec.rank;
   float d2[9];
+  {
+    // slots 0-5 hold the compositing adjoint's power moments; 6-8 d rgb
+    float mom[6];
 #pragma unroll
-  for (int f = 0; f < 9; ++f) d2[f] = g2d[(size_t)rank * 9 + f];
+    for (int f = 0; f < 6; ++f) mom[f] = g2d[(size_t)rank * 9 + f];
+    grad2d_from_moments(mom, rec.ca, rec.cb, rec.cc, rec.lo, d2);
+#pragma unroll
+    for (int f = 6; f < 9; ++f) d2[f] = g2d[(size_t)rank * 9 + f];
+  }
   Proj P;
   project(g, cm, op, li, P);
   float o_m[3], o_s[3], o_q[4];

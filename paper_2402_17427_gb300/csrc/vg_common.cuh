@@ -67,6 +67,26 @@ __device__ __forceinline__ float rcp_approx(float x) {
 //   e0 = ca dx dx, e1 = cb dx;  power2 = dy (cc dy + e1) + e0.
 // Written with explicit round-to-nearest intrinsics so the forward and the backward kernels take
 // bit-identical decisions.
+// The adjoint compositing accumulates, per splat, six moments of g = alpha dL/dalpha over the
+// pixels it reaches (dx = px - u, dy = py - v; FP32 sums):
+//   m = (sum dx g, sum dy g, sum dx^2 g, sum dx dy g, sum dy^2 g, sum g).
+// g is the loss's derivative with respect to the Gaussian's exponent in natural units,
+// P = -(a dx^2 + c dy^2) / 2 - b dx dy = ln 2 (ca dx^2 + cb dx dy + cc dy^2), alpha = opacity e^P.
+// The 2D gradient is linear in the moments with coefficients constant per splat, so it is formed
+// once per Gaussian from the totals:
+//   dL/du = -2 ln 2 (ca m0 + cb m1 / 2),  dL/dv = -2 ln 2 (cb m0 / 2 + cc m1)    (dP/du, dP/dv)
+//   dL/da = -m2 / 2,  dL/db = -m3,  dL/dc = -m4 / 2,  dL/dopacity = m5 / opacity.
+// Output order: du, dv, d conic (a, b, c), d opacity; lo = log2(opacity).
+__device__ __forceinline__ void grad2d_from_moments(const float* m, float ca, float cb, float cc, float lo, float* d) {
+  const float k = -1.3862943611198906f;   // -2 ln 2
+  d[0] = k * (ca * m[0] + 0.5f * cb * m[1]);
+  d[1] = k * (0.5f * cb * m[0] + cc * m[1]);
+  d[2] = -0.5f * m[2];
+  d[3] = -m[3];
+  d[4] = -0.5f * m[4];
+  d[5] = m[5] * exp2f(-lo);
+}
+
 __device__ __forceinline__ void splat_col(float ca, float cb, float dx, float& e0, float& e1) {
   e0 = __fmul_rn(__fmul_rn(ca, dx), dx);
   e1 = __fmul_rn(cb, dx);
