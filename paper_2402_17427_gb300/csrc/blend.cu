@@ -310,8 +310,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
               const bool ok1 = !done[p + 1] && !(p2.y > 0.f || q.y < lamin);
               const float2 a = make_float2(fminf(amax, ex2_approx(q.x)), fminf(amax, ex2_approx(q.y)));
               const float2 Tp = make_float2(T[p], T[p + 1]);
-              // 1 - a as fma(a, -1, 1): the same rounding, one packed instruction
-              const float2 Tn = __fmul2_rn(Tp, __ffma2_rn(a, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
+              const float2 Tn = __fmul2_rn(Tp, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a.x, -a.y)));
               const bool stop0 = ok0 && Tn.x < tmin, stop1 = ok1 && Tn.y < tmin;
               const bool blend0 = ok0 && !(stop0 && rule0), blend1 = ok1 && !(stop1 && rule0);
               float2 w = __fmul2_rn(a, Tp);

@@ -62,11 +62,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Exponent (log2 units) of one Gaussian at one pixel, split so that the terms that depend only
-// on the pixel column are shared by the pixels of a thread:
-//   e0 = ca dx dx, e1 = cb dx;  power2 = dy (cc dy + e1) + e0.
-// Written with explicit round-to-nearest intrinsics so the forward and the backward kernels take
-// bit-identical decisions.
 // The adjoint compositing accumulates, per splat, six moments of g = alpha dL/dalpha over the
 // pixels it reaches (dx = px - u, dy = py - v; FP32 sums):
 //   m = (sum dx g, sum dy g, sum dx^2 g, sum dx dy g, sum dy^2 g, sum g).
@@ -87,6 +82,11 @@ __device__ __forceinline__ void grad2d_from_moments(const float* m, float ca, fl
   d[5] = m[5] * exp2f(-lo);
 }
 
+// Exponent (log2 units) of one Gaussian at one pixel, split so that the terms that depend only
+// on the pixel column are shared by the pixels of a thread:
+//   e0 = ca dx dx, e1 = cb dx;  power2 = dy (cc dy + e1) + e0.
+// Written with explicit round-to-nearest intrinsics so the forward and the backward kernels take
+// bit-identical decisions.
 __device__ __forceinline__ void splat_col(float ca, float cb, float dx, float& e0, float& e1) {
   e0 = __fmul_rn(__fmul_rn(ca, dx), dx);
   e1 = __fmul_rn(cb, dx);
