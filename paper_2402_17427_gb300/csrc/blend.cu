@@ -181,7 +181,7 @@ __device__ __forceinline__ int next_item(unsigned* counter, int count, int* s_it
 }
 
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(TileShape<TS, false>::kThreads)
+__global__ void __launch_bounds__(TileShape<TS, false>::kThreads, TS == 16 ? 9 : 1)
 blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ vsplats,
                      const uint32_t* __restrict__ lists, const uint2* __restrict__ ranges,
                      const uint32_t* __restrict__ order, int item_begin, int item_count, WsHeader* __restrict__ hdr) {
@@ -396,7 +396,7 @@ blend_forward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict_
 }
 
 template <int TS, bool ABS, bool COUNT>
-__global__ void __launch_bounds__(TileShape<TS, true>::kThreads)
+__global__ void __launch_bounds__(TileShape<TS, true>::kThreads, TS == 16 ? 16 : 1)
 blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict__ vsplats,
                       const uint32_t* __restrict__ lists, const uint2* __restrict__ ranges,
                       const uint32_t* __restrict__ order, int item_begin, int item_count, float* __restrict__ g2d,
