@@ -45,16 +45,16 @@ OPS_EVAL, OPS_BLEND_FWD, OPS_BLEND_BWD = 11, 7, 37
 TRAFFIC_SOURCES = ("paper_2402_17427_gb300/csrc/blend.cu", "paper_2402_17427_gb300/csrc/vg_common.cuh",
                    "paper_2402_17427_gb300/csrc/internal.h")
 PROFILED_TRAFFIC = {
-    "sources_sha256": "00a000ce294a1f82d732c6b7645856d07fe83c499b260a154c6b7b7d778eb59c",
-    "blend": 18666752 + 1185024,
-    "blend_backward": 67482624 + 1193984,
+    "sources_sha256": "e2f064939af67d976a6365269fa504b6e3f65432138c7c6fa2af94ce5adf4a0f",
+    "blend": 18660864 + 1536768,
+    "blend_backward": 67457536 + 1475328,
 }
 # Warp instructions issued per launch (smsp__inst_executed.sum) of the compositing kernels on this
 # workload, from the same captures; held to the same source hash.
 PROFILED_INSTRUCTIONS = {
-    "sources_sha256": "00a000ce294a1f82d732c6b7645856d07fe83c499b260a154c6b7b7d778eb59c",
-    "blend": 257461382,
-    "blend_backward": 397828373,
+    "sources_sha256": "e2f064939af67d976a6365269fa504b6e3f65432138c7c6fa2af94ce5adf4a0f",
+    "blend": 259017717,
+    "blend_backward": 357429896,
 }
 
 
