@@ -125,6 +125,38 @@ def test_tiny_scenes_forward_backward(n, W, H, tile, deg, seed, bg, stop):
     check_grads(gpu, ref, ~(orc.rec["grad_amb"] | orc.rec["rect_amb"]))
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_opaque_splats_clamped_at_alpha_max(tile):
+    """Splats whose opacity is nearly 1 reach alpha_max near their centres: there alpha is clamped
+    and does not depend on the Gaussian's power, so the adjoint drops that pixel's power gradient.
+    Random opacities (logits ~ N(0, 1)) almost never get there; this scene makes half the splats
+    nearly opaque and large (~11 px on screen), checks that clamped steps are blended, and compares
+    the image and every gradient with the FP64 adjoint."""
+    g, cam, _ = scenes.tiny_scene(n=60, width=64, height=48, degree=2, seed=11, log_scale=(-0.5, 0.3))
+    rng = np.random.default_rng(11)
+    opaque = rng.random(g.n) < 0.5
+    g.opacity_logits = np.where(opaque, rng.uniform(5.0, 10.0, g.n), g.opacity_logits).astype(np.float32)
+    s = R.RasterSettings(tile_size=tile)
+    r, params, out, orc = render_both(g, cam, s)
+    check_image(orc, out)
+    # blended steps at alpha_max, from the oracle's per-pixel traces
+    a, b, c = (orc.rec["conic"][:, k] for k in range(3))
+    clamped = 0
+    for y in range(cam.height):
+        for x in range(cam.width):
+            _, ids = orc.pixel_trace(x, y)
+            if ids.size:
+                dx, dy = x - orc.rec["u"][ids], y - orc.rec["v"][ids]
+                power = -0.5 * (a[ids] * dx * dx + c[ids] * dy * dy) - b[ids] * dx * dy
+                clamped += int((orc.rec["opacity"][ids] * np.exp(power) >= s.alpha_max).sum())
+    assert clamped >= 20, clamped
+    w = np.random.default_rng(tile).standard_normal((3, cam.height, cam.width)).astype(np.float32)
+    w[:, orc.amb.astype(bool)] = 0
+    gpu = run_backward(r, params, g, cam, out, w)
+    ref = orc.backward(w.astype(np.float64))
+    check_grads(gpu, ref, ~(orc.rec["grad_amb"] | orc.rec["rect_amb"]))
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_empty_and_fully_culled_inputs():
