@@ -606,6 +606,24 @@ def serving_pattern(dev, seconds=30.0):
     d["workload"] = ("merged city: 16 cells, 20M Gaussians SH3 resident; Poisson 200 req/s for %.0f s; "
                      "50%% 1280x720, 35%% 1920x1080, 15%% 3840x2160; first 2 s excluded" % seconds)
     d["resident_gb"] = srv.resident_bytes / 1e9
+    # The same server offered more than it can take (Poisson 3000 req/s for 4 s, same resolution
+    # mix): the queue grows, so the throughput over the run, drain included, is the service
+    # capacity, and latencies are queueing-dominated.  Once with batches of up to max_batch
+    # requests, once with one request a batch (the same 3 slots in flight).
+    keys = ("requests", "duration_s", "throughput_rps", "mpix_per_s", "mean_batch", "batches", "max_inflight",
+            "p50_ms", "p99_ms", "rerenders")
+    sat = {}
+    for name, mb in (("batched", srv.max_batch), ("one_per_batch", 1)):
+        full = srv.max_batch
+        srv.max_batch = mb
+        try:
+            st = srv.serve(scenes.request_stream(seed=5001, rate_hz=3000.0, duration_s=4.0), warmup_s=0.5)
+        finally:
+            srv.max_batch = full
+        sat[name] = {k: v for k, v in st.summary().items() if k in keys}
+    sat["offered_rps"] = 3000.0
+    sat["batching_speedup"] = sat["batched"]["throughput_rps"] / max(sat["one_per_batch"]["throughput_rps"], 1e-9)
+    d["saturated"] = sat
     return d
 
 
