@@ -252,11 +252,16 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(const DevTables* __r
   // blocks that are already running
   __shared__ unsigned s_blk, s_base;
   __shared__ unsigned s_sm[8];
+  __shared__ unsigned s_dlo, s_dhi;   // the block's min / max depth key
   __shared__ unsigned s_h[kMaxPasses][kRadix];
   // the visible Gaussians' stage-3 inputs, packed densely in index order: Gaussian, segment,
   // mean, conic, and the 2D covariance's diagonal
   __shared__ float s_job[10][256];
-  if (threadIdx.x == 0) s_blk = atomicAdd(cp.ticket, 1u);
+  if (threadIdx.x == 0) {
+    s_blk = atomicAdd(cp.ticket, 1u);
+    s_dlo = 0xFFFFFFFFu;
+    s_dhi = 0u;
+  }
 #pragma unroll
   for (int p = 0; p < kMaxPasses; ++p) s_h[p][threadIdx.x] = 0;
   __syncthreads();
@@ -369,15 +374,17 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(const DevTables* __r
     const float4* src = reinterpret_cast<const float4*>(&sp);
     dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
   }
-  // min / max depth key over visible Gaussians (they fix the bits the depth sort needs)
+  // min / max depth key over visible Gaussians (they fix the bits the depth sort needs): per warp,
+  // then per block in shared memory, then one global atomic each per block (one per warp put
+  // ~31K same-address atomics per render on two words)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     lo_key = min(lo_key, __shfl_xor_sync(0xffffffffu, lo_key, o));
     hi_key = max(hi_key, __shfl_xor_sync(0xffffffffu, hi_key, o));
   }
   if ((threadIdx.x & 31) == 0 && lo_key <= hi_key) {
-    atomicMin(&hdr->dmin, lo_key);
-    atomicMax(&hdr->dmax, hi_key);
+    atomicMin(&s_dlo, lo_key);
+    atomicMax(&s_dhi, hi_key);
   }
   // 4. stable compaction of the visible Gaussians (index order): offsets within the block from
   //    the scan above, the block's offset by a decoupled look-back over the blocks before it
@@ -418,6 +425,10 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(const DevTables* __r
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0 && s_dlo <= s_dhi) {
+    atomicMin(&hdr->dmin, s_dlo);
+    atomicMax(&hdr->dmax, s_dhi);
+  }
   if (vis) {
     const unsigned at = s_base + ex;
     cp.vkeys[at] = key;
