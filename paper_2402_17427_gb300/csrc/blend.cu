@@ -542,53 +542,54 @@ blend_backward_kernel(const DevTables* __restrict__ tab, const Splat* __restrict
             // alpha it yields is below alpha_max and the clamp and its zero gradient are skipped
             // (the same values: the clamp would not act)
             auto pixels = [&](auto clamp) {
-            constexpr bool CL = decltype(clamp)::value;
+              constexpr bool CL = decltype(clamp)::value;
 #pragma unroll
-            for (int p = 0; p < S::kPPT; p += 2) {
-              const float2 dy = __fadd2_rn(make_float2(dyb[p / FP], dyb[(p + 1) / FP]),
-                                           make_float2((float)(p % FP), (float)((p + 1) % FP)));
-              const float2 p2 = __ffma2_rn(dy, __ffma2_rn(make_float2(f1.x, f1.x), dy, make_float2(e1, e1)),
-                                           make_float2(e0, e0));
-              const float2 q = __fadd2_rn(p2, make_float2(f1.y, f1.y));
-              const bool ok0 = pos < lastp[p] && !(p2.x > 0.f || q.x < lamin);
-              const bool ok1 = pos < lastp[p + 1] && !(p2.y > 0.f || q.y < lamin);
-              const float2 araw = make_float2(ex2_approx(q.x), ex2_approx(q.y));
-              const float2 a = CL ? make_float2(ok0 ? fminf(amax, araw.x) : 0.f, ok1 ? fminf(amax, araw.y) : 0.f)
-                                  : make_float2(ok0 ? araw.x : 0.f, ok1 ? araw.y : 0.f);
-              any = any || ok0 || ok1;
-              const float2 om = __ffma2_rn(a, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));   // 1 - a
-              const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-              const float2 Tp = make_float2(T[p], T[p + 1]), Bp = make_float2(B[p], B[p + 1]);
-              const float2 Tb = __fmul2_rn(Tp, rom);
-              const float2 aT = __fmul2_rn(a, Tb);
-              const float2 g0 = make_float2(G[p][0], G[p + 1][0]), g1 = make_float2(G[p][1], G[p + 1][1]),
-                           g2 = make_float2(G[p][2], G[p + 1][2]);
-              w6 = __ffma2_rn(aT, g0, w6);
-              w7 = __ffma2_rn(aT, g1, w7);
-              w8 = __ffma2_rn(aT, g2, w8);
-              const float2 cg = __ffma2_rn(make_float2(f2.x, f2.x), g2,
-                                           __ffma2_rn(make_float2(f1.w, f1.w), g1, __fmul2_rn(make_float2(f1.z, f1.z), g0)));
-              const float2 br = __fmul2_rn(Bp, rom);
-              const float2 dal = __ffma2_rn(Tb, cg, make_float2(-br.x, -br.y));
-              const float2 Bn = __ffma2_rn(cg, aT, Bp);
-              B[p] = Bn.x;
-              B[p + 1] = Bn.y;
-              // a pixel the Gaussian does not reach has a = 0, so 1 - a = 1, whose approximate
-              // reciprocal is exactly 1: Tb = T there, and T needs no select
-              T[p] = Tb.x;
-              T[p + 1] = Tb.y;
-              // where alpha is clamped to alpha_max it does not depend on the power (a pixel
-              // this Gaussian does not reach has a = 0, hence dal * a = 0)
-              float2 dpow = __fmul2_rn(dal, a);
-              if constexpr (CL) {
-                dpow.x = araw.x < amax ? dpow.x : 0.f;
-                dpow.y = araw.y < amax ? dpow.y : 0.f;
+              for (int p = 0; p < S::kPPT; p += 2) {
+                const float2 dy = __fadd2_rn(make_float2(dyb[p / FP], dyb[(p + 1) / FP]),
+                                             make_float2((float)(p % FP), (float)((p + 1) % FP)));
+                const float2 p2 = __ffma2_rn(dy, __ffma2_rn(make_float2(f1.x, f1.x), dy, make_float2(e1, e1)),
+                                             make_float2(e0, e0));
+                const float2 q = __fadd2_rn(p2, make_float2(f1.y, f1.y));
+                const bool ok0 = pos < lastp[p] && !(p2.x > 0.f || q.x < lamin);
+                const bool ok1 = pos < lastp[p + 1] && !(p2.y > 0.f || q.y < lamin);
+                const float2 araw = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+                const float2 a = CL ? make_float2(ok0 ? fminf(amax, araw.x) : 0.f, ok1 ? fminf(amax, araw.y) : 0.f)
+                                    : make_float2(ok0 ? araw.x : 0.f, ok1 ? araw.y : 0.f);
+                any = any || ok0 || ok1;
+                const float2 om = __ffma2_rn(a, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));   // 1 - a
+                const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+                const float2 Tp = make_float2(T[p], T[p + 1]), Bp = make_float2(B[p], B[p + 1]);
+                const float2 Tb = __fmul2_rn(Tp, rom);
+                const float2 aT = __fmul2_rn(a, Tb);
+                const float2 g0 = make_float2(G[p][0], G[p + 1][0]), g1 = make_float2(G[p][1], G[p + 1][1]),
+                             g2 = make_float2(G[p][2], G[p + 1][2]);
+                w6 = __ffma2_rn(aT, g0, w6);
+                w7 = __ffma2_rn(aT, g1, w7);
+                w8 = __ffma2_rn(aT, g2, w8);
+                const float2 cg = __ffma2_rn(make_float2(f2.x, f2.x), g2,
+                                             __ffma2_rn(make_float2(f1.w, f1.w), g1,
+                                                        __fmul2_rn(make_float2(f1.z, f1.z), g0)));
+                const float2 br = __fmul2_rn(Bp, rom);
+                const float2 dal = __ffma2_rn(Tb, cg, make_float2(-br.x, -br.y));
+                const float2 Bn = __ffma2_rn(cg, aT, Bp);
+                B[p] = Bn.x;
+                B[p + 1] = Bn.y;
+                // a pixel the Gaussian does not reach has a = 0, so 1 - a = 1, whose approximate
+                // reciprocal is exactly 1: Tb = T there, and T needs no select
+                T[p] = Tb.x;
+                T[p + 1] = Tb.y;
+                // where alpha is clamped to alpha_max it does not depend on the power (a pixel
+                // this Gaussian does not reach has a = 0, hence dal * a = 0)
+                float2 dpow = __fmul2_rn(dal, a);
+                if constexpr (CL) {
+                  dpow.x = araw.x < amax ? dpow.x : 0.f;
+                  dpow.y = araw.y < amax ? dpow.y : 0.f;
+                }
+                const float2 dpy = __fmul2_rn(dpow, dy);
+                s0 = __fadd2_rn(s0, dpow);
+                s1 = __fadd2_rn(s1, dpy);
+                s2 = __ffma2_rn(dpy, dy, s2);
               }
-              const float2 dpy = __fmul2_rn(dpow, dy);
-              s0 = __fadd2_rn(s0, dpow);
-              s1 = __fadd2_rn(s1, dpy);
-              s2 = __ffma2_rn(dpy, dy, s2);
-            }
             };
             if (f1.y >= lclamp) pixels(std::true_type()); else pixels(std::false_type());
             S0 = s0.x + s0.y;
