@@ -45,14 +45,14 @@ OPS_EVAL, OPS_BLEND_FWD, OPS_BLEND_BWD = 11, 7, 37
 TRAFFIC_SOURCES = ("paper_2402_17427_gb300/csrc/blend.cu", "paper_2402_17427_gb300/csrc/vg_common.cuh",
                    "paper_2402_17427_gb300/csrc/internal.h")
 PROFILED_TRAFFIC = {
-    "sources_sha256": "08a2670da373a727c2a83e325b2b69ab7da072d279fc5b901e644ad85c13099d",
+    "sources_sha256": "41622bed1adda167cb60d63ef8b9ece17d6e7f7cf8280c257725cd320cd9aed1",
     "blend": 18660864 + 1536768,
     "blend_backward": 67457536 + 1475328,
 }
 # Warp instructions issued per launch (smsp__inst_executed.sum) of the compositing kernels on this
 # workload, from the same captures; held to the same source hash.
 PROFILED_INSTRUCTIONS = {
-    "sources_sha256": "08a2670da373a727c2a83e325b2b69ab7da072d279fc5b901e644ad85c13099d",
+    "sources_sha256": "41622bed1adda167cb60d63ef8b9ece17d6e7f7cf8280c257725cd320cd9aed1",
     "blend": 259017717,
     "blend_backward": 357429896,
 }

@@ -72,7 +72,9 @@ __device__ __forceinline__ float rcp_approx(float x) {
 //   dL/du = -2 ln 2 (ca m0 + cb m1 / 2),  dL/dv = -2 ln 2 (cb m0 / 2 + cc m1)    (dP/du, dP/dv)
 //   dL/da = -m2 / 2,  dL/db = -m3,  dL/dc = -m4 / 2,  dL/dopacity = m5 / opacity.
 // Output order: du, dv, d conic (a, b, c), d opacity; lo = log2(opacity).
-__device__ __forceinline__ void grad2d_from_moments(const float* m, float ca, float cb, float cc, float lo, float* d) {
+// Host and device (a CPU test compiles it as host code against the per-pixel definitions).
+__host__ __device__ __forceinline__ void grad2d_from_moments(const float* m, float ca, float cb, float cc, float lo,
+                                                             float* d) {
   const float k = -1.3862943611198906f;   // -2 ln 2
   d[0] = k * (ca * m[0] + 0.5f * cb * m[1]);
   d[1] = k * (0.5f * cb * m[0] + cc * m[1]);
