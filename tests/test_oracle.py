@@ -463,6 +463,32 @@ def test_opacity_derivative_closed_form(oracle_lib):
     assert abs(gr["g2d"][0, 5] - r.rec["rgb"][0, 0] * math.exp(-rho2 / (2 * sig2))) < 1e-12
 
 
+def test_alpha_clamp_closed_form(oracle_lib):
+    """Single head-on Gaussian with opacity near 1: at the centre pixel alpha = min(0.99, o) = 0.99,
+    so the pixel is 0.99 c and does not depend on the opacity, the mean or the conic (their
+    derivatives are exactly 0 there; d pixel / d rgb = 0.99); 4 px away alpha < 0.99 and
+    d pixel / d opacity = c exp(-rho^2 / (2 sigma^2)) as without the clamp."""
+    f, Z, s = 80.0, 5.0, 0.19
+    cam = _cam_identity(64, 64, f)
+    g = _gauss([[0, 0, Z]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [8.0], [(0.7, 0.3, 0.1)])
+    r = oracle_lib.render(g, cam)
+    c = r.rec["rgb"][0, 0]
+    assert r.rec["opacity"][0] > 0.999
+    assert abs(r.image[0, 32, 32] - 0.99 * c) < 1e-12
+    dimg = np.zeros((3, 64, 64))
+    dimg[0, 32, 32] = 1.0
+    g2d = r.backward(dimg)["g2d"][0]
+    assert np.all(g2d[:6] == 0.0), g2d            # du, dv, d conic (3), d opacity
+    assert abs(g2d[6] - 0.99) < 1e-12 and g2d[7] == 0.0 and g2d[8] == 0.0
+    dimg[0, 32, 32] = 0.0
+    dimg[0, 32, 36] = 1.0
+    sig2 = (f * math.exp(float(np.float32(math.log(s)))) / Z) ** 2 + 0.3
+    G = math.exp(-16.0 / (2 * sig2))
+    assert r.rec["opacity"][0] * G < 0.99
+    g2d = r.backward(dimg)["g2d"][0]
+    assert abs(g2d[5] - c * G) < 1e-12
+
+
 # ------------------------------------------------------------------ loss (Eq. 1)
 
 def test_ssim_identity_and_scipy(oracle_lib):
