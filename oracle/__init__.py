@@ -85,7 +85,7 @@ def lib():
             L.or_get_records.argtypes = [P, P, P, P, P]
             L.or_pixel_trace.restype = ctypes.c_int32
             L.or_pixel_trace.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int32]
-            L.or_backward.argtypes = [P, P, P, P, P, P, P, P]
+            L.or_backward.argtypes = [P, P, P, P, P, P, P, P, P]
             L.or_sh_basis.argtypes = [ctypes.c_int, P, P, P]
             L.or_fd_directional.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_double, P, P]
             L.or_fd_directional.restype = None
@@ -254,13 +254,15 @@ class Render:
         return out, flags
 
     def backward(self, dL_dimg):
-        """Gradients w.r.t. raw parameters, plus the per-Gaussian 2D gradients [n, 9]."""
+        """Gradients w.r.t. raw parameters, plus the per-Gaussian 2D gradients [n, 9] and the
+        densification statistic g2d_abs [n] (sum over pixels of |dL/du| + |dL/dv| per pixel)."""
         s = self.scene
         dimg = np.ascontiguousarray(np.asarray(dL_dimg, np.float64))
         out = dict(means=np.zeros((s.n, 3)), log_scales=np.zeros((s.n, 3)), quats=np.zeros((s.n, 4)),
-                   logits=np.zeros(s.n), sh=np.zeros((s.n, s.K, 3)), g2d=np.zeros((s.n, 9)))
+                   logits=np.zeros(s.n), sh=np.zeros((s.n, s.K, 3)), g2d=np.zeros((s.n, 9)), g2d_abs=np.zeros(s.n))
         self._L.or_backward(self.h, _ptr(dimg), _ptr(out["means"]), _ptr(out["log_scales"]),
-                            _ptr(out["quats"]), _ptr(out["logits"]), _ptr(out["sh"]), _ptr(out["g2d"]))
+                            _ptr(out["quats"]), _ptr(out["logits"]), _ptr(out["sh"]), _ptr(out["g2d"]),
+                            _ptr(out["g2d_abs"]))
         return out
 
 

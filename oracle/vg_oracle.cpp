@@ -749,9 +749,11 @@ int32_t or_pixel_trace(void* h, int x, int y, double* T_after, uint32_t* gauss, 
 
 // Adjoint of the forward pass.  dL_dimg [3,H,W].  Outputs (overwritten, zeros for culled):
 // g_means [n,3], g_log_scales [n,3], g_quats [n,4], g_logits [n], g_sh [n,K,3], and optionally
-// g2d [n,9] = dL/d(u, v, conic a, b, c, opacity, r, g, b).
+// g2d [n,9] = dL/d(u, v, conic a, b, c, opacity, r, g, b) and g2d_abs [n], the densification
+// statistic: the sum over pixels of |dL/du| + |dL/dv| of each pixel's own contribution (the
+// per-pixel terms of g2d's first two columns, taken in absolute value before summing).
 void or_backward(void* h, const double* dL_dimg, double* g_means, double* g_log_scales, double* g_quats,
-                 double* g_logits, double* g_sh, double* g2d_out) {
+                 double* g_logits, double* g_sh, double* g2d_out, double* g2d_abs_out) {
   State* S = (State*)h;
   const OrOpts& op = S->op;
   const OrCamera& cm = S->cam;
@@ -759,18 +761,19 @@ void or_backward(void* h, const double* dL_dimg, double* g_means, double* g_log_
   int64_t n = S->sc.n;
   int K = S->K;
   int tiles = S->tiles_x * S->tiles_y;
-  std::vector<double> g2d(9 * (size_t)n, 0.0);
-  // per-tile partial sums, merged serially for a deterministic result
-  std::vector<std::vector<std::pair<uint32_t, std::array<double, 9>>>> parts(tiles);
+  std::vector<double> g2d(9 * (size_t)n, 0.0), g2d_abs((size_t)n, 0.0);
+  // per-tile partial sums (the nine g2d fields, then the absolute-value statistic), merged
+  // serially for a deterministic result
+  std::vector<std::vector<std::pair<uint32_t, std::array<double, 10>>>> parts(tiles);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int t = 0; t < tiles; ++t) {
     if (!S->rendered_tile[t]) continue;
     int tx = t % S->tiles_x, ty = t / S->tiles_x;
-    std::vector<std::array<double, 9>> acc;
+    std::vector<std::array<double, 10>> acc;
     std::vector<uint32_t> ids;
     int32_t s0 = S->ranges[2 * t];
     int32_t len = S->ranges[2 * t + 1] - s0;
-    acc.assign(len, std::array<double, 9>{});
+    acc.assign(len, std::array<double, 10>{});
     for (int y = ty * TS; y < std::min(H, (ty + 1) * TS); ++y)
       for (int x = tx * TS; x < std::min(W, (tx + 1) * TS); ++x) {
         std::vector<Step> tr;
@@ -797,8 +800,10 @@ void or_backward(void* h, const double* dL_dimg, double* g_means, double* g_log_
           a[5] += dl_da * s.G;
           double dl_dpow = dl_da * s.alpha;
           double dx = x - g.u, dy = y - g.v;
-          a[0] += dl_dpow * (g.a * dx + g.b * dy);
-          a[1] += dl_dpow * (g.b * dx + g.c * dy);
+          const double du = dl_dpow * (g.a * dx + g.b * dy), dv = dl_dpow * (g.b * dx + g.c * dy);
+          a[0] += du;
+          a[1] += dv;
+          a[9] += std::fabs(du) + std::fabs(dv);
           a[2] += dl_dpow * (-0.5 * dx * dx);
           a[3] += dl_dpow * (-dx * dy);
           a[4] += dl_dpow * (-0.5 * dy * dy);
@@ -807,9 +812,12 @@ void or_backward(void* h, const double* dL_dimg, double* g_means, double* g_log_
     for (int32_t j = 0; j < len; ++j) parts[t].push_back({S->vals[s0 + j], acc[j]});
   }
   for (int t = 0; t < tiles; ++t)
-    for (auto& pr : parts[t])
+    for (auto& pr : parts[t]) {
       for (int f = 0; f < 9; ++f) g2d[9 * (size_t)pr.first + f] += pr.second[f];
+      g2d_abs[pr.first] += pr.second[9];
+    }
   if (g2d_out) std::memcpy(g2d_out, g2d.data(), g2d.size() * sizeof(double));
+  if (g2d_abs_out) std::memcpy(g2d_abs_out, g2d_abs.data(), g2d_abs.size() * sizeof(double));
 
   // chain rule per Gaussian
 #pragma omp parallel for schedule(static)

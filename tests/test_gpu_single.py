@@ -125,6 +125,24 @@ def test_tiny_scenes_forward_backward(n, W, H, tile, deg, seed, bg, stop):
     check_grads(gpu, ref, ~(orc.rec["grad_amb"] | orc.rec["rect_amb"]))
 
 
+def test_means2d_abs_statistic_matches_oracle():
+    """The adjoint variant that also accumulates the densification statistic (per Gaussian, the sum
+    over pixels of |dL/du| + |dL/dv| of each pixel's contribution, added to the caller's buffer):
+    the statistic and every gradient group against the FP64 oracle."""
+    g, cam, _ = scenes.tiny_scene(n=200, width=48, height=40, degree=2, seed=2)
+    r, params, out, orc = render_both(g, cam)
+    w = np.random.default_rng(2).standard_normal((3, cam.height, cam.width)).astype(np.float32)
+    w[:, orc.amb.astype(bool)] = 0
+    acc = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+    gpu = run_backward(r, params, g, cam, out, w, means2d_abs=acc)
+    ref = orc.backward(w.astype(np.float64))
+    keep = ~(orc.rec["grad_amb"] | orc.rec["rect_amb"])
+    check_grads(gpu, ref, keep)
+    got, want = acc.cpu().numpy().astype(np.float64)[keep], ref["g2d_abs"][keep]
+    assert np.linalg.norm(want) > 0
+    assert np.linalg.norm(got - want) <= GRAD_TOL * np.linalg.norm(want), np.linalg.norm(got - want) / np.linalg.norm(want)
+
+
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_opaque_splats_clamped_at_alpha_max(tile):
     """Splats whose opacity is nearly 1 reach alpha_max near their centres: there alpha is clamped

@@ -463,6 +463,26 @@ def test_opacity_derivative_closed_form(oracle_lib):
     assert abs(gr["g2d"][0, 5] - r.rec["rgb"][0, 0] * math.exp(-rho2 / (2 * sig2))) < 1e-12
 
 
+def test_abs_gradient_statistic(oracle_lib):
+    """The densification statistic sums |dL/du| + |dL/dv| of each pixel's own contribution.  With
+    dL non-zero at one pixel each Gaussian has one such term, so the statistic equals |du| + |dv|
+    of the adjoint (which the finite-difference pins cover); in general it is at least that
+    (triangle inequality), with equality only where every pixel's terms share their signs."""
+    g, cam, _ = scenes.tiny_scene(n=60, width=40, height=32, degree=1, seed=3)
+    r = oracle_lib.render(g, cam)
+    one = np.zeros((3, 32, 40))
+    one[1, 17, 22] = 1.0
+    gr = r.backward(one)
+    assert np.abs(gr["g2d_abs"] - (np.abs(gr["g2d"][:, 0]) + np.abs(gr["g2d"][:, 1]))).max() < 1e-12
+    assert (gr["g2d_abs"] > 0).sum() >= 2
+    w = np.random.default_rng(3).standard_normal((3, 32, 40))
+    gr = r.backward(w)
+    lower = np.abs(gr["g2d"][:, 0]) + np.abs(gr["g2d"][:, 1])
+    assert (gr["g2d_abs"] >= lower - 1e-12).all()
+    assert (gr["g2d_abs"] > lower * (1 + 1e-6)).any()       # cancellation across pixels happens
+    assert (gr["g2d_abs"][~r.rec["visible"]] == 0).all()
+
+
 def test_alpha_clamp_closed_form(oracle_lib):
     """Single head-on Gaussian with opacity near 1: at the centre pixel alpha = min(0.99, o) = 0.99,
     so the pixel is 0.99 c and does not depend on the opacity, the mean or the conic (their
